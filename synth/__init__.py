@@ -1,0 +1,230 @@
+"""Seeded synthetic genotype panels in the packed 2-bit format.
+
+This module is shared by the CPU oracle's tests and by the CUDA path's tests and
+benchmark.  It holds no part of the CCC arithmetic: it only draws genotypes and
+packs/unpacks the storage format.
+
+Storage format (the vector model of Sec. 2.1, with the missing-value marker of
+Sec. 8 item 1):
+
+* every entry ``v_{i,q}`` is a pair of allele bits ``((v)_1, (v)_2)``; it is
+  stored as the 2-bit code ``2*(v)_1 + (v)_2``;
+* genotype 0 (homozygous, allele pair (0,0)) -> code ``0b00``;
+  genotype 1 (heterozygous, always stored as (0,1)) -> code ``0b01``;
+  genotype 2 (homozygous, (1,1)) -> code ``0b11``;
+  missing -> code ``0b10``, the pair (1,0) which the paper sets aside as the
+  missing-entry marker;
+* SNP ``i`` occupies uint64 words ``[i*ld, i*ld + ceil(n_f/32))``; entry ``q``
+  sits at bits ``2*(q%32) .. 2*(q%32)+1`` of word ``q//32`` (LSB first);
+  bits past ``n_f`` in the last word and words past ``ceil(n_f/32)`` are
+  padding that every consumer must ignore.
+
+Random numbers come from a counter-based SplitMix64 (Steele, Lea and Flood,
+"Fast splittable pseudorandom number generators", OOPSLA 2014), so that any
+entry can be regenerated independently of all others:
+
+    mix(z)            = the SplitMix64 finaliser (mix64 variant 13)
+    G                 = 0x9E3779B97F4A7C15
+    key(seed, p)      = mix(seed + (p+1)*G)                  per panel p
+    key(seed, p, i)   = mix(key(seed, p) + (i+1)*G)          per SNP i
+    u(p, i, q, t)     = mix(key(seed, p, i) + (2q + t + 1)*G)  t in {0, 1}
+    u_maf(p, i)       = mix(key(seed, p, i) + 0)             per-SNP draw
+
+Uniforms in [0,1) take the top 53 bits: ``(u >> 11) * 2**-53``.
+Stream t=0 decides "missing", stream t=1 draws the genotype.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "CODE_HOM0", "CODE_HET", "CODE_MISSING", "CODE_HOM1",
+    "mix64", "uniforms", "maf_beta_half", "genotypes_uniform", "genotypes_hwe",
+    "genotypes_analytic", "codes_from_genotypes", "pack", "unpack", "words_per_snp",
+    "panel_uniform", "panel_hwe", "panel_analytic", "default_ld",
+]
+
+CODE_HOM0 = 0b00
+CODE_HET = 0b01
+CODE_MISSING = 0b10
+CODE_HOM1 = 0b11
+
+_G = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser on a uint64 array (wrapping arithmetic)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def _key(seed: int, panel: int, snps: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        kp = mix64(np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + np.uint64(panel + 1) * _G)
+        return mix64(kp + (snps.astype(np.uint64) + np.uint64(1)) * _G)
+
+
+def _to_unit(u: np.ndarray) -> np.ndarray:
+    return (u >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniforms(seed: int, panel: int, snps: np.ndarray, n_f: int, stream: int) -> np.ndarray:
+    """u(p, i, q, t) for all listed SNPs and q in [0, n_f): float64 [len(snps), n_f]."""
+    snps = np.asarray(snps, dtype=np.int64)
+    k = _key(seed, panel, snps)[:, None]
+    q = np.arange(n_f, dtype=np.uint64)[None, :]
+    with np.errstate(over="ignore"):
+        ctr = k + (np.uint64(2) * q + np.uint64(stream + 1)) * _G
+    return _to_unit(mix64(ctr))
+
+
+def maf_beta_half(seed: int, panel: int, snps: np.ndarray) -> np.ndarray:
+    """Per-SNP minor-allele frequency: Beta(1/2,1/2) folded to [0, 1/2], floored at 0.01.
+
+    A Beta(1/2,1/2) variate is sin^2(pi*U/2) for U uniform on [0,1) (the arcsine
+    law).  It is folded as p = min(x, 1-x) and then raised to at least 0.01.
+    """
+    snps = np.asarray(snps, dtype=np.int64)
+    u = _to_unit(mix64(_key(seed, panel, snps)))
+    x = np.sin(0.5 * np.pi * u) ** 2
+    p = np.minimum(x, 1.0 - x)
+    return np.maximum(p, 0.01)
+
+
+def genotypes_uniform(seed, panel, snps, n_f, p_missing):
+    """Genotype 0/1/2 uniform, missing i.i.d. with probability p_missing (-1 marks missing)."""
+    um = uniforms(seed, panel, snps, n_f, 0)
+    ug = uniforms(seed, panel, snps, n_f, 1)
+    g = np.minimum((ug * 3.0).astype(np.int8), 2)
+    g[um < p_missing] = -1
+    return g
+
+
+def genotypes_hwe(seed, panel, snps, n_f, p_missing):
+    """Hardy-Weinberg genotypes: P(g) = (1-p)^2, 2p(1-p), p^2 with per-SNP p; -1 marks missing."""
+    p = maf_beta_half(seed, panel, snps)[:, None]
+    um = uniforms(seed, panel, snps, n_f, 0)
+    ug = uniforms(seed, panel, snps, n_f, 1)
+    t0 = (1.0 - p) ** 2
+    t1 = t0 + 2.0 * p * (1.0 - p)
+    g = np.where(ug < t0, 0, np.where(ug < t1, 1, 2)).astype(np.int8)
+    g[um < p_missing] = -1
+    return g
+
+
+def genotypes_analytic(n_v, n_f):
+    """The closed-form panel g_{i,q} = (i + q) mod 3, no missing entries."""
+    i = np.arange(n_v)[:, None]
+    q = np.arange(n_f)[None, :]
+    return ((i + q) % 3).astype(np.int8)
+
+
+_G2C = np.array([CODE_HOM0, CODE_HET, CODE_HOM1, CODE_MISSING], dtype=np.uint8)
+
+
+def codes_from_genotypes(g: np.ndarray) -> np.ndarray:
+    """Genotype array (0/1/2, -1 = missing) -> 2-bit codes (uint8 0..3)."""
+    g = np.asarray(g)
+    idx = np.where(g < 0, 3, g).astype(np.int64)
+    return _G2C[idx]
+
+
+def words_per_snp(n_f: int) -> int:
+    return (n_f + 31) // 32
+
+
+def default_ld(n_f: int) -> int:
+    """Row stride in uint64 words: ceil(n_f/32) rounded up to an even count (16-byte rows)."""
+    w = words_per_snp(n_f)
+    return max(2, (w + 1) // 2 * 2)
+
+
+def pack(codes: np.ndarray, ld: int | None = None, pad_seed: int | None = None,
+         out: np.ndarray | None = None, row0: int = 0) -> np.ndarray:
+    """Pack codes [n_v, n_f] (uint8 0..3) into uint64 words [n_v, ld].
+
+    With ``pad_seed`` set, the padding bits (past n_f in the last word, and the
+    words past ceil(n_f/32)) are filled with random garbage so that tests can
+    check that consumers ignore them; otherwise they are zero.  ``out`` and
+    ``row0`` let a caller pack a block of rows into a larger preallocated array.
+    """
+    codes = np.asarray(codes, dtype=np.uint8)
+    n_v, n_f = codes.shape
+    w = words_per_snp(n_f)
+    if ld is None:
+        ld = default_ld(n_f)
+    if ld < w:
+        raise ValueError("ld must be at least ceil(n_f/32)")
+    padded = np.zeros((n_v, w * 32), dtype=np.uint8)
+    padded[:, :n_f] = codes
+    blk = padded.reshape(n_v, w, 32).astype(np.uint64)
+    words = np.zeros((n_v, w), dtype=np.uint64)
+    for k in range(32):
+        words |= blk[:, :, k] << np.uint64(2 * k)
+    if out is None:
+        out = np.zeros((n_v, ld), dtype=np.uint64)
+        dst = out
+    else:
+        dst = out[row0:row0 + n_v]
+    dst[:, :w] = words
+    if pad_seed is not None:
+        with np.errstate(over="ignore"):
+            garbage = mix64(np.arange(n_v * ld, dtype=np.uint64).reshape(n_v, ld)
+                            + np.uint64(pad_seed) * _G)
+        tail = n_f - (w - 1) * 32
+        if tail < 32:
+            keep = np.uint64((1 << (2 * tail)) - 1)
+            dst[:, w - 1] = (dst[:, w - 1] & keep) | (garbage[:, w - 1] & ~keep)
+        if ld > w:
+            dst[:, w:] = garbage[:, w:]
+    elif ld > w:
+        dst[:, w:] = 0
+    return out
+
+
+def unpack(words: np.ndarray, n_f: int) -> np.ndarray:
+    """Inverse of :func:`pack`: uint64 [n_v, ld] -> codes uint8 [n_v, n_f]."""
+    words = np.asarray(words, dtype=np.uint64)
+    n_v = words.shape[0]
+    w = words_per_snp(n_f)
+    out = np.empty((n_v, w, 32), dtype=np.uint8)
+    for k in range(32):
+        out[:, :, k] = ((words[:, :w] >> np.uint64(2 * k)) & np.uint64(3)).astype(np.uint8)
+    return out.reshape(n_v, w * 32)[:, :n_f]
+
+
+def _panel(gen, n_v, n_f, ld, pad_seed, chunk):
+    if ld is None:
+        ld = default_ld(n_f)
+    out = np.zeros((n_v, ld), dtype=np.uint64)
+    for r0 in range(0, n_v, chunk):
+        r1 = min(n_v, r0 + chunk)
+        g = gen(np.arange(r0, r1))
+        pack(codes_from_genotypes(g), ld=ld, pad_seed=None if pad_seed is None else pad_seed + r0,
+             out=out, row0=r0)
+    return out
+
+
+def panel_uniform(n_v, n_f, seed=0, p_missing=0.02, panel=0, ld=None, pad_seed=None):
+    """Uniform-genotype panel (the small 2-way case): packed uint64 [n_v, ld]."""
+    chunk = max(1, (1 << 22) // max(n_f, 1))
+    return _panel(lambda s: genotypes_uniform(seed, panel, s, n_f, p_missing), n_v, n_f, ld,
+                  pad_seed, chunk)
+
+
+def panel_hwe(n_v, n_f, seed=1, p_missing=0.01, panel=0, ld=None, pad_seed=None):
+    """Hardy-Weinberg panel with Beta(1/2,1/2) minor-allele frequencies: packed uint64 [n_v, ld]."""
+    chunk = max(1, (1 << 22) // max(n_f, 1))
+    return _panel(lambda s: genotypes_hwe(seed, panel, s, n_f, p_missing), n_v, n_f, ld,
+                  pad_seed, chunk)
+
+
+def panel_analytic(n_v, n_f, ld=None):
+    """Closed-form panel g_{i,q} = (i+q) mod 3 (no missing): packed uint64 [n_v, ld]."""
+    return pack(codes_from_genotypes(genotypes_analytic(n_v, n_f)), ld=ld)
