@@ -1,0 +1,208 @@
+/*
+ * ccc.h -- C ABI of libccc, the GB300 (sm_103a) hot path for 2-way and 3-way
+ * Custom Correlation Coefficient (CCC) calculations.
+ *
+ * Method: Joubert, Nance, Climer, Weighill, Jacobson, "Parallel Accelerated
+ * Custom Correlation Coefficient Calculations for Genomics Applications",
+ * Parallel Computing (2018).  Section, equation and table numbers below refer
+ * to that paper.
+ *
+ * ---------------------------------------------------------------------------
+ * Input: the packed genotype panel (Sec. 2.1 vector model; Sec. 3.1 packing;
+ * Sec. 8 item 1 missing-value marker)
+ *
+ *   Every entry v_{i,q} of SNP vector i (0 <= i < n_v) for individual q
+ *   (0 <= q < n_f) is a pair of allele bits ((v)_1, (v)_2), stored as the
+ *   2-bit code 2*(v)_1 + (v)_2:
+ *       0b00 = (0,0)  homozygous, genotype 0
+ *       0b01 = (0,1)  heterozygous (always stored this way round)
+ *       0b11 = (1,1)  homozygous, genotype 2
+ *       0b10 = (1,0)  MISSING (the pair the paper reserves as the marker)
+ *   SNP i occupies the uint64 words geno[i*ld .. i*ld + ceil(n_f/32) - 1];
+ *   entry q sits at bits 2*(q%32)..2*(q%32)+1 of word q/32 (LSB first).
+ *   Bits past n_f in the last word and words past ceil(n_f/32) are ignored.
+ *   Requirements: n_f >= 1, n_v >= 1, ld >= ceil(n_f/32), ld even (16-byte
+ *   rows), geno 16-byte aligned, all device memory.
+ *
+ * Output indexing
+ *   2-way: pairs i < j only, row-major upper triangle without the diagonal,
+ *          p = i*(2*n_v - i - 1)/2 + (j - i - 1)      (ccc2_index)
+ *          4 values per pair in the order (a,b) = 00, 01, 10, 11, where a is
+ *          the allele of SNP i (the lower index) and b that of SNP j.
+ *   3-way: triples i < j < k only, slab-major: slab j, then i, then k,
+ *          t = S(j) + i*(n_v - 1 - j) + (k - j - 1),
+ *          S(j) = sum_{j' < j} j' (n_v - 1 - j')        (ccc3_index)
+ *          8 values per triple in the order abc = 000 .. 111 (a for i, b for
+ *          j, c for k).  A call over slabs [j_begin, j_end) writes entries
+ *          t - S(j_begin).
+ *
+ * Definitions computed (with rho_{i,q}(a) = number of alleles equal to a in
+ * v_{i,q}, 0 for a missing entry):
+ *   tally   r_{ij}^{ab}  = sum_q rho_{i,q}(a) rho_{j,q}(b)                 (Eq. 2 numerator)
+ *           r_{ijk}^{abc} = sum_q rho_{i,q}(a) rho_{j,q}(b) rho_{k,q}(c)    (Eq. 5 numerator)
+ *   counts  s_i^a = sum_q rho_{i,q}(a), n_i = number of non-missing entries (Eq. 1)
+ *   CCC     f_ij(a,b) (1 - gamma f_i(a)) (1 - gamma f_j(b))                (Eq. 3)
+ *           f_ijk(a,b,c) (1 - gamma f_i(a)) (1 - gamma f_j(b)) (1 - gamma f_k(c))  (Eq. 4)
+ *     with f_ij = r/(4 n_ij), f_ijk = r/(8 n_ijk) where n_ij (n_ijk) counts the
+ *     jointly non-missing entries, and f_i(a) = s_i^a/(2 n_i) (CCC_NORM_PERSNP)
+ *     or the pair's (triple's) own marginal (CCC_NORM_JOINT).  When nothing is
+ *     missing both reduce to Eqs. 1-5 as printed.  n_ij = 0 (n_ijk = 0) gives
+ *     zero tallies and zero CCC values; n_i = 0 gives f_i = 0.
+ *   Tallies are exact 32-bit integers.  CCC values are single precision; the
+ *   relative error against exact arithmetic is below 1e-6.
+ *
+ * Conventions for every entry point
+ *   - All buffers are caller-owned device memory unless stated otherwise; the
+ *     library allocates nothing.  Scratch space is the caller's workspace,
+ *     sized by ccc_workspace_size() and passed in ccc_opts.
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL is the legacy default stream).  They return once the work
+ *     is queued.
+ *   - Return value: CCC_OK, or a negative CCC_E* code for an argument error
+ *     found before anything was queued (nothing is written then), or
+ *     CCC_ECUDA when a launch was refused.  Errors found on the device (a
+ *     bounded wait that timed out) are recorded in the workspace status word,
+ *     read with ccc_status().
+ * ---------------------------------------------------------------------------
+ */
+#ifndef CCC_H_
+#define CCC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CCC_OK 0
+#define CCC_EINVAL (-1)       /* bad pointer, size, stride, alignment or option */
+#define CCC_ERANGE (-2)       /* a size beyond what the exact arithmetic allows */
+#define CCC_EUNSUPPORTED (-3) /* no usable sm_103a device, or path not available */
+#define CCC_ECUDA (-4)        /* a CUDA call failed */
+#define CCC_ETIMEOUT (-5)     /* a device-side bounded wait gave up (ccc_status) */
+#define CCC_ENOSPACE (-6)     /* workspace smaller than ccc_workspace_size() */
+
+/* Tally paths. */
+#define CCC_PATH_TC 0   /* tcgen05 tensor cores, e4m3 count operands, FP32 accumulate */
+#define CCC_PATH_POPC 1 /* bit planes, AND + population count on the CUDA cores */
+
+/* Normalisation of f_i with missing data (see above). */
+#define CCC_NORM_PERSNP 0
+#define CCC_NORM_JOINT 1
+
+/* Largest n_f accepted: every tally is an integer below 8 n_f and must stay
+ * exactly representable in the FP32 accumulators (< 2^24). */
+#define CCC_MAX_NF 2097151
+
+typedef struct ccc_panel {
+  const uint64_t *geno; /* device pointer to n_v rows of ld uint64 words */
+  int64_t n_f;          /* individuals (entries per SNP vector) */
+  int64_t n_v;          /* SNP vectors */
+  int64_t ld;           /* row stride in uint64 words */
+} ccc_panel;
+
+typedef struct ccc_opts {
+  int32_t path;           /* CCC_PATH_TC or CCC_PATH_POPC */
+  int32_t norm;           /* CCC_NORM_PERSNP or CCC_NORM_JOINT */
+  double gamma;           /* the constant of Eqs. 3-4; the paper fixes 2/3 */
+  void *workspace;        /* device scratch, 256-byte aligned */
+  size_t workspace_bytes; /* its size; must be >= ccc_workspace_size() */
+} ccc_opts;
+
+/* Operations, for ccc_workspace_size(). */
+#define CCC_OP_METRIC 1 /* ccc2_metric / ccc3_metric: status word and per-SNP factors */
+#define CCC_OP_2WAY 2
+#define CCC_OP_3WAY 3
+
+/* Fill *opts with the defaults: path TC, norm PERSNP, gamma 2/3, no workspace. */
+void ccc_opts_default(ccc_opts *opts);
+
+/*
+ * Bytes of workspace that the 2-way (op = CCC_OP_2WAY), 3-way
+ * (op = CCC_OP_3WAY) or metric-only (op = CCC_OP_METRIC) calls need for this
+ * panel and path.  Host only; touches no device memory.  Returns CCC_OK,
+ * CCC_EINVAL or CCC_ERANGE.
+ */
+int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, size_t *bytes);
+
+/*
+ * Per-SNP allele sums and non-missing counts (Eq. 1 numerators; Sec. 2.1):
+ * counts[3*i + 0] = s_i^0, counts[3*i + 1] = s_i^1, counts[3*i + 2] = n_i.
+ * counts: device int32[n_v][3].  Needs no workspace.
+ */
+int ccc_allele_counts(const ccc_panel *panel, int32_t *counts, void *stream);
+
+/*
+ * 2-way tallies of all pairs i < j (Eq. 2 numerators; Sec. 3.1 maps them to a
+ * GEMM-shaped product B = V^T o_2 V whose entries are 2x2 tally tables).
+ * tally: device int32[n_v (n_v - 1) / 2][4].
+ */
+int ccc2_tally(const ccc_panel *panel, int32_t *tally, const ccc_opts *opts, void *stream);
+
+/*
+ * 2-way CCC values (Eq. 3) from tallies produced by ccc2_tally and counts from
+ * ccc_allele_counts.  tally: device int32[npairs][4]; counts: device
+ * int32[n_v][3]; ccc: device float[npairs][4].  Uses opts->norm, opts->gamma
+ * and a workspace of ccc_workspace_size(.., CCC_OP_METRIC, ..) bytes (the
+ * per-SNP factors 1 - gamma f_i(a) are formed there once).
+ */
+int ccc2_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, const ccc_opts *opts,
+                float *ccc, void *stream);
+
+/*
+ * Fused 2-way: allele counts, tallies and CCC values in one pass (Eqs. 1-3),
+ * the CCC computed in the tally kernel's epilogue.  tally: device
+ * int32[npairs][4]; ccc: device float[npairs][4].  Needs the workspace.
+ */
+int ccc2_tally_metric(const ccc_panel *panel, int32_t *tally, float *ccc, const ccc_opts *opts,
+                      void *stream);
+
+/*
+ * 3-way tallies of all triples i < j < k with j in [j_begin, j_end) (Eq. 5
+ * numerators).  For a fixed j the slab is computed as one GEMM-shaped product
+ * of an operand masked elementwise by v_j with the panel, the role that the
+ * matrices X_{j,xi} play in Sec. 3.2.  tally: device int32[S(j_end) -
+ * S(j_begin)][8].  Needs the workspace.  0 <= j_begin <= j_end <= n_v.
+ */
+int ccc3_tally(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
+               const ccc_opts *opts, void *stream);
+
+/*
+ * 3-way CCC values (Eq. 4) from tallies of ccc3_tally over the same slabs and
+ * counts from ccc_allele_counts.  ccc: device float[..][8].  Workspace as for
+ * ccc2_metric (CCC_OP_METRIC).
+ */
+int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_t j_begin,
+                int64_t j_end, const ccc_opts *opts, float *ccc, void *stream);
+
+/* Fused 3-way: counts, tallies and CCC values (Eqs. 1, 4, 5).  Needs the workspace. */
+int ccc3_tally_metric(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
+                      float *ccc, const ccc_opts *opts, void *stream);
+
+/*
+ * Device-side status of the workspace: *status receives CCC_OK or the first
+ * CCC_E* code a kernel recorded (CCC_ETIMEOUT when a bounded wait gave up).
+ * Synchronises the stream.  Every call that takes a workspace clears the word
+ * first, so this reports on the calls since the last workspace call began.
+ */
+int ccc_status(const ccc_opts *opts, int32_t *status, void *stream);
+
+/* Index helpers (host): positions defined in the header comment; -1 if out of range. */
+int64_t ccc2_index(int64_t i, int64_t j, int64_t n_v);
+int64_t ccc3_index(int64_t i, int64_t j, int64_t k, int64_t n_v);
+int64_t ccc2_count(int64_t n_v);                       /* n_v (n_v - 1) / 2 */
+int64_t ccc3_count(int64_t n_v, int64_t j_begin, int64_t j_end); /* S(j_end) - S(j_begin) */
+
+/* Text for a status code. */
+const char *ccc_strerror(int status);
+
+/* Number of kernels this library has launched in this process (all entry points). */
+uint64_t ccc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCC_H_ */

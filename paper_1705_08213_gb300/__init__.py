@@ -1,0 +1,242 @@
+"""Python binding of libccc: the GB300 hot path for 2-way / 3-way CCC.
+
+Argument marshalling only: every function here has the name of a C entry
+point declared in ``include/ccc.h`` and forwards torch tensors' device
+pointers to it.  Every step of the computation runs in the library's CUDA
+kernels; there is no CPU fallback.  When the compiled library is missing the
+first call raises :class:`CCCError` -- build it with
+``paper_1705_08213_gb300.build.build()``.
+
+Genotype panels are torch tensors of shape [n_v, ld] holding the packed
+uint64 words (dtype int64 or uint64; the bits are what matter), on the GPU.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "CCCError", "load", "lib_path",
+    "CCC_OK", "CCC_EINVAL", "CCC_ERANGE", "CCC_EUNSUPPORTED", "CCC_ECUDA", "CCC_ETIMEOUT",
+    "CCC_ENOSPACE", "CCC_PATH_TC", "CCC_PATH_POPC", "CCC_NORM_PERSNP", "CCC_NORM_JOINT",
+    "CCC_OP_METRIC", "CCC_OP_2WAY", "CCC_OP_3WAY", "CCC_MAX_NF",
+    "ccc_panel", "ccc_opts", "ccc_opts_default", "ccc_workspace_size", "ccc_allele_counts",
+    "ccc2_tally", "ccc2_metric", "ccc2_tally_metric", "ccc3_tally", "ccc3_metric",
+    "ccc3_tally_metric", "ccc_status", "ccc2_index", "ccc3_index", "ccc2_count", "ccc3_count",
+    "ccc_strerror", "ccc_launch_count",
+]
+
+CCC_OK = 0
+CCC_EINVAL = -1
+CCC_ERANGE = -2
+CCC_EUNSUPPORTED = -3
+CCC_ECUDA = -4
+CCC_ETIMEOUT = -5
+CCC_ENOSPACE = -6
+CCC_PATH_TC = 0
+CCC_PATH_POPC = 1
+CCC_NORM_PERSNP = 0
+CCC_NORM_JOINT = 1
+CCC_OP_METRIC = 1
+CCC_OP_2WAY = 2
+CCC_OP_3WAY = 3
+CCC_MAX_NF = 2097151
+
+lib_path = _build.LIB
+
+
+class CCCError(RuntimeError):
+    """A libccc call returned a non-zero status (or the library is unavailable)."""
+
+    def __init__(self, name, status):
+        self.status = status
+        msg = _lib_strerror(status) if isinstance(status, int) else str(status)
+        super().__init__(f"{name}: {msg} ({status})")
+
+
+class ccc_panel(ctypes.Structure):
+    _fields_ = [("geno", ctypes.c_void_p), ("n_f", ctypes.c_int64), ("n_v", ctypes.c_int64),
+                ("ld", ctypes.c_int64)]
+
+
+class ccc_opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("norm", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load():
+    """Load libccc.so (built in-tree).  Raises CCCError when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(lib_path):
+        raise CCCError("load", f"{lib_path} not built; run paper_1705_08213_gb300.build.build()")
+    lib = ctypes.CDLL(lib_path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    lib.ccc_opts_default.argtypes = [P(ccc_opts)]
+    lib.ccc_opts_default.restype = None
+    lib.ccc_workspace_size.argtypes = [P(ccc_panel), P(ccc_opts), ctypes.c_int, P(ctypes.c_size_t)]
+    lib.ccc_allele_counts.argtypes = [P(ccc_panel), vp, vp]
+    lib.ccc2_tally.argtypes = [P(ccc_panel), vp, P(ccc_opts), vp]
+    lib.ccc2_metric.argtypes = [vp, vp, i64, P(ccc_opts), vp, vp]
+    lib.ccc2_tally_metric.argtypes = [P(ccc_panel), vp, vp, P(ccc_opts), vp]
+    lib.ccc3_tally.argtypes = [P(ccc_panel), i64, i64, vp, P(ccc_opts), vp]
+    lib.ccc3_metric.argtypes = [vp, vp, i64, i64, i64, P(ccc_opts), vp, vp]
+    lib.ccc3_tally_metric.argtypes = [P(ccc_panel), i64, i64, vp, vp, P(ccc_opts), vp]
+    lib.ccc_status.argtypes = [P(ccc_opts), P(ctypes.c_int32), vp]
+    for name in ("ccc_workspace_size", "ccc_allele_counts", "ccc2_tally", "ccc2_metric",
+                 "ccc2_tally_metric", "ccc3_tally", "ccc3_metric", "ccc3_tally_metric",
+                 "ccc_status"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.ccc2_index.argtypes = [i64, i64, i64]
+    lib.ccc2_index.restype = i64
+    lib.ccc3_index.argtypes = [i64, i64, i64, i64]
+    lib.ccc3_index.restype = i64
+    lib.ccc2_count.argtypes = [i64]
+    lib.ccc2_count.restype = i64
+    lib.ccc3_count.argtypes = [i64, i64, i64]
+    lib.ccc3_count.restype = i64
+    lib.ccc_strerror.argtypes = [ctypes.c_int]
+    lib.ccc_strerror.restype = ctypes.c_char_p
+    lib.ccc_launch_count.argtypes = []
+    lib.ccc_launch_count.restype = ctypes.c_uint64
+    _lib = lib
+    return lib
+
+
+def _lib_strerror(status):
+    try:
+        return load().ccc_strerror(status).decode()
+    except CCCError:
+        return "libccc unavailable"
+
+
+def _check(name, rc):
+    if rc != CCC_OK:
+        raise CCCError(name, rc)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _panel(geno, n_f):
+    if geno.dim() != 2 or not geno.is_contiguous() or geno.element_size() != 8:
+        raise CCCError("panel", CCC_EINVAL)
+    return ccc_panel(geno.data_ptr(), int(n_f), int(geno.shape[0]), int(geno.shape[1]))
+
+
+def ccc_opts_default(path=CCC_PATH_TC, norm=CCC_NORM_PERSNP, gamma=None, workspace=None):
+    """A ccc_opts filled by the library's defaults, then by the given fields."""
+    o = ccc_opts()
+    load().ccc_opts_default(ctypes.byref(o))
+    o.path = int(path)
+    o.norm = int(norm)
+    if gamma is not None:
+        o.gamma = float(gamma)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def ccc_workspace_size(geno_or_shape, n_f, opts, op):
+    """Workspace bytes for a panel (tensor or (n_v, ld) shape), opts and op."""
+    if hasattr(geno_or_shape, "shape") and hasattr(geno_or_shape, "data_ptr"):
+        p = _panel(geno_or_shape, n_f)
+    else:
+        n_v, ld = geno_or_shape
+        p = ccc_panel(None, int(n_f), int(n_v), int(ld))
+    out = ctypes.c_size_t(0)
+    _check("ccc_workspace_size", load().ccc_workspace_size(ctypes.byref(p), ctypes.byref(opts),
+                                                           int(op), ctypes.byref(out)))
+    return int(out.value)
+
+
+def ccc_allele_counts(geno, n_f, counts, stream=None):
+    p = _panel(geno, n_f)
+    _check("ccc_allele_counts", load().ccc_allele_counts(ctypes.byref(p), _ptr(counts), _stream(stream)))
+
+
+def ccc2_tally(geno, n_f, tally, opts, stream=None):
+    p = _panel(geno, n_f)
+    _check("ccc2_tally", load().ccc2_tally(ctypes.byref(p), _ptr(tally), ctypes.byref(opts),
+                                           _stream(stream)))
+
+
+def ccc2_metric(tally, counts, n_v, opts, ccc, stream=None):
+    _check("ccc2_metric", load().ccc2_metric(_ptr(tally), _ptr(counts), int(n_v), ctypes.byref(opts),
+                                             _ptr(ccc), _stream(stream)))
+
+
+def ccc2_tally_metric(geno, n_f, tally, ccc, opts, stream=None):
+    p = _panel(geno, n_f)
+    _check("ccc2_tally_metric", load().ccc2_tally_metric(ctypes.byref(p), _ptr(tally), _ptr(ccc),
+                                                         ctypes.byref(opts), _stream(stream)))
+
+
+def ccc3_tally(geno, n_f, j_begin, j_end, tally, opts, stream=None):
+    p = _panel(geno, n_f)
+    _check("ccc3_tally", load().ccc3_tally(ctypes.byref(p), int(j_begin), int(j_end), _ptr(tally),
+                                           ctypes.byref(opts), _stream(stream)))
+
+
+def ccc3_metric(tally, counts, n_v, j_begin, j_end, opts, ccc, stream=None):
+    _check("ccc3_metric", load().ccc3_metric(_ptr(tally), _ptr(counts), int(n_v), int(j_begin),
+                                             int(j_end), ctypes.byref(opts), _ptr(ccc),
+                                             _stream(stream)))
+
+
+def ccc3_tally_metric(geno, n_f, j_begin, j_end, tally, ccc, opts, stream=None):
+    p = _panel(geno, n_f)
+    _check("ccc3_tally_metric", load().ccc3_tally_metric(ctypes.byref(p), int(j_begin), int(j_end),
+                                                         _ptr(tally), _ptr(ccc), ctypes.byref(opts),
+                                                         _stream(stream)))
+
+
+def ccc_status(opts, stream=None):
+    """The workspace status word (synchronises the stream)."""
+    st = ctypes.c_int32(0)
+    _check("ccc_status", load().ccc_status(ctypes.byref(opts), ctypes.byref(st), _stream(stream)))
+    return int(st.value)
+
+
+def ccc2_index(i, j, n_v):
+    return int(load().ccc2_index(int(i), int(j), int(n_v)))
+
+
+def ccc3_index(i, j, k, n_v):
+    return int(load().ccc3_index(int(i), int(j), int(k), int(n_v)))
+
+
+def ccc2_count(n_v):
+    return int(load().ccc2_count(int(n_v)))
+
+
+def ccc3_count(n_v, j_begin, j_end):
+    return int(load().ccc3_count(int(n_v), int(j_begin), int(j_end)))
+
+
+def ccc_strerror(status):
+    return load().ccc_strerror(int(status)).decode()
+
+
+def ccc_launch_count():
+    return int(load().ccc_launch_count())

@@ -1,0 +1,327 @@
+// C ABI of libccc (declared in include/ccc.h): argument checks, workspace
+// layout and the launch sequence of every entry point.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "ccc_launch.h"
+
+namespace ccc {
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Largest n_v accepted: operand rows (2 n_v, padded) and tile indices stay in int32.
+constexpr int64_t kMaxNV = int64_t(1) << 26;
+
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  bool sm103 = false;
+};
+
+int query_device(DeviceInfo *info) {
+  static DeviceInfo cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CCC_ECUDA;
+  if (dev < 0 || dev >= 64) return CCC_EUNSUPPORTED;
+  DeviceInfo &c = cache[dev];
+  if (c.device != dev) {
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return CCC_ECUDA;
+    c.sms = sms;
+    c.sm103 = (major == 10 && minor == 3);
+    c.device = dev;
+  }
+  *info = c;
+  return c.sm103 ? CCC_OK : CCC_EUNSUPPORTED;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_panel(const ccc_panel *p) {
+  if (p == nullptr || p->geno == nullptr) return CCC_EINVAL;
+  if (p->n_f < 1 || p->n_v < 1) return CCC_EINVAL;
+  if (p->ld < (p->n_f + 31) / 32 || (p->ld & 1) != 0) return CCC_EINVAL;
+  if (!aligned(p->geno, 16)) return CCC_EINVAL;
+  if (p->n_f > CCC_MAX_NF || p->n_v > kMaxNV) return CCC_ERANGE;
+  return CCC_OK;
+}
+
+int check_opts(const ccc_opts *o) {
+  if (o == nullptr) return CCC_EINVAL;
+  if (o->path != CCC_PATH_TC && o->path != CCC_PATH_POPC) return CCC_EINVAL;
+  if (o->norm != CCC_NORM_PERSNP && o->norm != CCC_NORM_JOINT) return CCC_EINVAL;
+  if (!(o->gamma >= 0.0 && o->gamma <= 1.0)) return CCC_EINVAL;
+  return CCC_OK;
+}
+
+// Workspace layout shared by the 2-way and 3-way calls.
+struct Layout {
+  size_t status = 0;          // int32 status word
+  size_t w = 0;               // float [n_v][2] per-SNP factors
+  size_t counts = 0;          // int32 [n_v][3]
+  size_t op = 0;              // e4m3 operands [rows_pad][kpad] (TC path)
+  size_t planes = 0;          // uint64 [n_v][w64][4] (POPC path)
+  size_t lop = 0;             // masked 3-way operands (TC path)
+  size_t total = 0;
+  int64_t kpad = 0, rows_pad = 0, w64 = 0, lop_rows = 0;
+};
+
+int64_t tc_rows_pad(int64_t n_v) { return round_up(2 * n_v, 256) + 256; }
+
+Layout make_layout(int64_t n_f, int64_t n_v, int path, int op) {
+  Layout L;
+  size_t off = 0;
+  L.status = off;
+  off += kAlign;
+  L.w = off;
+  off = align_up(off + sizeof(float) * 2 * static_cast<size_t>(n_v), kAlign);
+  L.counts = off;
+  off = align_up(off + sizeof(int32_t) * 3 * static_cast<size_t>(n_v), kAlign);
+  if (op == CCC_OP_2WAY || op == CCC_OP_3WAY) {
+    if (path == CCC_PATH_TC) {
+      L.kpad = round_up(n_f, 128);
+      L.rows_pad = tc_rows_pad(n_v);
+      off = align_up(off, 1024);
+      L.op = off;
+      off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(L.kpad), 1024);
+      if (op == CCC_OP_3WAY) {
+        L.lop_rows = 0;  // filled in by the 3-way planner
+      }
+    } else {
+      L.w64 = (n_f + 63) / 64;
+      L.planes = off;
+      off = align_up(off + 32 * static_cast<size_t>(n_v) * static_cast<size_t>(L.w64), kAlign);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+int check_workspace(const ccc_opts *o, const Layout &L) {
+  if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
+  if (o->workspace_bytes < L.total) return CCC_ENOSPACE;
+  return CCC_OK;
+}
+
+template <typename T>
+T *at(const ccc_opts *o, size_t off) {
+  return reinterpret_cast<T *>(static_cast<uint8_t *>(o->workspace) + off);
+}
+
+int clear_status(const ccc_opts *o, const Layout &L, cudaStream_t s) {
+  return cudaMemsetAsync(at<int32_t>(o, L.status), 0, sizeof(int32_t), s) == cudaSuccess
+             ? CCC_OK
+             : CCC_ECUDA;
+}
+
+#define CCC_TRY(expr)         \
+  do {                        \
+    const int rc__ = (expr);  \
+    if (rc__ != CCC_OK) return rc__; \
+  } while (0)
+
+}  // namespace
+
+int note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError() == cudaSuccess ? CCC_OK : CCC_ECUDA;
+}
+
+int64_t pair_index(int64_t i, int64_t j, int64_t n_v) {
+  return i * (2 * n_v - i - 1) / 2 + (j - i - 1);
+}
+
+int64_t slab_offset(int64_t j, int64_t n_v) {
+  // sum_{j' < j} j' (n_v - 1 - j')
+  const int64_t s1 = (j - 1) * j / 2;
+  const int64_t s2 = (j - 1) * j * (2 * j - 1) / 6;
+  return s1 * (n_v - 1) - s2;
+}
+
+// The 2-way sequence: counts (+ factors), operand preparation, tally kernel.
+static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const ccc_opts *o,
+                    cudaStream_t s) {
+  CCC_TRY(check_panel(p));
+  CCC_TRY(check_opts(o));
+  if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
+  if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY);
+  CCC_TRY(check_workspace(o, L));
+  CCC_TRY(clear_status(o, L, s));
+  if (p->n_v < 2) return CCC_OK;
+  float *w = at<float>(o, L.w);
+  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
+  Tally2Args a;
+  a.n_v = p->n_v;
+  a.n_f = p->n_f;
+  a.w = w;
+  a.tally = tally;
+  a.ccc = out_ccc;
+  a.status = at<int32_t>(o, L.status);
+  a.gamma = static_cast<float>(o->gamma);
+  a.norm = o->norm;
+  if (o->path == CCC_PATH_TC) {
+    uint8_t *op = at<uint8_t>(o, L.op);
+    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    return launch_tally2_tc(a, op, L.rows_pad, L.kpad, dev.sms, s);
+  }
+  uint64_t *planes = at<uint64_t>(o, L.planes);
+  CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
+  return launch_tally2_popc(a, planes, L.w64, s);
+}
+
+static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t *tally,
+                    float *out_ccc, const ccc_opts *o, cudaStream_t s) {
+  CCC_TRY(check_panel(p));
+  CCC_TRY(check_opts(o));
+  if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
+  if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
+  if (j_begin < 0 || j_end < j_begin || j_end > p->n_v) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return CCC_EUNSUPPORTED;
+}
+
+}  // namespace ccc
+
+using namespace ccc;
+
+extern "C" {
+
+void ccc_opts_default(ccc_opts *opts) {
+  if (opts == nullptr) return;
+  memset(opts, 0, sizeof(*opts));
+  opts->path = CCC_PATH_TC;
+  opts->norm = CCC_NORM_PERSNP;
+  opts->gamma = 2.0 / 3.0;
+}
+
+int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, size_t *bytes) {
+  if (bytes == nullptr) return CCC_EINVAL;
+  CCC_TRY(check_opts(opts));
+  if (panel == nullptr || panel->n_f < 1 || panel->n_v < 1) return CCC_EINVAL;
+  if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
+  if (op != CCC_OP_2WAY && op != CCC_OP_3WAY && op != CCC_OP_METRIC) return CCC_EINVAL;
+  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op).total;
+  return CCC_OK;
+}
+
+int ccc_allele_counts(const ccc_panel *panel, int32_t *counts, void *stream) {
+  CCC_TRY(check_panel(panel));
+  if (counts == nullptr || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return launch_allele_counts(panel->geno, panel->n_f, panel->n_v, panel->ld, counts, nullptr,
+                              0.0, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_tally(const ccc_panel *panel, int32_t *tally, const ccc_opts *opts, void *stream) {
+  return run_2way(panel, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_tally_metric(const ccc_panel *panel, int32_t *tally, float *out_ccc, const ccc_opts *opts,
+                      void *stream) {
+  if (out_ccc == nullptr) return CCC_EINVAL;
+  return run_2way(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, const ccc_opts *opts,
+                float *out_ccc, void *stream) {
+  CCC_TRY(check_opts(opts));
+  if (n_v < 1 || n_v > kMaxNV) return CCC_EINVAL;
+  if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
+  if (!aligned(tally, 16) || !aligned(out_ccc, 16) || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  const Layout L = make_layout(1, n_v, opts->path, CCC_OP_METRIC);
+  CCC_TRY(check_workspace(opts, L));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CCC_TRY(clear_status(opts, L, s));
+  if (n_v < 2) return CCC_OK;
+  float *w = at<float>(opts, L.w);
+  if (opts->norm == CCC_NORM_PERSNP) CCC_TRY(launch_factors_from_counts(counts, n_v, w, opts->gamma, s));
+  return launch_metric2(tally, w, n_v, static_cast<float>(opts->gamma), opts->norm, out_ccc, s);
+}
+
+int ccc3_tally(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
+               const ccc_opts *opts, void *stream) {
+  return run_3way(panel, j_begin, j_end, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc3_tally_metric(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
+                      float *out_ccc, const ccc_opts *opts, void *stream) {
+  if (out_ccc == nullptr) return CCC_EINVAL;
+  return run_3way(panel, j_begin, j_end, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_t j_begin,
+                int64_t j_end, const ccc_opts *opts, float *out_ccc, void *stream) {
+  CCC_TRY(check_opts(opts));
+  if (n_v < 1 || n_v > kMaxNV || j_begin < 0 || j_end < j_begin || j_end > n_v) return CCC_EINVAL;
+  if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
+  if (!aligned(tally, 16) || !aligned(out_ccc, 16) || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return CCC_EUNSUPPORTED;
+}
+
+int ccc_status(const ccc_opts *opts, int32_t *status, void *stream) {
+  if (opts == nullptr || status == nullptr || opts->workspace == nullptr) return CCC_EINVAL;
+  if (opts->workspace_bytes < kAlign) return CCC_ENOSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(status, opts->workspace, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CCC_ECUDA;
+  return CCC_OK;
+}
+
+int64_t ccc2_index(int64_t i, int64_t j, int64_t n_v) {
+  if (i < 0 || j <= i || j >= n_v) return -1;
+  return pair_index(i, j, n_v);
+}
+
+int64_t ccc3_index(int64_t i, int64_t j, int64_t k, int64_t n_v) {
+  if (i < 0 || j <= i || k <= j || k >= n_v) return -1;
+  return slab_offset(j, n_v) + i * (n_v - 1 - j) + (k - j - 1);
+}
+
+int64_t ccc2_count(int64_t n_v) { return n_v < 2 ? 0 : n_v * (n_v - 1) / 2; }
+
+int64_t ccc3_count(int64_t n_v, int64_t j_begin, int64_t j_end) {
+  if (n_v < 1 || j_begin < 0 || j_end < j_begin || j_end > n_v) return -1;
+  return slab_offset(j_end, n_v) - slab_offset(j_begin, n_v);
+}
+
+const char *ccc_strerror(int status) {
+  switch (status) {
+    case CCC_OK: return "ok";
+    case CCC_EINVAL: return "invalid argument";
+    case CCC_ERANGE: return "size out of the supported range";
+    case CCC_EUNSUPPORTED: return "unsupported device or path";
+    case CCC_ECUDA: return "CUDA call failed";
+    case CCC_ETIMEOUT: return "device-side wait timed out";
+    case CCC_ENOSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+uint64_t ccc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

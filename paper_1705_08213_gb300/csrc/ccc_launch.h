@@ -1,0 +1,69 @@
+// Internal host-side launch interface between the C ABI (ccc_api.cu) and the
+// kernel translation units.  Every launcher returns CCC_OK or CCC_ECUDA.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ccc.h"
+
+namespace ccc {
+
+// Counts one kernel launch and converts a launch failure into CCC_ECUDA.
+int note_launch();
+
+int launch_allele_counts(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld,
+                         int32_t *counts, float *w, double gamma, cudaStream_t s);
+int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, double gamma,
+                               cudaStream_t s);
+int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s);
+int launch_planes(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint64_t *planes,
+                  int64_t w64, cudaStream_t s);
+
+// Shared description of a 2-way tally launch.
+struct Tally2Args {
+  int64_t n_v;
+  int64_t n_f;
+  const float *w;   // [n_v][2] per-SNP factors 1 - gamma f_i(a) (PERSNP), or null
+  int32_t *tally;   // [npairs][4]
+  float *ccc;       // [npairs][4] or null (tallies only)
+  int32_t *status;  // workspace status word
+  float gamma;
+  int32_t norm;
+};
+
+// Tensor-core 2-way tallies over the e4m3 operand matrix op[rows_pad][kpad].
+int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
+                     int num_sms, cudaStream_t s);
+// Popcount 2-way tallies over planes[n_v][w64][4].
+int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
+// CCC values from stored tallies.
+int launch_metric2(const int32_t *tally, const float *w, int64_t n_v, float gamma, int32_t norm,
+                   float *ccc, cudaStream_t s);
+
+// Shared description of a 3-way slab launch (slabs j in [j_begin, j_end)).
+struct Tally3Args {
+  int64_t n_v;
+  int64_t n_f;
+  int64_t j_begin, j_end;
+  const float *w;
+  int32_t *tally;  // [S(j_end) - S(j_begin)][8]
+  float *ccc;      // same, or null
+  int32_t *status;
+  float gamma;
+  int32_t norm;
+};
+
+int launch_tally3_tc(const Tally3Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
+                     uint8_t *lop, int64_t lop_rows, int num_sms, cudaStream_t s);
+int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
+int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
+                   int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);
+
+// Host index helpers (also exported through the C ABI).
+int64_t pair_index(int64_t i, int64_t j, int64_t n_v);
+int64_t slab_offset(int64_t j, int64_t n_v);
+
+}  // namespace ccc

@@ -1,0 +1,197 @@
+// Preparation passes over the packed panel: per-SNP allele counts (Eq. 1),
+// the e4m3 count operands for the tensor-core tallies, and the bit planes for
+// the popcount tallies.  All are O(n_f n_v) and HBM-bound.
+#include "ccc_dev.cuh"
+#include "ccc_launch.h"
+
+namespace ccc {
+
+namespace {
+
+constexpr uint64_t kEven = 0x5555555555555555ull;
+
+// Mask of the low bits of every valid 2-bit entry of word w of a row of n_f
+// entries (even bit positions only).
+__device__ __forceinline__ uint64_t valid_even_mask(int64_t w, int64_t n_f) {
+  const int64_t first = w * 32;
+  if (first + 32 <= n_f) return kEven;
+  if (first >= n_f) return 0;
+  const int tail = static_cast<int>(n_f - first);  // 1..31
+  return kEven & ((1ull << (2 * tail)) - 1ull);
+}
+
+// One warp per SNP.  For every word: l = (v)_2 bits, h = (v)_1 bits; the
+// missing marker is h & ~l; rho_1 = l + (h & l) for present entries.
+__global__ void k_allele_counts(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
+                                int64_t ld, int32_t *__restrict__ counts, float *__restrict__ w,
+                                double gamma) {
+  const int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_v) return;
+  const int64_t words = (n_f + 31) / 32;
+  const uint64_t *row = geno + i * ld;
+  int64_t n = 0, s1 = 0;
+  for (int64_t k = lane; k < words; k += 32) {
+    const uint64_t v = row[k];
+    const uint64_t valid = valid_even_mask(k, n_f);
+    const uint64_t l = v & valid;
+    const uint64_t h = (v >> 1) & valid;
+    const uint64_t present = valid & ~(h & ~l);
+    n += __popcll(present);
+    s1 += __popcll(l) + __popcll(h & l);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (lane == 0) {
+    const int64_t s0 = 2 * n - s1;
+    if (counts) {
+      counts[3 * i + 0] = static_cast<int32_t>(s0);
+      counts[3 * i + 1] = static_cast<int32_t>(s1);
+      counts[3 * i + 2] = static_cast<int32_t>(n);
+    }
+    if (w) {
+      // 1 - gamma f_i(a), f_i(a) = s_i^a / (2 n_i), rounded once to fp32.
+      const double f0 = n > 0 ? static_cast<double>(s0) / (2.0 * static_cast<double>(n)) : 0.0;
+      const double f1 = n > 0 ? static_cast<double>(s1) / (2.0 * static_cast<double>(n)) : 0.0;
+      w[2 * i + 0] = static_cast<float>(1.0 - gamma * f0);
+      w[2 * i + 1] = static_cast<float>(1.0 - gamma * f1);
+    }
+  }
+}
+
+// Per-SNP factors 1 - gamma f_i(a) from an int32[n_v][3] counts array.
+__global__ void k_factors_from_counts(const int32_t *__restrict__ counts, int64_t n_v,
+                                      float *__restrict__ w, double gamma) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_v) return;
+  const double n = counts[3 * i + 2];
+  const double f0 = n > 0 ? counts[3 * i + 0] / (2.0 * n) : 0.0;
+  const double f1 = n > 0 ? counts[3 * i + 1] / (2.0 * n) : 0.0;
+  w[2 * i + 0] = static_cast<float>(1.0 - gamma * f0);
+  w[2 * i + 1] = static_cast<float>(1.0 - gamma * f1);
+}
+
+// Four 2-bit codes (one byte) -> selector nibbles for __byte_perm.
+__device__ __forceinline__ uint32_t code_nibbles(uint32_t b) {
+  return (b & 0x3u) | ((b << 2) & 0x30u) | ((b << 4) & 0x300u) | ((b << 6) & 0x3000u);
+}
+
+// e4m3 bytes of rho(0) and rho(1) indexed by code: 0b00 -> (2,0), 0b01 -> (1,1),
+// 0b10 (missing) -> (0,0), 0b11 -> (0,2).  e4m3: 1.0 = 0x38, 2.0 = 0x40.
+constexpr uint32_t kRho0E4M3 = 0x00003840u;
+constexpr uint32_t kRho1E4M3 = 0x40003800u;
+
+// Operand rows for SNP i: row 2i holds rho_{i,q}(0), row 2i+1 holds rho_{i,q}(1),
+// q = 0 .. kpad-1 (zero past n_f).  Rows past 2 n_v are zero.  One thread per
+// packed word (32 entries -> 32 bytes in each of the two rows).
+__global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
+                              int64_t ld, uint8_t *__restrict__ op, int64_t kpad,
+                              int64_t snps_pad) {
+  const int64_t wpr = kpad / 32;  // words per operand row
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= wpr * snps_pad) return;
+  const int64_t i = t / wpr;
+  const int64_t k = t - i * wpr;
+  uint64_t v = 0xAAAAAAAAAAAAAAAAull;  // all entries "missing" -> zero operands
+  if (i < n_v && k * 32 < n_f) {
+    const uint64_t valid = valid_even_mask(k, n_f);
+    const uint64_t vm = valid | (valid << 1);
+    v = (geno[i * ld + k] & vm) | (0xAAAAAAAAAAAAAAAAull & ~vm);
+  }
+  uint32_t r0[8], r1[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t sel = code_nibbles(static_cast<uint32_t>(v >> (8 * b)) & 0xFFu);
+    r0[b] = __byte_perm(kRho0E4M3, 0u, sel);
+    r1[b] = __byte_perm(kRho1E4M3, 0u, sel);
+  }
+  uint4 *d0 = reinterpret_cast<uint4 *>(op + (2 * i) * kpad + k * 32);
+  uint4 *d1 = reinterpret_cast<uint4 *>(op + (2 * i + 1) * kpad + k * 32);
+  d0[0] = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+  d0[1] = make_uint4(r0[4], r0[5], r0[6], r0[7]);
+  d1[0] = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+  d1[1] = make_uint4(r1[4], r1[5], r1[6], r1[7]);
+}
+
+// Gather the 32 even-position bits of x into the low 32 bits.
+__device__ __forceinline__ uint64_t compact_even(uint64_t x) {
+  x &= kEven;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return x;
+}
+
+// Bit planes per 64 entries: P1 = l (one copy of allele 1 for het and hom 1),
+// P2 = h & l (the second copy, hom 1 only), M = present; rho_1 = P1 + P2,
+// rho_0 = 2M - P1 - P2.  planes[(i * w64 + b) * 4 + {0,1,2}] = {P1, P2, M}.
+__global__ void k_planes(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v, int64_t ld,
+                         uint64_t *__restrict__ planes, int64_t w64) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_v * w64) return;
+  const int64_t i = t / w64;
+  const int64_t b = t - i * w64;
+  uint64_t l = 0, h = 0, valid = 0;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int64_t k = 2 * b + half;
+    if (k * 32 < n_f) {
+      const uint64_t v = geno[i * ld + k];
+      const uint64_t vm = valid_even_mask(k, n_f);
+      l |= compact_even(v & vm) << (32 * half);
+      h |= compact_even((v >> 1) & vm) << (32 * half);
+      valid |= compact_even(vm) << (32 * half);
+    }
+  }
+  uint4 *d = reinterpret_cast<uint4 *>(planes + t * 4);
+  const uint64_t p1 = l;
+  const uint64_t p2 = h & l;
+  const uint64_t m = valid & (~h | l);
+  d[0] = make_uint4(static_cast<uint32_t>(p1), static_cast<uint32_t>(p1 >> 32),
+                    static_cast<uint32_t>(p2), static_cast<uint32_t>(p2 >> 32));
+  d[1] = make_uint4(static_cast<uint32_t>(m), static_cast<uint32_t>(m >> 32), 0u, 0u);
+}
+
+}  // namespace
+
+int launch_allele_counts(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld,
+                         int32_t *counts, float *w, double gamma, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = (n_v * 32 + threads - 1) / threads;
+  k_allele_counts<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, counts,
+                                                                     w, gamma);
+  return note_launch();
+}
+
+int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, double gamma,
+                               cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = (n_v + threads - 1) / threads;
+  k_factors_from_counts<<<static_cast<unsigned>(blocks), threads, 0, s>>>(counts, n_v, w, gamma);
+  return note_launch();
+}
+
+int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t total = (kpad / 32) * snps_pad;
+  const int64_t blocks = (total + threads - 1) / threads;
+  k_unpack_e4m3<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
+                                                                   snps_pad);
+  return note_launch();
+}
+
+int launch_planes(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint64_t *planes,
+                  int64_t w64, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = (n_v * w64 + threads - 1) / threads;
+  k_planes<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, planes, w64);
+  return note_launch();
+}
+
+}  // namespace ccc

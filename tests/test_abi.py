@@ -1,0 +1,135 @@
+"""The C ABI library loads and exports every symbol that include/ccc.h declares.
+
+Host-only calls (index helpers, workspace sizing, argument checks that fail
+before any device work) run here without a GPU.
+"""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1705_08213_gb300 as ccc
+from paper_1705_08213_gb300 import build as cbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ccc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cbuild.build()
+    return ccc.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("ccc_allele_counts", "ccc2_tally", "ccc2_metric", "ccc2_tally_metric", "ccc3_tally",
+              "ccc3_metric", "ccc3_tally_metric", "ccc_workspace_size", "ccc_status",
+              "ccc2_index", "ccc3_index", "ccc_strerror", "ccc_launch_count"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", ccc.lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_python_binding_names_match_header():
+    for n in declared_functions():
+        assert hasattr(ccc, n), n
+
+
+def test_index_helpers(lib):
+    n_v = 11
+    t = 0
+    for i in range(n_v):
+        for j in range(i + 1, n_v):
+            assert ccc.ccc2_index(i, j, n_v) == t
+            t += 1
+    assert ccc.ccc2_count(n_v) == t
+    assert ccc.ccc2_index(3, 3, n_v) == -1
+    t = 0
+    for j in range(n_v):
+        for i in range(j):
+            for k in range(j + 1, n_v):
+                assert ccc.ccc3_index(i, j, k, n_v) == t
+                t += 1
+    assert ccc.ccc3_count(n_v, 0, n_v) == t
+    assert ccc.ccc3_count(n_v, 3, 7) == ccc.ccc3_index(0, 7, 8, n_v) - ccc.ccc3_index(0, 3, 4, n_v)
+    assert ccc.ccc3_index(2, 1, 5, n_v) == -1
+
+
+def test_opts_default_and_strerror(lib):
+    o = ccc.ccc_opts_default()
+    assert o.path == ccc.CCC_PATH_TC and o.norm == ccc.CCC_NORM_PERSNP
+    assert abs(o.gamma - 2.0 / 3.0) < 1e-16
+    assert ccc.ccc_strerror(ccc.CCC_ETIMEOUT) == "device-side wait timed out"
+    assert ccc.ccc_strerror(12345) == "unknown status"
+
+
+def test_workspace_size(lib):
+    o = ccc.ccc_opts_default()
+    tc = ccc.ccc_workspace_size((1000, 32), 2000, o, ccc.CCC_OP_2WAY)
+    # e4m3 operand matrix: (round_up(2000, 256) + 256) rows x round_up(2000, 128) bytes dominates
+    assert tc >= (2048 + 256) * 2048
+    o.path = ccc.CCC_PATH_POPC
+    pc = ccc.ccc_workspace_size((1000, 32), 2000, o, ccc.CCC_OP_2WAY)
+    assert pc >= 1000 * 32 * 32
+    m = ccc.ccc_workspace_size((1000, 32), 2000, o, ccc.CCC_OP_METRIC)
+    assert 1000 * 8 <= m < pc
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_workspace_size((0, 2), 10, o, ccc.CCC_OP_2WAY)
+    assert e.value.status == ccc.CCC_EINVAL
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_workspace_size((10, 2), ccc.CCC_MAX_NF + 1, o, ccc.CCC_OP_2WAY)
+    assert e.value.status == ccc.CCC_ERANGE
+    o.path = 7
+    with pytest.raises(ccc.CCCError):
+        ccc.ccc_workspace_size((10, 2), 10, o, ccc.CCC_OP_2WAY)
+
+
+def test_argument_errors_before_device_work(lib):
+    o = ccc.ccc_opts_default()
+    P = ctypes.POINTER
+    # null panel / bad stride / odd ld / n_f too large: rejected before any device call
+    assert lib.ccc2_tally(None, None, ctypes.byref(o), None) == ccc.CCC_EINVAL
+    p = ccc.ccc_panel(16, 100, 10, 3)  # ld odd
+    assert lib.ccc2_tally(ctypes.byref(p), ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_EINVAL
+    p = ccc.ccc_panel(16, 100, 10, 2)  # ld < ceil(100/32) = 4
+    assert lib.ccc2_tally(ctypes.byref(p), ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_EINVAL
+    p = ccc.ccc_panel(8, 100, 10, 4)  # misaligned genotype pointer
+    assert lib.ccc2_tally(ctypes.byref(p), ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_EINVAL
+    p = ccc.ccc_panel(16, ccc.CCC_MAX_NF + 1, 10, 65536)
+    assert lib.ccc2_tally(ctypes.byref(p), ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_ERANGE
+    p = ccc.ccc_panel(16, 100, 10, 4)
+    assert lib.ccc3_tally(ctypes.byref(p), 5, 3, ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_EINVAL
+    assert lib.ccc3_tally(ctypes.byref(p), 0, 11, ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_EINVAL
+    o.norm = 5
+    assert lib.ccc2_tally(ctypes.byref(p), ctypes.c_void_p(256), ctypes.byref(o), None) == ccc.CCC_EINVAL
+    o = ccc.ccc_opts_default()
+    o.gamma = -0.5
+    assert lib.ccc2_metric(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, ctypes.byref(o),
+                           ctypes.c_void_p(256), None) == ccc.CCC_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(ccc, "_lib", None)
+    monkeypatch.setattr(ccc, "lib_path", str(tmp_path / "nope.so"))
+    with pytest.raises(ccc.CCCError):
+        ccc.load()
