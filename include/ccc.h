@@ -201,6 +201,17 @@ const char *ccc_strerror(int status);
 /* Number of kernels this library has launched in this process (all entry points). */
 uint64_t ccc_launch_count(void);
 
+/*
+ * Kernel timing, for instrumentation.  While enabled, every launch of a tally
+ * kernel (the dominant kernel of each 2-way and 3-way call) is bracketed by
+ * two CUDA events recorded on the call's stream, up to 4096 launches.
+ * ccc_timing_read() waits for the recorded events, returns the summed device
+ * time in milliseconds and the number of bracketed launches, and clears the
+ * record.  Host-side state, one record per process; not thread-safe.
+ */
+int ccc_timing_enable(int enable);
+int ccc_timing_read(double *total_ms, int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ __all__ = [
     "ccc_panel", "ccc_opts", "ccc_opts_default", "ccc_workspace_size", "ccc_allele_counts",
     "ccc2_tally", "ccc2_metric", "ccc2_tally_metric", "ccc3_tally", "ccc3_metric",
     "ccc3_tally_metric", "ccc_status", "ccc2_index", "ccc3_index", "ccc2_count", "ccc3_count",
-    "ccc_strerror", "ccc_launch_count",
+    "ccc_strerror", "ccc_launch_count", "ccc_timing_enable", "ccc_timing_read",
 ]
 
 CCC_OK = 0
@@ -108,6 +108,10 @@ def load():
     lib.ccc_strerror.restype = ctypes.c_char_p
     lib.ccc_launch_count.argtypes = []
     lib.ccc_launch_count.restype = ctypes.c_uint64
+    lib.ccc_timing_enable.argtypes = [ctypes.c_int]
+    lib.ccc_timing_enable.restype = ctypes.c_int
+    lib.ccc_timing_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
+    lib.ccc_timing_read.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -240,3 +244,15 @@ def ccc_strerror(status):
 
 def ccc_launch_count():
     return int(load().ccc_launch_count())
+
+
+def ccc_timing_enable(enable=True):
+    _check("ccc_timing_enable", load().ccc_timing_enable(1 if enable else 0))
+
+
+def ccc_timing_read():
+    """(summed device milliseconds, launches) of the bracketed tally kernels; clears the record."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check("ccc_timing_read", load().ccc_timing_read(ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)

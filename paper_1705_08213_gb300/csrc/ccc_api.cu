@@ -127,6 +127,31 @@ int clear_status(const ccc_opts *o, const Layout &L, cudaStream_t s) {
              : CCC_ECUDA;
 }
 
+// Events around tally-kernel launches (ccc_timing_enable / ccc_timing_read).
+struct KernelTiming {
+  static constexpr int kMax = 4096;
+  bool on = false;
+  int used = 0;
+  cudaEvent_t ev[2 * kMax] = {};
+};
+KernelTiming g_timing;
+
+// Records the "before" event; returns the slot or -1 when timing is off/full.
+int timing_begin(cudaStream_t s) {
+  if (!g_timing.on || g_timing.used >= KernelTiming::kMax) return -1;
+  const int k = g_timing.used;
+  for (int e = 0; e < 2; ++e)
+    if (g_timing.ev[2 * k + e] == nullptr && cudaEventCreate(&g_timing.ev[2 * k + e]) != cudaSuccess)
+      return -1;
+  if (cudaEventRecord(g_timing.ev[2 * k], s) != cudaSuccess) return -1;
+  return k;
+}
+
+void timing_end(int slot, cudaStream_t s) {
+  if (slot < 0) return;
+  if (cudaEventRecord(g_timing.ev[2 * slot + 1], s) == cudaSuccess) g_timing.used = slot + 1;
+}
+
 #define CCC_TRY(expr)         \
   do {                        \
     const int rc__ = (expr);  \
@@ -176,14 +201,21 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   a.status = at<int32_t>(o, L.status);
   a.gamma = static_cast<float>(o->gamma);
   a.norm = o->norm;
+  int rc;
   if (o->path == CCC_PATH_TC) {
     uint8_t *op = at<uint8_t>(o, L.op);
     CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
-    return launch_tally2_tc(a, op, L.rows_pad, L.kpad, dev.sms, s);
+    const int slot = timing_begin(s);
+    rc = launch_tally2_tc(a, op, L.rows_pad, L.kpad, dev.sms, s);
+    timing_end(slot, s);
+    return rc;
   }
   uint64_t *planes = at<uint64_t>(o, L.planes);
   CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
-  return launch_tally2_popc(a, planes, L.w64, s);
+  const int slot = timing_begin(s);
+  rc = launch_tally2_popc(a, planes, L.w64, s);
+  timing_end(slot, s);
+  return rc;
 }
 
 static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t *tally,
@@ -323,5 +355,26 @@ const char *ccc_strerror(int status) {
 }
 
 uint64_t ccc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int ccc_timing_enable(int enable) {
+  g_timing.on = enable != 0;
+  return CCC_OK;
+}
+
+int ccc_timing_read(double *total_ms, int64_t *launches) {
+  if (total_ms == nullptr || launches == nullptr) return CCC_EINVAL;
+  double sum = 0.0;
+  for (int k = 0; k < g_timing.used; ++k) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(g_timing.ev[2 * k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, g_timing.ev[2 * k], g_timing.ev[2 * k + 1]) != cudaSuccess)
+      return CCC_ECUDA;
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = g_timing.used;
+  g_timing.used = 0;
+  return CCC_OK;
+}
 
 }  // extern "C"

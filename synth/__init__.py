@@ -41,7 +41,7 @@ import numpy as np
 __all__ = [
     "CODE_HOM0", "CODE_HET", "CODE_MISSING", "CODE_HOM1",
     "mix64", "uniforms", "maf_beta_half", "genotypes_uniform", "genotypes_hwe",
-    "genotypes_analytic", "codes_from_genotypes", "pack", "unpack", "words_per_snp",
+    "genotypes_analytic", "codes_from_genotypes", "pack", "unpack", "words_per_snp", "fill_padding", "hwe_thresholds",
     "panel_uniform", "panel_hwe", "panel_analytic", "default_ld",
 ]
 
@@ -108,11 +108,10 @@ def genotypes_uniform(seed, panel, snps, n_f, p_missing):
 
 def genotypes_hwe(seed, panel, snps, n_f, p_missing):
     """Hardy-Weinberg genotypes: P(g) = (1-p)^2, 2p(1-p), p^2 with per-SNP p; -1 marks missing."""
-    p = maf_beta_half(seed, panel, snps)[:, None]
+    t0, t1 = hwe_thresholds(seed, panel, snps)
+    t0, t1 = t0[:, None], t1[:, None]
     um = uniforms(seed, panel, snps, n_f, 0)
     ug = uniforms(seed, panel, snps, n_f, 1)
-    t0 = (1.0 - p) ** 2
-    t1 = t0 + 2.0 * p * (1.0 - p)
     g = np.where(ug < t0, 0, np.where(ug < t1, 1, 2)).astype(np.int8)
     g[um < p_missing] = -1
     return g
@@ -145,6 +144,25 @@ def default_ld(n_f: int) -> int:
     return max(2, (w + 1) // 2 * 2)
 
 
+def fill_padding(words: np.ndarray, n_f: int, pad_seed: int, row0: int = 0) -> None:
+    """Overwrite the padding bits of packed rows with garbage (row index row0 + r).
+
+    Padding = the bits past n_f in the last word and the words past ceil(n_f/32).
+    """
+    n_v, ld = words.shape
+    w = words_per_snp(n_f)
+    with np.errstate(over="ignore"):
+        idx = (np.arange(n_v, dtype=np.uint64)[:, None] + np.uint64(row0)) * np.uint64(ld) \
+            + np.arange(ld, dtype=np.uint64)[None, :]
+        garbage = mix64(idx + np.uint64(pad_seed) * _G)
+    tail = n_f - (w - 1) * 32
+    if tail < 32:
+        keep = np.uint64((1 << (2 * tail)) - 1)
+        words[:, w - 1] = (words[:, w - 1] & keep) | (garbage[:, w - 1] & ~keep)
+    if ld > w:
+        words[:, w:] = garbage[:, w:]
+
+
 def pack(codes: np.ndarray, ld: int | None = None, pad_seed: int | None = None,
          out: np.ndarray | None = None, row0: int = 0) -> np.ndarray:
     """Pack codes [n_v, n_f] (uint8 0..3) into uint64 words [n_v, ld].
@@ -152,7 +170,8 @@ def pack(codes: np.ndarray, ld: int | None = None, pad_seed: int | None = None,
     With ``pad_seed`` set, the padding bits (past n_f in the last word, and the
     words past ceil(n_f/32)) are filled with random garbage so that tests can
     check that consumers ignore them; otherwise they are zero.  ``out`` and
-    ``row0`` let a caller pack a block of rows into a larger preallocated array.
+    ``row0`` let a caller pack a block of rows into a larger preallocated array
+    (row0 also indexes the padding garbage).
     """
     codes = np.asarray(codes, dtype=np.uint8)
     n_v, n_f = codes.shape
@@ -173,18 +192,10 @@ def pack(codes: np.ndarray, ld: int | None = None, pad_seed: int | None = None,
     else:
         dst = out[row0:row0 + n_v]
     dst[:, :w] = words
-    if pad_seed is not None:
-        with np.errstate(over="ignore"):
-            garbage = mix64(np.arange(n_v * ld, dtype=np.uint64).reshape(n_v, ld)
-                            + np.uint64(pad_seed) * _G)
-        tail = n_f - (w - 1) * 32
-        if tail < 32:
-            keep = np.uint64((1 << (2 * tail)) - 1)
-            dst[:, w - 1] = (dst[:, w - 1] & keep) | (garbage[:, w - 1] & ~keep)
-        if ld > w:
-            dst[:, w:] = garbage[:, w:]
-    elif ld > w:
+    if ld > w:
         dst[:, w:] = 0
+    if pad_seed is not None:
+        fill_padding(dst, n_f, pad_seed, row0)
     return out
 
 
@@ -206,20 +217,72 @@ def _panel(gen, n_v, n_f, ld, pad_seed, chunk):
     for r0 in range(0, n_v, chunk):
         r1 = min(n_v, r0 + chunk)
         g = gen(np.arange(r0, r1))
-        pack(codes_from_genotypes(g), ld=ld, pad_seed=None if pad_seed is None else pad_seed + r0,
-             out=out, row0=r0)
+        pack(codes_from_genotypes(g), ld=ld, pad_seed=pad_seed, out=out, row0=r0)
     return out
 
 
-def panel_uniform(n_v, n_f, seed=0, p_missing=0.02, panel=0, ld=None, pad_seed=None):
+_fast = None
+
+
+def _fast_lib():
+    """The C twin of the generators (synth/_gen.c), built on first use; None if unavailable."""
+    global _fast
+    if _fast is None:
+        try:
+            import ctypes
+
+            from . import build as _b
+            lib = ctypes.CDLL(_b.build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.synth_pack.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, dp, dp,
+                                       ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
+            lib.synth_pack.restype = None
+            _fast = lib
+        except Exception:  # no compiler: the numpy definitions are used
+            _fast = False
+    return _fast or None
+
+
+def _panel_fast(kind, n_v, n_f, ld, seed, panel, p_missing, pad_seed, t0=None, t1=None):
+    import ctypes
+    lib = _fast_lib()
+    if ld is None:
+        ld = default_ld(n_f)
+    out = np.zeros((n_v, ld), dtype=np.uint64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    a0 = None if t0 is None else np.ascontiguousarray(t0, dtype=np.float64)
+    a1 = None if t1 is None else np.ascontiguousarray(t1, dtype=np.float64)
+    lib.synth_pack(kind, n_v, n_f, ld, seed & 0xFFFFFFFFFFFFFFFF, panel, 0,
+                   None if a0 is None else a0.ctypes.data_as(dp),
+                   None if a1 is None else a1.ctypes.data_as(dp), float(p_missing),
+                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if pad_seed is not None:
+        fill_padding(out, n_f, pad_seed)
+    return out
+
+
+def panel_uniform(n_v, n_f, seed=0, p_missing=0.02, panel=0, ld=None, pad_seed=None, fast=True):
     """Uniform-genotype panel (the small 2-way case): packed uint64 [n_v, ld]."""
+    if fast and _fast_lib() is not None:
+        return _panel_fast(0, n_v, n_f, ld, seed, panel, p_missing, pad_seed)
     chunk = max(1, (1 << 22) // max(n_f, 1))
     return _panel(lambda s: genotypes_uniform(seed, panel, s, n_f, p_missing), n_v, n_f, ld,
                   pad_seed, chunk)
 
 
-def panel_hwe(n_v, n_f, seed=1, p_missing=0.01, panel=0, ld=None, pad_seed=None):
+def hwe_thresholds(seed, panel, snps):
+    """Per-SNP genotype thresholds t0 = (1-p)^2, t1 = t0 + 2p(1-p) of the Hardy-Weinberg draw."""
+    p = maf_beta_half(seed, panel, snps)
+    t0 = (1.0 - p) ** 2
+    return t0, t0 + 2.0 * p * (1.0 - p)
+
+
+def panel_hwe(n_v, n_f, seed=1, p_missing=0.01, panel=0, ld=None, pad_seed=None, fast=True):
     """Hardy-Weinberg panel with Beta(1/2,1/2) minor-allele frequencies: packed uint64 [n_v, ld]."""
+    if fast and _fast_lib() is not None:
+        t0, t1 = hwe_thresholds(seed, panel, np.arange(n_v))
+        return _panel_fast(1, n_v, n_f, ld, seed, panel, p_missing, pad_seed, t0, t1)
     chunk = max(1, (1 << 22) // max(n_f, 1))
     return _panel(lambda s: genotypes_hwe(seed, panel, s, n_f, p_missing), n_v, n_f, ld,
                   pad_seed, chunk)

@@ -92,3 +92,15 @@ def test_beta_half_folded_distribution():
 def test_ld_too_small_rejected():
     with pytest.raises(ValueError):
         synth.pack(np.zeros((1, 65), np.uint8), ld=2)
+
+
+@pytest.mark.parametrize("n_f", [1, 31, 32, 33, 100, 1000])
+def test_fast_generator_equals_numpy_definition(n_f):
+    """The C twin of the generator reproduces the numpy definitions bit for bit."""
+    assert synth._fast_lib() is not None
+    for fn, kw in ((synth.panel_uniform, dict(seed=0, p_missing=0.02)),
+                   (synth.panel_hwe, dict(seed=4, p_missing=0.05))):
+        for pad in (None, 5):
+            a = fn(37, n_f, pad_seed=pad, fast=True, **kw)
+            b = fn(37, n_f, pad_seed=pad, fast=False, **kw)
+            np.testing.assert_array_equal(a, b)
