@@ -182,6 +182,40 @@ int ccc3_tally_metric(const ccc_panel *panel, int64_t j_begin, int64_t j_end, in
                       float *ccc, const ccc_opts *opts, void *stream);
 
 /*
+ * Fused 2-way tensor-core call without a workspace, for callers that cannot
+ * allocate device memory: code inside a host framework that owns every device
+ * allocation through its own pool, plug-ins that are handed only their input
+ * and output buffers, or programs that may not allocate once they are running.
+ * The paper has no counterpart; it is an interface convenience of this library.
+ *
+ * Computes exactly what ccc2_tally_metric computes with opts->path ==
+ * CCC_PATH_TC (same kernels, same results), but keeps its scratch (status
+ * word, per-SNP factors, e4m3 count operands) in a fixed 32 MiB device array
+ * built into the library, which every GPU that loads the library holds until
+ * the process exits.  The workspace fields of *opts are ignored; opts->path
+ * must be CCC_PATH_TC.  Nothing is allocated: no cudaMalloc, no cudaFree.
+ *
+ *   panel, tally, ccc, opts, stream: as for ccc2_tally_metric.
+ *   status: optional device int32 owned by the caller (NULL allowed); when
+ *           given, it is cleared and receives CCC_ETIMEOUT if a device-side
+ *           bounded wait gives up.  With NULL that word lives in the built-in
+ *           scratch and is not reported.
+ * Limit: the panel must fit the built-in scratch,
+ *           256 + 8 n_v (rounded up to 1 KiB) + (round_up(2 n_v, 256) + 256)
+ *           * round_up(n_f, 128) <= 32 MiB
+ *         (for example n_v = 2,048 with n_f <= 7,680); larger panels return
+ *         CCC_ERANGE before anything is queued.
+ * Set-up: the first call on each device looks up the array's device address
+ *         (with that device current); make that first call before capturing
+ *         any stream into a CUDA graph.
+ * Sharing: every call on a device uses the same array and leaves its contents
+ *         behind; calls whose work overlaps on the GPU (different streams
+ *         without ordering between them) race on it and must not be issued.
+ */
+int ccc2_tally_metric_noalloc(const ccc_panel *panel, int32_t *tally, float *ccc,
+                              int32_t *status, const ccc_opts *opts, void *stream);
+
+/*
  * Device-side status of the workspace: *status receives CCC_OK or the first
  * CCC_E* code a kernel recorded (CCC_ETIMEOUT when a bounded wait gave up).
  * Synchronises the stream.  Every call that takes a workspace clears the word

@@ -27,6 +27,7 @@ __all__ = [
     "ccc2_tally", "ccc2_metric", "ccc2_tally_metric", "ccc3_tally", "ccc3_metric",
     "ccc3_tally_metric", "ccc_status", "ccc2_index", "ccc3_index", "ccc2_count", "ccc3_count",
     "ccc_strerror", "ccc_launch_count", "ccc_timing_enable", "ccc_timing_read",
+    "ccc2_tally_metric_noalloc",
 ]
 
 CCC_OK = 0
@@ -92,6 +93,8 @@ def load():
     lib.ccc3_metric.argtypes = [vp, vp, i64, i64, i64, P(ccc_opts), vp, vp]
     lib.ccc3_tally_metric.argtypes = [P(ccc_panel), i64, i64, vp, vp, P(ccc_opts), vp]
     lib.ccc_status.argtypes = [P(ccc_opts), P(ctypes.c_int32), vp]
+    lib.ccc2_tally_metric_noalloc.argtypes = [P(ccc_panel), vp, vp, vp, P(ccc_opts), vp]
+    lib.ccc2_tally_metric_noalloc.restype = ctypes.c_int
     for name in ("ccc_workspace_size", "ccc_allele_counts", "ccc2_tally", "ccc2_metric",
                  "ccc2_tally_metric", "ccc3_tally", "ccc3_metric", "ccc3_tally_metric",
                  "ccc_status"):
@@ -256,3 +259,15 @@ def ccc_timing_read():
     n = ctypes.c_int64(0)
     _check("ccc_timing_read", load().ccc_timing_read(ctypes.byref(ms), ctypes.byref(n)))
     return float(ms.value), int(n.value)
+
+
+def ccc2_tally_metric_noalloc(geno, n_f, tally, ccc, opts, status=None, stream=None):
+    """Fused 2-way tensor-core call using the library's built-in scratch (no workspace).
+
+    For callers that cannot allocate device memory; ``status`` is an optional
+    device int32 tensor that receives the device-side status.
+    """
+    p = _panel(geno, n_f)
+    _check("ccc2_tally_metric_noalloc",
+           load().ccc2_tally_metric_noalloc(ctypes.byref(p), _ptr(tally), _ptr(ccc), _ptr(status),
+                                            ctypes.byref(opts), _stream(stream)))
