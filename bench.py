@@ -1,23 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the CCC hot path on GB300: elementwise comparisons per second.
 
-A step is one pass of the whole 2-way hot path through the C ABI
-(ccc2_tally_metric): per-SNP allele counts, the e4m3 count-operand unpack, and
-the tcgen05 tally kernel with the fused CCC epilogue writing all tallies and
-CCC values of the upper triangle to HBM.  A comparison is one (pair, individual)
-element pair producing four tallies (Sec. 6).
+A comparison is one element pair (2-way) or triple (3-way) of one individual,
+producing four (eight) tallies (Sec. 6).  A step is one pass of the whole hot
+path through the C ABI over one synthetic panel resident in HBM.
 
-Default workload (one GPU): 2-way CCC at scale, n_v = 20,000 SNP vectors x
-n_f = 16,384 individuals, Hardy-Weinberg genotypes with Beta(1/2,1/2) minor
-allele frequencies floored at 0.01, 1% missing entries, seed 1; synthetic
-(the counter-based generator in synth/).
+Workloads (``--workload``):
+  2way    default; 2-way CCC at scale: n_v = 20,000 SNP vectors x n_f = 16,384
+          individuals, Hardy-Weinberg genotypes, Beta(1/2,1/2) minor-allele
+          frequencies floored at 0.01, 1% missing, seed 1.  Step =
+          ccc2_tally_metric: allele counts, e4m3 count-operand unpack, the
+          tcgen05 tally kernel with the fused CCC epilogue writing every
+          tally and CCC value of the upper triangle (6.4 GB).
+  3way    3-way CCC: n_v = 1,536 x n_f = 8,192, same genotype model, seed 4;
+          step = ccc3_tally_metric over all slabs (602,800,640 triples, 38.6 GB).
+  filter  2-way with thresholded output: n_v = 200,000 x n_f = 4,096, same
+          model, seed 5, plus 1,000 planted near-duplicate pairs (1% of entries
+          redrawn); step = ccc2_filter keeping pairs with max CCC > 0.16.
+  small   2-way, n_v = 256 x n_f = 1,024, uniform genotypes, 2% missing, seed 0.
+  batched 64 independent 2-way panels, n_v ~ U{500..8000}, n_f ~ U{2000..50000}
+          (shape draws seed 2), Hardy-Weinberg model (seed 2, panel index k);
+          step = ccc2_batched with the schedule chosen by ccc2_batched_tune,
+          captured once in a CUDA graph and replayed; compared with 64
+          sequential ccc2_tally_metric calls.
 
 Prints ONE JSON line (rank 0).  Under torchrun with N ranks every rank runs an
-independent panel of the same shape (seed 1 + rank); there is no data-path
+independent panel of the same shape (seed + rank); there is no data-path
 collective (weak scaling), only a barrier around the timed region.
 
 --impl reference times the CPU oracle (oracle/, all host cores) on a bounded
-random sample of pairs of the same workload in every step.
+random sample of the same workload in every step.
 """
 
 from __future__ import annotations
@@ -39,35 +51,95 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-METRIC = "2-way CCC elementwise comparisons/sec on 1 GB300"
 UNIT = "comparisons/s"
-WORKLOAD = ("2-way CCC at scale: n_v=20000 SNP vectors x n_f=16384 individuals, Hardy-Weinberg "
-            "genotypes, Beta(1/2,1/2) MAF floored at 0.01, 1% missing, seed 1; all 199,990,000 "
-            "unique pairs, 4 int32 tallies + 4 fp32 CCC per pair")
+
+WORKLOADS = {
+    "2way": dict(
+        kind=2, n_v=20000, n_f=16384, seed=1, model="hwe", p_missing=0.01,
+        metric="2-way CCC elementwise comparisons/sec on 1 GB300",
+        text=("2-way CCC at scale: n_v=20000 SNP vectors x n_f=16384 individuals, Hardy-Weinberg "
+              "genotypes, Beta(1/2,1/2) MAF floored at 0.01, 1% missing, seed 1; all 199,990,000 "
+              "unique pairs, 4 int32 tallies + 4 fp32 CCC per pair")),
+    "3way": dict(
+        kind=3, n_v=1536, n_f=8192, seed=4, model="hwe", p_missing=0.01,
+        metric="3-way CCC elementwise comparisons/sec on 1 GB300",
+        text=("3-way CCC: n_v=1536 x n_f=8192, Hardy-Weinberg genotypes, Beta(1/2,1/2) MAF floored "
+              "at 0.01, 1% missing, seed 4; all 602,800,640 unique triples i<j<k (slabs of fixed j), "
+              "8 int32 tallies + 8 fp32 CCC per triple")),
+    "filter": dict(
+        kind=2, n_v=200000, n_f=4096, seed=5, model="hwe", p_missing=0.01, planted=1000,
+        threshold=0.16, metric="2-way CCC elementwise comparisons/sec on 1 GB300",
+        text=("2-way CCC large, thresholded output: n_v=200000 x n_f=4096, Hardy-Weinberg genotypes, "
+              "Beta(1/2,1/2) MAF floored at 0.01, 1% missing, seed 5, 1000 planted near-duplicate "
+              "pairs (1% of entries redrawn); 19,999,900,000 pairs, kept if max CCC > 0.16")),
+    "batched": dict(
+        kind=2, n_panels=64, seed=2, model="hwe", p_missing=0.01,
+        metric="2-way CCC elementwise comparisons/sec on 1 GB300",
+        text=("2-way CCC batched: 64 independent panels, n_v uniform in [500,8000], n_f uniform in "
+              "[2000,50000] (shape seed 2), Hardy-Weinberg genotypes, Beta(1/2,1/2) MAF floored at "
+              "0.01, 1% missing; one persistent launch over all panels' tiles, CUDA-graph replay")),
+    "small": dict(
+        kind=2, n_v=256, n_f=1024, seed=0, model="uniform", p_missing=0.02,
+        metric="2-way CCC elementwise comparisons/sec on 1 GB300",
+        text=("2-way CCC plain: n_v=256 x n_f=1024, genotypes uniform on {0,1,2}, 2% missing, "
+              "seed 0; all 32,640 unique pairs")),
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-v", type=int, default=20000)
-    ap.add_argument("--n-f", type=int, default=16384)
+    ap.add_argument("--workload", default="2way", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-v", type=int, default=None)
+    ap.add_argument("--n-f", type=int, default=None)
     ap.add_argument("--path", default="tc", choices=["tc", "popc"])
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--skip-e2e", action="store_true", help="no host-buffer end-to-end timing")
     ap.add_argument("--skip-popc", action="store_true", help="no popcount-path comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
-    return ap.parse_args()
+    a = ap.parse_args()
+    w = dict(WORKLOADS[a.workload])
+    if a.n_v is not None:
+        w["n_v"] = a.n_v
+    if a.n_f is not None:
+        w["n_f"] = a.n_f
+    if a.steps is None:
+        a.steps = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10}[a.workload]
+    if a.workload == "batched":
+        rng = np.random.default_rng(w["seed"])
+        w["shapes"] = [(int(rng.integers(500, 8001)), int(rng.integers(2000, 50001)))
+                       for _ in range(w["n_panels"])]
+        w["n_v"], w["n_f"] = max(v for v, _ in w["shapes"]), max(f for _, f in w["shapes"])
+    return a, w
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def make_panel(w, rank=0):
+    seed = w["seed"] + rank
+    if w["model"] == "uniform":
+        g = synth.panel_uniform(w["n_v"], w["n_f"], seed=seed, p_missing=w["p_missing"])
+    else:
+        g = synth.panel_hwe(w["n_v"], w["n_f"], seed=seed, p_missing=w["p_missing"])
+    if w.get("planted"):
+        synth.plant_near_duplicates(g, w["n_f"], w["planted"], seed=seed + 1000)
+    return g
+
+
+def comparisons(w):
+    if "shapes" in w:
+        return sum(v * (v - 1) // 2 * f for v, f in w["shapes"])
+    n_v, n_f = w["n_v"], w["n_f"]
+    if w["kind"] == 2:
+        return n_v * (n_v - 1) // 2 * n_f
+    return n_v * (n_v - 1) * (n_v - 2) // 6 * n_f
 
 
 def measured_peaks():
@@ -81,7 +153,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling around the timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -92,6 +164,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.thread = None
+        self.t_on = self.t_off = None
 
     def start(self):
         try:
@@ -104,11 +177,16 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
-        time.sleep(0.3)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark_on(self):
+        self.t_on = time.monotonic()
+
+    def mark_off(self):
+        self.t_off = time.monotonic()
 
     def stop(self):
         if self.proc is None:
@@ -122,7 +200,11 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lo = (self.t_on or 0) - 0.11
+        hi = (self.t_off or 1e30) + 0.11
+        for t, line in self.lines:
+            if not (lo <= t <= hi):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -136,7 +218,8 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0,
+                    "reasons": ["no samples inside the timed region"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
 
@@ -149,69 +232,251 @@ def gpu_id_for(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(geno, n_f, n_v, seconds, seed=7):
-    """Oracle on host cores over random pairs of the same panel, ~`seconds` of CPU work."""
+def oracle_sample(geno, w, rng, budget):
+    """One oracle call on a random sample of the workload; returns comparisons done."""
+    import oracle
+    n_v, n_f = w["n_v"], w["n_f"]
+    if w["kind"] == 2:
+        i = rng.integers(0, n_v - 1, size=budget)
+        j = i + 1 + (rng.random(budget) * (n_v - 1 - i)).astype(np.int64)
+        oracle.ccc2_pairs(geno, n_f, i, j)
+        return budget * n_f
+    j = rng.integers(1, n_v - 1, size=budget)
+    i = (rng.random(budget) * j).astype(np.int64)
+    k = j + 1 + (rng.random(budget) * (n_v - 1 - j)).astype(np.int64)
+    oracle.ccc3_triples(geno, n_f, i, j, k)
+    return budget * n_f
+
+
+def cpu_baseline(geno, w, seconds, seed=7):
+    """The oracle on host cores over random pairs (triples) of the same panel."""
     import oracle
     rng = np.random.default_rng(seed)
-    batch = 8192
-    done = 0
+    budget = max(64, int(4e8 // w["n_f"]))
+    done, calls = 0, 0
     t0 = time.perf_counter()
     while True:
-        i = rng.integers(0, n_v - 1, size=batch)
-        j = i + 1 + (rng.random(batch) * (n_v - 1 - i)).astype(np.int64)
-        oracle.ccc2_pairs(geno, n_f, i, j)
-        done += batch
+        done += oracle_sample(geno, w, rng, budget)
+        calls += 1
         el = time.perf_counter() - t0
-        if el >= seconds or done >= 64 * batch:
+        if el >= seconds or calls >= 200:
             break
-    return {"value": done * n_f / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{done} uniformly random pairs (i<j) of the same panel, all {n_f} "
-                      f"individuals each, {el:.1f} s on the host cores"}
+    what = "pairs (i<j)" if w["kind"] == 2 else "triples (i<j<k)"
+    return {"value": done / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{calls * budget} uniformly random {what} of the same panel, all "
+                      f"{w['n_f']} individuals each, {el:.1f} s on the host cores"}
 
 
-def run_reference(args):
+def run_reference(args, w):
     """The CPU oracle timed on this workload (rank 0 only)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    n_v, n_f = args.n_v, args.n_f
-    geno = synth.panel_hwe(n_v, n_f, seed=1, p_missing=0.01)
+    geno = make_panel(w)
     rng = np.random.default_rng(11)
-    pairs_per_step = 4096
-
-    def step():
-        i = rng.integers(0, n_v - 1, size=pairs_per_step)
-        j = i + 1 + (rng.random(pairs_per_step) * (n_v - 1 - i)).astype(np.int64)
-        oracle.ccc2_pairs(geno, n_f, i, j)
-
+    budget = max(64, int(6e7 // w["n_f"]))
     for _ in range(args.warmup):
-        step()
+        oracle_sample(geno, w, rng, budget)
     t0 = time.perf_counter()
+    done = 0
     for _ in range(args.steps):
-        step()
+        done += oracle_sample(geno, w, rng, budget)
     el = time.perf_counter() - t0
-    value = args.steps * pairs_per_step * n_f / el
+    value = done / el
+    what = "pairs" if w["kind"] == 2 else "triples"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_v": n_v, "n_f": n_f,
-                   "sample_per_step": f"{pairs_per_step} random pairs x {n_f} individuals"},
+        "impl": "reference", "metric": w["metric"], "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
+        "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"],
+                   "sample_per_step": f"{budget} random {what} x {w['n_f']} individuals"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                         "sample": f"{pairs_per_step} uniformly random pairs per step, "
-                                   f"{args.steps} timed steps"},
+                         "sample": f"{budget} uniformly random {what} per step, {args.steps} "
+                                   "timed steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+class Runner:
+    """Device buffers and one step of the chosen workload through the C ABI."""
+
+    def __init__(self, ccc, torch, dev, w, path, geno_np):
+        self.ccc, self.torch, self.dev, self.w, self.path = ccc, torch, dev, w, path
+        n_v, n_f = w["n_v"], w["n_f"]
+        self.host_geno = torch.from_numpy(geno_np.view(np.int64)).pin_memory()
+        self.geno = self.host_geno.to(dev)
+        op = ccc.CCC_OP_2WAY if w["kind"] == 2 else ccc.CCC_OP_3WAY
+        o0 = ccc.ccc_opts_default(path=path)
+        self.ws = torch.empty(ccc.ccc_workspace_size(self.geno, n_f, o0, op), dtype=torch.uint8,
+                              device=dev)
+        self.opts = ccc.ccc_opts_default(path=path, workspace=self.ws)
+        self.filter = "threshold" in w
+        if self.filter:
+            self.cap = 1 << 20
+            self.hits = torch.zeros(self.cap * 40, dtype=torch.uint8, device=dev)
+            self.n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
+            self.out_bytes = 8
+        else:
+            rows = ccc.ccc2_count(n_v) if w["kind"] == 2 else ccc.ccc3_count(n_v, 0, n_v)
+            width = 4 if w["kind"] == 2 else 8
+            self.tally = torch.empty((rows, width), dtype=torch.int32, device=dev)
+            self.out = torch.empty((rows, width), dtype=torch.float32, device=dev)
+            self.out_bytes = rows * width * 8
+
+    def step(self, stream):
+        ccc, w = self.ccc, self.w
+        if self.filter:
+            ccc.ccc2_filter(self.geno, w["n_f"], w["threshold"], self.hits, self.cap, self.n_hits,
+                            self.opts, stream)
+        elif w["kind"] == 2:
+            ccc.ccc2_tally_metric(self.geno, w["n_f"], self.tally, self.out, self.opts, stream)
+        else:
+            ccc.ccc3_tally_metric(self.geno, w["n_f"], 0, w["n_v"], self.tally, self.out, self.opts,
+                                  stream)
+
+    def e2e(self, stream, steps):
+        """Host panel -> device, the step, results -> pinned host memory, per step."""
+        torch = self.torch
+        if self.filter:
+            host = [torch.empty(1, dtype=torch.int64, pin_memory=True)]
+            dev = [self.n_hits]
+        else:
+            host = [torch.empty(self.tally.shape, dtype=torch.int32, pin_memory=True),
+                    torch.empty(self.out.shape, dtype=torch.float32, pin_memory=True)]
+            dev = [self.tally, self.out]
+
+        def one():
+            self.geno.copy_(self.host_geno, non_blocking=True)
+            self.step(stream)
+            for h, d in zip(host, dev):
+                h.copy_(d, non_blocking=True)
+
+        one()
+        torch.cuda.synchronize(self.dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one()
+        e1.record(stream)
+        torch.cuda.synchronize(self.dev)
+        if self.filter:
+            self.hit_count = int(host[0].item())
+        return e0.elapsed_time(e1) / steps, self.host_geno.numel() * 8, self.out_bytes
+
+
+def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
+    """The batched workload: autotune, capture one CUDA graph, replay it."""
+    shapes = w["shapes"]
+    genos_np = [synth.panel_hwe(v, f, seed=w["seed"] + 1000 * rank, panel=k,
+                                p_missing=w["p_missing"]) for k, (v, f) in enumerate(shapes)]
+    genos = [torch.from_numpy(g.view(np.int64)).to(dev) for g in genos_np]
+    n_fs = [f for _, f in shapes]
+    tallies = [torch.empty((ccc.ccc2_count(v), 4), dtype=torch.int32, device=dev) for v, _ in shapes]
+    cccs = [torch.empty((ccc.ccc2_count(v), 4), dtype=torch.float32, device=dev) for v, _ in shapes]
+    opts = ccc.ccc_opts_default()
+    ws = torch.empty(ccc.ccc2_batched_workspace_size(genos, n_fs, opts), dtype=torch.uint8,
+                     device=dev)
+    opts = ccc.ccc_opts_default(workspace=ws)
+    cmp_per_step = comparisons(w)
+    with torch.cuda.stream(stream):
+        group, order = ccc.ccc2_batched_tune(genos, n_fs, tallies, cccs, opts, stream)
+        for _ in range(max(args.warmup, 1)):
+            ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts, stream)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts, stream)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_id_for(torch, dev))
+    sampler.start()
+    time.sleep(0.5)
+    launches0 = ccc.ccc_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark_on()
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sampler.mark_off()
+    ms_graph = e0.elapsed_time(e1) / args.steps
+    # Same steps through the C ABI directly, with the library's kernel events.
+    ccc.ccc_timing_enable(True)
+    ccc.ccc_timing_read()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(args.steps):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts, stream)
+    d1.record(stream)
+    torch.cuda.synchronize(dev)
+    kernel_ms, kernel_n = ccc.ccc_timing_read()
+    ccc.ccc_timing_enable(False)
+    direct_launches = ccc.ccc_launch_count() - launches0
+    ms_direct = d0.elapsed_time(d1) / args.steps
+    clocks = sampler.stop()
+    # 64 sequential single-panel calls, one shared workspace.
+    o0 = ccc.ccc_opts_default()
+    wss = torch.empty(max(ccc.ccc_workspace_size(g, f, o0, ccc.CCC_OP_2WAY)
+                          for g, f in zip(genos, n_fs)), dtype=torch.uint8, device=dev)
+    os_ = ccc.ccc_opts_default(workspace=wss)
+    for g, f, t, c in zip(genos, n_fs, tallies, cccs):
+        ccc.ccc2_tally_metric(g, f, t, c, os_, stream)
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nseq = max(1, min(args.steps, 3))
+    s0.record(stream)
+    for _ in range(nseq):
+        for g, f, t, c in zip(genos, n_fs, tallies, cccs):
+            ccc.ccc2_tally_metric(g, f, t, c, os_, stream)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = s0.elapsed_time(s1) / nseq
+    bf16_peak, _, peak_src = measured_peaks()
+    kstep = kernel_ms / args.steps
+    achieved = 8.0 * cmp_per_step / (kstep * 1e-3) / 1e12
+    peak = 2.0 * bf16_peak
+    result = {
+        "metric": w["metric"], "value": cmp_per_step / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "e4m3 operands, fp32 accumulate", "data": "synthetic",
+        "config": {"workload": w["text"], "panels": len(shapes), "comparisons": cmp_per_step,
+                   "schedule": {"group": group, "order": order, "tuned_by": "ccc2_batched_tune"},
+                   "l2": "inputs larger than L2"},
+        "gpu_launches": int(direct_launches // args.steps),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_tally2_tc_batched",
+                     "kernel_ms_per_step": kstep, "kernel_launches": kernel_n,
+                     "note": "kernel time from the library's events over the same number of direct "
+                             "(not graph) steps right after the graph replays",
+                     "peak_note": f"e4m3 dense = 2 x {peak_src} bf16 burst {bf16_peak:.0f}"},
+        "clocks": clocks,
+        "direct_calls": {"ms_per_step": ms_direct, "value": cmp_per_step / (ms_direct * 1e-3)},
+        "sequential_64_calls": {"ms_per_step": ms_seq, "value": cmp_per_step / (ms_seq * 1e-3),
+                                "batched_speedup": ms_seq / ms_graph},
+    }
+    if not args.skip_cpu:
+        k = int(np.argmax([v for v, _ in shapes]))
+        wk = dict(kind=2, n_v=shapes[k][0], n_f=shapes[k][1])
+        result["cpu_baseline"] = cpu_baseline(genos_np[k], wk, args.cpu_seconds)
+        result["cpu_baseline"]["sample"] += f" (panel {k}, the largest)"
+    print(json.dumps(result), flush=True)
+    return 0
+
+
 def main():
-    args = parse()
+    args, w = parse()
     if args.impl == "reference":
-        return run_reference(args)
+        if args.workload == "batched":
+            k = int(np.argmax([v for v, _ in w["shapes"]]))
+            w = dict(w, n_v=w["shapes"][k][0], n_f=w["shapes"][k][1], seed=w["seed"])
+        return run_reference(args, w)
 
     import torch
 
@@ -232,35 +497,28 @@ def main():
         pg.barrier()
     ccc.load()
 
-    n_v, n_f = args.n_v, args.n_f
-    npairs = n_v * (n_v - 1) // 2
-    cmp_per_step = npairs * n_f
+    if args.workload == "batched":
+        if world > 1:
+            raise SystemExit("the batched workload runs on one GPU")
+            side = torch.cuda.Stream(dev)  # CUDA graphs are captured on a non-default stream
+        with torch.cuda.stream(side):
+            return run_batched(args, w, ccc, torch, dev, side, rank, world, pg)
     path = ccc.CCC_PATH_TC if args.path == "tc" else ccc.CCC_PATH_POPC
-
-    geno_np = synth.panel_hwe(n_v, n_f, seed=1 + rank, p_missing=0.01)
-    host_geno = torch.from_numpy(geno_np.view(np.int64)).pin_memory()
-    geno = host_geno.to(dev)
-    opts0 = ccc.ccc_opts_default(path=path)
-    ws = torch.empty(ccc.ccc_workspace_size(geno, n_f, opts0, ccc.CCC_OP_2WAY), dtype=torch.uint8,
-                     device=dev)
-    opts = ccc.ccc_opts_default(path=path, workspace=ws)
-    tally = torch.empty((npairs, 4), dtype=torch.int32, device=dev)
-    out = torch.empty((npairs, 4), dtype=torch.float32, device=dev)
+    cmp_per_step = comparisons(w)
+    geno_np = make_panel(w, rank)
+    run = Runner(ccc, torch, dev, w, path, geno_np)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        ccc.ccc2_tally_metric(geno, n_f, tally, out, opts, stream)
-
+    sampler = ClockSampler(gpu_id_for(torch, dev)) if local == 0 else None
+    if sampler:
+        sampler.start()  # its start-up overlaps the warm-up, never the timed region
     for _ in range(max(args.warmup, 0)):
-        step()
+        run.step(stream)
     torch.cuda.synchronize(dev)
-    if ccc.ccc_status(opts) != ccc.CCC_OK:
+    if ccc.ccc_status(run.opts) != ccc.CCC_OK:
         raise RuntimeError("device status not ok after warm-up")
 
     # ---------------------------------------------------------------- timed region
-    sampler = ClockSampler(gpu_id_for(torch, dev)) if local == 0 else None
-    if sampler:
-        sampler.start()
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize(dev)
@@ -269,119 +527,102 @@ def main():
     launches0 = ccc.ccc_launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.mark_on()
     ev0.record(stream)
     for _ in range(args.steps):
-        step()
+        run.step(stream)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.mark_off()
     if pg is not None:
         pg.barrier()
     launches = ccc.ccc_launch_count() - launches0
     kernel_ms, kernel_n = ccc.ccc_timing_read()
     ccc.ccc_timing_enable(False)
     clocks = sampler.stop() if sampler else None
-    elapsed_ms = ev0.elapsed_time(ev1)
-    ms_per_step = elapsed_ms / args.steps
+    ms_per_step = ev0.elapsed_time(ev1) / args.steps
     if pg is not None:
         t = torch.tensor([ms_per_step], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms_per_step = float(t.item())
-    if ccc.ccc_status(opts) != ccc.CCC_OK:
+    if ccc.ccc_status(run.opts) != ccc.CCC_OK:
         raise RuntimeError("device status not ok after the timed region")
     value = world * cmp_per_step / (ms_per_step * 1e-3)
 
-    # Roofline of the dominant kernel (the tally kernel), from its own events.
+    # Roofline of the dominant kernel (the tally kernel), from its own events:
+    # summed duration of its launches in the timed region / steps.
     bf16_peak, hbm_peak, peak_src = measured_peaks()
-    kernel_avg_ms = kernel_ms / max(kernel_n, 1)
+    kernel_step_ms = kernel_ms / args.steps
+    kname = {(2, True): "k_tally2_tc", (3, True): "k_tally3_tc", (2, False): "k_tally2_popc",
+             (3, False): "k_tally3_popc"}[(w["kind"], path == ccc.CCC_PATH_TC)]
     if path == ccc.CCC_PATH_TC:
-        flops = 8.0 * cmp_per_step  # 4 MAC per comparison, 2 flops per MAC
-        achieved = flops / (kernel_avg_ms * 1e-3) / 1e12
+        flops = (8.0 if w["kind"] == 2 else 16.0) * cmp_per_step  # 4 (8) MAC per comparison
+        achieved = flops / (kernel_step_ms * 1e-3) / 1e12
         peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_tally2_tc", "kernel_ms": kernel_avg_ms,
+                "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n,
+                "per_unit": f"{'8' if w['kind'] == 2 else '16'} flops per comparison",
                 "peak_note": f"e4m3 dense peak = 2 x {peak_src} bf16 burst {bf16_peak:.0f} TFLOP/s "
                              "(kind::i8 is not available on sm_103a)"}
     else:
-        popc = 9.0 * cmp_per_step / 64.0  # nine 64-bit AND+POPC per 64 comparisons
-        achieved = popc / (kernel_avg_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "Tpopc64/s",
-                "frac": None, "traffic": None, "kernel": "k_tally2_popc",
-                "kernel_ms": kernel_avg_ms}
+        per = 9.0 / 64.0 if w["kind"] == 2 else 27.0 / 64.0
+        achieved = per * cmp_per_step / (kernel_step_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "T popc64/s",
+                "frac": None, "traffic": None, "kernel": kname,
+                "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n}
 
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "metric": w["metric"], "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "e4m3 operands, fp32 accumulate" if path == ccc.CCC_PATH_TC else "u64 bit planes",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_v": n_v, "n_f": n_f, "path": args.path,
-                   "parallelism": f"{world} independent panels (one per GPU)" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2: 655 MB e4m3 operand matrix read and 6.4 GB of "
-                         "tallies+CCC written per step (L2 129 MB)"},
+        "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"], "path": args.path,
+                   "parallelism": (f"{world} independent panels (one per GPU)" if world > 1
+                                   else "1 GPU"),
+                   "l2": ("inputs larger than L2 (operand matrix and outputs exceed the 129 MB L2)"
+                          if w["n_v"] * w["n_f"] * 2 > 129e6 else
+                          "small case: inputs fit L2, launch-bound")},
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clocks,
     }
 
-    # ---------------------------------------------------------------- end to end
     if not args.skip_e2e and rank == 0:
-        host_tally = torch.empty((npairs, 4), dtype=torch.int32, pin_memory=True)
-        host_ccc = torch.empty((npairs, 4), dtype=torch.float32, pin_memory=True)
-        e2e_steps = max(1, min(args.steps, 5))
-
-        def e2e_step():
-            geno.copy_(host_geno, non_blocking=True)
-            ccc.ccc2_tally_metric(geno, n_f, tally, out, opts, stream)
-            host_tally.copy_(tally, non_blocking=True)
-            host_ccc.copy_(out, non_blocking=True)
-
-        e2e_step()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_ms, bi, bo = run.e2e(stream, max(1, min(args.steps, 5)))
         result["e2e"] = {"value": cmp_per_step / (e2e_ms * 1e-3), "unit": UNIT,
-                         "h2d_bytes_per_step": host_geno.numel() * 8,
-                         "d2h_bytes_per_step": npairs * 32, "ms_per_step": e2e_ms,
-                         "note": "pinned host panel -> device, ccc2_tally_metric, all tallies and "
-                                 "CCC values -> pinned host, one stream"}
-        del host_tally, host_ccc
+                         "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
+                         "note": "pinned host panel -> device, the same C ABI call, all results "
+                                 "-> pinned host memory, one stream"}
+        if run.filter:
+            result["config"]["hits_per_step"] = run.hit_count
 
-    # ---------------------------------------------------------------- popcount path
-    if not args.skip_popc and rank == 0 and path == ccc.CCC_PATH_TC:
-        del ws
-        opts_p0 = ccc.ccc_opts_default(path=ccc.CCC_PATH_POPC)
-        wsp = torch.empty(ccc.ccc_workspace_size(geno, n_f, opts_p0, ccc.CCC_OP_2WAY),
+    if (not args.skip_popc and rank == 0 and path == ccc.CCC_PATH_TC and w["kind"] == 2
+            and not run.filter):
+        del run.ws
+        o0 = ccc.ccc_opts_default(path=ccc.CCC_PATH_POPC)
+        wsp = torch.empty(ccc.ccc_workspace_size(run.geno, w["n_f"], o0, ccc.CCC_OP_2WAY),
                           dtype=torch.uint8, device=dev)
-        opts_p = ccc.ccc_opts_default(path=ccc.CCC_PATH_POPC, workspace=wsp)
-        ccc.ccc2_tally_metric(geno, n_f, tally, out, opts_p, stream)
+        run.opts = ccc.ccc_opts_default(path=ccc.CCC_PATH_POPC, workspace=wsp)
+        run.step(stream)
         torch.cuda.synchronize(dev)
-        ccc.ccc_timing_enable(True)
-        ccc.ccc_timing_read()
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         nps = 2
         p0.record(stream)
         for _ in range(nps):
-            ccc.ccc2_tally_metric(geno, n_f, tally, out, opts_p, stream)
+            run.step(stream)
         p1.record(stream)
         torch.cuda.synchronize(dev)
-        pk_ms, pk_n = ccc.ccc_timing_read()
-        ccc.ccc_timing_enable(False)
         pms = p0.elapsed_time(p1) / nps
         result["popc_path"] = {"value": cmp_per_step / (pms * 1e-3), "unit": UNIT,
-                               "ms_per_step": pms, "kernel_ms": pk_ms / max(pk_n, 1),
-                               "tc_speedup": pms / ms_per_step}
+                               "ms_per_step": pms, "tc_speedup": pms / ms_per_step}
 
-    # ---------------------------------------------------------------- CPU baseline
     if not args.skip_cpu and rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(geno_np, n_f, n_v, args.cpu_seconds)
+        result["cpu_baseline"] = cpu_baseline(geno_np, w, args.cpu_seconds)
 
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -109,6 +109,8 @@ typedef struct ccc_opts {
   double gamma;           /* the constant of Eqs. 3-4; the paper fixes 2/3 */
   void *workspace;        /* device scratch, 256-byte aligned */
   size_t workspace_bytes; /* its size; must be >= ccc_workspace_size() */
+  int32_t group;          /* tensor-core tile order: column blocks per L2 group; 0 = 8 */
+  int32_t order;          /* ccc2_batched panel order: 0 = most tile work first, 1 = as given */
 } ccc_opts;
 
 /* Operations, for ccc_workspace_size(). */
@@ -116,7 +118,8 @@ typedef struct ccc_opts {
 #define CCC_OP_2WAY 2
 #define CCC_OP_3WAY 3
 
-/* Fill *opts with the defaults: path TC, norm PERSNP, gamma 2/3, no workspace. */
+/* Fill *opts with the defaults: path TC, norm PERSNP, gamma 2/3, no workspace,
+ * automatic schedule (group 0, order 0). */
 void ccc_opts_default(ccc_opts *opts);
 
 /*
@@ -158,6 +161,52 @@ int ccc2_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, const 
  */
 int ccc2_tally_metric(const ccc_panel *panel, int32_t *tally, float *ccc, const ccc_opts *opts,
                       void *stream);
+
+/* One pair kept by ccc2_filter. */
+typedef struct ccc_hit {
+  int32_t i, j;      /* the pair, i < j */
+  int32_t tally[4];  /* r^{00}, r^{01}, r^{10}, r^{11} */
+  float ccc[4];      /* CCC(0,0), CCC(0,1), CCC(1,0), CCC(1,1) */
+} ccc_hit;
+
+/*
+ * 2-way with thresholded output (Sec. 8 item 6: in practice only the few
+ * values above a threshold are wanted).  Computes the tallies and CCC values
+ * of every pair i < j exactly as ccc2_tally_metric does, but stores only the
+ * pairs whose largest CCC value exceeds `threshold`: they are appended in no
+ * particular order to hits[0 .. min(total, cap)), and *n_hits (a device
+ * int64 owned by the caller, cleared by the call) receives the total number
+ * of such pairs, which may exceed cap (then only cap of them were stored).
+ * Needs the CCC_OP_2WAY workspace.  Either path.  threshold must be finite.
+ */
+int ccc2_filter(const ccc_panel *panel, float threshold, ccc_hit *hits, int64_t cap,
+                int64_t *n_hits, const ccc_opts *opts, void *stream);
+
+/*
+ * Batched 2-way over independent panels (many SNP panels of uneven n_v and n_f,
+ * as in a multi-study run): for every panel k, the tallies and CCC values that
+ * ccc2_tally_metric would write to tally[k] and ccc[k].  On the tensor-core
+ * path all tiles of up to 64 panels run in one persistent launch, so small
+ * panels fill the SMs that large ones leave idle; opts->order and opts->group
+ * choose the schedule (see ccc2_batched_tune).  panels: host array of
+ * n_panels panels; tally, ccc: host arrays of n_panels device pointers (ccc
+ * may be NULL for tallies only).  Workspace: ccc2_batched_workspace_size().
+ * The call queues only stream work (memsets and kernels), so it can be
+ * captured into a CUDA graph once a first call has run outside capture.
+ */
+int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc_opts *opts,
+                                size_t *bytes);
+int ccc2_batched(const ccc_panel *panels, int n_panels, int32_t *const *tally,
+                 float *const *ccc, const ccc_opts *opts, void *stream);
+
+/*
+ * Schedule autotuner for ccc2_batched: runs the batch once for each candidate
+ * (group 4, 8, 16 x order 0, 1), timing each with CUDA events on the stream
+ * (synchronising it), and stores the fastest group and order in *opts.  The
+ * outputs hold a correct result afterwards.
+ */
+int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tally,
+                      float *const *ccc, ccc_opts *opts, void *stream);
 
 /*
  * 3-way tallies of all triples i < j < k with j in [j_begin, j_end) (Eq. 5

@@ -27,7 +27,8 @@ __all__ = [
     "ccc2_tally", "ccc2_metric", "ccc2_tally_metric", "ccc3_tally", "ccc3_metric",
     "ccc3_tally_metric", "ccc_status", "ccc2_index", "ccc3_index", "ccc2_count", "ccc3_count",
     "ccc_strerror", "ccc_launch_count", "ccc_timing_enable", "ccc_timing_read",
-    "ccc2_tally_metric_noalloc",
+    "ccc2_tally_metric_noalloc", "ccc_hit", "ccc2_filter", "ccc2_batched_workspace_size",
+    "ccc2_batched", "ccc2_batched_tune",
 ]
 
 CCC_OK = 0
@@ -63,9 +64,15 @@ class ccc_panel(ctypes.Structure):
                 ("ld", ctypes.c_int64)]
 
 
+class ccc_hit(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("tally", ctypes.c_int32 * 4),
+                ("ccc", ctypes.c_float * 4)]
+
+
 class ccc_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("norm", ctypes.c_int32), ("gamma", ctypes.c_double),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("group", ctypes.c_int32), ("order", ctypes.c_int32)]
 
 
 _lib = None
@@ -93,6 +100,14 @@ def load():
     lib.ccc3_metric.argtypes = [vp, vp, i64, i64, i64, P(ccc_opts), vp, vp]
     lib.ccc3_tally_metric.argtypes = [P(ccc_panel), i64, i64, vp, vp, P(ccc_opts), vp]
     lib.ccc_status.argtypes = [P(ccc_opts), P(ctypes.c_int32), vp]
+    lib.ccc2_batched_workspace_size.argtypes = [P(ccc_panel), ctypes.c_int, P(ccc_opts),
+                                                P(ctypes.c_size_t)]
+    lib.ccc2_batched.argtypes = [P(ccc_panel), ctypes.c_int, P(vp), P(vp), P(ccc_opts), vp]
+    lib.ccc2_batched_tune.argtypes = [P(ccc_panel), ctypes.c_int, P(vp), P(vp), P(ccc_opts), vp]
+    for name in ("ccc2_batched_workspace_size", "ccc2_batched", "ccc2_batched_tune"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.ccc2_filter.argtypes = [P(ccc_panel), ctypes.c_float, vp, i64, vp, P(ccc_opts), vp]
+    lib.ccc2_filter.restype = ctypes.c_int
     lib.ccc2_tally_metric_noalloc.argtypes = [P(ccc_panel), vp, vp, vp, P(ccc_opts), vp]
     lib.ccc2_tally_metric_noalloc.restype = ctypes.c_int
     for name in ("ccc_workspace_size", "ccc_allele_counts", "ccc2_tally", "ccc2_metric",
@@ -191,6 +206,49 @@ def ccc2_tally(geno, n_f, tally, opts, stream=None):
 def ccc2_metric(tally, counts, n_v, opts, ccc, stream=None):
     _check("ccc2_metric", load().ccc2_metric(_ptr(tally), _ptr(counts), int(n_v), ctypes.byref(opts),
                                              _ptr(ccc), _stream(stream)))
+
+
+def _panels(genos, n_fs):
+    arr = (ccc_panel * len(genos))()
+    for k, (g, n_f) in enumerate(zip(genos, n_fs)):
+        arr[k] = _panel(g, n_f)
+    return arr
+
+
+def _ptrs(tensors):
+    if tensors is None:
+        return None
+    return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+def ccc2_batched_workspace_size(genos, n_fs, opts):
+    out = ctypes.c_size_t(0)
+    arr = _panels(genos, n_fs)
+    _check("ccc2_batched_workspace_size",
+           load().ccc2_batched_workspace_size(arr, len(genos), ctypes.byref(opts), ctypes.byref(out)))
+    return int(out.value)
+
+
+def ccc2_batched(genos, n_fs, tallies, cccs, opts, stream=None):
+    """Batched 2-way: lists of panels (device tensors), their n_f, and output tensors."""
+    _check("ccc2_batched", load().ccc2_batched(_panels(genos, n_fs), len(genos), _ptrs(tallies),
+                                               _ptrs(cccs), ctypes.byref(opts), _stream(stream)))
+
+
+def ccc2_batched_tune(genos, n_fs, tallies, cccs, opts, stream=None):
+    """Measure the schedule candidates and store the fastest group / order in opts."""
+    _check("ccc2_batched_tune", load().ccc2_batched_tune(_panels(genos, n_fs), len(genos),
+                                                         _ptrs(tallies), _ptrs(cccs),
+                                                         ctypes.byref(opts), _stream(stream)))
+    return int(opts.group), int(opts.order)
+
+
+def ccc2_filter(geno, n_f, threshold, hits, cap, n_hits, opts, stream=None):
+    """Thresholded 2-way output: hits is a device buffer of cap ccc_hit records (40 bytes
+    each; may be None when cap is 0); n_hits a device int64 tensor receiving the total."""
+    p = _panel(geno, n_f)
+    _check("ccc2_filter", load().ccc2_filter(ctypes.byref(p), float(threshold), _ptr(hits), int(cap),
+                                             _ptr(n_hits), ctypes.byref(opts), _stream(stream)))
 
 
 def ccc2_tally_metric(geno, n_f, tally, ccc, opts, stream=None):

@@ -64,6 +64,7 @@ int check_opts(const ccc_opts *o) {
   if (o->path != CCC_PATH_TC && o->path != CCC_PATH_POPC) return CCC_EINVAL;
   if (o->norm != CCC_NORM_PERSNP && o->norm != CCC_NORM_JOINT) return CCC_EINVAL;
   if (!(o->gamma >= 0.0 && o->gamma <= 1.0)) return CCC_EINVAL;
+  if (o->group < 0 || o->group > 4096 || (o->order != 0 && o->order != 1)) return CCC_EINVAL;
   return CCC_OK;
 }
 
@@ -80,6 +81,12 @@ struct Layout {
 };
 
 int64_t tc_rows_pad(int64_t n_v) { return round_up(2 * n_v, 256) + 256; }
+
+// Panels accepted by one ccc2_batched call.
+constexpr int kMaxPanelsPerCall = 1024;
+
+// Bytes of masked 3-way operands staged per batch of slabs.
+constexpr size_t kLopBytes = size_t(2) << 30;
 
 Layout make_layout(int64_t n_f, int64_t n_v, int path, int op) {
   Layout L;
@@ -98,7 +105,17 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op) {
       L.op = off;
       off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(L.kpad), 1024);
       if (op == CCC_OP_3WAY) {
-        L.lop_rows = 0;  // filled in by the 3-way planner
+        // Masked operands of as many slabs as fit in kLopBytes, but at least
+        // the largest slab (j = n_v - 2).
+        const int64_t all_rows = tc3_lop_rows(0, n_v);
+        const int64_t max_slab = tc3_lop_rows(n_v - 1, n_v);
+        int64_t cap = static_cast<int64_t>(kLopBytes / static_cast<size_t>(L.kpad));
+        cap = cap / 128 * 128;
+        if (cap < max_slab) cap = max_slab;
+        L.lop_rows = all_rows < cap ? all_rows : cap;
+        if (L.lop_rows < 128) L.lop_rows = 128;
+        L.lop = off;
+        off = align_up(off + static_cast<size_t>(L.lop_rows) * static_cast<size_t>(L.kpad), 1024);
       }
     } else {
       L.w64 = (n_f + 63) / 64;
@@ -176,23 +193,49 @@ int64_t slab_offset(int64_t j, int64_t n_v) {
   return s1 * (n_v - 1) - s2;
 }
 
+// Thresholded output of a 2-way call (ccc2_filter); null for plain output.
+struct FilterSpec {
+  ccc_hit *hits;
+  int64_t cap;
+  int64_t *n_hits;
+  float threshold;
+};
+
 // The 2-way sequence: counts (+ factors), operand preparation, tally kernel.
 static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const ccc_opts *o,
-                    cudaStream_t s) {
+                    cudaStream_t s, const FilterSpec *filter = nullptr) {
   CCC_TRY(check_panel(p));
   CCC_TRY(check_opts(o));
-  if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
-  if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
+  if (filter == nullptr) {
+    if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
+    if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
+  } else {
+    if (filter->n_hits == nullptr || !aligned(filter->n_hits, 8) || filter->cap < 0) return CCC_EINVAL;
+    if (filter->cap > 0 && (filter->hits == nullptr || !aligned(filter->hits, 8))) return CCC_EINVAL;
+    if (!(filter->threshold == filter->threshold) || filter->threshold > 3.0e38f ||
+        filter->threshold < -3.0e38f)
+      return CCC_EINVAL;
+  }
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
   const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY);
   CCC_TRY(check_workspace(o, L));
   CCC_TRY(clear_status(o, L, s));
+  if (filter != nullptr &&
+      cudaMemsetAsync(filter->n_hits, 0, sizeof(int64_t), s) != cudaSuccess)
+    return CCC_ECUDA;
   if (p->n_v < 2) return CCC_OK;
   float *w = at<float>(o, L.w);
-  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
+  if ((out_ccc != nullptr || filter != nullptr) && o->norm == CCC_NORM_PERSNP)
     CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   Tally2Args a;
+  a.group = o->group;
+  if (filter != nullptr) {
+    a.hits = filter->cap > 0 ? filter->hits : reinterpret_cast<ccc_hit *>(filter->n_hits);
+    a.n_hits = reinterpret_cast<unsigned long long *>(filter->n_hits);
+    a.cap = filter->cap;
+    a.threshold = filter->threshold;
+  }
   a.n_v = p->n_v;
   a.n_f = p->n_f;
   a.w = w;
@@ -218,6 +261,9 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   return rc;
 }
 
+// The 3-way sequence over slabs [j_begin, j_end): counts (+ factors), operand
+// preparation, then per batch of slabs the masked operands and the tally kernel
+// (tensor cores), or one popcount kernel over all slabs.
 static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t *tally,
                     float *out_ccc, const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_panel(p));
@@ -225,9 +271,167 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
   if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
   if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
   if (j_begin < 0 || j_end < j_begin || j_end > p->n_v) return CCC_EINVAL;
+  if (p->n_v > 65535) return CCC_ERANGE;
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
-  return CCC_EUNSUPPORTED;
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY);
+  CCC_TRY(check_workspace(o, L));
+  CCC_TRY(clear_status(o, L, s));
+  if (slab_offset(j_end, p->n_v) == slab_offset(j_begin, p->n_v)) return CCC_OK;
+  float *w = at<float>(o, L.w);
+  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
+  Tally3Args a;
+  a.n_v = p->n_v;
+  a.n_f = p->n_f;
+  a.j_begin = j_begin;
+  a.j_end = j_end;
+  a.w = w;
+  a.tally = tally;
+  a.ccc = out_ccc;
+  a.status = at<int32_t>(o, L.status);
+  a.gamma = static_cast<float>(o->gamma);
+  a.norm = o->norm;
+  if (o->path == CCC_PATH_TC) {
+    uint8_t *op = at<uint8_t>(o, L.op);
+    uint8_t *lop = at<uint8_t>(o, L.lop);
+    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    // Slab 0 has no i < j and slab n_v - 1 no k > j.
+    const int64_t jb = j_begin > 1 ? j_begin : 1;
+    const int64_t je = j_end < p->n_v - 1 ? j_end : p->n_v - 1;
+    int64_t j0 = jb;
+    while (j0 < je) {
+      int64_t j1 = j0 + 1;
+      while (j1 < je && tc3_lop_rows(j0, j1 + 1) <= L.lop_rows) ++j1;
+      if (tc3_lop_rows(j0, j1) > L.lop_rows) return CCC_ERANGE;
+      CCC_TRY(launch_mask3(p->geno, p->n_f, p->n_v, p->ld, lop, L.kpad, j0, j1, s));
+      const int slot = timing_begin(s);
+      const int rc = launch_tally3_tc(a, op, L.rows_pad, L.kpad, lop, L.lop_rows, j0, j1, dev.sms, s);
+      timing_end(slot, s);
+      if (rc != CCC_OK) return rc;
+      j0 = j1;
+    }
+    return CCC_OK;
+  }
+  uint64_t *planes = at<uint64_t>(o, L.planes);
+  CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
+  const int slot = timing_begin(s);
+  const int rc = launch_tally3_popc(a, planes, L.w64, s);
+  timing_end(slot, s);
+  return rc;
+}
+
+// Workspace of a batch: [status][per panel: factors, operands (or bit planes)].
+struct BatchLayout {
+  size_t total = 0;
+  size_t w[kMaxPanelsPerCall] = {}, op[kMaxPanelsPerCall] = {};
+  int64_t kpad[kMaxPanelsPerCall] = {}, rows_pad[kMaxPanelsPerCall] = {}, w64[kMaxPanelsPerCall] = {};
+};
+
+static int batch_layout(const ccc_panel *panels, int n, int path, BatchLayout *B) {
+  size_t off = kAlign;
+  for (int k = 0; k < n; ++k) {
+    const ccc_panel &p = panels[k];
+    B->w[k] = off;
+    off = align_up(off + sizeof(float) * 2 * static_cast<size_t>(p.n_v), kAlign);
+    if (path == CCC_PATH_TC) {
+      B->kpad[k] = round_up(p.n_f, 128);
+      B->rows_pad[k] = tc_rows_pad(p.n_v);
+      off = align_up(off, 1024);
+      B->op[k] = off;
+      off = align_up(off + static_cast<size_t>(B->rows_pad[k]) * static_cast<size_t>(B->kpad[k]), 1024);
+    } else {
+      B->w64[k] = (p.n_f + 63) / 64;
+      B->op[k] = off;
+      off = align_up(off + 32 * static_cast<size_t>(p.n_v) * static_cast<size_t>(B->w64[k]), kAlign);
+    }
+  }
+  B->total = off;
+  return CCC_OK;
+}
+
+static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, float *const *out_ccc,
+                       const ccc_opts *o, cudaStream_t s) {
+  CCC_TRY(check_opts(o));
+  if (panels == nullptr || tally == nullptr || n < 1 || n > kMaxPanelsPerCall) return CCC_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    CCC_TRY(check_panel(&panels[k]));
+    if (tally[k] == nullptr || !aligned(tally[k], 16)) return CCC_EINVAL;
+    if (out_ccc != nullptr && (out_ccc[k] == nullptr || !aligned(out_ccc[k], 16))) return CCC_EINVAL;
+  }
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  static thread_local BatchLayout B;
+  batch_layout(panels, n, o->path, &B);
+  if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
+  if (o->workspace_bytes < B.total) return CCC_ENOSPACE;
+  int32_t *status = at<int32_t>(o, 0);
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return CCC_ECUDA;
+  static thread_local Tally2Args args[kMaxPanelsPerCall];
+  static thread_local const uint8_t *ops[kMaxPanelsPerCall];
+  static thread_local int order[kMaxPanelsPerCall];
+  for (int k = 0; k < n; ++k) {
+    const ccc_panel &p = panels[k];
+    float *w = at<float>(o, B.w[k]);
+    if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP && p.n_v >= 2)
+      CCC_TRY(launch_allele_counts(p.geno, p.n_f, p.n_v, p.ld, nullptr, w, o->gamma, s));
+    Tally2Args a;
+    a.n_v = p.n_v;
+    a.n_f = p.n_f;
+    a.w = w;
+    a.tally = tally[k];
+    a.ccc = out_ccc != nullptr ? out_ccc[k] : nullptr;
+    a.status = status;
+    a.gamma = static_cast<float>(o->gamma);
+    a.norm = o->norm;
+    a.group = o->group;
+    args[k] = a;
+    if (p.n_v < 2) continue;
+    if (o->path == CCC_PATH_TC) {
+      CCC_TRY(launch_unpack_e4m3(p.geno, p.n_f, p.n_v, p.ld, at<uint8_t>(o, B.op[k]), B.kpad[k],
+                                 B.rows_pad[k] / 2, s));
+    } else {
+      uint64_t *planes = at<uint64_t>(o, B.op[k]);
+      CCC_TRY(launch_planes(p.geno, p.n_f, p.n_v, p.ld, planes, B.w64[k], s));
+      const int slot = timing_begin(s);
+      const int rc = launch_tally2_popc(a, planes, B.w64[k], s);
+      timing_end(slot, s);
+      if (rc != CCC_OK) return rc;
+    }
+  }
+  if (o->path != CCC_PATH_TC) return CCC_OK;
+  // Panel order: most tile work (tiles x K stages) first, or as given.
+  for (int k = 0; k < n; ++k) order[k] = k;
+  if (o->order == 0) {
+    auto work = [&](int k) {
+      const int64_t nv = panels[k].n_v;
+      const int64_t nI = (nv + 63) / 64, nJ = (nv + 127) / 128;
+      return (nI * nJ - (nI / 2) * (nI / 2 - 1) - (nI / 2) * (nI & 1)) * (B.kpad[k] / 128);
+    };
+    for (int x = 1; x < n; ++x)
+      for (int y = x; y > 0 && work(order[y]) > work(order[y - 1]); --y) {
+        const int t = order[y];
+        order[y] = order[y - 1];
+        order[y - 1] = t;
+      }
+  }
+  static thread_local Tally2Args oargs[kMaxBatchPanels];
+  static thread_local int64_t orows[kMaxBatchPanels], okpad[kMaxBatchPanels];
+  for (int c0 = 0; c0 < n; c0 += kMaxBatchPanels) {
+    const int m = n - c0 < kMaxBatchPanels ? n - c0 : kMaxBatchPanels;
+    for (int x = 0; x < m; ++x) {
+      const int k = order[c0 + x];
+      oargs[x] = args[k];
+      ops[x] = at<uint8_t>(o, B.op[k]);
+      orows[x] = B.rows_pad[k];
+      okpad[x] = B.kpad[k];
+    }
+    const int slot = timing_begin(s);
+    const int rc = launch_tally2_tc_batched(oargs, ops, orows, okpad, m, o->group, dev.sms, s);
+    timing_end(slot, s);
+    if (rc != CCC_OK) return rc;
+  }
+  return CCC_OK;
 }
 
 }  // namespace ccc
@@ -273,6 +477,72 @@ int ccc2_tally_metric(const ccc_panel *panel, int32_t *tally, float *out_ccc, co
   return run_2way(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
 }
 
+int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc_opts *opts,
+                                size_t *bytes) {
+  if (bytes == nullptr || panels == nullptr || n_panels < 1 || n_panels > kMaxPanelsPerCall)
+    return CCC_EINVAL;
+  CCC_TRY(check_opts(opts));
+  for (int k = 0; k < n_panels; ++k) {
+    if (panels[k].n_f < 1 || panels[k].n_v < 1) return CCC_EINVAL;
+    if (panels[k].n_f > CCC_MAX_NF || panels[k].n_v > kMaxNV) return CCC_ERANGE;
+  }
+  static thread_local BatchLayout B;
+  batch_layout(panels, n_panels, opts->path, &B);
+  *bytes = B.total;
+  return CCC_OK;
+}
+
+int ccc2_batched(const ccc_panel *panels, int n_panels, int32_t *const *tally, float *const *ccc,
+                 const ccc_opts *opts, void *stream) {
+  return run_batched(panels, n_panels, tally, ccc, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tally, float *const *ccc,
+                      ccc_opts *opts, void *stream) {
+  if (opts == nullptr) return CCC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int groups[3] = {4, 8, 16};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return CCC_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return CCC_ECUDA;
+  }
+  ccc_opts o = *opts;
+  float best = -1.f;
+  int best_g = 8, best_o = 0, rc = CCC_OK;
+  for (int ord = 0; ord < 2 && rc == CCC_OK; ++ord)
+    for (int gi = 0; gi < 3 && rc == CCC_OK; ++gi) {
+      o.group = groups[gi];
+      o.order = ord;
+      cudaEventRecord(e0, s);
+      rc = run_batched(panels, n_panels, tally, ccc, &o, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (rc == CCC_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = CCC_ECUDA;
+      if (rc == CCC_OK && (best < 0.f || ms < best)) {
+        best = ms;
+        best_g = groups[gi];
+        best_o = ord;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CCC_OK) return rc;
+  opts->group = best_g;
+  opts->order = best_o;
+  // Leave the outputs as the chosen schedule writes them (all schedules agree).
+  return run_batched(panels, n_panels, tally, ccc, opts, s);
+}
+
+int ccc2_filter(const ccc_panel *panel, float threshold, ccc_hit *hits, int64_t cap,
+                int64_t *n_hits, const ccc_opts *opts, void *stream) {
+  FilterSpec f{hits, cap, n_hits, threshold};
+  return run_2way(panel, nullptr, nullptr, opts, static_cast<cudaStream_t>(stream), &f);
+}
+
 int ccc2_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, const ccc_opts *opts,
                 float *out_ccc, void *stream) {
   CCC_TRY(check_opts(opts));
@@ -308,9 +578,17 @@ int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_
   if (n_v < 1 || n_v > kMaxNV || j_begin < 0 || j_end < j_begin || j_end > n_v) return CCC_EINVAL;
   if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
   if (!aligned(tally, 16) || !aligned(out_ccc, 16) || !aligned(counts, 4)) return CCC_EINVAL;
+  if (j_end - j_begin > 65535) return CCC_ERANGE;
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
-  return CCC_EUNSUPPORTED;
+  const Layout L = make_layout(1, n_v, opts->path, CCC_OP_METRIC);
+  CCC_TRY(check_workspace(opts, L));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CCC_TRY(clear_status(opts, L, s));
+  float *w = at<float>(opts, L.w);
+  if (opts->norm == CCC_NORM_PERSNP) CCC_TRY(launch_factors_from_counts(counts, n_v, w, opts->gamma, s));
+  return launch_metric3(tally, w, n_v, j_begin, j_end, static_cast<float>(opts->gamma), opts->norm,
+                        out_ccc, s);
 }
 
 int ccc_status(const ccc_opts *opts, int32_t *status, void *stream) {

@@ -32,7 +32,24 @@ struct Tally2Args {
   int32_t *status;  // workspace status word
   float gamma;
   int32_t norm;
+  // Thresholded output: when hits is set, nothing is written to tally / ccc;
+  // pairs whose largest CCC value exceeds threshold are appended to hits.
+  ccc_hit *hits = nullptr;
+  unsigned long long *n_hits = nullptr;
+  int64_t cap = 0;
+  float threshold = 0.f;
+  // Column blocks per L2 group of the tensor-core tile order (0 = default 8).
+  int32_t group = 0;
 };
+
+// Panels per batched tensor-core launch (kernel parameter space).
+constexpr int kMaxBatchPanels = 64;
+
+// One persistent tensor-core launch over all tiles of n <= kMaxBatchPanels
+// panels, in the given order; ops[k] is panel k's operand matrix.
+int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
+                             const int64_t *rows_pad, const int64_t *kpad, int n, int group,
+                             int num_sms, cudaStream_t s);
 
 // Tensor-core 2-way tallies over the e4m3 operand matrix op[rows_pad][kpad].
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
@@ -56,8 +73,16 @@ struct Tally3Args {
   int32_t norm;
 };
 
+// Masked 3-way operands L_j for the slabs [j0, j1) into lop (rows as tc3_lop_rows).
+int launch_mask3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *lop,
+                 int64_t kpad, int64_t j0, int64_t j1, cudaStream_t s);
+// L rows of the slabs [j0, j1) (each slab padded to 32 SNPs i, 4 rows per SNP).
+int64_t tc3_lop_rows(int64_t j0, int64_t j1);
+int64_t tc3_num_tiles(int64_t j0, int64_t j1, int64_t n_v);
+// Tensor-core 3-way tallies of the slabs [j0, j1) (inside [a.j_begin, a.j_end)).
 int launch_tally3_tc(const Tally3Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
-                     uint8_t *lop, int64_t lop_rows, int num_sms, cudaStream_t s);
+                     uint8_t *lop, int64_t lop_rows, int64_t j0, int64_t j1, int num_sms,
+                     cudaStream_t s);
 int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
 int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
                    int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);

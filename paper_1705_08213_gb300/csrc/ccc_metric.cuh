@@ -68,8 +68,37 @@ __device__ __forceinline__ void ccc3_values(const int32_t (&r)[8], float wi0, fl
   }
 }
 
+// Append pair (i, j) to the hit list when its largest CCC value exceeds the threshold.
+__device__ __forceinline__ void filter_pair(ccc_hit *hits, unsigned long long *n_hits, int64_t cap,
+                                            float threshold, int64_t i, int64_t j, int32_t r00,
+                                            int32_t r01, int32_t r10, int32_t r11, float4 c) {
+  const float mx = fmaxf(fmaxf(c.x, c.y), fmaxf(c.z, c.w));
+  if (!(mx > threshold)) return;
+  const unsigned long long slot = atomicAdd(n_hits, 1ull);
+  if (static_cast<int64_t>(slot) >= cap) return;
+  ccc_hit h;
+  h.i = static_cast<int32_t>(i);
+  h.j = static_cast<int32_t>(j);
+  h.tally[0] = r00;
+  h.tally[1] = r01;
+  h.tally[2] = r10;
+  h.tally[3] = r11;
+  h.ccc[0] = c.x;
+  h.ccc[1] = c.y;
+  h.ccc[2] = c.z;
+  h.ccc[3] = c.w;
+  hits[slot] = h;
+}
+
 __device__ __forceinline__ int64_t dev_pair_index(int64_t i, int64_t j, int64_t n_v) {
   return i * (2 * n_v - i - 1) / 2 + (j - i - 1);
+}
+
+// Triples in slabs 0 .. j-1: S(j) = sum_{j' < j} j' (n_v - 1 - j').
+__host__ __device__ __forceinline__ int64_t slab_offset_dev(int64_t j, int64_t n_v) {
+  const int64_t s1 = (j - 1) * j / 2;
+  const int64_t s2 = (j - 1) * j * (2 * j - 1) / 6;
+  return s1 * (n_v - 1) - s2;
 }
 
 }  // namespace ccc

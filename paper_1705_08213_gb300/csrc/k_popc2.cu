@@ -118,8 +118,10 @@ __global__ void __launch_bounds__(THREADS)
   for (int x = 0; x < 4; ++x) {
     const int64_t i = I * TS + ty + 16 * x;
     if (i >= n_v) continue;
+    const bool filter = args.hits != nullptr;
+    const bool want_ccc = filter || args.ccc != nullptr;
     float wi0 = 1.f, wi1 = 1.f;
-    if (args.ccc != nullptr && args.norm == CCC_NORM_PERSNP) {
+    if (want_ccc && args.norm == CCC_NORM_PERSNP) {
       wi0 = __ldg(args.w + 2 * i);
       wi1 = __ldg(args.w + 2 * i + 1);
     }
@@ -136,16 +138,21 @@ __global__ void __launch_bounds__(THREADS)
       const int32_t r01 = 2 * Y - r11;
       const int32_t r00 = 4 * Z - 2 * X - 2 * Y + r11;
       const int64_t pidx = row_base + j;
-      reinterpret_cast<int4 *>(args.tally)[pidx] = make_int4(r00, r01, r10, r11);
-      if (args.ccc != nullptr) {
+      if (!filter) reinterpret_cast<int4 *>(args.tally)[pidx] = make_int4(r00, r01, r10, r11);
+      if (want_ccc) {
         float wj0 = 1.f, wj1 = 1.f;
         if (args.norm == CCC_NORM_PERSNP) {
           const float2 wj = __ldg(reinterpret_cast<const float2 *>(args.w) + j);
           wj0 = wj.x;
           wj1 = wj.y;
         }
-        reinterpret_cast<float4 *>(args.ccc)[pidx] =
+        const float4 cv =
             ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
+        if (filter)
+          filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10, r11,
+                      cv);
+        else
+          reinterpret_cast<float4 *>(args.ccc)[pidx] = cv;
       }
     }
   }

@@ -41,7 +41,7 @@ import numpy as np
 __all__ = [
     "CODE_HOM0", "CODE_HET", "CODE_MISSING", "CODE_HOM1",
     "mix64", "uniforms", "maf_beta_half", "genotypes_uniform", "genotypes_hwe",
-    "genotypes_analytic", "codes_from_genotypes", "pack", "unpack", "words_per_snp", "fill_padding", "hwe_thresholds",
+    "genotypes_analytic", "codes_from_genotypes", "pack", "unpack", "words_per_snp", "fill_padding", "hwe_thresholds", "plant_near_duplicates",
     "panel_uniform", "panel_hwe", "panel_analytic", "default_ld",
 ]
 
@@ -291,3 +291,32 @@ def panel_hwe(n_v, n_f, seed=1, p_missing=0.01, panel=0, ld=None, pad_seed=None,
 def panel_analytic(n_v, n_f, ld=None):
     """Closed-form panel g_{i,q} = (i+q) mod 3 (no missing): packed uint64 [n_v, ld]."""
     return pack(codes_from_genotypes(genotypes_analytic(n_v, n_f)), ld=ld)
+
+
+def plant_near_duplicates(geno: np.ndarray, n_f: int, n_pairs: int, seed: int, redraw: float = 0.01,
+                          p_missing: float = 0.01):
+    """Overwrite SNP rows with near-copies of other rows, in place.
+
+    For each of ``n_pairs`` disjoint (source, target) pairs drawn with a seeded
+    generator, the target row becomes a copy of the source row in which a
+    fraction ``redraw`` of the entries is redrawn: genotype 0/1/2 with the
+    source row's own genotype frequencies, missing with probability p_missing.
+    Returns the (source, target) pairs as an int64 array [n_pairs, 2] with
+    source < target or source > target as drawn.
+    """
+    n_v = geno.shape[0]
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(n_v, size=2 * n_pairs, replace=False)
+    pairs = rows.reshape(n_pairs, 2)
+    for src, dst in pairs:
+        codes = unpack(geno[src:src + 1], n_f)[0].copy()
+        present = codes[codes != CODE_MISSING]
+        freq = np.array([np.mean(present == c) for c in (CODE_HOM0, CODE_HET, CODE_HOM1)])
+        freq = freq / freq.sum() if freq.sum() > 0 else np.full(3, 1 / 3)
+        sel = rng.random(n_f) < redraw
+        k = int(sel.sum())
+        new = np.array([CODE_HOM0, CODE_HET, CODE_HOM1], np.uint8)[rng.choice(3, size=k, p=freq)]
+        new[rng.random(k) < p_missing] = CODE_MISSING
+        codes[sel] = new
+        pack(codes[None, :], ld=geno.shape[1], out=geno, row0=dst)
+    return pairs.astype(np.int64)

@@ -1,0 +1,122 @@
+"""GPU batched 2-way panels (ccc2_batched): one persistent launch over many panels."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import assert_ccc_close, assert_tally_equal, run_2way, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_08213_gb300 import build
+    build.build()
+
+
+def _batch(shapes, seed):
+    return [synth.panel_hwe(n_v, n_f, seed=seed, panel=k, p_missing=0.02, pad_seed=k)
+            for k, (n_v, n_f) in enumerate(shapes)]
+
+
+def _run_batched(genos_np, shapes, path=0, tune=False, group=0, order=0):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    genos = [to_device(g) for g in genos_np]
+    n_fs = [n_f for _, n_f in shapes]
+    tallies = [torch.full((max(ccc.ccc2_count(n_v), 1), 4), -7, dtype=torch.int32, device="cuda")
+               for n_v, _ in shapes]
+    cccs = [torch.full((max(ccc.ccc2_count(n_v), 1), 4), -7.0, dtype=torch.float32, device="cuda")
+            for n_v, _ in shapes]
+    opts = ccc.ccc_opts_default(path=path)
+    opts.group, opts.order = group, order
+    ws = torch.empty(ccc.ccc2_batched_workspace_size(genos, n_fs, opts), dtype=torch.uint8,
+                     device="cuda")
+    opts.workspace = ws.data_ptr()
+    opts.workspace_bytes = ws.numel()
+    if tune:
+        g, o = ccc.ccc2_batched_tune(genos, n_fs, tallies, cccs, opts)
+        assert g in (4, 8, 16) and o in (0, 1)
+    else:
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    return ([t[:ccc.ccc2_count(n_v)].cpu().numpy() for t, (n_v, _) in zip(tallies, shapes)],
+            [c[:ccc.ccc2_count(n_v)].cpu().numpy() for c, (n_v, _) in zip(cccs, shapes)])
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_small_panels_against_oracle(path):
+    shapes = [(130, 700), (1, 50), (2, 33), (65, 1000), (300, 129), (200, 4000)]
+    genos = _batch(shapes, seed=51)
+    ts, cs = _run_batched(genos, shapes, path=path)
+    for g, (n_v, n_f), t, c in zip(genos, shapes, ts, cs):
+        et, ec = oracle.ccc2_all(g, n_f)
+        assert_tally_equal(t, et, f"panel n_v={n_v} n_f={n_f}")
+        assert_ccc_close(c, ec, what=f"panel n_v={n_v} n_f={n_f}")
+
+
+def test_batched_equals_single_calls_many_panels():
+    rng = np.random.default_rng(3)
+    shapes = [(int(rng.integers(2, 700)), int(rng.integers(1, 3000))) for _ in range(70)]
+    genos = _batch(shapes, seed=52)
+    for group, order in ((0, 0), (4, 1), (16, 0)):
+        ts, cs = _run_batched(genos, shapes, group=group, order=order)
+        for g, (n_v, n_f), t, c in zip(genos[:12], shapes[:12], ts[:12], cs[:12]):
+            t1, c1 = run_2way(g, n_f, 0)
+            np.testing.assert_array_equal(t, t1)
+            np.testing.assert_array_equal(c, c1)
+        for g, (n_v, n_f), t in zip(genos[60:], shapes[60:], ts[60:]):  # second launch chunk
+            np.testing.assert_array_equal(t, run_2way(g, n_f, 0)[0])
+
+
+def test_autotune_then_correct():
+    shapes = [(500, 2000), (900, 3000), (260, 5000), (40, 100)]
+    genos = _batch(shapes, seed=53)
+    ts, cs = _run_batched(genos, shapes, tune=True)
+    for g, (n_v, n_f), t, c in zip(genos, shapes, ts, cs):
+        t1, c1 = run_2way(g, n_f, 0)
+        np.testing.assert_array_equal(t, t1)
+        np.testing.assert_array_equal(c, c1)
+
+
+def test_cuda_graph_capture_and_replay():
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    shapes = [(300, 1000), (700, 2500), (64, 128)]
+    genos_np = _batch(shapes, seed=54)
+    genos = [to_device(g) for g in genos_np]
+    n_fs = [n_f for _, n_f in shapes]
+    tallies = [torch.zeros((ccc.ccc2_count(n_v), 4), dtype=torch.int32, device="cuda")
+               for n_v, _ in shapes]
+    cccs = [torch.zeros((ccc.ccc2_count(n_v), 4), dtype=torch.float32, device="cuda")
+            for n_v, _ in shapes]
+    opts = ccc.ccc_opts_default()
+    ws = torch.empty(ccc.ccc2_batched_workspace_size(genos, n_fs, opts), dtype=torch.uint8,
+                     device="cuda")
+    opts = ccc.ccc_opts_default(workspace=ws)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts, stream=s)  # first call outside capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts, stream=s)
+    for t in tallies:
+        t.zero_()
+    for c in cccs:
+        c.zero_()
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    for g, (n_v, n_f), t, c in zip(genos_np, shapes, tallies, cccs):
+        et, ec = oracle.ccc2_all(g, n_f)
+        assert_tally_equal(t.cpu().numpy(), et, "graph replay")
+        assert_ccc_close(c.cpu().numpy(), ec, what="graph replay")
