@@ -183,6 +183,47 @@ int ccc2_filter(const ccc_panel *panel, float threshold, ccc_hit *hits, int64_t 
                 int64_t *n_hits, const ccc_opts *opts, void *stream);
 
 /*
+ * 2-way over a row range -- one "phase" in the sense of Sec. 8 item 3, where a
+ * run computes and stores only part of the results when all of them do not fit
+ * in memory at once: the pairs (i, j) with i_begin <= i < i_end and every
+ * j > i, with tallies and CCC values as ccc2_tally_metric computes them,
+ * stored at index ccc2_index(i, j, n_v) - ccc2_index(i_begin, i_begin + 1, n_v)
+ * (these rows are contiguous in the upper-triangle order).  tally, ccc:
+ * device [ccc2_rows_count(n_v, i_begin, i_end)][4].  Workspace: CCC_OP_2WAY.
+ * 0 <= i_begin <= i_end <= n_v.  Row ranges that start on a multiple of 64
+ * waste no tensor-core work.
+ */
+int ccc2_tally_metric_rows(const ccc_panel *panel, int64_t i_begin, int64_t i_end,
+                           int32_t *tally, float *ccc, const ccc_opts *opts, void *stream);
+
+/* Pairs of the rows [i_begin, i_end): sum of (n_v - 1 - i); -1 if out of range. */
+int64_t ccc2_rows_count(int64_t n_v, int64_t i_begin, int64_t i_end);
+
+/*
+ * Host helper: split the rows [0, n_v) into n_phases contiguous ranges,
+ * bounds[0] = 0 < ... <= bounds[n_phases] = n_v, with inner bounds on
+ * multiples of 64 and about equal pair counts.  bounds: host int64[n_phases + 1].
+ */
+int ccc2_phase_bounds(int64_t n_v, int n_phases, int64_t *bounds);
+
+/*
+ * Phased 2-way output to host memory.  Computes all pairs as
+ * ccc2_tally_metric does, phase by phase (ccc2_phase_bounds), into two
+ * staging buffers in the workspace, and copies each finished phase to the
+ * caller's host arrays while the next phase computes, so that device-to-host
+ * copies overlap the tensor-core work.  host_tally, host_ccc: host memory
+ * [npairs][4] (pinned, or the copies do not overlap; host_ccc may be NULL for
+ * tallies only).  Workspace: ccc2_stream_workspace_size().  The copies run on
+ * two internal streams created (with four events) by the first call on each
+ * device; the caller's stream is made to wait for them, so synchronising the
+ * caller's stream means every result is on the host.  n_phases >= 2.
+ */
+int ccc2_stream_workspace_size(const ccc_panel *panel, int n_phases, const ccc_opts *opts,
+                               size_t *bytes);
+int ccc2_stream(const ccc_panel *panel, int n_phases, int32_t *host_tally, float *host_ccc,
+                const ccc_opts *opts, void *stream);
+
+/*
  * Batched 2-way over independent panels (many SNP panels of uneven n_v and n_f,
  * as in a multi-study run): for every panel k, the tallies and CCC values that
  * ccc2_tally_metric would write to tally[k] and ccc[k].  On the tensor-core
@@ -213,7 +254,8 @@ int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tal
  * numerators).  For a fixed j the slab is computed as one GEMM-shaped product
  * of an operand masked elementwise by v_j with the panel, the role that the
  * matrices X_{j,xi} play in Sec. 3.2.  tally: device int32[S(j_end) -
- * S(j_begin)][8].  Needs the workspace.  0 <= j_begin <= j_end <= n_v.
+ * S(j_begin)][8].  Needs the workspace.  0 <= j_begin <= j_end <= n_v,
+ * n_v <= 65535.
  */
 int ccc3_tally(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
                const ccc_opts *opts, void *stream);

@@ -28,7 +28,8 @@ __all__ = [
     "ccc3_tally_metric", "ccc_status", "ccc2_index", "ccc3_index", "ccc2_count", "ccc3_count",
     "ccc_strerror", "ccc_launch_count", "ccc_timing_enable", "ccc_timing_read",
     "ccc2_tally_metric_noalloc", "ccc_hit", "ccc2_filter", "ccc2_batched_workspace_size",
-    "ccc2_batched", "ccc2_batched_tune",
+    "ccc2_batched", "ccc2_batched_tune", "ccc2_tally_metric_rows", "ccc2_rows_count",
+    "ccc2_phase_bounds", "ccc2_stream_workspace_size", "ccc2_stream",
 ]
 
 CCC_OK = 0
@@ -106,6 +107,17 @@ def load():
     lib.ccc2_batched_tune.argtypes = [P(ccc_panel), ctypes.c_int, P(vp), P(vp), P(ccc_opts), vp]
     for name in ("ccc2_batched_workspace_size", "ccc2_batched", "ccc2_batched_tune"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.ccc2_tally_metric_rows.argtypes = [P(ccc_panel), i64, i64, vp, vp, P(ccc_opts), vp]
+    lib.ccc2_tally_metric_rows.restype = ctypes.c_int
+    lib.ccc2_rows_count.argtypes = [i64, i64, i64]
+    lib.ccc2_rows_count.restype = i64
+    lib.ccc2_phase_bounds.argtypes = [i64, ctypes.c_int, P(i64)]
+    lib.ccc2_phase_bounds.restype = ctypes.c_int
+    lib.ccc2_stream_workspace_size.argtypes = [P(ccc_panel), ctypes.c_int, P(ccc_opts),
+                                               P(ctypes.c_size_t)]
+    lib.ccc2_stream_workspace_size.restype = ctypes.c_int
+    lib.ccc2_stream.argtypes = [P(ccc_panel), ctypes.c_int, vp, vp, P(ccc_opts), vp]
+    lib.ccc2_stream.restype = ctypes.c_int
     lib.ccc2_filter.argtypes = [P(ccc_panel), ctypes.c_float, vp, i64, vp, P(ccc_opts), vp]
     lib.ccc2_filter.restype = ctypes.c_int
     lib.ccc2_tally_metric_noalloc.argtypes = [P(ccc_panel), vp, vp, vp, P(ccc_opts), vp]
@@ -241,6 +253,44 @@ def ccc2_batched_tune(genos, n_fs, tallies, cccs, opts, stream=None):
                                                          _ptrs(tallies), _ptrs(cccs),
                                                          ctypes.byref(opts), _stream(stream)))
     return int(opts.group), int(opts.order)
+
+
+def ccc2_tally_metric_rows(geno, n_f, i_begin, i_end, tally, ccc, opts, stream=None):
+    """2-way over the rows [i_begin, i_end) (one phase)."""
+    p = _panel(geno, n_f)
+    _check("ccc2_tally_metric_rows",
+           load().ccc2_tally_metric_rows(ctypes.byref(p), int(i_begin), int(i_end), _ptr(tally),
+                                         _ptr(ccc), ctypes.byref(opts), _stream(stream)))
+
+
+def ccc2_rows_count(n_v, i_begin, i_end):
+    return int(load().ccc2_rows_count(int(n_v), int(i_begin), int(i_end)))
+
+
+def ccc2_phase_bounds(n_v, n_phases):
+    b = (ctypes.c_int64 * (n_phases + 1))()
+    _check("ccc2_phase_bounds", load().ccc2_phase_bounds(int(n_v), int(n_phases), b))
+    return [int(x) for x in b]
+
+
+def ccc2_stream_workspace_size(geno_or_shape, n_f, n_phases, opts):
+    if hasattr(geno_or_shape, "data_ptr"):
+        p = _panel(geno_or_shape, n_f)
+    else:
+        n_v, ld = geno_or_shape
+        p = ccc_panel(None, int(n_f), int(n_v), int(ld))
+    out = ctypes.c_size_t(0)
+    _check("ccc2_stream_workspace_size",
+           load().ccc2_stream_workspace_size(ctypes.byref(p), int(n_phases), ctypes.byref(opts),
+                                             ctypes.byref(out)))
+    return int(out.value)
+
+
+def ccc2_stream(geno, n_f, n_phases, host_tally, host_ccc, opts, stream=None):
+    """Phased 2-way output into host tensors (pinned for overlap)."""
+    p = _panel(geno, n_f)
+    _check("ccc2_stream", load().ccc2_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally),
+                                             _ptr(host_ccc), ctypes.byref(opts), _stream(stream)))
 
 
 def ccc2_filter(geno, n_f, threshold, hits, cap, n_hits, opts, stream=None):

@@ -193,6 +193,25 @@ int64_t slab_offset(int64_t j, int64_t n_v) {
   return s1 * (n_v - 1) - s2;
 }
 
+int64_t rows_count(int64_t n_v, int64_t i_begin, int64_t i_end) {
+  return pair_index(i_end, i_end + 1, n_v) - pair_index(i_begin, i_begin + 1, n_v);
+}
+
+// Balanced phase bounds on multiples of 64 rows.
+static void phase_bounds(int64_t n_v, int n_phases, int64_t *bounds) {
+  const int64_t total = rows_count(n_v, 0, n_v);
+  bounds[0] = 0;
+  int64_t r = 0;
+  for (int p = 1; p < n_phases; ++p) {
+    const double target = static_cast<double>(total) * p / n_phases;
+    while (r < n_v && static_cast<double>(rows_count(n_v, 0, r)) < target) r += 64;
+    if (r > n_v) r = n_v;
+    if (r < bounds[p - 1]) r = bounds[p - 1];
+    bounds[p] = r;
+  }
+  bounds[n_phases] = n_v;
+}
+
 // Thresholded output of a 2-way call (ccc2_filter); null for plain output.
 struct FilterSpec {
   ccc_hit *hits;
@@ -203,7 +222,8 @@ struct FilterSpec {
 
 // The 2-way sequence: counts (+ factors), operand preparation, tally kernel.
 static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const ccc_opts *o,
-                    cudaStream_t s, const FilterSpec *filter = nullptr) {
+                    cudaStream_t s, const FilterSpec *filter = nullptr, int64_t i_begin = 0,
+                    int64_t i_end = -1) {
   CCC_TRY(check_panel(p));
   CCC_TRY(check_opts(o));
   if (filter == nullptr) {
@@ -230,6 +250,11 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
     CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   Tally2Args a;
   a.group = o->group;
+  if (i_end >= 0) {
+    a.i_begin = i_begin;
+    a.i_end = i_end;
+    a.pair0 = pair_index(i_begin, i_begin + 1, p->n_v);
+  }
   if (filter != nullptr) {
     a.hits = filter->cap > 0 ? filter->hits : reinterpret_cast<ccc_hit *>(filter->n_hits);
     a.n_hits = reinterpret_cast<unsigned long long *>(filter->n_hits);
@@ -475,6 +500,173 @@ int ccc2_tally_metric(const ccc_panel *panel, int32_t *tally, float *out_ccc, co
                       void *stream) {
   if (out_ccc == nullptr) return CCC_EINVAL;
   return run_2way(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_tally_metric_rows(const ccc_panel *panel, int64_t i_begin, int64_t i_end,
+                           int32_t *tally, float *out_ccc, const ccc_opts *opts, void *stream) {
+  if (panel == nullptr || i_begin < 0 || i_end < i_begin || i_end > panel->n_v) return CCC_EINVAL;
+  if (out_ccc == nullptr) return CCC_EINVAL;
+  if (i_begin == i_end || rows_count(panel->n_v, i_begin, i_end) == 0) {
+    CCC_TRY(check_panel(panel));
+    CCC_TRY(check_opts(opts));
+    return CCC_OK;
+  }
+  return run_2way(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream), nullptr, i_begin,
+                  i_end);
+}
+
+int64_t ccc2_rows_count(int64_t n_v, int64_t i_begin, int64_t i_end) {
+  if (n_v < 1 || i_begin < 0 || i_end < i_begin || i_end > n_v) return -1;
+  return rows_count(n_v, i_begin, i_end);
+}
+
+int ccc2_phase_bounds(int64_t n_v, int n_phases, int64_t *bounds) {
+  if (bounds == nullptr || n_v < 1 || n_phases < 1 || n_phases > 1 << 20) return CCC_EINVAL;
+  phase_bounds(n_v, n_phases, bounds);
+  return CCC_OK;
+}
+
+namespace {
+
+// Internal copy streams and events of ccc2_stream, one set per device.
+struct StreamRes {
+  bool ready = false;
+  cudaStream_t copy[2] = {};
+  cudaEvent_t computed[2] = {}, copied[2][2] = {};
+};
+StreamRes g_stream_res[64];
+
+int stream_res(int dev, StreamRes **out) {
+  StreamRes &r = g_stream_res[dev];
+  if (!r.ready) {
+    for (int k = 0; k < 2; ++k) {
+      if (cudaStreamCreateWithFlags(&r.copy[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.computed[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.copied[k][0], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.copied[k][1], cudaEventDisableTiming) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    r.ready = true;
+  }
+  *out = &r;
+  return CCC_OK;
+}
+
+// Largest phase of a split, in pairs.
+int64_t max_phase_pairs(int64_t n_v, int n_phases) {
+  int64_t b[1025];
+  if (n_phases > 1024) return -1;
+  phase_bounds(n_v, n_phases, b);
+  int64_t m = 0;
+  for (int k = 0; k < n_phases; ++k) {
+    const int64_t c = rows_count(n_v, b[k], b[k + 1]);
+    if (c > m) m = c;
+  }
+  return m;
+}
+
+}  // namespace
+
+int ccc2_stream_workspace_size(const ccc_panel *panel, int n_phases, const ccc_opts *opts,
+                               size_t *bytes) {
+  if (bytes == nullptr || panel == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
+  size_t base = 0;
+  CCC_TRY(ccc_workspace_size(panel, opts, CCC_OP_2WAY, &base));
+  const int64_t m = max_phase_pairs(panel->n_v, n_phases);
+  *bytes = align_up(base, 1024) + 2 * align_up(static_cast<size_t>(m) * 32, 1024);
+  return CCC_OK;
+}
+
+int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *host_ccc,
+                const ccc_opts *o, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CCC_TRY(check_panel(p));
+  CCC_TRY(check_opts(o));
+  if (host_tally == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
+  size_t need = 0;
+  CCC_TRY(ccc2_stream_workspace_size(p, n_phases, o, &need));
+  if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
+  if (o->workspace_bytes < need) return CCC_ENOSPACE;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return CCC_ECUDA;
+  StreamRes *R = nullptr;
+  CCC_TRY(stream_res(d, &R));
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY);
+  CCC_TRY(clear_status(o, L, s));
+  if (p->n_v < 2) return CCC_OK;
+  const bool want_ccc = host_ccc != nullptr;
+  const int64_t slot_pairs = max_phase_pairs(p->n_v, n_phases);
+  const size_t slot_bytes = align_up(static_cast<size_t>(slot_pairs) * 32, 1024);
+  const size_t slot0 = align_up(L.total, 1024);
+  // Preparation once for all phases.
+  float *w = at<float>(o, L.w);
+  if (want_ccc && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
+  uint8_t *op = nullptr;
+  uint64_t *planes = nullptr;
+  if (o->path == CCC_PATH_TC) {
+    op = at<uint8_t>(o, L.op);
+    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+  } else {
+    planes = at<uint64_t>(o, L.planes);
+    CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
+  }
+  int64_t bounds[1025];
+  phase_bounds(p->n_v, n_phases, bounds);
+  for (int ph = 0; ph < n_phases; ++ph) {
+    const int64_t i0 = bounds[ph], i1 = bounds[ph + 1];
+    const int64_t cnt = rows_count(p->n_v, i0, i1);
+    if (cnt == 0) continue;
+    const int k = ph & 1;
+    int32_t *st = at<int32_t>(o, slot0 + k * slot_bytes);
+    float *sc = reinterpret_cast<float *>(st + 4 * slot_pairs);
+    if (ph >= 2) {  // the slot's previous copies must have finished
+      if (cudaStreamWaitEvent(s, R->copied[k][0], 0) != cudaSuccess ||
+          cudaStreamWaitEvent(s, R->copied[k][1], 0) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    Tally2Args a;
+    a.n_v = p->n_v;
+    a.n_f = p->n_f;
+    a.w = w;
+    a.tally = st;
+    a.ccc = want_ccc ? sc : nullptr;
+    a.status = at<int32_t>(o, L.status);
+    a.gamma = static_cast<float>(o->gamma);
+    a.norm = o->norm;
+    a.group = o->group;
+    a.i_begin = i0;
+    a.i_end = i1;
+    a.pair0 = pair_index(i0, i0 + 1, p->n_v);
+    const int slot = timing_begin(s);
+    const int rc = o->path == CCC_PATH_TC ? launch_tally2_tc(a, op, L.rows_pad, L.kpad, dev.sms, s)
+                                          : launch_tally2_popc(a, planes, L.w64, s);
+    timing_end(slot, s);
+    if (rc != CCC_OK) return rc;
+    if (cudaEventRecord(R->computed[k], s) != cudaSuccess) return CCC_ECUDA;
+    // Tallies on one copy stream, CCC values on the other.
+    if (cudaStreamWaitEvent(R->copy[0], R->computed[k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_tally + 4 * a.pair0, st, static_cast<size_t>(cnt) * 16,
+                        cudaMemcpyDeviceToHost, R->copy[0]) != cudaSuccess ||
+        cudaEventRecord(R->copied[k][0], R->copy[0]) != cudaSuccess)
+      return CCC_ECUDA;
+    if (want_ccc) {
+      if (cudaStreamWaitEvent(R->copy[1], R->computed[k], 0) != cudaSuccess ||
+          cudaMemcpyAsync(host_ccc + 4 * a.pair0, sc, static_cast<size_t>(cnt) * 16,
+                          cudaMemcpyDeviceToHost, R->copy[1]) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    if (cudaEventRecord(R->copied[k][1], R->copy[1]) != cudaSuccess) return CCC_ECUDA;
+  }
+  for (int k = 0; k < 2; ++k)
+    if (cudaEventRecord(R->copied[k][0], R->copy[0]) != cudaSuccess ||
+        cudaEventRecord(R->copied[k][1], R->copy[1]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, R->copied[k][0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s, R->copied[k][1], 0) != cudaSuccess)
+      return CCC_ECUDA;
+  return CCC_OK;
 }
 
 int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc_opts *opts,

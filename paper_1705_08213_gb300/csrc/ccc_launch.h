@@ -40,6 +40,11 @@ struct Tally2Args {
   float threshold = 0.f;
   // Column blocks per L2 group of the tensor-core tile order (0 = default 8).
   int32_t group = 0;
+  // Row range of a phase: only pairs with i_begin <= i < i_end are computed and
+  // pair (i, j) is stored at index pair_index(i, j) - pair0.
+  int64_t i_begin = 0;
+  int64_t i_end = int64_t(1) << 62;
+  int64_t pair0 = 0;
 };
 
 // Panels per batched tensor-core launch (kernel parameter space).

@@ -65,11 +65,11 @@ __device__ __forceinline__ void load_stage(const uint64_t *__restrict__ planes, 
 
 __global__ void __launch_bounds__(THREADS)
     k_tally2_popc(const uint64_t *__restrict__ planes, int64_t w64, const Tally2Args args,
-                  int64_t nB) {
+                  int64_t nB, int64_t t0) {
   __shared__ uint64_t sI[3][KC][LDS];
   __shared__ uint64_t sJ[3][KC][LDS];
   int64_t I, J;
-  tile_coords(blockIdx.x, nB, I, J);
+  tile_coords(t0 + blockIdx.x, nB, I, J);
   const int64_t n_v = args.n_v;
   const int tx = threadIdx.x & 15;
   const int ty = threadIdx.x >> 4;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     const int64_t i = I * TS + ty + 16 * x;
-    if (i >= n_v) continue;
+    if (i >= n_v || i < args.i_begin || i >= args.i_end) continue;
     const bool filter = args.hits != nullptr;
     const bool want_ccc = filter || args.ccc != nullptr;
     float wi0 = 1.f, wi1 = 1.f;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(THREADS)
       wi0 = __ldg(args.w + 2 * i);
       wi1 = __ldg(args.w + 2 * i + 1);
     }
-    const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1;
+    const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1 - args.pair0;
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       const int64_t j = J * TS + tx + 16 * y;
@@ -186,9 +186,15 @@ __global__ void k_metric2(const int32_t *__restrict__ tally, const float *__rest
 
 int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s) {
   const int64_t nB = (a.n_v + TS - 1) / TS;
-  const int64_t tiles = nB * (nB + 1) / 2;
+  // Row blocks [B0, B1) of the phase; tiles before row B are B nB - B (B - 1) / 2.
+  const int64_t B0 = (a.i_begin > 0 ? a.i_begin : 0) / TS;
+  const int64_t B1 = a.i_end < a.n_v ? (a.i_end + TS - 1) / TS : nB;
+  auto start = [&](int64_t r) { return r * nB - r * (r - 1) / 2; };
+  const int64_t t0 = start(B0);
+  const int64_t tiles = start(B1) - t0;
+  if (tiles <= 0) return CCC_OK;
   if (tiles > 0x7fffffffLL) return CCC_ERANGE;
-  k_tally2_popc<<<static_cast<unsigned>(tiles), THREADS, 0, s>>>(planes, w64, a, nB);
+  k_tally2_popc<<<static_cast<unsigned>(tiles), THREADS, 0, s>>>(planes, w64, a, nB, t0);
   return note_launch();
 }
 

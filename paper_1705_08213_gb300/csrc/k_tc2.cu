@@ -34,8 +34,9 @@ constexpr int SNP_J = BN / 2;
 struct TriSched {
   struct Params {
     int nI, nJ, group;
+    int I0, I1;  // row blocks [I0, I1) (a phase); 0, nI for the whole triangle
   };
-  int nI, nJ, nG, G;
+  int nI, nJ, nG, G, I0;
   int g, I, J, col_end, row_end;
   bool valid;
 
@@ -43,16 +44,28 @@ struct TriSched {
     col_end = min((g + 1) * G, nJ);
     row_end = min(nI, 2 * col_end);
   }
+  // From group g on, the first group holding a row >= I0; rows start at I0.
+  __device__ void enter_group() {
+    while (g < nG) {
+      set_group();
+      if (I0 < row_end) {
+        I = I0;
+        J = max(g * G, I >> 1);
+        return;
+      }
+      ++g;
+    }
+    valid = false;
+  }
   __device__ void init(const Params &p, int64_t start) {
-    nI = p.nI;
+    nI = min(p.nI, p.I1);
     nJ = p.nJ;
     G = p.group;
+    I0 = p.I0;
     nG = (nJ + G - 1) / G;
-    valid = nI > 0 && nJ > 0;
-    g = 0;
-    I = 0;
-    if (valid) set_group();
-    J = 0;
+    valid = nI > I0 && nJ > 0;
+    g = (I0 >> 1) / G;
+    if (valid) enter_group();
     advance(start);
   }
   __device__ void advance(int64_t step) {
@@ -64,14 +77,11 @@ struct TriSched {
       }
       step -= rem + 1;
       if (++I >= row_end) {
-        if (++g >= nG) {
-          valid = false;
-          return;
-        }
-        set_group();
-        I = 0;
+        ++g;
+        enter_group();
+      } else {
+        J = max(g * G, I >> 1);
       }
-      J = max(g * G, I >> 1);
     }
   }
   __device__ int map_index() const { return 0; }
@@ -132,8 +142,8 @@ struct Epi2 {
           r11 = __float2int_rn(o1);
         }
         const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + 2 * p + a;
-        if (i < j && j < n_v) {
-          const int64_t pidx = row_base + j;
+        if (i < j && j < n_v && i >= args.i_begin && i < args.i_end) {
+          const int64_t pidx = row_base + j - args.pair0;
           if (!filter) reinterpret_cast<int4 *>(args.tally)[pidx] = make_int4(r00, r01, r10, r11);
           if (want_ccc) {
             float wj0 = 1.f, wj1 = 1.f;
@@ -234,10 +244,11 @@ struct EpiBatch {
   }
 };
 
-__global__ void __launch_bounds__(64 + 32 * 8, 1)
+template <int EW>
+__global__ void __launch_bounds__(64 + 32 * EW, 1)
     k_tally2_tc_batched(const __grid_constant__ BatchMaps maps,
                         const __grid_constant__ BatchParams bp) {
-  persistent_gemm<BatchSched, EpiBatch, 8>(maps.a, maps.b, bp, bp, 0, bp.p[0].args.status);
+  persistent_gemm<BatchSched, EpiBatch, EW>(maps.a, maps.b, bp, bp, 0, bp.p[0].args.status);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -253,11 +264,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-int64_t tc2_num_tiles(int64_t n_v) {
+int64_t tc2_num_tiles(int64_t n_v, int64_t I0 = 0, int64_t I1 = int64_t(1) << 40) {
   const int64_t nI = (n_v + SNP_I - 1) / SNP_I;
   const int64_t nJ = (n_v + SNP_J - 1) / SNP_J;
   int64_t t = 0;
-  for (int64_t I = 0; I < nI; ++I) t += nJ - (I >> 1);
+  for (int64_t I = I0; I < nI && I < I1; ++I) t += nJ - (I >> 1);
   return t;
 }
 
@@ -286,7 +297,9 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
   static bool attr_set = false;
   if (n < 1 || n > kMaxBatchPanels) return CCC_EINVAL;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_tally2_tc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tally2_tc_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(SMEM_BYTES)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES)) != cudaSuccess)
       return CCC_ECUDA;
     attr_set = true;
@@ -302,6 +315,8 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
     q.tri.nI = static_cast<int>((args[k].n_v + SNP_I - 1) / SNP_I);
     q.tri.nJ = static_cast<int>((args[k].n_v + SNP_J - 1) / SNP_J);
     q.tri.group = group > 0 ? group : 8;
+    q.tri.I0 = 0;
+    q.tri.I1 = q.tri.nI;
     q.nkb = static_cast<int>(kpad[k] / BK);
     q.tiles = args[k].n_v >= 2 ? tc2_num_tiles(args[k].n_v) : 0;
     tiles += q.tiles;
@@ -310,8 +325,15 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
       return CCC_ECUDA;
   }
   if (tiles == 0) return CCC_OK;
+  // Epilogue warps from the work-weighted K length of the batch.
+  double kw = 0.0;
+  for (int k = 0; k < n; ++k) kw += static_cast<double>(bp.p[k].tiles) * bp.p[k].nkb;
+  const int mean_nkb = static_cast<int>(kw / static_cast<double>(tiles));
   const int grid = static_cast<int>(tiles < num_sms ? tiles : num_sms);
-  k_tally2_tc_batched<<<grid, 64 + 32 * 8, SMEM_BYTES, s>>>(maps, bp);
+  if (epilogue_warps(mean_nkb) == 4)
+    k_tally2_tc_batched<4><<<grid, 64 + 32 * 4, SMEM_BYTES, s>>>(maps, bp);
+  else
+    k_tally2_tc_batched<8><<<grid, 64 + 32 * 8, SMEM_BYTES, s>>>(maps, bp);
   return note_launch();
 }
 
@@ -334,8 +356,11 @@ int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, i
   sp.nI = static_cast<int>((a.n_v + SNP_I - 1) / SNP_I);
   sp.nJ = static_cast<int>((a.n_v + SNP_J - 1) / SNP_J);
   sp.group = a.group > 0 ? a.group : 8;
+  sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / SNP_I);
+  sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + SNP_I - 1) / SNP_I : sp.nI);
   const int nkb = static_cast<int>(kpad / BK);
-  const int64_t tiles = tc2_num_tiles(a.n_v);
+  const int64_t tiles = tc2_num_tiles(a.n_v, sp.I0, sp.I1);
+  if (tiles == 0) return CCC_OK;
   const int grid = static_cast<int>(tiles < num_sms ? tiles : num_sms);
   if (epilogue_warps(nkb) == 4)
     k_tally2_tc<4><<<grid, 64 + 32 * 4, SMEM_BYTES, s>>>(tmA, tmB, a, sp, nkb);

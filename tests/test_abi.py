@@ -133,3 +133,21 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(ccc, "lib_path", str(tmp_path / "nope.so"))
     with pytest.raises(ccc.CCCError):
         ccc.load()
+
+
+def test_phase_bounds_and_row_counts(lib):
+    for n_v in (1, 2, 63, 64, 65, 300, 20000, 200000):
+        total = ccc.ccc2_count(n_v)
+        assert ccc.ccc2_rows_count(n_v, 0, n_v) == total
+        for n_ph in (1, 2, 3, 7, 64):
+            b = ccc.ccc2_phase_bounds(n_v, n_ph)
+            assert b[0] == 0 and b[-1] == n_v and all(x <= y for x, y in zip(b, b[1:]))
+            assert all(x % 64 == 0 or x == n_v for x in b[1:-1])
+            counts = [ccc.ccc2_rows_count(n_v, x, y) for x, y in zip(b, b[1:])]
+            assert sum(counts) == total
+            if n_v >= 20000:  # balanced to within one 64-row band
+                assert max(counts) - min(counts) <= 2 * 64 * n_v
+    assert ccc.ccc2_rows_count(10, 3, 2) == -1
+    o = ccc.ccc_opts_default()
+    a = ccc.ccc2_stream_workspace_size((20000, 512), 16384, 8, o)
+    assert a > ccc.ccc_workspace_size((20000, 512), 16384, o, ccc.CCC_OP_2WAY)
