@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--n-v", type=int, default=None)
     ap.add_argument("--n-f", type=int, default=None)
     ap.add_argument("--path", default="tc", choices=["tc", "popc"])
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 1, 2],
+                    help="2-way tensor-core tiles: 0 automatic, 1 one SM, 2 SM pairs")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--skip-e2e", action="store_true", help="no host-buffer end-to-end timing")
     ap.add_argument("--skip-popc", action="store_true", help="no popcount-path comparison")
@@ -304,16 +306,17 @@ def run_reference(args, w):
 class Runner:
     """Device buffers and one step of the chosen workload through the C ABI."""
 
-    def __init__(self, ccc, torch, dev, w, path, geno_np):
+    def __init__(self, ccc, torch, dev, w, path, geno_np, tile=0):
         self.ccc, self.torch, self.dev, self.w, self.path = ccc, torch, dev, w, path
+        self.tile = tile
         n_v, n_f = w["n_v"], w["n_f"]
         self.host_geno = torch.from_numpy(geno_np.view(np.int64)).pin_memory()
         self.geno = self.host_geno.to(dev)
         op = ccc.CCC_OP_2WAY if w["kind"] == 2 else ccc.CCC_OP_3WAY
-        o0 = ccc.ccc_opts_default(path=path)
+        o0 = ccc.ccc_opts_default(path=path, tile=tile)
         self.ws = torch.empty(ccc.ccc_workspace_size(self.geno, n_f, o0, op), dtype=torch.uint8,
                               device=dev)
-        self.opts = ccc.ccc_opts_default(path=path, workspace=self.ws)
+        self.opts = ccc.ccc_opts_default(path=path, workspace=self.ws, tile=tile)
         self.filter = "threshold" in w
         if self.filter:
             self.cap = 1 << 20
@@ -355,11 +358,12 @@ class Runner:
                     torch.empty(self.out.shape, dtype=torch.float32, pin_memory=True)]
             dev = []
             del self.tally, self.out, self.ws
-            o0 = ccc.ccc_opts_default(path=self.path)
+            o0 = ccc.ccc_opts_default(path=self.path, tile=self.tile)
             self.ws_stream = torch.empty(
                 ccc.ccc2_stream_workspace_size(self.geno, w["n_f"], phases, o0), dtype=torch.uint8,
                 device=self.dev)
-            self.opts = ccc.ccc_opts_default(path=self.path, workspace=self.ws_stream)
+            self.opts = ccc.ccc_opts_default(path=self.path, workspace=self.ws_stream,
+                                             tile=self.tile)
         else:
             host = [torch.empty(self.tally.shape, dtype=torch.int32, pin_memory=True),
                     torch.empty(self.out.shape, dtype=torch.float32, pin_memory=True)]
@@ -525,7 +529,7 @@ def main():
     path = ccc.CCC_PATH_TC if args.path == "tc" else ccc.CCC_PATH_POPC
     cmp_per_step = comparisons(w)
     geno_np = make_panel(w, rank)
-    run = Runner(ccc, torch, dev, w, path, geno_np)
+    run = Runner(ccc, torch, dev, w, path, geno_np, tile=args.tile)
     stream = torch.cuda.current_stream(dev)
 
     sampler = ClockSampler(gpu_id_for(torch, dev)) if local == 0 else None
@@ -600,6 +604,7 @@ def main():
         "dtype": "e4m3 operands, fp32 accumulate" if path == ccc.CCC_PATH_TC else "u64 bit planes",
         "data": "synthetic",
         "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"], "path": args.path,
+                   "tile": {0: "automatic", 1: "128x256 on one SM", 2: "256x256 on an SM pair"}[args.tile],
                    "parallelism": (f"{world} independent panels (one per GPU)" if world > 1
                                    else "1 GPU"),
                    "l2": ("inputs larger than L2 (operand matrix and outputs exceed the 129 MB L2)"

@@ -111,6 +111,9 @@ typedef struct ccc_opts {
   size_t workspace_bytes; /* its size; must be >= ccc_workspace_size() */
   int32_t group;          /* tensor-core tile order: column blocks per L2 group; 0 = 8 */
   int32_t order;          /* ccc2_batched panel order: 0 = most tile work first, 1 = as given */
+  int32_t tile;           /* 2-way tensor-core tiles: 1 = 128 x 256 on one SM, 2 = 256 x 256
+                             on a pair of SMs (cta_group::2), 0 = automatic (pairs) */
+  int32_t reserved;       /* zero */
 } ccc_opts;
 
 /* Operations, for ccc_workspace_size(). */

@@ -73,7 +73,8 @@ class ccc_hit(ctypes.Structure):
 class ccc_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("norm", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("group", ctypes.c_int32), ("order", ctypes.c_int32)]
+                ("group", ctypes.c_int32), ("order", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -177,12 +178,13 @@ def _panel(geno, n_f):
     return ccc_panel(geno.data_ptr(), int(n_f), int(geno.shape[0]), int(geno.shape[1]))
 
 
-def ccc_opts_default(path=CCC_PATH_TC, norm=CCC_NORM_PERSNP, gamma=None, workspace=None):
+def ccc_opts_default(path=CCC_PATH_TC, norm=CCC_NORM_PERSNP, gamma=None, workspace=None, tile=0):
     """A ccc_opts filled by the library's defaults, then by the given fields."""
     o = ccc_opts()
     load().ccc_opts_default(ctypes.byref(o))
     o.path = int(path)
     o.norm = int(norm)
+    o.tile = int(tile)
     if gamma is not None:
         o.gamma = float(gamma)
     if workspace is not None:

@@ -56,6 +56,9 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
                              const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                              int num_sms, cudaStream_t s);
 
+// 256 x 256 tiles on SM pairs (cta_group::2); same arguments as launch_tally2_tc.
+int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
+                          int num_sms, cudaStream_t s);
 // Tensor-core 2-way tallies over the e4m3 operand matrix op[rows_pad][kpad].
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      int num_sms, cudaStream_t s);

@@ -17,6 +17,7 @@
 #include "ccc_launch.h"
 #include "ccc_metric.cuh"
 #include "tc_pipeline.cuh"
+#include "tc_pipeline_pair.cuh"
 
 #include <string.h>
 
@@ -35,14 +36,15 @@ struct TriSched {
   struct Params {
     int nI, nJ, group;
     int I0, I1;  // row blocks [I0, I1) (a phase); 0, nI for the whole triangle
+    int shift;   // row block I needs column blocks J >= I >> shift (1: 64/128-SNP, 0: square)
   };
-  int nI, nJ, nG, G, I0;
+  int nI, nJ, nG, G, I0, sh;
   int g, I, J, col_end, row_end;
   bool valid;
 
   __device__ void set_group() {
     col_end = min((g + 1) * G, nJ);
-    row_end = min(nI, 2 * col_end);
+    row_end = min(nI, col_end << sh);
   }
   // From group g on, the first group holding a row >= I0; rows start at I0.
   __device__ void enter_group() {
@@ -50,7 +52,7 @@ struct TriSched {
       set_group();
       if (I0 < row_end) {
         I = I0;
-        J = max(g * G, I >> 1);
+        J = max(g * G, I >> sh);
         return;
       }
       ++g;
@@ -62,9 +64,10 @@ struct TriSched {
     nJ = p.nJ;
     G = p.group;
     I0 = p.I0;
+    sh = p.shift;
     nG = (nJ + G - 1) / G;
     valid = nI > I0 && nJ > 0;
-    g = (I0 >> 1) / G;
+    g = (I0 >> sh) / G;
     if (valid) enter_group();
     advance(start);
   }
@@ -80,7 +83,7 @@ struct TriSched {
         ++g;
         enter_group();
       } else {
-        J = max(g * G, I >> 1);
+        J = max(g * G, I >> sh);
       }
     }
   }
@@ -90,12 +93,26 @@ struct TriSched {
   __device__ int b_row() const { return J * BN; }
 };
 
+// Row / column block of a tile as the 2-way epilogue sees it: I in 64-SNP
+// units (A rows 128 I ..), J in 128-SNP units (B rows 256 J ..).
+struct Tile2 {
+  int I, J;
+};
+
 struct Epi2 {
   using Params = Tally2Args;
 
-  // Accumulator lane = A row (2i + a) of the tile, column = 2j + b.
   template <int NC>
   __device__ static void tile(const Params &args, const TriSched &sc, int quarter, int lane,
+                              uint32_t t_base, uint32_t release_bar, int c0) {
+    body<NC, false>(args, Tile2{sc.I, sc.J}, quarter, lane, t_base, release_bar, c0);
+  }
+
+  // Accumulator lane = A row (2i + a) of the tile, column = 2j + b.  The
+  // release arrive goes to a CTA-local barrier, or (CLUSTER) to a barrier given
+  // by its cluster address.
+  template <int NC, bool CLUSTER>
+  __device__ static void body(const Params &args, Tile2 sc, int quarter, int lane,
                               uint32_t t_base, uint32_t release_bar, int c0) {
     const int row = quarter * 32 + lane;
     const int il = row >> 1;
@@ -116,7 +133,10 @@ struct Epi2 {
       tmem_ld_wait();
       if (c == c0 + NC - 1) {
         tc_fence_before();
-        mbar_arrive(release_bar);
+        if (CLUSTER)
+          mbar_arrive_cluster(release_bar);
+        else
+          mbar_arrive(release_bar);
       }
 #pragma unroll
       for (int p = 0; p < 8; ++p) {
@@ -171,6 +191,30 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1)
     k_tally2_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const Tally2Args args, TriSched::Params sp, int nkb) {
   persistent_gemm<TriSched, Epi2, EW>(&tmA, &tmB, sp, args, nkb, args.status);
+}
+
+// ---------------------------------------------------------------- SM pairs
+
+// 256 x 256 tiles (128 SNPs i x 128 SNPs j) on pairs of SMs.
+struct TriSchedPair : TriSched {
+  __device__ int a_row() const { return I * 256; }
+  __device__ int b_row() const { return J * 256; }
+};
+
+struct Epi2Pair {
+  using Params = Tally2Args;
+  template <int NC>
+  __device__ static void tile(const Params &args, int I64, int J, int quarter, int lane,
+                              uint32_t t_base, uint32_t release_cluster_bar, int c0) {
+    Epi2::body<NC, true>(args, Tile2{I64, J}, quarter, lane, t_base, release_cluster_bar, c0);
+  }
+};
+
+template <int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
+    k_tally2_tc_pair(const __grid_constant__ CUtensorMap tm, const Tally2Args args,
+                     TriSched::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<TriSchedPair, Epi2Pair, EW>(&tm, sp, args, nkb, args.status);
 }
 
 // ---------------------------------------------------------------- batched panels
@@ -315,6 +359,7 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
     q.tri.nI = static_cast<int>((args[k].n_v + SNP_I - 1) / SNP_I);
     q.tri.nJ = static_cast<int>((args[k].n_v + SNP_J - 1) / SNP_J);
     q.tri.group = group > 0 ? group : 8;
+    q.tri.shift = 1;
     q.tri.I0 = 0;
     q.tri.I1 = q.tri.nI;
     q.nkb = static_cast<int>(kpad[k] / BK);
@@ -337,6 +382,69 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
   return note_launch();
 }
 
+// Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
+int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1) {
+  const int64_t nB = (n_v + 127) / 128;
+  int64_t t = 0;
+  for (int64_t I = I0; I < nB && I < I1; ++I) t += nB - I;
+  return t;
+}
+
+int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
+                          int num_sms, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_tally2_tc_pair<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_pair<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+      return CCC_ECUDA;
+    attr_set = true;
+  }
+  CUtensorMap tm;
+  if (!make_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
+  TriSched::Params sp;
+  sp.nI = static_cast<int>((a.n_v + 127) / 128);
+  sp.nJ = sp.nI;
+  sp.group = a.group > 0 ? a.group : 8;
+  sp.shift = 0;
+  sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / 128);
+  sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.nI);
+  const int nkb = static_cast<int>(kpad / BK);
+  const int64_t tiles = tc2_pair_tiles(a.n_v, sp.I0, sp.I1);
+  if (tiles == 0) return CCC_OK;
+  const int ew = epilogue_warps(nkb);
+  // Persistent grid: as many SM pairs as can be resident at once.
+  static int max_clusters[2] = {0, 0};
+  int &mc = max_clusters[ew == 4 ? 0 : 1];
+  if (mc == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(static_cast<unsigned>(64 + 32 * ew), 1, 1);
+    cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e =
+        ew == 4 ? cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair<4>, &cfg)
+                : cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair<8>, &cfg);
+    if (e != cudaSuccess || n < 1) return CCC_ECUDA;
+    mc = n < num_sms / 2 ? n : num_sms / 2;
+  }
+  const int64_t clusters = tiles < mc ? tiles : mc;
+  const int grid = static_cast<int>(2 * clusters);
+  if (ew == 4)
+    k_tally2_tc_pair<4><<<grid, 64 + 32 * 4, tcp::SMEM_BYTES, s>>>(tm, a, sp, nkb);
+  else
+    k_tally2_tc_pair<8><<<grid, 64 + 32 * 8, tcp::SMEM_BYTES, s>>>(tm, a, sp, nkb);
+  return note_launch();
+}
+
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      int num_sms, cudaStream_t s) {
   static bool attr_set = false;
@@ -356,6 +464,7 @@ int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, i
   sp.nI = static_cast<int>((a.n_v + SNP_I - 1) / SNP_I);
   sp.nJ = static_cast<int>((a.n_v + SNP_J - 1) / SNP_J);
   sp.group = a.group > 0 ? a.group : 8;
+  sp.shift = 1;
   sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / SNP_I);
   sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + SNP_I - 1) / SNP_I : sp.nI);
   const int nkb = static_cast<int>(kpad / BK);
