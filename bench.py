@@ -103,7 +103,13 @@ def parse():
     ap.add_argument("--skip-popc", action="store_true", help="no popcount-path comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--source-hash", action="store_true",
+                    help="print the hash of the CUDA sources (for profiles/ncu_traffic.json) and exit")
     a = ap.parse_args()
+    if a.source_hash:
+        for k in KERNEL_SOURCES:
+            print(k, source_hash(k))
+        raise SystemExit(0)
     w = dict(WORKLOADS[a.workload])
     if a.n_v is not None:
         w["n_v"] = a.n_v
@@ -142,6 +148,39 @@ def comparisons(w):
     if w["kind"] == 2:
         return n_v * (n_v - 1) // 2 * n_f
     return n_v * (n_v - 1) * (n_v - 2) // 6 * n_f
+
+
+# Device-code files of each tally kernel: a traffic figure stays valid while they are unchanged.
+KERNEL_SOURCES = {
+    "k_tally2_tc_pair": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "ccc_dev.cuh",
+                         "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally3_tc": ["k_tc3.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+}
+
+
+def source_hash(kernel="k_tally2_tc_pair"):
+    """SHA-256 of the device-code files of a tally kernel, identifying what an ncu capture measured."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES.get(kernel, []):
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_1705_08213_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from profiles/ncu_traffic.json, or None
+    when that capture was taken on different CUDA sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f).get(f"{kernel}@{workload}")
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != source_hash(kernel):
+        return None
+    return float(rec["dram_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -578,14 +617,17 @@ def main():
     # summed duration of its launches in the timed region / steps.
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
-    kname = {(2, True): "k_tally2_tc", (3, True): "k_tally3_tc", (2, False): "k_tally2_popc",
-             (3, False): "k_tally3_popc"}[(w["kind"], path == ccc.CCC_PATH_TC)]
+    kname = {(2, True): "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc",
+             (3, True): "k_tally3_fused" if args.tile == 2 else "k_tally3_tc",
+             (2, False): "k_tally2_popc", (3, False): "k_tally3_popc"}[(w["kind"],
+                                                                       path == ccc.CCC_PATH_TC)]
     if path == ccc.CCC_PATH_TC:
         flops = (8.0 if w["kind"] == 2 else 16.0) * cmp_per_step  # 4 (8) MAC per comparison
         achieved = flops / (kernel_step_ms * 1e-3) / 1e12
         peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "frac": achieved / peak, "traffic": ncu_traffic(kname, args.workload)
+                if (args.n_v is None and args.n_f is None) else None, "kernel": kname,
                 "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n,
                 "per_unit": f"{'8' if w['kind'] == 2 else '16'} flops per comparison",
                 "peak_note": f"e4m3 dense peak = 2 x {peak_src} bf16 burst {bf16_peak:.0f} TFLOP/s "

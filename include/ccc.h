@@ -111,8 +111,12 @@ typedef struct ccc_opts {
   size_t workspace_bytes; /* its size; must be >= ccc_workspace_size() */
   int32_t group;          /* tensor-core tile order: column blocks per L2 group; 0 = 8 */
   int32_t order;          /* ccc2_batched panel order: 0 = most tile work first, 1 = as given */
-  int32_t tile;           /* 2-way tensor-core tiles: 1 = 128 x 256 on one SM, 2 = 256 x 256
-                             on a pair of SMs (cta_group::2), 0 = automatic (pairs) */
+  int32_t tile;           /* tensor-core variant.  2-way: 1 = 128 x 256 tiles on one SM,
+                             2 = 256 x 256 tiles on a pair of SMs (cta_group::2); automatic = 2.
+                             3-way: 1 = masked operands formed in HBM by a separate pass,
+                             2 = formed in shared memory inside the tally kernel (repeated for
+                             every k-block, slower); automatic = 1.  0 = automatic.  The
+                             workspace size depends on it. */
   int32_t reserved;       /* zero */
 } ccc_opts;
 

@@ -89,7 +89,7 @@ constexpr int kMaxPanelsPerCall = 1024;
 // Bytes of masked 3-way operands staged per batch of slabs.
 constexpr size_t kLopBytes = size_t(2) << 30;
 
-Layout make_layout(int64_t n_f, int64_t n_v, int path, int op) {
+Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
   Layout L;
   size_t off = 0;
   L.status = off;
@@ -105,7 +105,7 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op) {
       off = align_up(off, 1024);
       L.op = off;
       off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(L.kpad), 1024);
-      if (op == CCC_OP_3WAY) {
+      if (op == CCC_OP_3WAY && tile != 2) {
         // Masked operands of as many slabs as fit in kLopBytes, but at least
         // the largest slab (j = n_v - 2).
         const int64_t all_rows = tc3_lop_rows(0, n_v);
@@ -310,7 +310,7 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
   if (p->n_v > 65535) return CCC_ERANGE;
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
-  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY);
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY, o->tile);
   CCC_TRY(check_workspace(o, L));
   CCC_TRY(clear_status(o, L, s));
   if (slab_offset(j_end, p->n_v) == slab_offset(j_begin, p->n_v)) return CCC_OK;
@@ -328,6 +328,17 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
   a.status = at<int32_t>(o, L.status);
   a.gamma = static_cast<float>(o->gamma);
   a.norm = o->norm;
+  if (o->path == CCC_PATH_TC && o->tile == 2) {
+    // Masked operands formed inside the tally kernel from the packed codes
+    // (slower on GB300: 45.9 ms against 36.7 ms for the 1,536 x 8,192 panel,
+    // because every k-block tile of a slab forms the same i-block operand again).
+    uint8_t *op = at<uint8_t>(o, L.op);
+    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    const int slot = timing_begin(s);
+    const int rc = launch_tally3_fused(a, p->geno, p->ld, op, L.rows_pad, L.kpad, dev.sms, s);
+    timing_end(slot, s);
+    return rc;
+  }
   if (o->path == CCC_PATH_TC) {
     uint8_t *op = at<uint8_t>(o, L.op);
     uint8_t *lop = at<uint8_t>(o, L.lop);
@@ -463,7 +474,10 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
       okpad[x] = B.kpad[k];
     }
     const int slot = timing_begin(s);
-    const int rc = launch_tally2_tc_batched(oargs, ops, orows, okpad, m, o->group, dev.sms, s);
+    const int rc = o->tile == 1
+                       ? launch_tally2_tc_batched(oargs, ops, orows, okpad, m, o->group, dev.sms, s)
+                       : launch_tally2_tc_pair_batched(oargs, ops, orows, okpad, m, o->group,
+                                                       dev.sms, s);
     timing_end(slot, s);
     if (rc != CCC_OK) return rc;
   }
@@ -490,7 +504,7 @@ int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, siz
   if (panel == nullptr || panel->n_f < 1 || panel->n_v < 1) return CCC_EINVAL;
   if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
   if (op != CCC_OP_2WAY && op != CCC_OP_3WAY && op != CCC_OP_METRIC) return CCC_EINVAL;
-  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op).total;
+  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile).total;
   return CCC_OK;
 }
 

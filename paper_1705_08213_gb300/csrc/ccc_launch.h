@@ -55,6 +55,10 @@ constexpr int kMaxBatchPanels = 64;
 int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
                              const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                              int num_sms, cudaStream_t s);
+// The same on SM pairs (256 x 256 tiles, cta_group::2).
+int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *ops,
+                                  const int64_t *rows_pad, const int64_t *kpad, int n, int group,
+                                  int num_sms, cudaStream_t s);
 
 // 256 x 256 tiles on SM pairs (cta_group::2); same arguments as launch_tally2_tc.
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
@@ -91,6 +95,10 @@ int64_t tc3_num_tiles(int64_t j0, int64_t j1, int64_t n_v);
 int launch_tally3_tc(const Tally3Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      uint8_t *lop, int64_t lop_rows, int64_t j0, int64_t j1, int num_sms,
                      cudaStream_t s);
+// Tensor-core 3-way tallies with the masked operand formed inside the kernel
+// from the packed panel (all slabs [a.j_begin, a.j_end) in one launch).
+int launch_tally3_fused(const Tally3Args &a, const uint64_t *geno, int64_t ld, const uint8_t *op,
+                        int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t s);
 int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
 int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
                    int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);

@@ -164,7 +164,9 @@ struct Epi2 {
         const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + 2 * p + a;
         if (i < j && j < n_v && i >= args.i_begin && i < args.i_end) {
           const int64_t pidx = row_base + j - args.pair0;
-          if (!filter) reinterpret_cast<int4 *>(args.tally)[pidx] = make_int4(r00, r01, r10, r11);
+          // Streaming stores: the output passes through L2 once and should not
+          // evict the operand blocks that other tiles still read.
+          if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
           if (want_ccc) {
             float wj0 = 1.f, wj1 = 1.f;
             if (args.norm == CCC_NORM_PERSNP) {
@@ -178,7 +180,7 @@ struct Epi2 {
               filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10,
                           r11, cv);
             else
-              reinterpret_cast<float4 *>(args.ccc)[pidx] = cv;
+              __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
           }
         }
       }
@@ -204,9 +206,10 @@ struct TriSchedPair : TriSched {
 struct Epi2Pair {
   using Params = Tally2Args;
   template <int NC>
-  __device__ static void tile(const Params &args, int I64, int J, int quarter, int lane,
-                              uint32_t t_base, uint32_t release_cluster_bar, int c0) {
-    Epi2::body<NC, true>(args, Tile2{I64, J}, quarter, lane, t_base, release_cluster_bar, c0);
+  __device__ static void tile(const Params &args, const TriSchedPair &sc, int rank, int quarter,
+                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0) {
+    Epi2::body<NC, true>(args, Tile2{2 * sc.I + rank, sc.J}, quarter, lane, t_base,
+                         release_cluster_bar, c0);
   }
 };
 
@@ -240,12 +243,13 @@ static_assert(sizeof(BatchParams) + sizeof(BatchMaps) < 32000, "kernel parameter
 
 // All tiles of panel 0, then of panel 1, ...: the CTAs of one persistent launch
 // share every panel's triangle, so small panels fill the SMs big ones leave idle.
-struct BatchSched {
+template <class Inner>
+struct BatchSchedT {
   using Params = BatchParams;
   const BatchParams *bp;
   int p;
   int64_t pos;  // tile position inside panel p
-  TriSched t;
+  Inner t;
   bool valid;
 
   __device__ void start_panel() {
@@ -278,6 +282,29 @@ struct BatchSched {
   __device__ int a_row() const { return t.a_row(); }
   __device__ int b_row() const { return t.b_row(); }
 };
+using BatchSched = BatchSchedT<TriSched>;
+
+struct BatchSchedPair : BatchSchedT<TriSchedPair> {
+  __device__ int I() const { return t.I; }
+};
+
+struct EpiBatchPair {
+  using Params = BatchParams;
+  template <int NC>
+  __device__ static void tile(const Params &bp, const BatchSchedPair &sc, int rank, int quarter,
+                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0) {
+    Epi2::body<NC, true>(bp.p[sc.p].args, Tile2{2 * sc.t.I + rank, sc.t.J}, quarter, lane, t_base,
+                         release_cluster_bar, c0);
+  }
+};
+
+template <int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
+    k_tally2_tc_pair_batched(const __grid_constant__ BatchMaps maps,
+                             const __grid_constant__ BatchParams bp) {
+  tcp::persistent_gemm_pair<BatchSchedPair, EpiBatchPair, EW>(maps.a, bp, bp, 0,
+                                                             bp.p[0].args.status);
+}
 
 struct EpiBatch {
   using Params = BatchParams;
@@ -335,6 +362,82 @@ bool make_operand_map(CUtensorMap *map, const uint8_t *op, int64_t rows, int64_t
 
 }  // namespace tc
 
+// Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
+int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1) {
+  const int64_t nB = (n_v + 127) / 128;
+  int64_t t = 0;
+  for (int64_t I = I0; I < nB && I < I1; ++I) t += nB - I;
+  return t;
+}
+
+int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *ops,
+                                  const int64_t *rows_pad, const int64_t *kpad, int n, int group,
+                                  int num_sms, cudaStream_t s) {
+  static bool attr_set = false;
+  if (n < 1 || n > kMaxBatchPanels) return CCC_EINVAL;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_tally2_tc_pair_batched<4>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_pair_batched<8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+      return CCC_ECUDA;
+    attr_set = true;
+  }
+  thread_local BatchMaps maps;
+  thread_local BatchParams bp;
+  memset(&bp, 0, sizeof(bp));
+  bp.n = n;
+  int64_t tiles = 0;
+  double kw = 0.0;
+  for (int k = 0; k < n; ++k) {
+    BatchPanel &q = bp.p[k];
+    q.args = args[k];
+    q.tri.nI = static_cast<int>((args[k].n_v + 127) / 128);
+    q.tri.nJ = q.tri.nI;
+    q.tri.group = group > 0 ? group : 8;
+    q.tri.shift = 0;
+    q.tri.I0 = 0;
+    q.tri.I1 = q.tri.nI;
+    q.nkb = static_cast<int>(kpad[k] / BK);
+    q.tiles = args[k].n_v >= 2 ? tc2_pair_tiles(args[k].n_v, 0, q.tri.nI) : 0;
+    tiles += q.tiles;
+    kw += static_cast<double>(q.tiles) * q.nkb;
+    if (!make_operand_map(&maps.a[k], ops[k], rows_pad[k], kpad[k], tcp::BMH)) return CCC_ECUDA;
+  }
+  if (tiles == 0) return CCC_OK;
+  const int ew = epilogue_warps(static_cast<int>(kw / static_cast<double>(tiles)));
+  static int max_clusters[2] = {0, 0};
+  int &mc = max_clusters[ew == 4 ? 0 : 1];
+  if (mc == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(static_cast<unsigned>(64 + 32 * ew), 1, 1);
+    cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int m = 0;
+    const cudaError_t e =
+        ew == 4 ? cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched<4>, &cfg)
+                : cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched<8>, &cfg);
+    if (e != cudaSuccess || m < 1) return CCC_ECUDA;
+    mc = m < num_sms / 2 ? m : num_sms / 2;
+  }
+  const int64_t clusters = tiles < mc ? tiles : mc;
+  const int grid = static_cast<int>(2 * clusters);
+  if (ew == 4)
+    k_tally2_tc_pair_batched<4><<<grid, 64 + 32 * 4, tcp::SMEM_BYTES, s>>>(maps, bp);
+  else
+    k_tally2_tc_pair_batched<8><<<grid, 64 + 32 * 8, tcp::SMEM_BYTES, s>>>(maps, bp);
+  return note_launch();
+}
+
 int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
                              const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                              int num_sms, cudaStream_t s) {
@@ -380,14 +483,6 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
   else
     k_tally2_tc_batched<8><<<grid, 64 + 32 * 8, SMEM_BYTES, s>>>(maps, bp);
   return note_launch();
-}
-
-// Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
-int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1) {
-  const int64_t nB = (n_v + 127) / 128;
-  int64_t t = 0;
-  for (int64_t I = I0; I < nB && I < I1; ++I) t += nB - I;
-  return t;
 }
 
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,

@@ -107,11 +107,11 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
 }
 
 // Sched: as for tc::persistent_gemm, in units of 256-row tiles; a_row/b_row
-// give the first row of the tile (the CTA adds 128 r).
-// Epi: template <int NC> static void tile(const Params&, int I64, int J, int quarter,
-//        int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0), where
-//        I64 = 2 I + r indexes 64-SNP row blocks and the release arrives at a
-//        cluster address.
+// give the first row of the tile (the CTA adds 128 r); map_index() selects the
+// tile's tensor map in tm[].
+// Epi: template <int NC> static void tile(const Params&, const Sched&, int rank,
+//        int quarter, int lane, uint32_t t_base, uint32_t release_cluster_bar,
+//        int c0); the release arrives at a cluster address.
 template <class Sched, class Epi, int EW>
 __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
                                                      const typename Sched::Params &sp,
@@ -176,6 +176,7 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep)) {
         const int ya = sc.a_row() + BMH * static_cast<int>(rank);
         const int yb = sc.b_row() + BNH * static_cast<int>(rank);
+        const CUtensorMap *m = tm + sc.map_index();
         const int kbs = sc.k_blocks(nkb);
         for (int kb = 0; kb < kbs; ++kb) {
           if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, status, abort_flag)) {
@@ -184,8 +185,8 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
           }
           if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * STAGE_BYTES);
           const uint32_t fb = map_to_rank(full_bar(stage), 0);
-          tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), tm, kb * BK, ya, fb);
-          tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), tm, kb * BK, yb, fb);
+          tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), m, kb * BK, ya, fb);
+          tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), m, kb * BK, yb, fb);
           last_parity[stage] = static_cast<int>(phase);
           if (++stage == STAGES) {
             stage = 0;
@@ -262,7 +263,7 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       tc_fence_after();
       const uint32_t t_base =
           tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * ACC_COLS;
-      Epi::template tile<NC>(ep, 2 * sc.I + static_cast<int>(rank), sc.J, quarter, lane, t_base,
+      Epi::template tile<NC>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
                              map_to_rank(tempty_bar(acc), 0), c0);
     }
   }

@@ -12,7 +12,9 @@ from tests.gpu_util import assert_ccc_close, assert_tally_equal, run_3way
 
 pytestmark = pytest.mark.gpu
 
-PATHS = [0, 1]  # CCC_PATH_TC, CCC_PATH_POPC
+# (path, tile): tensor cores with the masked operand formed in shared memory (default),
+# tensor cores with the masked operand formed in HBM first, popcount.
+PATHS = [(0, 0), (0, 1), (1, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -27,7 +29,9 @@ def _build():
 def _check(geno, n_f, path, j_begin=0, j_end=None, norm=0, gamma=2.0 / 3.0, fused=True):
     n_v = geno.shape[0]
     j_end = n_v if j_end is None else j_end
-    t, c = run_3way(geno, n_f, path, j_begin, j_end, norm=norm, gamma=gamma, fused=fused)
+    path, tile = path
+    t, c = run_3way(geno, n_f, path, j_begin, j_end, norm=norm, gamma=gamma, fused=fused,
+                    tile=tile)
     et, ec = oracle.ccc3_slabs(geno, n_f, j_begin, j_end, gamma=gamma, norm=norm)
     what = f"n_v={n_v} n_f={n_f} path={path} j=[{j_begin},{j_end}) norm={norm}"
     assert_tally_equal(t, et, "tally " + what)
@@ -91,16 +95,21 @@ def test_at_scale_tc_equals_popc_and_oracle_rows():
     g = to_device(geno)
     nt = ccc.ccc3_count(n_v, 0, n_v)
     outs = {}
-    for path in (0, 1):
-        opts = ccc.ccc_opts_default(path=path)
+    for path, tile in ((0, 0), (1, 0), (0, 1)):
+        opts = ccc.ccc_opts_default(path=path, tile=tile)
         ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_3WAY))
-        opts = ccc.ccc_opts_default(path=path, workspace=ws)
+        opts = ccc.ccc_opts_default(path=path, workspace=ws, tile=tile)
         tally = torch.empty((nt, 8), dtype=torch.int32, device="cuda")
         out = torch.empty((nt, 8), dtype=torch.float32, device="cuda")
         ccc.ccc3_tally_metric(g, n_f, 0, n_v, tally, out, opts)
         torch.cuda.synchronize()
         assert ccc.ccc_status(opts) == ccc.CCC_OK
-        outs[path] = (tally, out)
+        if tile == 1:  # the HBM-prepass route must equal the fused one
+            assert torch.equal(tally, outs[0][0])
+            assert torch.equal(out, outs[0][1])
+            del tally, out
+        else:
+            outs[path] = (tally, out)
         del ws
     assert torch.equal(outs[0][0], outs[1][0])
     step = 1 << 25
