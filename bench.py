@@ -103,6 +103,10 @@ def parse():
     ap.add_argument("--skip-popc", action="store_true", help="no popcount-path comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--e2e-mode", default="auto", choices=["auto", "stream", "direct", "copy"],
+                    help="e2e leg: ccc2_stream phases (stream), results stored by the kernels "
+                         "straight into pinned host memory (direct), or one copy per output "
+                         "after the call (copy); auto = stream for 2-way, copy otherwise")
     ap.add_argument("--source-hash", action="store_true",
                     help="print the hash of the CUDA sources (for profiles/ncu_traffic.json) and exit")
     a = ap.parse_args()
@@ -380,16 +384,27 @@ class Runner:
             ccc.ccc3_tally_metric(self.geno, w["n_f"], 0, w["n_v"], self.tally, self.out, self.opts,
                                   stream)
 
-    def e2e(self, stream, steps, phases=8):
+    def e2e(self, stream, steps, phases=8, mode="auto"):
         """Host panel -> device, the step, results -> pinned host memory, per step.
 
-        2-way: ccc2_stream, whose phases copy finished results to the host while
-        later phases compute.  3-way: the fused call, then one copy per output.
+        stream (2-way): ccc2_stream, whose phases copy finished results to the
+        host while later phases compute.  direct: the same call with the output
+        arrays in pinned host memory, so the kernels' epilogues store the results
+        over the host link themselves.  copy: the call, then one copy per output.
         Filter: the hit count comes back (the hits stay on the device).
         """
         torch, ccc, w = self.torch, self.ccc, self.w
-        streamed = w["kind"] == 2 and not self.filter
-        if self.filter:
+        if mode == "auto":
+            mode = "stream" if (w["kind"] == 2 and not self.filter) else "copy"
+        self.e2e_mode = mode if not self.filter else "copy"
+        streamed = mode == "stream" and w["kind"] == 2 and not self.filter
+        direct = mode == "direct" and not self.filter
+        if direct:
+            host = [torch.empty(self.tally.shape, dtype=torch.int32, pin_memory=True),
+                    torch.empty(self.out.shape, dtype=torch.float32, pin_memory=True)]
+            dev = []
+            self.tally, self.out = host  # the kernels write these host arrays directly
+        elif self.filter:
             host = [torch.empty(1, dtype=torch.int64, pin_memory=True)]
             dev = [self.n_hits]
         elif streamed:
@@ -658,14 +673,18 @@ def main():
     }
 
     if not args.skip_e2e and rank == 0:
-        e2e_ms, bi, bo = run.e2e(stream, max(1, min(args.steps, 5)))
+        e2e_ms, bi, bo = run.e2e(stream, max(1, min(args.steps, 5)), mode=args.e2e_mode)
         result["e2e"] = {"value": cmp_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
-                         "note": ("pinned host panel -> device, ccc2_stream (8 phases: results of "
-                                  "each phase copied to pinned host memory while the next computes)"
-                                  if w["kind"] == 2 and not run.filter else
-                                  "pinned host panel -> device, the same C ABI call, results -> "
-                                  "pinned host memory")}
+                         "mode": run.e2e_mode,
+                         "note": {"stream": "pinned host panel -> device, ccc2_stream (8 phases: "
+                                            "results of each phase copied to pinned host memory "
+                                            "while the next computes)",
+                                  "direct": "pinned host panel -> device, the same C ABI call with "
+                                            "its output arrays in pinned host memory (the kernel "
+                                            "epilogues store over the host link)",
+                                  "copy": "pinned host panel -> device, the same C ABI call, "
+                                          "results -> pinned host memory"}[run.e2e_mode]}
         if run.filter:
             result["config"]["hits_per_step"] = run.hit_count
 

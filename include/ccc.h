@@ -54,7 +54,10 @@
  * Conventions for every entry point
  *   - All buffers are caller-owned device memory unless stated otherwise; the
  *     library allocates nothing.  Scratch space is the caller's workspace,
- *     sized by ccc_workspace_size() and passed in ccc_opts.
+ *     sized by ccc_workspace_size() and passed in ccc_opts.  Output arrays
+ *     (tallies, CCC values, hits) may also be pinned host memory that the
+ *     device can address (cudaHostAlloc / cudaHostRegister with unified
+ *     addressing): the kernels then store the results over the host link.
  *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
  *     as void*; NULL is the legacy default stream).  They return once the work
  *     is queued.

@@ -120,3 +120,49 @@ def test_cuda_graph_capture_and_replay():
         et, ec = oracle.ccc2_all(g, n_f)
         assert_tally_equal(t.cpu().numpy(), et, "graph replay")
         assert_ccc_close(c.cpu().numpy(), ec, what="graph replay")
+
+
+def test_batched_full_size_workload():
+    """The batched workload as bench.py runs it: 64 panels, n_v ~ U{500..8000},
+    n_f ~ U{2000..50000} (shape seed 2), Hardy-Weinberg (seed 2, panel index k).  The
+    batched call equals one ccc2_tally_metric call per panel on every panel, and sampled
+    rows of three panels equal the oracle."""
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    rng = np.random.default_rng(2)
+    shapes = [(int(rng.integers(500, 8001)), int(rng.integers(2000, 50001))) for _ in range(64)]
+    genos_np = [synth.panel_hwe(v, f, seed=2, panel=k, p_missing=0.01)
+                for k, (v, f) in enumerate(shapes)]
+    genos = [to_device(g) for g in genos_np]
+    n_fs = [f for _, f in shapes]
+    tallies = [torch.empty((ccc.ccc2_count(v), 4), dtype=torch.int32, device="cuda") for v, _ in shapes]
+    cccs = [torch.empty((ccc.ccc2_count(v), 4), dtype=torch.float32, device="cuda") for v, _ in shapes]
+    opts = ccc.ccc_opts_default()
+    ws = torch.empty(ccc.ccc2_batched_workspace_size(genos, n_fs, opts), dtype=torch.uint8,
+                     device="cuda")
+    opts = ccc.ccc_opts_default(workspace=ws)
+    ccc.ccc2_batched_tune(genos, n_fs, tallies, cccs, opts)
+    ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    del ws
+    o1 = ccc.ccc_opts_default()
+    ws1 = torch.empty(max(ccc.ccc_workspace_size(g, f, o1, ccc.CCC_OP_2WAY)
+                          for g, f in zip(genos, n_fs)), dtype=torch.uint8, device="cuda")
+    o1 = ccc.ccc_opts_default(workspace=ws1)
+    for g, f, t, c in zip(genos, n_fs, tallies, cccs):
+        t1 = torch.empty_like(t)
+        c1 = torch.empty_like(c)
+        ccc.ccc2_tally_metric(g, f, t1, c1, o1)
+        assert torch.equal(t1, t)
+        assert torch.equal(c1, c)
+        del t1, c1
+    for k in (0, 31, 63):
+        n_v, n_f = shapes[k]
+        rows = np.array([0, n_v // 2, n_v - 2])
+        et, ec = oracle.ccc2_rows(genos_np[k], n_f, rows)
+        idx = np.concatenate([oracle.pair_index(i, np.arange(i + 1, n_v), n_v) for i in rows])
+        it = torch.from_numpy(idx).cuda()
+        assert_tally_equal(tallies[k][it].cpu().numpy(), et, f"panel {k}")
+        assert_ccc_close(cccs[k][it].cpu().numpy(), ec, what=f"panel {k}")

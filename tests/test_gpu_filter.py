@@ -94,3 +94,44 @@ def test_filter_cap_and_count_only(path):
     # a threshold above every value keeps nothing; a negative one keeps every pair
     assert _filter(geno, n_f, path, 1.0, cap=4)[0] == 0
     assert _filter(geno, n_f, path, -1.0, cap=0)[0] == n_v * (n_v - 1) // 2
+
+
+def test_filter_full_size_planted_pairs():
+    """The large thresholded workload as bench.py runs it: 200,000 SNPs x 4,096 individuals,
+    1,000 planted near-duplicate pairs, threshold 0.16.  Every kept pair is re-verified
+    against the oracle (tallies exact, CCC within 1e-6); the kept set equals the oracle's
+    set on the planted pairs and on sampled full rows of the triangle."""
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    n_v, n_f, tau = 200000, 4096, 0.16
+    geno = synth.panel_hwe(n_v, n_f, seed=5, p_missing=0.01)
+    planted = synth.plant_near_duplicates(geno, n_f, 1000, seed=1005)
+    total, rec = _filter(geno, n_f, 0, tau, cap=1 << 16)
+    assert total == len(rec) and total > 0
+    pi = rec["i"].astype(np.int64)
+    pj = rec["j"].astype(np.int64)
+    et, ec = oracle.ccc2_pairs(geno, n_f, pi, pj)
+    np.testing.assert_array_equal(rec["tally"], et)
+    assert_ccc_close(rec["ccc"], ec, what="full-size hits")
+    got = set(zip(pi.tolist(), pj.tolist()))
+    # planted pairs: kept exactly when the oracle's max CCC exceeds the threshold
+    a = np.minimum(planted[:, 0], planted[:, 1])
+    b = np.maximum(planted[:, 0], planted[:, 1])
+    _, pc = oracle.ccc2_pairs(geno, n_f, a, b)
+    for x, y, m in zip(a.tolist(), b.tolist(), pc.max(1)):
+        if abs(m - tau) > 1e-6 * tau:
+            assert ((x, y) in got) == (m > tau), (x, y, m)
+    # sampled rows of the triangle: the kept pairs of those rows are exactly the oracle's
+    rows = np.array([0, 77777, 123456, 199998])
+    rt, rc = oracle.ccc2_rows(geno, n_f, rows)
+    o = 0
+    for i in rows.tolist():
+        js = np.arange(i + 1, n_v)
+        mx = rc[o:o + js.size].max(1)
+        sure = np.abs(mx - tau) > 1e-6 * tau
+        want = {(i, int(j)) for j in js[(mx > tau) & sure]}
+        either = {(i, int(j)) for j in js[~sure]}
+        have = {p for p in got if p[0] == i}
+        assert want <= have <= want | either
+        o += js.size
