@@ -96,8 +96,10 @@ def parse():
     ap.add_argument("--n-v", type=int, default=None)
     ap.add_argument("--n-f", type=int, default=None)
     ap.add_argument("--path", default="tc", choices=["tc", "popc"])
-    ap.add_argument("--tile", type=int, default=0, choices=[0, 1, 2],
-                    help="2-way tensor-core tiles: 0 automatic, 1 one SM, 2 SM pairs")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="tensor-core variant (0 automatic). 2-way: 1 one SM, 2 SM pairs; 3-way: "
+                         "1 masked operands in HBM, 2 masked operands in shared memory, "
+                         "3 genotype classes of v_j")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--skip-e2e", action="store_true", help="no host-buffer end-to-end timing")
     ap.add_argument("--skip-popc", action="store_true", help="no popcount-path comparison")
@@ -160,6 +162,8 @@ KERNEL_SOURCES = {
                          "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally3_tc": ["k_tc3.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally3_class": ["k_tc3c.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "ccc_dev.cuh",
+                       "ccc_metric.cuh", "ccc_launch.h"],
 }
 
 
@@ -633,18 +637,22 @@ def main():
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
     kname = {(2, True): "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc",
-             (3, True): "k_tally3_fused" if args.tile == 2 else "k_tally3_tc",
+             (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(args.tile, "k_tally3_class"),
              (2, False): "k_tally2_popc", (3, False): "k_tally3_popc"}[(w["kind"],
                                                                        path == ccc.CCC_PATH_TC)]
     if path == ccc.CCC_PATH_TC:
-        flops = (8.0 if w["kind"] == 2 else 16.0) * cmp_per_step  # 4 (8) MAC per comparison
+        # MACs per comparison (pair or triple, one individual): 2-way 4; 3-way with the
+        # masked operand L_j 8; 3-way by genotype classes 4 (the product over the ~1% of
+        # individuals with v_j missing is not counted).
+        per_cmp = 8.0 if (w["kind"] == 2 or kname == "k_tally3_class") else 16.0
+        flops = per_cmp * cmp_per_step
         achieved = flops / (kernel_step_ms * 1e-3) / 1e12
         peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kname, args.workload)
                 if (args.n_v is None and args.n_f is None) else None, "kernel": kname,
                 "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n,
-                "per_unit": f"{'8' if w['kind'] == 2 else '16'} flops per comparison",
+                "per_unit": f"{per_cmp:.0f} flops per comparison",
                 "peak_note": f"e4m3 dense peak = 2 x {peak_src} bf16 burst {bf16_peak:.0f} TFLOP/s "
                              "(kind::i8 is not available on sm_103a)"}
     else:
@@ -661,7 +669,11 @@ def main():
         "dtype": "e4m3 operands, fp32 accumulate" if path == ccc.CCC_PATH_TC else "u64 bit planes",
         "data": "synthetic",
         "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"], "path": args.path,
-                   "tile": {0: "automatic", 1: "128x256 on one SM", 2: "256x256 on an SM pair"}[args.tile],
+                   "tile": ({0: "automatic (256x256 on an SM pair)", 1: "128x256 on one SM",
+                             2: "256x256 on an SM pair"} if w["kind"] == 2 else
+                            {0: "automatic (genotype classes of v_j on SM pairs)",
+                             1: "masked operands L_j formed in HBM", 2: "L_j formed in shared memory",
+                             3: "genotype classes of v_j on SM pairs"})[args.tile],
                    "parallelism": (f"{world} independent panels (one per GPU)" if world > 1
                                    else "1 GPU"),
                    "l2": ("inputs larger than L2 (operand matrix and outputs exceed the 129 MB L2)"

@@ -116,10 +116,13 @@ typedef struct ccc_opts {
   int32_t order;          /* ccc2_batched panel order: 0 = most tile work first, 1 = as given */
   int32_t tile;           /* tensor-core variant.  2-way: 1 = 128 x 256 tiles on one SM,
                              2 = 256 x 256 tiles on a pair of SMs (cta_group::2); automatic = 2.
-                             3-way: 1 = masked operands formed in HBM by a separate pass,
-                             2 = formed in shared memory inside the tally kernel (repeated for
-                             every k-block, slower); automatic = 1.  0 = automatic.  The
-                             workspace size depends on it. */
+                             3-way: 1 = masked operands L_j formed in HBM by a separate pass,
+                             2 = L_j formed in shared memory inside the tally kernel (repeated
+                             for every k-block, slower), 3 = genotype classes of v_j on SM
+                             pairs: r^{abc} from the 2-way tallies r_ik, a sign-masked product
+                             over all individuals and a product over those with v_j missing
+                             (half the tensor work of 1 and 2); automatic = 3.  0 = automatic.
+                             The workspace size depends on it. */
   int32_t reserved;       /* zero */
 } ccc_opts;
 

@@ -59,14 +59,26 @@ int check_panel(const ccc_panel *p) {
   return CCC_OK;
 }
 
+#define CCC_TRY_INNER(expr)          \
+  do {                               \
+    const int rc__ = (expr);         \
+    if (rc__ != CCC_OK) return rc__; \
+  } while (0)
+
 int check_opts(const ccc_opts *o) {
   if (o == nullptr) return CCC_EINVAL;
   if (o->path != CCC_PATH_TC && o->path != CCC_PATH_POPC) return CCC_EINVAL;
   if (o->norm != CCC_NORM_PERSNP && o->norm != CCC_NORM_JOINT) return CCC_EINVAL;
   if (!(o->gamma >= 0.0 && o->gamma <= 1.0)) return CCC_EINVAL;
   if (o->group < 0 || o->group > 4096 || (o->order != 0 && o->order != 1)) return CCC_EINVAL;
-  if (o->tile < 0 || o->tile > 2) return CCC_EINVAL;
+  if (o->tile < 0 || o->tile > 3) return CCC_EINVAL;
   return CCC_OK;
+}
+
+// Options of a 2-way call: tile 3 names a 3-way variant only.
+int check_opts2(const ccc_opts *o) {
+  CCC_TRY_INNER(check_opts(o));
+  return o->tile > 2 ? CCC_EINVAL : CCC_OK;
 }
 
 // Workspace layout shared by the 2-way and 3-way calls.
@@ -77,8 +89,12 @@ struct Layout {
   size_t op = 0;              // e4m3 operands [rows_pad][kpad] (TC path)
   size_t planes = 0;          // uint64 [n_v][w64][4] (POPC path)
   size_t lop = 0;             // masked 3-way operands (TC path)
+  size_t rtab = 0;            // int32 [pairs][4] 2-way tallies (3-way classes)
+  size_t cbuf = 0;            // compacted count rows per slab (3-way classes)
+  size_t missing = 0;         // int32 [cbuf_slabs] missing entries of v_j
   size_t total = 0;
-  int64_t kpad = 0, rows_pad = 0, w64 = 0, lop_rows = 0;
+  int64_t kpad = 0, rows_pad = 0, w64 = 0, lop_rows = 0, cbuf_slabs = 0;
+  int64_t mask_rows = 0;      // masked rows after R in op (3-way classes)
 };
 
 int64_t tc_rows_pad(int64_t n_v) { return round_up(2 * n_v, 256) + 256; }
@@ -104,8 +120,36 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
       L.rows_pad = tc_rows_pad(n_v);
       off = align_up(off, 1024);
       L.op = off;
-      off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(L.kpad), 1024);
-      if (op == CCC_OP_3WAY && tile != 2) {
+      if (op == CCC_OP_3WAY && (tile == 0 || tile == 3)) {
+        // Masked rows of as many slabs as fit in kLopBytes (at least the
+        // largest slab) right after R, so that one tensor map covers both.
+        const int64_t all_rows = tc3_class_mask_rows(0, n_v, n_v);
+        const int64_t max_slab = tc3_class_mask_rows((n_v - 1) / 2, (n_v - 1) / 2 + 1, n_v);
+        int64_t cap = static_cast<int64_t>(kLopBytes / static_cast<size_t>(L.kpad));
+        if (cap < max_slab) cap = max_slab;
+        L.mask_rows = all_rows < cap ? all_rows : cap;
+        if (L.mask_rows < 1) L.mask_rows = 1;
+      }
+      off = align_up(off + static_cast<size_t>(L.rows_pad + L.mask_rows) * static_cast<size_t>(L.kpad),
+                     1024);
+      if (op == CCC_OP_3WAY && (tile == 0 || tile == 3)) {
+        // 2-way tallies of all pairs, and the compacted rows of as many slabs
+        // as fit in kLopBytes (TMA row coordinates stay below 2^31).
+        L.rtab = off;
+        off = align_up(off + 16 * static_cast<size_t>(n_v) * static_cast<size_t>(n_v - 1) / 2 + 16,
+                       1024);
+        const int64_t per_slab = tc3_class_cbuf_rows(1, n_v) * tc3_class_cap();
+        int64_t nb = static_cast<int64_t>(kLopBytes) / per_slab;
+        const int64_t nb_rows = (int64_t(1) << 31) / (2 * n_v) - 1;
+        if (nb > nb_rows) nb = nb_rows;
+        if (nb > n_v) nb = n_v;
+        if (nb < 1) nb = 1;
+        L.cbuf_slabs = nb;
+        L.cbuf = off;
+        off = align_up(off + static_cast<size_t>(nb) * static_cast<size_t>(per_slab), 1024);
+        L.missing = off;
+        off = align_up(off + sizeof(int32_t) * static_cast<size_t>(nb), kAlign);
+      } else if (op == CCC_OP_3WAY && tile == 1) {
         // Masked operands of as many slabs as fit in kLopBytes, but at least
         // the largest slab (j = n_v - 2).
         const int64_t all_rows = tc3_lop_rows(0, n_v);
@@ -236,7 +280,7 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
                     cudaStream_t s, const FilterSpec *filter = nullptr, int64_t i_begin = 0,
                     int64_t i_end = -1) {
   CCC_TRY(check_panel(p));
-  CCC_TRY(check_opts(o));
+  CCC_TRY(check_opts2(o));
   if (filter == nullptr) {
     if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
     if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
@@ -328,6 +372,50 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
   a.status = at<int32_t>(o, L.status);
   a.gamma = static_cast<float>(o->gamma);
   a.norm = o->norm;
+  if (o->path == CCC_PATH_TC && (o->tile == 0 || o->tile == 3)) {
+    // Genotype classes of v_j: 2-way tallies r_ik of the pairs i < k with
+    // i < j_end - 1, then per batch of slabs the compacted rows of the
+    // individuals with v_j missing and the class kernel.
+    uint8_t *op = at<uint8_t>(o, L.op);
+    int32_t *rtab = at<int32_t>(o, L.rtab);
+    uint8_t *cbuf = at<uint8_t>(o, L.cbuf);
+    int32_t *missing = at<int32_t>(o, L.missing);
+    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    const int64_t jb = j_begin > 1 ? j_begin : 1;
+    const int64_t je = j_end < p->n_v - 1 ? j_end : p->n_v - 1;
+    if (jb >= je) return CCC_OK;
+    Tally2Args a2;
+    a2.n_v = p->n_v;
+    a2.n_f = p->n_f;
+    a2.w = nullptr;
+    a2.tally = rtab;
+    a2.ccc = nullptr;
+    a2.status = a.status;
+    a2.gamma = a.gamma;
+    a2.norm = a.norm;
+    a2.i_begin = 0;
+    a2.i_end = je - 1;
+    a2.pair0 = 0;
+    CCC_TRY(launch_tally2_tc_pair(a2, op, L.rows_pad, L.kpad, dev.sms, s));
+    int64_t j0 = jb;
+    while (j0 < je) {
+      int64_t j1 = j0 + 1;
+      while (j1 < je && j1 - j0 < L.cbuf_slabs &&
+             tc3_class_mask_rows(j0, j1 + 1, p->n_v) <= L.mask_rows)
+        ++j1;
+      if (tc3_class_mask_rows(j0, j1, p->n_v) > L.mask_rows) return CCC_ERANGE;
+      CCC_TRY(launch_compact3(p->geno, p->n_f, p->n_v, p->ld, cbuf, missing, j0, j1, s));
+      CCC_TRY(launch_mask3c(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad, missing, j0, j1,
+                            s));
+      const int slot = timing_begin(s);
+      const int rc = launch_tally3_class(a, op, L.rows_pad + L.mask_rows, L.rows_pad, L.kpad, rtab,
+                                         cbuf, missing, j0, j1, dev.sms, s);
+      timing_end(slot, s);
+      if (rc != CCC_OK) return rc;
+      j0 = j1;
+    }
+    return CCC_OK;
+  }
   if (o->path == CCC_PATH_TC && o->tile == 2) {
     // Masked operands formed inside the tally kernel from the packed codes
     // (slower on GB300: 45.9 ms against 36.7 ms for the 1,536 x 8,192 panel,
@@ -399,7 +487,7 @@ static int batch_layout(const ccc_panel *panels, int n, int path, BatchLayout *B
 
 static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, float *const *out_ccc,
                        const ccc_opts *o, cudaStream_t s) {
-  CCC_TRY(check_opts(o));
+  CCC_TRY(check_opts2(o));
   if (panels == nullptr || tally == nullptr || n < 1 || n > kMaxPanelsPerCall) return CCC_EINVAL;
   for (int k = 0; k < n; ++k) {
     CCC_TRY(check_panel(&panels[k]));
@@ -504,6 +592,7 @@ int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, siz
   if (panel == nullptr || panel->n_f < 1 || panel->n_v < 1) return CCC_EINVAL;
   if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
   if (op != CCC_OP_2WAY && op != CCC_OP_3WAY && op != CCC_OP_METRIC) return CCC_EINVAL;
+  if (op != CCC_OP_3WAY && opts->tile > 2) return CCC_EINVAL;
   *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile).total;
   return CCC_OK;
 }
@@ -533,7 +622,7 @@ int ccc2_tally_metric_rows(const ccc_panel *panel, int64_t i_begin, int64_t i_en
   if (out_ccc == nullptr) return CCC_EINVAL;
   if (i_begin == i_end || rows_count(panel->n_v, i_begin, i_end) == 0) {
     CCC_TRY(check_panel(panel));
-    CCC_TRY(check_opts(opts));
+    CCC_TRY(check_opts2(opts));
     return CCC_OK;
   }
   return run_2way(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream), nullptr, i_begin,
@@ -606,7 +695,7 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
                 const ccc_opts *o, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CCC_TRY(check_panel(p));
-  CCC_TRY(check_opts(o));
+  CCC_TRY(check_opts2(o));
   if (host_tally == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
   size_t need = 0;
   CCC_TRY(ccc2_stream_workspace_size(p, n_phases, o, &need));
@@ -699,7 +788,7 @@ int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc
                                 size_t *bytes) {
   if (bytes == nullptr || panels == nullptr || n_panels < 1 || n_panels > kMaxPanelsPerCall)
     return CCC_EINVAL;
-  CCC_TRY(check_opts(opts));
+  CCC_TRY(check_opts2(opts));
   for (int k = 0; k < n_panels; ++k) {
     if (panels[k].n_f < 1 || panels[k].n_v < 1) return CCC_EINVAL;
     if (panels[k].n_f > CCC_MAX_NF || panels[k].n_v > kMaxNV) return CCC_ERANGE;

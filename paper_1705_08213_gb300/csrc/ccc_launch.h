@@ -99,6 +99,29 @@ int launch_tally3_tc(const Tally3Args &a, const uint8_t *op, int64_t rows_pad, i
 // from the packed panel (all slabs [a.j_begin, a.j_end) in one launch).
 int launch_tally3_fused(const Tally3Args &a, const uint64_t *geno, int64_t ld, const uint8_t *op,
                         int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t s);
+// 3-way tallies by genotype classes of v_j (k_tc3c.cu), per batch of slabs
+// [j0, j1):
+//   launch_compact3  missing[j - j0] = individuals with v_j missing and, when
+//                    at most tc3_class_cap(), the count rows of every SNP
+//                    restricted to them (cbuf, tc3_class_cbuf_rows(j1 - j0, n_v)
+//                    rows of tc3_class_cap() bytes);
+//   launch_mask3c    the masked rows of the batch (tc3_class_mask_rows(j0, j1,
+//                    n_v) rows of kpad bytes) into op from row mrow0 on, op's
+//                    first rows being the count matrix R;
+//   launch_tally3_class  the tallies, with the 2-way tallies rtab ([pair][4],
+//                    pairs i < k with i < j1 - 1).
+int64_t tc3_class_cap();
+int64_t tc3_class_cbuf_rows(int64_t n_slabs, int64_t n_v);
+int64_t tc3_class_mask_rows(int64_t j0, int64_t j1, int64_t n_v);
+int launch_compact3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *cbuf,
+                    int32_t *missing, int64_t j0, int64_t j1, cudaStream_t s);
+int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                  int64_t kpad, int64_t mrow0, const int32_t *missing, int64_t j0, int64_t j1,
+                  cudaStream_t s);
+int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows, int64_t mrow0,
+                        int64_t kpad, const int32_t *rtab, const uint8_t *cbuf,
+                        const int32_t *missing, int64_t j0, int64_t j1, int num_sms,
+                        cudaStream_t s);
 int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
 int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
                    int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);

@@ -1,0 +1,747 @@
+// 3-way tallies by genotype classes of the middle SNP, on SM pairs.
+//
+// Sec. 3.2 obtains the tallies of a slab of fixed j from products of count
+// matrices masked by the column v_j.  Here the mask is split by the genotype
+// class of v_j at each individual q: C0 (hom 0, rho_j = (2, 0)), C1 (het,
+// (1, 1)), C2 (hom 1, (0, 2)), CM (missing, (0, 0)).  With
+// X_S = sum_{q in S} rho_i(a) rho_k(c),
+//     r_{ijk}^{a0c} = 2 X_C0 + X_C1,      r_{ijk}^{a1c} = X_C1 + 2 X_C2,
+// and the 2-way tally r_{ik}^{ac} = X_C0 + X_C1 + X_C2 + X_CM (Eq. 4) gives
+//     r_{ijk}^{a0c} = r_{ik}^{ac} - D + T,   r_{ijk}^{a1c} = r_{ik}^{ac} - D - T,
+//     T = X_C0 - X_C2 = sum_q rho_i(a) s_j(q) rho_k(c),   s_j in {+1, 0, -1},
+//     D = X_CM.
+// Per triple the tensor cores then form 4 products over the n_f individuals
+// (T) plus 4 over the few individuals with v_j missing (D), instead of the 8
+// of the masked operand L_j = rho_i(a) rho_j(b) of k_tc3.cu; the 2-way tallies
+// r_ik come from one 2-way tally pass.
+//
+// Passes per batch of slabs:
+//   k_compact3  the individuals with v_j missing; when there are at most kCap
+//               of them, the count rows of every SNP restricted to them;
+//   k_mask3c    for the side of the slab with fewer SNPs (i < j or k > j),
+//               rows R(s, x) * s_j in e4m3 (values 0, +-1, +-2), and, when v_j
+//               has more than kCap missing entries, rows R(s, x) * [v_j missing];
+//   k_tally3_class  the tiles of the batch.  A cluster of two CTAs
+//               (cta_group::2, M = 256) takes 128 SNPs i (64 per CTA, rows
+//               (i, a)) and up to 80 SNPs k (N <= 160 columns (k, c)); TMEM
+//               holds two T accumulators (double buffered) and one D
+//               accumulator, 3 x 160 of the 512 columns.  TMA brings every
+//               operand tile; T runs over the n_f individuals (one operand
+//               masked, the other plain R), D over the compacted rows (or the
+//               missing-masked rows).  The epilogue reads T and D from TMEM and
+//               r_ik from the 2-way tally table and writes the 8 tallies and 8
+//               CCC values (Eq. 7 with the Eq. 8 frequencies) of every triple
+//               i < j < k of the tile.
+#include "ccc_launch.h"
+#include "ccc_metric.cuh"
+#include "tc_pipeline.cuh"
+#include "tc_pipeline_pair.cuh"
+
+namespace ccc {
+namespace {
+
+using tcp::cluster_rank;
+using tcp::cluster_sync;
+using tcp::map_to_rank;
+
+constexpr int kSnpI = 128;            // SNPs i per pair tile
+constexpr int kSnpK = 80;             // SNPs k per pair tile (at most)
+constexpr int kNMax = 2 * kSnpK;      // accumulator columns
+constexpr int kBK = 128;              // individuals per k-block
+constexpr int kUK = 32;               // K per MMA
+constexpr int kABytes = 128 * kBK;    // A rows per CTA x 128 bytes
+constexpr int kBRows = kNMax / 2;     // B rows per CTA
+constexpr int kBBytes = kBRows * kBK;
+constexpr int kStages = 6;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kCap = 256;             // compacted missing columns per slab
+constexpr int kNumBars = 2 * kStages + 2 + 2 + 1 + 1;
+constexpr uint32_t kColT0 = 0, kColT1 = kNMax, kColD = 2 * kNMax;
+constexpr size_t kSmemBytes =
+    1024 + static_cast<size_t>(kStages) * (kABytes + kBBytes) + kNumBars * 8 + 64;
+
+static_assert(kBBytes % 1024 == 0, "B tiles keep the 1024-byte swizzle alignment");
+static_assert(3 * kNMax <= 512, "three accumulators in 512 TMEM columns");
+static_assert(kSmemBytes <= 232448, "dynamic shared memory limit");
+
+constexpr uint64_t kEven = 0x5555555555555555ull;
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      "selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// mbar_wait_bounded with cluster-scope acquire (arrivals from the peer CTA).
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint32_t bar, uint32_t parity,
+                                                          int32_t *status,
+                                                          volatile int *abort_flag) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  uint32_t spins = 0;
+  while (true) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (((++spins) & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (global_timer_ns() - t0 > 2000000000ull) {
+        record_error(status, CCC_ETIMEOUT);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// P(x) = sum_{j < x} min(j, n_v - 1 - j): SNPs on the masked side of the
+// slabs before x.  Slab j owns 4 min(j, n_v - 1 - j) masked rows (2 per SNP
+// for s_j, 2 for the missing mask).
+__host__ __device__ inline int64_t mask_prefix(int64_t x, int64_t n_v) {
+  const int64_t h = (n_v - 1) / 2;  // min(j, n_v - 1 - j) = j for j <= h
+  if (x <= h + 1) return x * (x - 1) / 2;
+  const int64_t lo = h * (h + 1) / 2;
+  // sum_{j = h + 1}^{x - 1} (n_v - 1 - j) = sum_{t = n_v - x}^{n_v - 2 - h} t
+  const int64_t a = n_v - x, b = n_v - 2 - h;
+  return lo + (b * (b + 1) - (a - 1) * a) / 2;
+}
+
+// Tiles of the slabs [j0, j1): slab j has ceil(j / 128) i-blocks times
+// ceil((n_v - 1 - j) / 80) k-blocks, i-block-major.
+struct ClassSched {
+  struct Params {
+    int j0, j1, n_v, nkb;
+    int mrow0;               // first masked row (operand buffer rows after R)
+    const int32_t *missing;  // entries of v_j missing, per slab of the batch
+  };
+  int j, j0, j1, n_v, nkb, mrow0;
+  const int32_t *missing_;
+  int mt, nt, m, n;
+  bool valid;
+
+  __device__ void set_slab() {
+    mt = static_cast<int>(cdiv(j, kSnpI));
+    nt = static_cast<int>(cdiv(n_v - 1 - j, kSnpK));
+  }
+  __device__ void skip_empty() {
+    while (j < j1) {
+      set_slab();
+      if (mt > 0 && nt > 0) return;
+      ++j;
+    }
+    valid = false;
+  }
+  __device__ void init(const Params &p, int64_t start) {
+    j = j0 = p.j0;
+    j1 = p.j1;
+    n_v = p.n_v;
+    nkb = p.nkb;
+    mrow0 = p.mrow0;
+    missing_ = p.missing;
+    m = n = 0;
+    valid = true;
+    skip_empty();
+    advance(start);
+  }
+  __device__ void advance(int64_t step) {
+    while (valid && step > 0) {
+      const int64_t pos = static_cast<int64_t>(m) * nt + n;
+      const int64_t rem = static_cast<int64_t>(mt) * nt - 1 - pos;
+      if (step <= rem) {
+        m = static_cast<int>((pos + step) / nt);
+        n = static_cast<int>((pos + step) % nt);
+        return;
+      }
+      step -= rem + 1;
+      ++j;
+      m = n = 0;
+      skip_empty();
+    }
+  }
+  __device__ int i0() const { return kSnpI * m; }
+  __device__ int k0() const { return j + 1 + kSnpK * n; }
+  // Accumulator columns of the tile: 2 per SNP k, rounded up to 32.
+  __device__ int ncols() const {
+    const int nk = min(kSnpK, n_v - k0());
+    return (2 * nk + 31) / 32 * 32;
+  }
+  __device__ int slab() const { return j - j0; }
+  // The masked operand holds the side of the slab with fewer SNPs: i < j when
+  // 2 j <= n_v - 1, else k > j.
+  __device__ bool i_masked() const { return 2 * j <= n_v - 1; }
+  __device__ int side() const { return min(j, n_v - 1 - j); }
+  // First row of slab j's masked rows in the operand buffer.
+  __device__ int mrow() const { return mrow0 + static_cast<int>(4 * (mask_prefix(j, n_v) - mask_prefix(j0, n_v))); }
+  __device__ int missing() const { return __ldg(missing_ + (j - j0)); }
+  // k-blocks of the D phase, and whether they run over all of R (masked).
+  __device__ int d_blocks(bool *full) const {
+    const int c = missing();
+    *full = c > kCap;
+    return *full ? nkb : static_cast<int>(cdiv(c, kBK));
+  }
+};
+
+// Per-byte masks of 16 individuals from their 2-bit codes w (code t at bits
+// 2t, 2t+1): keep[g] has byte b = 0xFF where the selected class holds for
+// individual 4g + b, neg[g] byte b = 0x80 where the sign flips.
+__device__ __forceinline__ uint32_t spread4(uint32_t bits) {
+  // bits 0, 2, 4, 6 -> bytes 0..3 (value 0 or 1)
+  return (bits & 1u) | ((bits & 4u) << 6) | ((bits & 16u) << 12) | ((bits & 64u) << 18);
+}
+
+__device__ __forceinline__ void class_masks(uint32_t w, bool missing_mode, uint32_t (&keep)[4],
+                                            uint32_t (&neg)[4]) {
+  uint32_t kb, nb;
+  if (!missing_mode) {
+    kb = ~(w ^ (w >> 1)) & 0x55555555u;  // codes 00 and 11 (homozygous)
+    nb = w & (w >> 1) & 0x55555555u;     // code 11: s_j = -1
+  } else {
+    kb = (w >> 1) & ~w & 0x55555555u;  // code 10: missing
+    nb = 0u;
+  }
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const uint32_t yk = spread4((kb >> (8 * g)) & 0x55u);
+    const uint32_t yn = spread4((nb >> (8 * g)) & 0x55u);
+    keep[g] = (yk << 8) - yk;
+    neg[g] = yn << 7;
+  }
+}
+
+struct ClassArgs {
+  Tally3Args t;
+  const int32_t *rtab;  // 2-way tallies [pair][4]
+};
+
+__global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
+    k_tally3_class(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmCA, const __grid_constant__ CUtensorMap tmCB,
+                   const ClassArgs args, ClassSched::Params sp) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kABytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kStages * kBBytes);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int32_t *status = args.t.status;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * kStages + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * kStages + 2 + a); };
+  const uint32_t dempty_bar = bar0 + 8u * (2 * kStages + 4);
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 5);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    // The leader's tempty / dempty gather its own epilogue warps and one
+    // forwarded arrival from the follower, whose tempty gathers its warps.
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), leader ? kEpiWarps + 1 : kEpiWarps);
+    }
+    mbar_init(dempty_bar, kEpiWarps + 1);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    tma_prefetch_desc(&tmCA);
+    tma_prefetch_desc(&tmCB);
+  }
+  if (warp == 1) {
+    tcp::tmem_alloc_pair(smem_u32(tmem_slot), 512);
+    tcp::tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int64_t cstart = blockIdx.x >> 1;
+  const int64_t cstep = gridDim.x >> 1;
+  const int64_t n_v = args.t.n_v;
+  const int nkb = sp.nkb;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs)
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_parity[kStages];
+      for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
+      bool ok = true;
+      ClassSched sc;
+      // One k-block: wait for the stage, expect the bytes (leader), load A and B.
+      auto step = [&](const CUtensorMap *ma, int ya, const CUtensorMap *mb, int yb, int x) -> bool {
+        if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, status, abort_flag)) return false;
+        if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * (kABytes + kBBytes));
+        const uint32_t fb = map_to_rank(full_bar(stage), 0);
+        tcp::tma_load_2d_pair(smem_u32(sA + stage * kABytes), ma, x, ya, fb);
+        tcp::tma_load_2d_pair(smem_u32(sB + stage * kBBytes), mb, x, yb, fb);
+        last_parity[stage] = static_cast<int>(phase);
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        return true;
+      };
+      for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep)) {
+        const int half_n = sc.ncols() / 2;
+        const int ia = 2 * (sc.i0() + 64 * static_cast<int>(rank));  // i-side row offset
+        const int kb_row = static_cast<int>(rank) * half_n;         // k-side row offset
+        const int mrow = sc.mrow();
+        const int side2 = 2 * sc.side();
+        const bool im = sc.i_masked();
+        // T: the masked side from the masked rows, the other side from R.
+        const int ya = im ? mrow + ia : ia;
+        const int yb = im ? 2 * sc.k0() + kb_row : mrow + 2 * (sc.k0() - sc.j - 1) + kb_row;
+        for (int kb = 0; kb < nkb && ok; ++kb) ok = step(&tmA, ya, &tmB, yb, kb * kBK);
+        bool dfull;
+        const int nd = sc.d_blocks(&dfull);
+        if (dfull) {
+          // D over all individuals: the missing-masked rows follow the s_j rows.
+          const int yda = im ? ya + side2 : ya;
+          const int ydb = im ? yb : yb + side2;
+          for (int kb = 0; kb < nd && ok; ++kb) ok = step(&tmA, yda, &tmB, ydb, kb * kBK);
+        } else {
+          const int cb = sc.slab() * static_cast<int>(2 * n_v);
+          for (int kb = 0; kb < nd && ok; ++kb)
+            ok = step(&tmCA, cb + ia, &tmCB, cb + 2 * sc.k0() + kb_row, kb * kBK);
+        }
+      }
+      if (!ok) {
+        if (leader) {
+          for (int s = 0; s < kStages; ++s)
+            if (last_parity[s] >= 0)
+              mbar_wait_timeout(full_bar(s), static_cast<uint32_t>(last_parity[s]));
+        } else {
+          const uint64_t t0 = global_timer_ns();
+          while (global_timer_ns() - t0 < 1000000ull) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      // ---------------- MMA issuer (leader CTA)
+      int stage = 0;
+      uint32_t phase = 0;
+      int lt = 0;
+      bool ok = true;
+      ClassSched sc;
+      auto kblock = [&](uint32_t d_tmem, uint32_t idesc, bool first) -> bool {
+        if (!mbar_wait_bounded(full_bar(stage), phase, status, abort_flag)) return false;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + stage * kABytes);
+        const uint32_t b0 = smem_u32(sB + stage * kBBytes);
+#pragma unroll
+        for (int k = 0; k < kBK / kUK; ++k)
+          tcp::mma_f8f6f4_pair(d_tmem, smem_desc_sw128(a0 + k * kUK), smem_desc_sw128(b0 + k * kUK),
+                               idesc, (!first || k != 0) ? 1u : 0u);
+        tcp::mma_commit_pair(empty_bar(stage), 0x3);
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        return true;
+      };
+      for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep), ++lt) {
+        const int acc = lt & 1;
+        if (!mbar_wait_cluster_bounded(tempty_bar(acc), ((lt >> 1) & 1) ^ 1u, status, abort_flag))
+          break;
+        tc_fence_after();
+        const uint32_t idesc = idesc_e4m3_f32(256, static_cast<uint32_t>(sc.ncols()));
+        const uint32_t t_tmem = tmem_base + (acc ? kColT1 : kColT0);
+        for (int kb = 0; kb < nkb && ok; ++kb) ok = kblock(t_tmem, idesc, kb == 0);
+        if (!ok) break;
+        bool dfull;
+        const int nd = sc.d_blocks(&dfull);
+        if (nd > 0) {
+          if (!mbar_wait_cluster_bounded(dempty_bar, (lt & 1) ^ 1u, status, abort_flag)) break;
+          tc_fence_after();
+          for (int kb = 0; kb < nd && ok; ++kb) ok = kblock(tmem_base + kColD, idesc, kb == 0);
+          if (!ok) break;
+        }
+        tcp::mma_commit_pair(tfull_bar(acc), 0x3);
+      }
+      tcp::mma_commit_pair(drain_bar, 0x1);
+      mbar_wait_timeout(drain_bar, 0);
+    } else if (lane == 0) {
+      // ---------------- follower: forward the epilogue's release to the leader
+      int lt = 0;
+      ClassSched sc;
+      for (sc.init(sp, cstart); sc.valid; sc.advance(cstep), ++lt) {
+        const int acc = lt & 1;
+        if (!mbar_wait_bounded(tempty_bar(acc), (lt >> 1) & 1, status, abort_flag)) break;
+        tc_fence_before();
+        mbar_arrive_cluster(map_to_rank(dempty_bar, 0));
+        mbar_arrive_cluster(map_to_rank(tempty_bar(acc), 0));
+      }
+    }
+  } else {
+    // ---------------- epilogue (both CTAs)
+    const int ew = warp - 2;  // 0..7
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int L = quarter * 32 + lane;  // TMEM lane = A row of this CTA
+    const int a = L & 1;
+    const int32_t *__restrict__ rtab = args.rtab;
+    const float *__restrict__ wv = args.t.w;
+    int4 *__restrict__ tally_out = reinterpret_cast<int4 *>(args.t.tally);
+    float4 *__restrict__ ccc_out = reinterpret_cast<float4 *>(args.t.ccc);
+    const bool want_ccc = ccc_out != nullptr;
+    const bool persnp = args.t.norm == CCC_NORM_PERSNP;
+    const float gamma = args.t.gamma;
+    const int64_t s_begin = slab_offset_dev(args.t.j_begin, n_v);
+    int lt = 0;
+    ClassSched sc;
+    for (sc.init(sp, cstart); sc.valid; sc.advance(cstep), ++lt) {
+      const int acc = lt & 1;
+      const bool got = mbar_wait_bounded(tfull_bar(acc), (lt >> 1) & 1, status, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      const int64_t j = sc.j;
+      const int64_t i = sc.i0() + 64 * static_cast<int64_t>(rank) + (L >> 1);
+      const bool row_ok = i < j;
+      const int ncols = sc.ncols();
+      const int64_t k_first = sc.k0();
+      bool dfull;
+      const bool has_d = sc.d_blocks(&dfull) > 0;
+      int nch = (ncols - kNMax / 2 * half) / 16;
+      nch = nch < 0 ? 0 : (nch > 5 ? 5 : nch);
+      const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16);
+      const uint32_t t_x = lane_base + (acc ? kColT1 : kColT0);
+      const uint32_t t_d = lane_base + kColD;
+      // The accumulators of this tile have been read: the leader's warps arrive
+      // on its barriers, the follower's on its own tempty (forwarded by warp 1).
+      auto release = [&]() {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (leader) mbar_arrive(dempty_bar);
+          mbar_arrive(tempty_bar(acc));
+        }
+      };
+      if (nch == 0) {
+        release();
+        continue;
+      }
+      const int64_t span = n_v - 1 - j;
+      const int64_t base = slab_offset_dev(j, n_v) - s_begin + i * span - (j + 1);
+      const int64_t pbase = i * (2 * n_v - i - 1) / 2 - i - 1;  // pair (i, k) at pbase + k
+      float wi = 1.f, wj0 = 1.f, wj1 = 1.f;
+      if (want_ccc && persnp) {
+        if (row_ok) wi = __ldg(wv + 2 * i + a);
+        wj0 = __ldg(wv + 2 * j);
+        wj1 = __ldg(wv + 2 * j + 1);
+      }
+      for (int c = 0; c < nch; ++c) {
+        const int col = kNMax / 2 * half + 16 * c;
+        const int64_t kc = k_first + col / 2;
+        uint32_t x[16], d[16];
+        tmem_ld_32x32b_x16(t_x + col, x);
+        if (has_d) tmem_ld_32x32b_x16(t_d + col, d);
+        // Every global load of the chunk is issued before its stores.
+        int2 r[8];
+        float2 wk[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int64_t k = kc + kk;
+          const bool ok = row_ok && k < n_v;
+          r[kk] = ok ? __ldg(reinterpret_cast<const int2 *>(rtab + 4 * (pbase + k)) + a)
+                     : make_int2(0, 0);
+          wk[kk] = (ok && want_ccc && persnp) ? __ldg(reinterpret_cast<const float2 *>(wv) + k)
+                                              : make_float2(1.f, 1.f);
+        }
+        tmem_ld_wait();
+        if (!has_d) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) d[e] = 0u;
+        }
+        if (c == nch - 1) release();
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int64_t k = kc + kk;
+          const bool ok = row_ok && k < n_v;
+          const int32_t t0 = __float2int_rn(__uint_as_float(x[2 * kk]));
+          const int32_t t1 = __float2int_rn(__uint_as_float(x[2 * kk + 1]));
+          const int32_t d0 = __float2int_rn(__uint_as_float(d[2 * kk]));
+          const int32_t d1 = __float2int_rn(__uint_as_float(d[2 * kk + 1]));
+          const int32_t u0 = r[kk].x - d0, u1 = r[kk].y - d1;
+          // r^{a b c}: b0c0, b0c1, b1c0, b1c1
+          const int4 tv = make_int4(u0 + t0, u1 + t1, u0 - t0, u1 - t1);
+          const int64_t t = base + k;
+          if (ok) __stcs(tally_out + 2 * t + a, tv);
+          if (want_ccc) {
+            const int32_t own = tv.x + tv.y + tv.z + tv.w;  // sum over b, c (fixed a)
+            const int32_t n8 = own + __shfl_xor_sync(0xffffffffu, own, 1);
+            const int32_t b0 = tv.x + tv.y, b1 = tv.z + tv.w;
+            const int32_t c0 = tv.x + tv.z, c1 = tv.y + tv.w;
+            const int32_t rb0 = b0 + __shfl_xor_sync(0xffffffffu, b0, 1);
+            const int32_t rb1 = b1 + __shfl_xor_sync(0xffffffffu, b1, 1);
+            const int32_t q0 = c0 + __shfl_xor_sync(0xffffffffu, c0, 1);
+            const int32_t q1 = c1 + __shfl_xor_sync(0xffffffffu, c1, 1);
+            if (ok) {
+              float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (n8 != 0) {
+                const float dn = static_cast<float>(n8);
+                float fi = wi, fj0 = wj0, fj1 = wj1, fk0 = wk[kk].x, fk1 = wk[kk].y;
+                if (!persnp) {
+                  fi = joint_factor(own, dn, gamma);
+                  fj0 = joint_factor(rb0, dn, gamma);
+                  fj1 = joint_factor(rb1, dn, gamma);
+                  fk0 = joint_factor(q0, dn, gamma);
+                  fk1 = joint_factor(q1, dn, gamma);
+                }
+                out.x = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.x), dn), fi), fj0), fk0);
+                out.y = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.y), dn), fi), fj0), fk1);
+                out.z = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.z), dn), fi), fj1), fk0);
+                out.w = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.w), dn), fi), fj1), fk1);
+              }
+              __stcs(ccc_out + 2 * t + a, out);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  if (warp == 1) tcp::tmem_dealloc_pair(tmem_base, 512);
+}
+
+// Per slab j of [j0, j0 + gridDim.x): the individuals with v_j missing (first
+// kCap of them, in order) and their count; when there are at most kCap, the
+// rows 2 s + x (x = allele) of every SNP s restricted to those individuals,
+// as e4m3 counts rho_s(x), zero-padded to a multiple of 128 columns:
+// cbuf[(slab * 2 n_v + 2 s + x) * kCap + column].
+__global__ void __launch_bounds__(256) k_compact3(const uint64_t *__restrict__ geno, int64_t n_f,
+                                                  int64_t n_v, int64_t ld, int64_t j0,
+                                                  uint8_t *__restrict__ cbuf,
+                                                  int32_t *__restrict__ missing, int snps_per_cta) {
+  __shared__ int pos[kCap];
+  __shared__ int warp_tot[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t j = j0 + blockIdx.x;
+  const int64_t nw = (n_f + 31) / 32;
+  int running = 0;
+  for (int64_t base = 0; base < nw; base += 256) {
+    const int64_t wi = base + tid;
+    uint64_t miss = 0;
+    if (wi < nw) {
+      const uint64_t v = geno[j * ld + wi];
+      uint64_t valid = kEven;
+      const int64_t tail = n_f - wi * 32;
+      if (tail < 32) valid &= (1ull << (2 * tail)) - 1ull;
+      miss = (v >> 1) & ~v & valid;
+    }
+    const int c = __popcll(miss);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    int before = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      before += q < warp ? warp_tot[q] : 0;
+      tot += warp_tot[q];
+    }
+    int o = running + before + x - c;
+    while (miss != 0 && o < kCap) {
+      const int b = __ffsll(static_cast<long long>(miss)) - 1;
+      pos[o++] = static_cast<int>(wi * 32 + (b >> 1));
+      miss &= miss - 1;
+    }
+    running += tot;
+    __syncthreads();
+  }
+  if (blockIdx.y == 0 && tid == 0) missing[blockIdx.x] = running;
+  if (running == 0 || running > kCap) return;
+  const int ncols = (running + kBK - 1) / kBK * kBK;
+  const int64_t s_lo = static_cast<int64_t>(blockIdx.y) * snps_per_cta;
+  const int64_t s_hi = s_lo + snps_per_cta < n_v ? s_lo + snps_per_cta : n_v;
+  for (int64_t s = s_lo + warp; s < s_hi; s += 8) {
+    uint8_t *row0 = cbuf + (static_cast<int64_t>(blockIdx.x) * 2 * n_v + 2 * s) * kCap;
+    for (int idx = lane; idx < ncols; idx += 32) {
+      uint32_t code = 2u;  // missing: both counts 0
+      if (idx < running) {
+        const int q = pos[idx];
+        code = static_cast<uint32_t>(__ldg(geno + s * ld + (q >> 5)) >> (2 * (q & 31))) & 3u;
+      }
+      // e4m3: 0 -> 0x00, 1 -> 0x38, 2 -> 0x40
+      const uint8_t e0 = code == 0u ? 0x40 : (code == 1u ? 0x38 : 0x00);
+      const uint8_t e1 = code == 3u ? 0x40 : (code == 1u ? 0x38 : 0x00);
+      row0[idx] = e0;
+      row0[kCap + idx] = e1;
+    }
+  }
+}
+
+// Masked rows of the slabs [j0, j0 + gridDim.y): for slab j, the SNPs s of
+// its smaller side (s < j when 2 j <= n_v - 1, else s > j), rows
+//   mrow(j) + 2 t + x             = R(s, x) * s_j        (t = index of s on that side)
+//   mrow(j) + 2 side + 2 t + x    = R(s, x) * [v_j missing]  (only when v_j has
+//                                                          more than kCap missing)
+// in the operand buffer op (rows of kpad bytes; R occupies the first rows).
+// A CTA takes every gridDim.x-th row of its slab; a thread 16 bytes at a time.
+__global__ void __launch_bounds__(256) k_mask3c(const uint64_t *__restrict__ geno, int64_t n_f,
+                                                int64_t n_v, int64_t ld, uint8_t *__restrict__ op,
+                                                int64_t kpad, int64_t mrow0, int64_t j0,
+                                                const int32_t *__restrict__ missing) {
+  const int64_t j = j0 + blockIdx.y;
+  const int64_t side = j < n_v - 1 - j ? j : n_v - 1 - j;
+  const bool im = 2 * j <= n_v - 1;
+  const bool dfull = __ldg(missing + blockIdx.y) > kCap;
+  const int64_t rows = (dfull ? 4 : 2) * side;
+  const int chunks = static_cast<int>(kpad / 16);
+  const int64_t mrow = mrow0 + 4 * (mask_prefix(j, n_v) - mask_prefix(j0, n_v));
+  const int64_t words = (n_f + 31) / 32;
+  const uint64_t *__restrict__ gj = geno + j * ld;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const bool dmask = r >= 2 * side;
+    const int64_t rt = dmask ? r - 2 * side : r;
+    const int64_t s = im ? (rt >> 1) : j + 1 + (rt >> 1);
+    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(op + (2 * s + (rt & 1)) * kpad);
+    uint4 *__restrict__ dst = reinterpret_cast<uint4 *>(op + (mrow + r) * kpad);
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+      const int wi = c >> 1;
+      uint32_t w = 0u;
+      if (wi < words) w = static_cast<uint32_t>(__ldg(gj + wi) >> (32 * (c & 1)));
+      uint32_t keep[4], neg[4];
+      class_masks(w, dmask, keep, neg);
+      const uint4 v = __ldg(src + c);
+      uint4 o;
+      o.x = (v.x & keep[0]) | neg[0];
+      o.y = (v.y & keep[1]) | neg[1];
+      o.z = (v.z & keep[2]) | neg[2];
+      o.w = (v.w & keep[3]) | neg[3];
+      dst[c] = o;
+    }
+  }
+}
+
+}  // namespace
+
+int64_t tc3_class_cbuf_rows(int64_t n_slabs, int64_t n_v) { return n_slabs * 2 * n_v; }
+int64_t tc3_class_cap() { return kCap; }
+int64_t tc3_class_mask_rows(int64_t j0, int64_t j1, int64_t n_v) {
+  return 4 * (mask_prefix(j1, n_v) - mask_prefix(j0, n_v));
+}
+
+int launch_compact3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *cbuf,
+                    int32_t *missing, int64_t j0, int64_t j1, cudaStream_t s) {
+  if (j1 <= j0) return CCC_OK;
+  const int snps_per_cta = 64;
+  const dim3 grid(static_cast<unsigned>(j1 - j0), static_cast<unsigned>(cdiv(n_v, snps_per_cta)), 1);
+  k_compact3<<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, j0, cbuf, missing, snps_per_cta);
+  return note_launch();
+}
+
+int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                  int64_t kpad, int64_t mrow0, const int32_t *missing, int64_t j0, int64_t j1,
+                  cudaStream_t s) {
+  if (j1 <= j0) return CCC_OK;
+  // About 4 CTAs per SM in total; each slab's rows are spread over bx CTAs.
+  int64_t bx = cdiv(4 * 160, j1 - j0);
+  if (bx < 2) bx = 2;
+  if (bx > 256) bx = 256;
+  const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(j1 - j0), 1);
+  k_mask3c<<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, op, kpad, mrow0, j0, missing);
+  return note_launch();
+}
+
+int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows, int64_t mrow0,
+                        int64_t kpad, const int32_t *rtab, const uint8_t *cbuf,
+                        const int32_t *missing, int64_t j0, int64_t j1, int num_sms,
+                        cudaStream_t s) {
+  if (j1 <= j0) return CCC_OK;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_tally3_class, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes)) != cudaSuccess)
+      return CCC_ECUDA;
+    attr_set = true;
+  }
+  int64_t tiles = 0;
+  for (int64_t j = j0; j < j1; ++j) tiles += cdiv(j, kSnpI) * cdiv(a.n_v - 1 - j, kSnpK);
+  if (tiles == 0) return CCC_OK;
+  CUtensorMap tmA, tmB, tmCA, tmCB;
+  const int64_t crows = tc3_class_cbuf_rows(j1 - j0, a.n_v);
+  if (!tc::make_operand_map(&tmA, op, op_rows, kpad, 128) ||
+      !tc::make_operand_map(&tmB, op, op_rows, kpad, kBRows) ||
+      !tc::make_operand_map(&tmCA, cbuf, crows, kCap, 128) ||
+      !tc::make_operand_map(&tmCB, cbuf, crows, kCap, kBRows))
+    return CCC_ECUDA;
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tally3_class, &cfg) != cudaSuccess || n < 1)
+      return CCC_ECUDA;
+    max_clusters = n < num_sms / 2 ? n : num_sms / 2;
+  }
+  const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
+  ClassArgs ca;
+  ca.t = a;
+  ca.rtab = rtab;
+  ClassSched::Params sp;
+  sp.j0 = static_cast<int>(j0);
+  sp.j1 = static_cast<int>(j1);
+  sp.n_v = static_cast<int>(a.n_v);
+  sp.nkb = static_cast<int>(kpad / kBK);
+  sp.mrow0 = static_cast<int>(mrow0);
+  sp.missing = missing;
+  k_tally3_class<<<static_cast<unsigned>(2 * clusters), kThreads, kSmemBytes, s>>>(tmA, tmB, tmCA,
+                                                                                   tmCB, ca, sp);
+  return note_launch();
+}
+
+}  // namespace ccc

@@ -104,6 +104,28 @@ def test_workspace_size(lib):
         ccc.ccc_workspace_size((10, 2), 10, o, ccc.CCC_OP_2WAY)
 
 
+def test_workspace_size_3way_variants(lib):
+    """3-way tile variants: the genotype-class route (automatic, tile 3) holds the 2-way
+    tallies of all pairs and per-slab compacted rows (2 n_v rows x 256 bytes); the
+    masked-operand route (tile 1) holds L_j batches; tile 3 is not a 2-way variant."""
+    n_v, ld, n_f = 1536, 256, 8192
+    sizes = {}
+    for tile in (0, 1, 2, 3):
+        o = ccc.ccc_opts_default(tile=tile)
+        sizes[tile] = ccc.ccc_workspace_size((n_v, ld), n_f, o, ccc.CCC_OP_3WAY)
+    assert sizes[0] == sizes[3]
+    assert sizes[3] >= 16 * n_v * (n_v - 1) // 2 + n_v * 2 * n_v * 256
+    assert sizes[2] < sizes[1] and sizes[2] < sizes[3]
+    o = ccc.ccc_opts_default(tile=3)
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_workspace_size((n_v, ld), n_f, o, ccc.CCC_OP_2WAY)
+    assert e.value.status == ccc.CCC_EINVAL
+    o.tile = 4
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_workspace_size((n_v, ld), n_f, o, ccc.CCC_OP_3WAY)
+    assert e.value.status == ccc.CCC_EINVAL
+
+
 def test_argument_errors_before_device_work(lib):
     o = ccc.ccc_opts_default()
     P = ctypes.POINTER

@@ -12,9 +12,9 @@ from tests.gpu_util import assert_ccc_close, assert_tally_equal, run_3way
 
 pytestmark = pytest.mark.gpu
 
-# (path, tile): tensor cores with the masked operand formed in shared memory (default),
-# tensor cores with the masked operand formed in HBM first, popcount.
-PATHS = [(0, 0), (0, 1), (1, 0)]
+# (path, tile): tensor cores by genotype classes of v_j on SM pairs (default), tensor cores
+# with the masked operand L_j formed in HBM first, L_j formed in shared memory, popcount.
+PATHS = [(0, 0), (0, 1), (0, 2), (1, 0)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -81,11 +81,35 @@ def test_degenerate_snps(path):
     _check(geno, n_f, path, norm=1)
 
 
+@pytest.mark.parametrize("path", PATHS)
+def test_missing_counts_around_the_compaction_capacity(path):
+    """SNPs with exactly 0, 1, 127, 128, 129, 255, 256, 257, 400 and all 600 entries
+    missing: the class kernel restricts the missing-column product to 128-column blocks
+    of at most 256 individuals and masks all of R beyond that."""
+    n_f = 600
+    counts = [0, 1, 127, 128, 129, 255, 256, 257, 400, 600]
+    g = synth.genotypes_uniform(7, 0, np.arange(3 * len(counts)), n_f, 0.0)
+    rng = np.random.default_rng(12)
+    for s, m in enumerate(counts):
+        g[3 * s, rng.choice(n_f, size=m, replace=False)] = -1
+    geno = synth.pack(synth.codes_from_genotypes(g), pad_seed=4)
+    _check(geno, n_f, path)
+    _check(geno, n_f, path, 5, 21, norm=1)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("p_missing", [0.0, 0.35])
+def test_missing_rates(path, p_missing):
+    geno = synth.panel_hwe(150, 700, seed=13, p_missing=p_missing, pad_seed=5)
+    _check(geno, 700, path)
+
+
 def test_at_scale_tc_equals_popc_and_oracle_rows():
     """1,536 SNPs x 8,192 individuals (Hardy-Weinberg, 1% missing), all 602,800,640
-    triples: tensor-core tallies equal the popcount tallies (tallies reach 8 n_f =
-    65,536), CCC values agree, and sampled (i, j) rows equal the oracle.  The masked
-    operands of this size span many slab batches."""
+    triples: the genotype-class tallies (default) equal the popcount tallies and the
+    masked-operand tallies (tallies reach 8 n_f = 65,536), CCC values agree, and sampled
+    (i, j) rows equal the oracle.  The masked operands of this size span many slab
+    batches."""
     import torch
 
     import paper_1705_08213_gb300 as ccc
@@ -104,7 +128,7 @@ def test_at_scale_tc_equals_popc_and_oracle_rows():
         ccc.ccc3_tally_metric(g, n_f, 0, n_v, tally, out, opts)
         torch.cuda.synchronize()
         assert ccc.ccc_status(opts) == ccc.CCC_OK
-        if tile == 1:  # the HBM-prepass route must equal the fused one
+        if tile == 1:  # the masked-operand route must equal the class route
             assert torch.equal(tally, outs[0][0])
             assert torch.equal(out, outs[0][1])
             del tally, out
