@@ -92,6 +92,7 @@ struct Layout {
   size_t rtab = 0;            // int32 [pairs][4] 2-way tallies (3-way classes)
   size_t cbuf = 0;            // compacted count rows per slab (3-way classes)
   size_t missing = 0;         // int32 [cbuf_slabs] missing entries of v_j
+  size_t dscratch = 0;        // D counts of the wide class tiles in flight
   size_t total = 0;
   int64_t kpad = 0, rows_pad = 0, w64 = 0, lop_rows = 0, cbuf_slabs = 0;
   int64_t mask_rows = 0;      // masked rows after R in op (3-way classes)
@@ -149,6 +150,8 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
         off = align_up(off + static_cast<size_t>(nb) * static_cast<size_t>(per_slab), 1024);
         L.missing = off;
         off = align_up(off + sizeof(int32_t) * static_cast<size_t>(nb), kAlign);
+        L.dscratch = off;
+        off = align_up(off + static_cast<size_t>(tc3_class_dscratch_bytes()), kAlign);
       } else if (op == CCC_OP_3WAY && tile == 1) {
         // Masked operands of as many slabs as fit in kLopBytes, but at least
         // the largest slab (j = n_v - 2).
@@ -409,7 +412,8 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
                             s));
       const int slot = timing_begin(s);
       const int rc = launch_tally3_class(a, op, L.rows_pad + L.mask_rows, L.rows_pad, L.kpad, rtab,
-                                         cbuf, missing, j0, j1, dev.sms, s);
+                                         cbuf, missing, at<uint32_t>(o, L.dscratch), j0, j1,
+                                         dev.sms, s);
       timing_end(slot, s);
       if (rc != CCC_OK) return rc;
       j0 = j1;

@@ -118,10 +118,13 @@ int launch_compact3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, 
 int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                   int64_t kpad, int64_t mrow0, const int32_t *missing, int64_t j0, int64_t j1,
                   cudaStream_t s);
+//                    dscratch (tc3_class_dscratch_bytes()) holds the D counts
+//                    of the tiles in flight when n_f <= 16383.
+int64_t tc3_class_dscratch_bytes();
 int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows, int64_t mrow0,
                         int64_t kpad, const int32_t *rtab, const uint8_t *cbuf,
-                        const int32_t *missing, int64_t j0, int64_t j1, int num_sms,
-                        cudaStream_t s);
+                        const int32_t *missing, uint32_t *dscratch, int64_t j0, int64_t j1,
+                        int num_sms, cudaStream_t s);
 int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
 int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
                    int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);

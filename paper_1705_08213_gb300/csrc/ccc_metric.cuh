@@ -6,7 +6,9 @@
 //   JOINT  factor w = (n - gamma R) / n         gamma's own rounding (amplified at most 2x,
 //                                               i.e. <= u) + fma + division = 3u
 //   products f * w_i * w_j (* w_k)              2 (3) roundings
-// Worst case: 2-way 5u (PERSNP) / 9u (JOINT); 3-way 7u / 13u = 7.8e-7 < 1e-6.
+//   3-way PERSNP evaluates ((r * (1/n)) * (w_i w_j)) * w_k: 1/n, r * (1/n),
+//   w_i w_j and two products, 5 roundings besides the three factors'.
+// Worst case: 2-way 5u (PERSNP) / 9u (JOINT); 3-way 8u / 13u = 7.8e-7 < 1e-6.
 // There is no cancellation: every factor is at least 1 - gamma >= 1/3 for gamma <= 2/3.
 #pragma once
 
@@ -39,6 +41,11 @@ __device__ __forceinline__ float4 ccc2_values(int32_t r00, int32_t r01, int32_t 
   return c;
 }
 
+// 3-way PERSNP value from the tally r, 1/n (rounded), w_i w_j (rounded) and w_k.
+__device__ __forceinline__ float ccc3_persnp(int32_t r, float inv_n, float wij, float wk) {
+  return __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r), inv_n), wij), wk);
+}
+
 // r[abc] with a most significant; wi/wj/wk per-SNP factors (PERSNP).
 __device__ __forceinline__ void ccc3_values(const int32_t (&r)[8], float wi0, float wi1,
                                             float wj0, float wj1, float wk0, float wk1,
@@ -61,6 +68,13 @@ __device__ __forceinline__ void ccc3_values(const int32_t (&r)[8], float wi0, fl
     wk1 = joint_factor(r[1] + r[3] + r[5] + r[7], d, gamma);
   }
   const float wi[2] = {wi0, wi1}, wj[2] = {wj0, wj1}, wk[2] = {wk0, wk1};
+  if (norm != CCC_NORM_JOINT) {
+    const float inv = __frcp_rn(d);
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      out[t] = ccc3_persnp(r[t], inv, __fmul_rn(wi[t >> 2], wj[(t >> 1) & 1]), wk[t & 1]);
+    return;
+  }
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const float f = __fdiv_rn(static_cast<float>(r[t]), d);

@@ -165,8 +165,15 @@ struct Epi3 {
                 fk0 = joint_factor(q0, d, args.gamma);
                 fk1 = joint_factor(q1, d, args.gamma);
               }
-              out.x = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r0), d), fi), fj), fk0);
-              out.y = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r1), d), fi), fj), fk1);
+              if (persnp) {
+                const float inv = __frcp_rn(d);
+                const float wij = __fmul_rn(fi, fj);
+                out.x = ccc3_persnp(r0, inv, wij, fk0);
+                out.y = ccc3_persnp(r1, inv, wij, fk1);
+              } else {
+                out.x = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r0), d), fi), fj), fk0);
+                out.y = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r1), d), fi), fj), fk1);
+              }
             }
             __stcs(reinterpret_cast<float2 *>(args.ccc) + 4 * t + ab, out);
           }

@@ -52,7 +52,7 @@ constexpr int kUK = 32;               // K per MMA
 constexpr int kABytes = 128 * kBK;    // A rows per CTA x 128 bytes
 constexpr int kBRows = kNMax / 2;     // B rows per CTA
 constexpr int kBBytes = kBRows * kBK;
-constexpr int kStages = 6;
+constexpr int kStages = 8;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kCap = 256;             // compacted missing columns per slab
@@ -125,8 +125,9 @@ __host__ __device__ inline int64_t mask_prefix(int64_t x, int64_t n_v) {
 }
 
 // Tiles of the slabs [j0, j1): slab j has ceil(j / 128) i-blocks times
-// ceil((n_v - 1 - j) / 80) k-blocks, i-block-major.
-struct ClassSched {
+// ceil((n_v - 1 - j) / SNPK) k-blocks, i-block-major.
+template <int SNPK>
+struct ClassSchedT {
   struct Params {
     int j0, j1, n_v, nkb;
     int mrow0;               // first masked row (operand buffer rows after R)
@@ -139,7 +140,7 @@ struct ClassSched {
 
   __device__ void set_slab() {
     mt = static_cast<int>(cdiv(j, kSnpI));
-    nt = static_cast<int>(cdiv(n_v - 1 - j, kSnpK));
+    nt = static_cast<int>(cdiv(n_v - 1 - j, SNPK));
   }
   __device__ void skip_empty() {
     while (j < j1) {
@@ -177,10 +178,10 @@ struct ClassSched {
     }
   }
   __device__ int i0() const { return kSnpI * m; }
-  __device__ int k0() const { return j + 1 + kSnpK * n; }
+  __device__ int k0() const { return j + 1 + SNPK * n; }
   // Accumulator columns of the tile: 2 per SNP k, rounded up to 32.
   __device__ int ncols() const {
-    const int nk = min(kSnpK, n_v - k0());
+    const int nk = min(SNPK, n_v - k0());
     return (2 * nk + 31) / 32 * 32;
   }
   __device__ int slab() const { return j - j0; }
@@ -198,6 +199,7 @@ struct ClassSched {
     return *full ? nkb : static_cast<int>(cdiv(c, kBK));
   }
 };
+using ClassSched = ClassSchedT<kSnpK>;
 
 // Per-byte masks of 16 individuals from their 2-bit codes w (code t at bits
 // 2t, 2t+1): keep[g] has byte b = 0xFF where the selected class holds for
@@ -229,6 +231,7 @@ __device__ __forceinline__ void class_masks(uint32_t w, bool missing_mode, uint3
 struct ClassArgs {
   Tally3Args t;
   const int32_t *rtab;  // 2-way tallies [pair][4]
+  uint32_t *dscratch;   // wide tiles: [cta][2][k][lane] D counts
 };
 
 __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
@@ -326,9 +329,9 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
         // T: the masked side from the masked rows, the other side from R.
         const int ya = im ? mrow + ia : ia;
         const int yb = im ? 2 * sc.k0() + kb_row : mrow + 2 * (sc.k0() - sc.j - 1) + kb_row;
-        for (int kb = 0; kb < nkb && ok; ++kb) ok = step(&tmA, ya, &tmB, yb, kb * kBK);
         bool dfull;
-        const int nd = sc.d_blocks(&dfull);
+        const int nd = sc.d_blocks(&dfull);  // loaded before the T loop needs it
+        for (int kb = 0; kb < nkb && ok; ++kb) ok = step(&tmA, ya, &tmB, yb, kb * kBK);
         if (dfull) {
           // D over all individuals: the missing-masked rows follow the s_j rows.
           const int yda = im ? ya + side2 : ya;
@@ -355,44 +358,55 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   } else if (warp == 1) {
     if (lane == 0 && leader) {
       // ---------------- MMA issuer (leader CTA)
+      // Descriptors of stage 0; a stage and a 32-byte K step only move the
+      // start-address field (address >> 4), so every MMA's descriptors are
+      // one add away from these.
+      const uint64_t dA0 = smem_desc_sw128(smem_u32(sA));
+      const uint64_t dB0 = smem_desc_sw128(smem_u32(sB));
       int stage = 0;
       uint32_t phase = 0;
       int lt = 0;
       bool ok = true;
       ClassSched sc;
-      auto kblock = [&](uint32_t d_tmem, uint32_t idesc, bool first) -> bool {
-        if (!mbar_wait_bounded(full_bar(stage), phase, status, abort_flag)) return false;
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(sA + stage * kABytes);
-        const uint32_t b0 = smem_u32(sB + stage * kBBytes);
-#pragma unroll
-        for (int k = 0; k < kBK / kUK; ++k)
-          tcp::mma_f8f6f4_pair(d_tmem, smem_desc_sw128(a0 + k * kUK), smem_desc_sw128(b0 + k * kUK),
-                               idesc, (!first || k != 0) ? 1u : 0u);
-        tcp::mma_commit_pair(empty_bar(stage), 0x3);
-        if (++stage == kStages) {
-          stage = 0;
-          phase ^= 1u;
-        }
-        return true;
-      };
       for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep), ++lt) {
         const int acc = lt & 1;
         if (!mbar_wait_cluster_bounded(tempty_bar(acc), ((lt >> 1) & 1) ^ 1u, status, abort_flag))
           break;
         tc_fence_after();
         const uint32_t idesc = idesc_e4m3_f32(256, static_cast<uint32_t>(sc.ncols()));
-        const uint32_t t_tmem = tmem_base + (acc ? kColT1 : kColT0);
-        for (int kb = 0; kb < nkb && ok; ++kb) ok = kblock(t_tmem, idesc, kb == 0);
-        if (!ok) break;
         bool dfull;
-        const int nd = sc.d_blocks(&dfull);
-        if (nd > 0) {
-          if (!mbar_wait_cluster_bounded(dempty_bar, (lt & 1) ^ 1u, status, abort_flag)) break;
-          tc_fence_after();
-          for (int kb = 0; kb < nd && ok; ++kb) ok = kblock(tmem_base + kColD, idesc, kb == 0);
-          if (!ok) break;
+        const int nd = sc.d_blocks(&dfull);  // loaded before the T loop needs it
+        for (int phase_d = 0; phase_d < 2 && ok; ++phase_d) {
+          const int nblk = phase_d == 0 ? nkb : nd;
+          if (nblk == 0) continue;
+          if (phase_d == 1) {
+            if (!mbar_wait_cluster_bounded(dempty_bar, (lt & 1) ^ 1u, status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t d_tmem = tmem_base + (phase_d ? kColD : (acc ? kColT1 : kColT0));
+          for (int kb = 0; kb < nblk; ++kb) {
+            if (!mbar_wait_bounded(full_bar(stage), phase, status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t da = dA0 + static_cast<uint64_t>(stage * (kABytes >> 4));
+            const uint64_t db = dB0 + static_cast<uint64_t>(stage * (kBBytes >> 4));
+            tcp::mma_f8f6f4_pair(d_tmem, da, db, idesc, kb != 0 ? 1u : 0u);
+#pragma unroll
+            for (int k = 1; k < kBK / kUK; ++k)
+              tcp::mma_f8f6f4_pair(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), idesc, 1u);
+            tcp::mma_commit_pair(empty_bar(stage), 0x3);
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
         }
+        if (!ok) break;
         tcp::mma_commit_pair(tfull_bar(acc), 0x3);
       }
       tcp::mma_commit_pair(drain_bar, 0x1);
@@ -524,16 +538,494 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
                   fk0 = joint_factor(q0, dn, gamma);
                   fk1 = joint_factor(q1, dn, gamma);
                 }
-                out.x = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.x), dn), fi), fj0), fk0);
-                out.y = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.y), dn), fi), fj0), fk1);
-                out.z = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.z), dn), fi), fj1), fk0);
-                out.w = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.w), dn), fi), fj1), fk1);
+                if (persnp) {
+                  const float inv = __frcp_rn(dn);
+                  const float g0 = __fmul_rn(fi, fj0), g1 = __fmul_rn(fi, fj1);
+                  out.x = ccc3_persnp(tv.x, inv, g0, fk0);
+                  out.y = ccc3_persnp(tv.y, inv, g0, fk1);
+                  out.z = ccc3_persnp(tv.z, inv, g1, fk0);
+                  out.w = ccc3_persnp(tv.w, inv, g1, fk1);
+                } else {
+                  out.x = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.x), dn), fi), fj0), fk0);
+                  out.y = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.y), dn), fi), fj0), fk1);
+                  out.z = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.z), dn), fi), fj1), fk0);
+                  out.w = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.w), dn), fi), fj1), fk1);
+                }
               }
               __stcs(ccc_out + 2 * t + a, out);
             }
           }
         }
       }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  if (warp == 1) tcp::tmem_dealloc_pair(tmem_base, 512);
+}
+
+// ---------------------------------------------------------------------------
+// The same tallies on tiles of 128 SNPs i x 128 SNPs k (N = 256 columns), for
+// n_f <= kWideMaxNf.  A k-block of TMA loads costs about as long as an N = 256
+// MMA k-block on GB300, so wide tiles keep the tensor cores busy where N = 160
+// ones cannot; TMEM then holds only the two T accumulators (2 x 256 columns).
+// The D product of tile u is formed in tile u's own accumulator before its T
+// phase -- issued in the middle of tile u-1's T phase -- and each epilogue
+// thread moves its part of it (16-bit counts, D <= 4 n_f) to its own slots of
+// a small global scratch (two tiles per CTA, 128 KB, L2-resident) before the
+// T phase of tile u overwrites the accumulator.
+namespace wide {
+constexpr int kSnpK = 128;
+constexpr int kN = 256;
+constexpr int kStages = 6;
+constexpr int kTile = 128 * kBK;                  // 128 rows x 128 bytes
+constexpr int kStageBytes = 2 * kTile;            // A + B per CTA
+constexpr int kDWords = 128 * 128;                // per tile: [k (0..127)][lane] x (u16 c = 0, u16 c = 1)
+constexpr int kMaxCtas = 256;                     // CTAs the D scratch is sized for
+constexpr int kNumBars = 2 * kStages + 2 + 2 + 3;  // full, empty, tfull, tempty, dready, ddone, drain
+constexpr size_t kSmem = 1024 + static_cast<size_t>(kStages) * kStageBytes + kNumBars * 8 + 64;
+static_assert(kSmem <= 232448, "dynamic shared memory limit");
+using Sched = ClassSchedT<kSnpK>;
+}  // namespace wide
+
+constexpr int64_t kWideMaxNf = 16383;  // 4 n_f < 2^16
+
+// MODE 0: tallies only; 1: tallies and CCC, PERSNP; 2: tallies and CCC, JOINT.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
+    k_tally3_class_w(const __grid_constant__ CUtensorMap tmOp,
+                     const __grid_constant__ CUtensorMap tmC, const ClassArgs args,
+                     wide::Sched::Params sp) {
+  constexpr int kStages = wide::kStages;
+  constexpr int kTile = wide::kTile;
+  constexpr int kStageBytes = wide::kStageBytes;
+  constexpr int kDWords = wide::kDWords;
+  constexpr int kNumBars = wide::kNumBars;
+  constexpr int kN = wide::kN;
+  using Sched = wide::Sched;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kTile;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+  uint32_t *dsc = args.dscratch + static_cast<int64_t>(blockIdx.x) * 2 * kDWords;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int32_t *status = args.t.status;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * kStages + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * kStages + 2 + a); };
+  const uint32_t dready_bar = bar0 + 8u * (2 * kStages + 4);
+  const uint32_t ddone_bar = bar0 + 8u * (2 * kStages + 5);
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 6);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    // The leader's tempty / ddone gather its epilogue warps and one arrival
+    // forwarded by the follower, whose own barriers gather its warps.
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), leader ? kEpiWarps + 1 : kEpiWarps);
+    }
+    mbar_init(dready_bar, 1);
+    mbar_init(ddone_bar, leader ? kEpiWarps + 1 : kEpiWarps);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmOp);
+    tma_prefetch_desc(&tmC);
+  }
+  if (warp == 1) {
+    tcp::tmem_alloc_pair(smem_u32(tmem_slot), 512);
+    tcp::tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int64_t cstart = blockIdx.x >> 1;
+  const int64_t cstep = gridDim.x >> 1;
+  const int64_t n_v = args.t.n_v;
+  const int nkb = sp.nkb;
+  // T k-blocks of a tile before the next tile's D phase is issued.
+  const int ins = (3 * nkb) / 4;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs)
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_parity[kStages];
+      for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
+      bool ok = true;
+      auto step = [&](const CUtensorMap *m, int ya, int yb, int x) -> bool {
+        if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, status, abort_flag)) return false;
+        if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * kStageBytes);
+        const uint32_t fb = map_to_rank(full_bar(stage), 0);
+        tcp::tma_load_2d_pair(smem_u32(sA + stage * kTile), m, x, ya, fb);
+        tcp::tma_load_2d_pair(smem_u32(sB + stage * kTile), m, x, yb, fb);
+        last_parity[stage] = static_cast<int>(phase);
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        return true;
+      };
+      // Rows of a tile: i side of this CTA, k side of this CTA.
+      auto rows_t = [&](const Sched &t, int *ya, int *yb) {
+        const int ia = 2 * (t.i0() + 64 * static_cast<int>(rank));
+        const int kr = 2 * t.k0() + 128 * static_cast<int>(rank);
+        const int mrow = t.mrow();
+        if (t.i_masked()) {
+          *ya = mrow + ia;
+          *yb = kr;
+        } else {
+          *ya = ia;
+          *yb = mrow + (kr - 2 * (t.j + 1));
+        }
+      };
+      auto d_phase = [&](const Sched &t) -> bool {
+        bool dfull;
+        const int nd = t.d_blocks(&dfull);
+        if (nd == 0) return true;
+        if (dfull) {
+          int ya, yb;
+          rows_t(t, &ya, &yb);
+          const int side2 = 2 * t.side();
+          if (t.i_masked()) ya += side2; else yb += side2;
+          for (int kb = 0; kb < nd; ++kb)
+            if (!step(&tmOp, ya, yb, kb * kBK)) return false;
+        } else {
+          const int cb = t.slab() * static_cast<int>(2 * n_v);
+          const int ia = cb + 2 * (t.i0() + 64 * static_cast<int>(rank));
+          const int kr = cb + 2 * t.k0() + 128 * static_cast<int>(rank);
+          for (int kb = 0; kb < nd; ++kb)
+            if (!step(&tmC, ia, kr, kb * kBK)) return false;
+        }
+        return true;
+      };
+      Sched sc, nx;
+      sc.init(sp, cstart);
+      nx = sc;
+      nx.advance(cstep);
+      if (sc.valid) ok = d_phase(sc);
+      while (sc.valid && ok) {
+        int ya, yb;
+        rows_t(sc, &ya, &yb);
+        for (int kb = 0; kb < ins && ok; ++kb) ok = step(&tmOp, ya, yb, kb * kBK);
+        if (ok && nx.valid) ok = d_phase(nx);
+        for (int kb = ins; kb < nkb && ok; ++kb) ok = step(&tmOp, ya, yb, kb * kBK);
+        sc = nx;
+        nx.advance(cstep);
+      }
+      if (!ok) {
+        if (leader) {
+          for (int s = 0; s < kStages; ++s)
+            if (last_parity[s] >= 0)
+              mbar_wait_timeout(full_bar(s), static_cast<uint32_t>(last_parity[s]));
+        } else {
+          const uint64_t t0 = global_timer_ns();
+          while (global_timer_ns() - t0 < 1000000ull) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      // ---------------- MMA issuer (leader CTA)
+      const uint64_t dA0 = smem_desc_sw128(smem_u32(sA));
+      const uint64_t dB0 = smem_desc_sw128(smem_u32(sB));
+      constexpr uint32_t idesc = idesc_e4m3_f32(256, kN);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int dcount = 0;  // D phases issued
+      auto kblocks = [&](uint32_t d_tmem, int n) -> bool {
+        for (int kb = 0; kb < n; ++kb) {
+          if (!mbar_wait_bounded(full_bar(stage), phase, status, abort_flag)) return false;
+          tc_fence_after();
+          const uint64_t da = dA0 + static_cast<uint64_t>(stage * (kTile >> 4));
+          const uint64_t db = dB0 + static_cast<uint64_t>(stage * (kTile >> 4));
+          tcp::mma_f8f6f4_pair(d_tmem, da, db, idesc, kb != 0 ? 1u : 0u);
+#pragma unroll
+          for (int k = 1; k < kBK / kUK; ++k)
+            tcp::mma_f8f6f4_pair(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), idesc, 1u);
+          tcp::mma_commit_pair(empty_bar(stage), 0x3);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        return true;
+      };
+      // The T k-blocks [kb0, kb1) continue an accumulation started at kb 0.
+      auto tblocks = [&](uint32_t d_tmem, int kb0, int kb1) -> bool {
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait_bounded(full_bar(stage), phase, status, abort_flag)) return false;
+          tc_fence_after();
+          const uint64_t da = dA0 + static_cast<uint64_t>(stage * (kTile >> 4));
+          const uint64_t db = dB0 + static_cast<uint64_t>(stage * (kTile >> 4));
+          tcp::mma_f8f6f4_pair(d_tmem, da, db, idesc, kb != 0 ? 1u : 0u);
+#pragma unroll
+          for (int k = 1; k < kBK / kUK; ++k)
+            tcp::mma_f8f6f4_pair(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), idesc, 1u);
+          tcp::mma_commit_pair(empty_bar(stage), 0x3);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        return true;
+      };
+      // D phase of tile u (buffer u & 1), after the epilogue released the buffer.
+      auto d_phase = [&](const Sched &t, int u) -> bool {
+        bool dfull;
+        const int nd = t.d_blocks(&dfull);
+        if (nd == 0) return true;
+        if (!mbar_wait_cluster_bounded(tempty_bar(u & 1), ((u >> 1) & 1) ^ 1u, status, abort_flag))
+          return false;
+        tc_fence_after();
+        if (!kblocks(tmem_base + (u & 1) * kN, nd)) return false;
+        tcp::mma_commit_pair(dready_bar, 0x3);
+        ++dcount;
+        return true;
+      };
+      Sched sc, nx;
+      sc.init(sp, cstart);
+      nx = sc;
+      nx.advance(cstep);
+      int u = 0;
+      if (sc.valid) ok = d_phase(sc, 0);
+      int d_of_cur = 0;  // index of the current tile's D phase
+      while (sc.valid && ok) {
+        bool dfull;
+        const bool has_d = sc.d_blocks(&dfull) > 0;
+        // Buffer u & 1 is free (no D) or its D has been moved to shared memory.
+        if (has_d) {
+          if (!mbar_wait_cluster_bounded(ddone_bar, static_cast<uint32_t>(d_of_cur & 1), status,
+                                         abort_flag))
+            break;
+        } else if (!mbar_wait_cluster_bounded(tempty_bar(u & 1), ((u >> 1) & 1) ^ 1u, status,
+                                              abort_flag)) {
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (u & 1) * kN;
+        ok = tblocks(d_tmem, 0, ins);
+        const int d_next = dcount;
+        if (ok && nx.valid) ok = d_phase(nx, u + 1);
+        if (ok) ok = tblocks(d_tmem, ins, nkb);
+        if (!ok) break;
+        tcp::mma_commit_pair(tfull_bar(u & 1), 0x3);
+        d_of_cur = d_next;
+        sc = nx;
+        nx.advance(cstep);
+        ++u;
+      }
+      tcp::mma_commit_pair(drain_bar, 0x1);
+      mbar_wait_timeout(drain_bar, 0);
+    } else if (lane == 0) {
+      // ---------------- follower: forward the epilogue's releases to the leader
+      int dcount = 0;
+      Sched sc, pv;
+      sc.init(sp, cstart);
+      for (int u = 0;; ++u) {
+        if (sc.valid) {
+          bool dfull;
+          if (sc.d_blocks(&dfull) > 0) {
+            if (!mbar_wait_bounded(ddone_bar, static_cast<uint32_t>(dcount & 1), status, abort_flag))
+              break;
+            tc_fence_before();
+            mbar_arrive_cluster(map_to_rank(ddone_bar, 0));
+            ++dcount;
+          }
+        }
+        if (u >= 1) {
+          const int v = u - 1;
+          if (!mbar_wait_bounded(tempty_bar(v & 1), (v >> 1) & 1, status, abort_flag)) break;
+          tc_fence_before();
+          mbar_arrive_cluster(map_to_rank(tempty_bar(v & 1), 0));
+        }
+        if (!sc.valid) break;
+        sc.advance(cstep);
+      }
+    }
+  } else {
+    // ---------------- epilogue (both CTAs)
+    const int ew = warp - 2;  // 0..7
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int L = quarter * 32 + lane;  // TMEM lane = A row of this CTA
+    const int a = L & 1;
+    const int32_t *__restrict__ rtab = args.rtab;
+    const float *__restrict__ wv = args.t.w;
+    int4 *__restrict__ tally_out = reinterpret_cast<int4 *>(args.t.tally);
+    float4 *__restrict__ ccc_out = reinterpret_cast<float4 *>(args.t.ccc);
+    constexpr bool want_ccc = MODE != 0;
+    constexpr bool persnp = MODE == 1;
+    const float gamma = args.t.gamma;
+    const int64_t s_begin = slab_offset_dev(args.t.j_begin, n_v);
+    const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16);
+    int dcount = 0;
+    bool ok_all = true;
+    Sched sc, pv;
+    bool pv_has_d = false;
+    sc.init(sp, cstart);
+    for (int u = 0; ok_all; ++u) {
+      // (1) move the D accumulator of tile u to this thread's shared-memory slot
+      bool cur_has_d = false;
+      if (sc.valid) {
+        bool dfull;
+        cur_has_d = sc.d_blocks(&dfull) > 0;
+        if (cur_has_d) {
+          const bool got = mbar_wait_bounded(dready_bar, static_cast<uint32_t>(dcount & 1), status,
+                                             abort_flag);
+          if (!__all_sync(0xffffffffu, got)) break;
+          tc_fence_after();
+          uint32_t *slot = dsc + (u & 1) * kDWords;
+#pragma unroll 1
+          for (int m = 0; m < 4; ++m) {
+            uint32_t v[32];
+            tmem_ld_32x32b_x32(lane_base + (u & 1) * kN + 128 * half + 32 * m, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const uint32_t d0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[2 * e])));
+              const uint32_t d1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[2 * e + 1])));
+              __stcg(slot + (64 * half + 16 * m + e) * 128 + L, (d0 & 0xFFFFu) | (d1 << 16));
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(ddone_bar);  // the follower's is forwarded by warp 1
+          ++dcount;
+        }
+      }
+      // (2) the tallies and CCC values of tile u - 1
+      if (u >= 1) {
+        const int v = u - 1;
+        const int acc = v & 1;
+        const bool got = mbar_wait_bounded(tfull_bar(acc), (v >> 1) & 1, status, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) break;
+        tc_fence_after();
+        const int64_t j = pv.j;
+        const int64_t i = pv.i0() + 64 * static_cast<int64_t>(rank) + (L >> 1);
+        const bool row_ok = i < j;
+        const int64_t k_first = pv.k0();
+        const uint32_t t_x = lane_base + acc * kN;
+        const uint32_t *slot = dsc + acc * kDWords;
+        const int64_t span = n_v - 1 - j;
+        const int64_t base = slab_offset_dev(j, n_v) - s_begin + i * span - (j + 1);
+        const int64_t pbase = i * (2 * n_v - i - 1) / 2 - i - 1;  // pair (i, k) at pbase + k
+        float wi = 1.f, wj0 = 1.f, wj1 = 1.f;
+        if (want_ccc && persnp) {
+          if (row_ok) wi = __ldg(wv + 2 * i + a);
+          wj0 = __ldg(wv + 2 * j);
+          wj1 = __ldg(wv + 2 * j + 1);
+        }
+        constexpr int nch = 8;
+        for (int c = 0; c < nch; ++c) {
+          const int kl = 64 * half + 8 * c;  // first local SNP k of the chunk
+          const int64_t kc = k_first + kl;
+          uint32_t x[16];
+          tmem_ld_32x32b_x16(t_x + 2 * kl, x);
+          int2 r[8];
+          float2 wk[8];
+          uint32_t dd[8];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int64_t k = kc + kk;
+            const bool ok = row_ok && k < n_v;
+            r[kk] = ok ? __ldg(reinterpret_cast<const int2 *>(rtab + 4 * (pbase + k)) + a)
+                       : make_int2(0, 0);
+            wk[kk] = (ok && want_ccc && persnp) ? __ldg(reinterpret_cast<const float2 *>(wv) + k)
+                                                : make_float2(1.f, 1.f);
+            dd[kk] = pv_has_d ? __ldcg(slot + (kl + kk) * 128 + L) : 0u;
+          }
+          tmem_ld_wait();
+          if (c == nch - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(acc));  // the follower's is forwarded
+          }
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int64_t k = kc + kk;
+            const bool ok = row_ok && k < n_v;
+            const int32_t t0 = __float2int_rn(__uint_as_float(x[2 * kk]));
+            const int32_t t1 = __float2int_rn(__uint_as_float(x[2 * kk + 1]));
+            const int32_t d0 = static_cast<int32_t>(dd[kk] & 0xFFFFu);
+            const int32_t d1 = static_cast<int32_t>(dd[kk] >> 16);
+            const int32_t u0 = r[kk].x - d0, u1 = r[kk].y - d1;
+            // r^{a b c}: b0c0, b0c1, b1c0, b1c1
+            const int4 tv = make_int4(u0 + t0, u1 + t1, u0 - t0, u1 - t1);
+            const int64_t t = base + k;
+            if (ok) __stcs(tally_out + 2 * t + a, tv);
+            if (want_ccc) {
+              const int32_t own = tv.x + tv.y + tv.z + tv.w;  // sum over b, c (fixed a)
+              const int32_t n8 = own + __shfl_xor_sync(0xffffffffu, own, 1);
+              int32_t rb0 = 0, rb1 = 0, q0 = 0, q1 = 0;
+              if constexpr (!persnp) {
+                const int32_t b0 = tv.x + tv.y, b1 = tv.z + tv.w;
+                const int32_t c0 = tv.x + tv.z, c1 = tv.y + tv.w;
+                rb0 = b0 + __shfl_xor_sync(0xffffffffu, b0, 1);
+                rb1 = b1 + __shfl_xor_sync(0xffffffffu, b1, 1);
+                q0 = c0 + __shfl_xor_sync(0xffffffffu, c0, 1);
+                q1 = c1 + __shfl_xor_sync(0xffffffffu, c1, 1);
+              }
+              if (ok) {
+                float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (n8 != 0) {
+                  const float dn = static_cast<float>(n8);
+                  float fi = wi, fj0 = wj0, fj1 = wj1, fk0 = wk[kk].x, fk1 = wk[kk].y;
+                  if (!persnp) {
+                    fi = joint_factor(own, dn, gamma);
+                    fj0 = joint_factor(rb0, dn, gamma);
+                    fj1 = joint_factor(rb1, dn, gamma);
+                    fk0 = joint_factor(q0, dn, gamma);
+                    fk1 = joint_factor(q1, dn, gamma);
+                  }
+                  if (persnp) {
+                    const float inv = __frcp_rn(dn);
+                    const float g0 = __fmul_rn(fi, fj0), g1 = __fmul_rn(fi, fj1);
+                    out.x = ccc3_persnp(tv.x, inv, g0, fk0);
+                    out.y = ccc3_persnp(tv.y, inv, g0, fk1);
+                    out.z = ccc3_persnp(tv.z, inv, g1, fk0);
+                    out.w = ccc3_persnp(tv.w, inv, g1, fk1);
+                  } else {
+                    out.x = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.x), dn), fi), fj0), fk0);
+                    out.y = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.y), dn), fi), fj0), fk1);
+                    out.z = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.z), dn), fi), fj1), fk0);
+                    out.w = __fmul_rn(__fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(tv.w), dn), fi), fj1), fk1);
+                  }
+                }
+                __stcs(ccc_out + 2 * t + a, out);
+              }
+            }
+          }
+        }
+      }
+      if (!sc.valid) break;
+      pv = sc;
+      pv_has_d = cur_has_d;
+      sc.advance(cstep);
     }
   }
 
@@ -635,25 +1127,43 @@ __global__ void __launch_bounds__(256) k_mask3c(const uint64_t *__restrict__ gen
   const int64_t mrow = mrow0 + 4 * (mask_prefix(j, n_v) - mask_prefix(j0, n_v));
   const int64_t words = (n_f + 31) / 32;
   const uint64_t *__restrict__ gj = geno + j * ld;
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-    const bool dmask = r >= 2 * side;
-    const int64_t rt = dmask ? r - 2 * side : r;
-    const int64_t s = im ? (rt >> 1) : j + 1 + (rt >> 1);
-    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(op + (2 * s + (rt & 1)) * kpad);
-    uint4 *__restrict__ dst = reinterpret_cast<uint4 *>(op + (mrow + r) * kpad);
+  // Rows r, r + gridDim.x, ... in groups of 4 so that 8 loads per thread are in flight.
+  constexpr int kRows = 4;
+  for (int64_t r0 = blockIdx.x; r0 < rows; r0 += static_cast<int64_t>(gridDim.x) * kRows) {
+    const uint4 *src[kRows];
+    uint4 *dst[kRows];
+    bool dm[kRows], live[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int64_t ru = r0 + static_cast<int64_t>(u) * gridDim.x;
+      live[u] = ru < rows;
+      const int64_t r = live[u] ? ru : r0;
+      dm[u] = r >= 2 * side;
+      const int64_t rt = dm[u] ? r - 2 * side : r;
+      const int64_t sn = im ? (rt >> 1) : j + 1 + (rt >> 1);
+      src[u] = reinterpret_cast<const uint4 *>(op + (2 * sn + (rt & 1)) * kpad);
+      dst[u] = reinterpret_cast<uint4 *>(op + (mrow + r) * kpad);
+    }
     for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
       const int wi = c >> 1;
       uint32_t w = 0u;
       if (wi < words) w = static_cast<uint32_t>(__ldg(gj + wi) >> (32 * (c & 1)));
-      uint32_t keep[4], neg[4];
-      class_masks(w, dmask, keep, neg);
-      const uint4 v = __ldg(src + c);
-      uint4 o;
-      o.x = (v.x & keep[0]) | neg[0];
-      o.y = (v.y & keep[1]) | neg[1];
-      o.z = (v.z & keep[2]) | neg[2];
-      o.w = (v.w & keep[3]) | neg[3];
-      dst[c] = o;
+      uint4 v[kRows];
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) v[u] = live[u] ? __ldg(src[u] + c) : make_uint4(0u, 0u, 0u, 0u);
+      uint32_t ks[4], ns[4], km[4], nm[4];
+      class_masks(w, false, ks, ns);
+      class_masks(w, true, km, nm);
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        if (!live[u]) continue;
+        uint4 o;
+        o.x = (v[u].x & (dm[u] ? km[0] : ks[0])) | (dm[u] ? nm[0] : ns[0]);
+        o.y = (v[u].y & (dm[u] ? km[1] : ks[1])) | (dm[u] ? nm[1] : ns[1]);
+        o.z = (v[u].z & (dm[u] ? km[2] : ks[2])) | (dm[u] ? nm[2] : ns[2]);
+        o.w = (v[u].w & (dm[u] ? km[3] : ks[3])) | (dm[u] ? nm[3] : ns[3]);
+        dst[u][c] = o;
+      }
     }
   }
 }
@@ -688,11 +1198,80 @@ int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, ui
   return note_launch();
 }
 
+// Wide tiles (k_tally3_class_w) when 4 n_f fits in 16 bits, else N = 160 tiles.
+template <int MODE>
+static int launch_wide_mode(const CUtensorMap &tmOp, const CUtensorMap &tmC, const ClassArgs &ca,
+                            const wide::Sched::Params &sp, int64_t tiles, int num_sms,
+                            cudaStream_t s) {
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    if (cudaFuncSetAttribute(k_tally3_class_w<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(wide::kSmem)) != cudaSuccess)
+      return CCC_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = wide::kSmem;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tally3_class_w<MODE>, &cfg) != cudaSuccess || n < 1)
+      return CCC_ECUDA;
+    max_clusters = n < num_sms / 2 ? n : num_sms / 2;
+    if (max_clusters > wide::kMaxCtas / 2) max_clusters = wide::kMaxCtas / 2;
+  }
+  const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
+  k_tally3_class_w<MODE><<<static_cast<unsigned>(2 * clusters), kThreads, wide::kSmem, s>>>(
+      tmOp, tmC, ca, sp);
+  return note_launch();
+}
+
+// Wide tiles (k_tally3_class_w) when 4 n_f fits in 16 bits, else N = 160 tiles.
+static int launch_tally3_class_w(const Tally3Args &a, const uint8_t *op, int64_t op_rows,
+                                 int64_t mrow0, int64_t kpad, const int32_t *rtab,
+                                 const uint8_t *cbuf, const int32_t *missing, uint32_t *dscratch,
+                                 int64_t j0, int64_t j1, int num_sms, cudaStream_t s) {
+  int64_t tiles = 0;
+  for (int64_t j = j0; j < j1; ++j) tiles += cdiv(j, kSnpI) * cdiv(a.n_v - 1 - j, wide::kSnpK);
+  if (tiles == 0) return CCC_OK;
+  CUtensorMap tmOp, tmC;
+  const int64_t crows = tc3_class_cbuf_rows(j1 - j0, a.n_v);
+  if (!tc::make_operand_map(&tmOp, op, op_rows, kpad, 128) ||
+      !tc::make_operand_map(&tmC, cbuf, crows, kCap, 128))
+    return CCC_ECUDA;
+  ClassArgs ca;
+  ca.t = a;
+  ca.rtab = rtab;
+  ca.dscratch = dscratch;
+  wide::Sched::Params sp;
+  sp.j0 = static_cast<int>(j0);
+  sp.j1 = static_cast<int>(j1);
+  sp.n_v = static_cast<int>(a.n_v);
+  sp.nkb = static_cast<int>(kpad / kBK);
+  sp.mrow0 = static_cast<int>(mrow0);
+  sp.missing = missing;
+  if (a.ccc == nullptr) return launch_wide_mode<0>(tmOp, tmC, ca, sp, tiles, num_sms, s);
+  if (a.norm == CCC_NORM_PERSNP) return launch_wide_mode<1>(tmOp, tmC, ca, sp, tiles, num_sms, s);
+  return launch_wide_mode<2>(tmOp, tmC, ca, sp, tiles, num_sms, s);
+}
+
+int64_t tc3_class_dscratch_bytes() {
+  return static_cast<int64_t>(wide::kMaxCtas) * 2 * wide::kDWords * 4;
+}
+
 int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows, int64_t mrow0,
                         int64_t kpad, const int32_t *rtab, const uint8_t *cbuf,
-                        const int32_t *missing, int64_t j0, int64_t j1, int num_sms,
-                        cudaStream_t s) {
+                        const int32_t *missing, uint32_t *dscratch, int64_t j0, int64_t j1,
+                        int num_sms, cudaStream_t s) {
   if (j1 <= j0) return CCC_OK;
+  if (a.n_f <= kWideMaxNf && dscratch != nullptr)
+    return launch_tally3_class_w(a, op, op_rows, mrow0, kpad, rtab, cbuf, missing, dscratch, j0, j1,
+                                 num_sms, s);
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_tally3_class, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -104,6 +104,18 @@ def test_missing_rates(path, p_missing):
     _check(geno, 700, path)
 
 
+@pytest.mark.parametrize("path", PATHS)
+def test_long_vectors(path):
+    """n_f = 16,400 > 16,383: the class route's D counts may pass 16 bits, so it runs the
+    narrower tiles that keep D in tensor memory; one SNP has 300 missing entries."""
+    n_f = 16400
+    geno = synth.panel_hwe(45, n_f, seed=14, p_missing=0.01, pad_seed=6)
+    codes = synth.unpack(geno, n_f)
+    codes[7, :300] = synth.CODE_MISSING
+    geno = synth.pack(codes, pad_seed=6)
+    _check(geno, n_f, path)
+
+
 def test_at_scale_tc_equals_popc_and_oracle_rows():
     """1,536 SNPs x 8,192 individuals (Hardy-Weinberg, 1% missing), all 602,800,640
     triples: the genotype-class tallies (default) equal the popcount tallies and the
