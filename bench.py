@@ -164,6 +164,8 @@ KERNEL_SOURCES = {
     "k_tally3_tc": ["k_tc3.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally3_class": ["k_tc3c.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "ccc_dev.cuh",
                        "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally3_class_w": ["k_tc3c.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "ccc_dev.cuh",
+                         "ccc_metric.cuh", "ccc_launch.h"],
 }
 
 
@@ -637,14 +639,15 @@ def main():
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
     kname = {(2, True): "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc",
-             (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(args.tile, "k_tally3_class"),
+             (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(
+                 args.tile, "k_tally3_class_w" if w["n_f"] <= 16383 else "k_tally3_class"),
              (2, False): "k_tally2_popc", (3, False): "k_tally3_popc"}[(w["kind"],
                                                                        path == ccc.CCC_PATH_TC)]
     if path == ccc.CCC_PATH_TC:
         # MACs per comparison (pair or triple, one individual): 2-way 4; 3-way with the
         # masked operand L_j 8; 3-way by genotype classes 4 (the product over the ~1% of
         # individuals with v_j missing is not counted).
-        per_cmp = 8.0 if (w["kind"] == 2 or kname == "k_tally3_class") else 16.0
+        per_cmp = 8.0 if (w["kind"] == 2 or kname.startswith("k_tally3_class")) else 16.0
         flops = per_cmp * cmp_per_step
         achieved = flops / (kernel_step_ms * 1e-3) / 1e12
         peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)

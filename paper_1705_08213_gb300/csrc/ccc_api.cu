@@ -95,7 +95,8 @@ struct Layout {
   size_t dscratch = 0;        // D counts of the wide class tiles in flight
   size_t total = 0;
   int64_t kpad = 0, rows_pad = 0, w64 = 0, lop_rows = 0, cbuf_slabs = 0;
-  int64_t mask_rows = 0;      // masked rows after R in op (3-way classes)
+  int64_t mask_rows = 0;      // masked rows per batch buffer after R in op (3-way classes)
+  int halves = 1;             // batch buffers (2: the next batch is prepared during this one)
 };
 
 int64_t tc_rows_pad(int64_t n_v) { return round_up(2 * n_v, 256) + 256; }
@@ -130,26 +131,29 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
         if (cap < max_slab) cap = max_slab;
         L.mask_rows = all_rows < cap ? all_rows : cap;
         if (L.mask_rows < 1) L.mask_rows = 1;
-      }
-      off = align_up(off + static_cast<size_t>(L.rows_pad + L.mask_rows) * static_cast<size_t>(L.kpad),
-                     1024);
-      if (op == CCC_OP_3WAY && (tile == 0 || tile == 3)) {
-        // 2-way tallies of all pairs, and the compacted rows of as many slabs
-        // as fit in kLopBytes (TMA row coordinates stay below 2^31).
-        L.rtab = off;
-        off = align_up(off + 16 * static_cast<size_t>(n_v) * static_cast<size_t>(n_v - 1) / 2 + 16,
-                       1024);
         const int64_t per_slab = tc3_class_cbuf_rows(1, n_v) * tc3_class_cap();
-        int64_t nb = static_cast<int64_t>(kLopBytes) / per_slab;
-        const int64_t nb_rows = (int64_t(1) << 31) / (2 * n_v) - 1;
+        int64_t nb = static_cast<int64_t>(kLopBytes / 2) / per_slab;
+        const int64_t nb_rows = (int64_t(1) << 30) / (2 * n_v) - 1;
         if (nb > nb_rows) nb = nb_rows;
         if (nb > n_v) nb = n_v;
         if (nb < 1) nb = 1;
         L.cbuf_slabs = nb;
+        L.halves = (all_rows > L.mask_rows || n_v > nb) ? 2 : 1;
+      }
+      off = align_up(off + static_cast<size_t>(L.rows_pad + L.halves * L.mask_rows) *
+                               static_cast<size_t>(L.kpad),
+                     1024);
+      if (op == CCC_OP_3WAY && (tile == 0 || tile == 3)) {
+        // 2-way tallies of all pairs; compacted rows of cbuf_slabs slabs and
+        // their missing counts, per batch buffer.
+        L.rtab = off;
+        off = align_up(off + 16 * static_cast<size_t>(n_v) * static_cast<size_t>(n_v - 1) / 2 + 16,
+                       1024);
+        const size_t per_slab = static_cast<size_t>(tc3_class_cbuf_rows(1, n_v) * tc3_class_cap());
         L.cbuf = off;
-        off = align_up(off + static_cast<size_t>(nb) * static_cast<size_t>(per_slab), 1024);
+        off = align_up(off + L.halves * static_cast<size_t>(L.cbuf_slabs) * per_slab, 1024);
         L.missing = off;
-        off = align_up(off + sizeof(int32_t) * static_cast<size_t>(nb), kAlign);
+        off = align_up(off + L.halves * sizeof(int32_t) * static_cast<size_t>(L.cbuf_slabs), kAlign);
         L.dscratch = off;
         off = align_up(off + static_cast<size_t>(tc3_class_dscratch_bytes()), kAlign);
       } else if (op == CCC_OP_3WAY && tile == 1) {
@@ -258,6 +262,31 @@ static void phase_bounds(int64_t n_v, int n_phases, int64_t *bounds) {
     bounds[p] = r;
   }
   bounds[n_phases] = n_v;
+}
+
+// Side stream on which the 3-way class route prepares the next batch of slabs
+// (compacted rows, masked rows) while the current batch's tally kernel runs.
+struct PrepRes {
+  bool ready = false;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, prepared[2] = {}, consumed[2] = {};
+};
+PrepRes g_prep_res[64];
+
+int prep_res(int dev, PrepRes **out) {
+  PrepRes &r = g_prep_res[dev];
+  if (!r.ready) {
+    if (cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming) != cudaSuccess)
+      return CCC_ECUDA;
+    for (int k = 0; k < 2; ++k)
+      if (cudaEventCreateWithFlags(&r.prepared[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.consumed[k], cudaEventDisableTiming) != cudaSuccess)
+        return CCC_ECUDA;
+    r.ready = true;
+  }
+  *out = &r;
+  return CCC_OK;
 }
 
 // 2-way tensor-core tally launch with the tile shape chosen by opts->tile;
@@ -400,22 +429,43 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
     a2.i_end = je - 1;
     a2.pair0 = 0;
     CCC_TRY(launch_tally2_tc_pair(a2, op, L.rows_pad, L.kpad, dev.sms, s));
+    // Batches of slabs alternate between L.halves buffers; with two, batch
+    // b + 1 is prepared on the side stream while batch b's tally kernel runs.
+    PrepRes *P = nullptr;
+    cudaStream_t ps = s;
+    if (L.halves == 2) {
+      CCC_TRY(prep_res(dev.device, &P));
+      ps = P->side;
+      if (cudaEventRecord(P->fork, s) != cudaSuccess || cudaStreamWaitEvent(ps, P->fork, 0) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    const size_t cbuf_half = static_cast<size_t>(L.cbuf_slabs) *
+                             static_cast<size_t>(tc3_class_cbuf_rows(1, p->n_v) * tc3_class_cap());
+    const int64_t op_rows = L.rows_pad + L.halves * L.mask_rows;
     int64_t j0 = jb;
-    while (j0 < je) {
+    for (int b = 0; j0 < je; ++b) {
       int64_t j1 = j0 + 1;
       while (j1 < je && j1 - j0 < L.cbuf_slabs &&
              tc3_class_mask_rows(j0, j1 + 1, p->n_v) <= L.mask_rows)
         ++j1;
       if (tc3_class_mask_rows(j0, j1, p->n_v) > L.mask_rows) return CCC_ERANGE;
-      CCC_TRY(launch_compact3(p->geno, p->n_f, p->n_v, p->ld, cbuf, missing, j0, j1, s));
-      CCC_TRY(launch_mask3c(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad, missing, j0, j1,
-                            s));
+      const int h = L.halves == 2 ? (b & 1) : 0;
+      uint8_t *cb = cbuf + h * cbuf_half;
+      int32_t *ms = missing + h * L.cbuf_slabs;
+      const int64_t mrow0 = L.rows_pad + h * L.mask_rows;
+      if (P != nullptr && b >= 2 && cudaStreamWaitEvent(ps, P->consumed[h], 0) != cudaSuccess)
+        return CCC_ECUDA;
+      CCC_TRY(launch_compact3(p->geno, p->n_f, p->n_v, p->ld, cb, ms, j0, j1, ps));
+      CCC_TRY(launch_mask3c(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, mrow0, ms, j0, j1, ps));
+      if (P != nullptr && (cudaEventRecord(P->prepared[h], ps) != cudaSuccess ||
+                           cudaStreamWaitEvent(s, P->prepared[h], 0) != cudaSuccess))
+        return CCC_ECUDA;
       const int slot = timing_begin(s);
-      const int rc = launch_tally3_class(a, op, L.rows_pad + L.mask_rows, L.rows_pad, L.kpad, rtab,
-                                         cbuf, missing, at<uint32_t>(o, L.dscratch), j0, j1,
-                                         dev.sms, s);
+      const int rc = launch_tally3_class(a, op, op_rows, mrow0, L.kpad, rtab, cb, ms,
+                                         at<uint32_t>(o, L.dscratch), j0, j1, dev.sms, s);
       timing_end(slot, s);
       if (rc != CCC_OK) return rc;
+      if (P != nullptr && cudaEventRecord(P->consumed[h], s) != cudaSuccess) return CCC_ECUDA;
       j0 = j1;
     }
     return CCC_OK;

@@ -587,6 +587,13 @@ constexpr int kDWords = 128 * 128;                // per tile: [k (0..127)][lane
 constexpr int kMaxCtas = 256;                     // CTAs the D scratch is sized for
 constexpr int kNumBars = 2 * kStages + 2 + 2 + 3;  // full, empty, tfull, tempty, dready, ddone, drain
 constexpr size_t kSmem = 1024 + static_cast<size_t>(kStages) * kStageBytes + kNumBars * 8 + 64;
+// Epilogue: 2 warps per TMEM lane quarter; warp g of a quarter takes the
+// 8-SNP chunks c = g, g + 2, ... of the tile's 16 (12 warps measured slower:
+// their register cap of 146 cost more than the added overlap gave).
+constexpr int kEpiWarps = 8;
+constexpr int kGroups = kEpiWarps / 4;
+constexpr int kChunks = kSnpK / 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 static_assert(kSmem <= 232448, "dynamic shared memory limit");
 using Sched = ClassSchedT<kSnpK>;
 }  // namespace wide
@@ -595,7 +602,7 @@ constexpr int64_t kWideMaxNf = 16383;  // 4 n_f < 2^16
 
 // MODE 0: tallies only; 1: tallies and CCC, PERSNP; 2: tallies and CCC, JOINT.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
+__global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
     k_tally3_class_w(const __grid_constant__ CUtensorMap tmOp,
                      const __grid_constant__ CUtensorMap tmC, const ClassArgs args,
                      wide::Sched::Params sp) {
@@ -605,6 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   constexpr int kDWords = wide::kDWords;
   constexpr int kNumBars = wide::kNumBars;
   constexpr int kN = wide::kN;
+  constexpr int kEpiWarps = wide::kEpiWarps;
   using Sched = wide::Sched;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -869,9 +877,8 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
     }
   } else {
     // ---------------- epilogue (both CTAs)
-    const int ew = warp - 2;  // 0..7
     const int quarter = warp & 3;
-    const int half = ew >> 2;
+    const int group = (warp - 2) >> 2;  // chunks group, group + kGroups, ...
     const int L = quarter * 32 + lane;  // TMEM lane = A row of this CTA
     const int a = L & 1;
     const int32_t *__restrict__ rtab = args.rtab;
@@ -901,15 +908,15 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
           tc_fence_after();
           uint32_t *slot = dsc + (u & 1) * kDWords;
 #pragma unroll 1
-          for (int m = 0; m < 4; ++m) {
-            uint32_t v[32];
-            tmem_ld_32x32b_x32(lane_base + (u & 1) * kN + 128 * half + 32 * m, v);
+          for (int c = group; c < wide::kChunks; c += wide::kGroups) {
+            uint32_t v[16];
+            tmem_ld_32x32b_x16(lane_base + (u & 1) * kN + 16 * c, v);
             tmem_ld_wait();
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+            for (int e = 0; e < 8; ++e) {
               const uint32_t d0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[2 * e])));
               const uint32_t d1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[2 * e + 1])));
-              __stcg(slot + (64 * half + 16 * m + e) * 128 + L, (d0 & 0xFFFFu) | (d1 << 16));
+              __stcg(slot + (8 * c + e) * 128 + L, (d0 & 0xFFFFu) | (d1 << 16));
             }
           }
           tc_fence_before();
@@ -940,17 +947,18 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
           wj0 = __ldg(wv + 2 * j);
           wj1 = __ldg(wv + 2 * j + 1);
         }
-        constexpr int nch = 8;
-        for (int c = 0; c < nch; ++c) {
-          const int kl = 64 * half + 8 * c;  // first local SNP k of the chunk
+        constexpr int KC = 8;  // SNPs k per chunk (16 accumulator columns)
+        const int c_last = group + wide::kGroups * ((wide::kChunks - 1 - group) / wide::kGroups);
+        for (int c = group; c < wide::kChunks; c += wide::kGroups) {
+          const int kl = KC * c;  // first local SNP k of the chunk
           const int64_t kc = k_first + kl;
-          uint32_t x[16];
+          uint32_t x[2 * KC];
           tmem_ld_32x32b_x16(t_x + 2 * kl, x);
-          int2 r[8];
-          float2 wk[8];
-          uint32_t dd[8];
+          int2 r[KC];
+          float2 wk[KC];
+          uint32_t dd[KC];
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
+          for (int kk = 0; kk < KC; ++kk) {
             const int64_t k = kc + kk;
             const bool ok = row_ok && k < n_v;
             r[kk] = ok ? __ldg(reinterpret_cast<const int2 *>(rtab + 4 * (pbase + k)) + a)
@@ -960,13 +968,13 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
             dd[kk] = pv_has_d ? __ldcg(slot + (kl + kk) * 128 + L) : 0u;
           }
           tmem_ld_wait();
-          if (c == nch - 1) {
+          if (c == c_last) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(acc));  // the follower's is forwarded
           }
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
+          for (int kk = 0; kk < KC; ++kk) {
             const int64_t k = kc + kk;
             const bool ok = row_ok && k < n_v;
             const int32_t t0 = __float2int_rn(__uint_as_float(x[2 * kk]));
@@ -1215,7 +1223,7 @@ static int launch_wide_mode(const CUtensorMap &tmOp, const CUtensorMap &tmC, con
     attr.val.clusterDim.y = 1;
     attr.val.clusterDim.z = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(wide::kThreads, 1, 1);
     cfg.dynamicSmemBytes = wide::kSmem;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
@@ -1226,7 +1234,7 @@ static int launch_wide_mode(const CUtensorMap &tmOp, const CUtensorMap &tmC, con
     if (max_clusters > wide::kMaxCtas / 2) max_clusters = wide::kMaxCtas / 2;
   }
   const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
-  k_tally3_class_w<MODE><<<static_cast<unsigned>(2 * clusters), kThreads, wide::kSmem, s>>>(
+  k_tally3_class_w<MODE><<<static_cast<unsigned>(2 * clusters), wide::kThreads, wide::kSmem, s>>>(
       tmOp, tmC, ca, sp);
   return note_launch();
 }
