@@ -190,7 +190,7 @@ def ncu_traffic(kernel, workload):
         return None
     if not rec or rec.get("source_hash") != source_hash(kernel):
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return float(rec.get("dram_bytes_per_step", rec.get("dram_bytes_per_launch")))
 
 
 def measured_peaks():
