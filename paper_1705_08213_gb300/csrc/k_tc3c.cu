@@ -672,8 +672,9 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
   const int64_t cstep = gridDim.x >> 1;
   const int64_t n_v = args.t.n_v;
   const int nkb = sp.nkb;
-  // T k-blocks of a tile before the next tile's D phase is issued.
-  const int ins = (3 * nkb) / 4;
+  // T k-blocks of a tile before the next tile's D phase is issued: late enough
+  // that the epilogue has finished the buffer it reuses (7/8 of a tile).
+  const int ins = (7 * nkb) / 8;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1049,17 +1050,23 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
 // rows 2 s + x (x = allele) of every SNP s restricted to those individuals,
 // as e4m3 counts rho_s(x), zero-padded to a multiple of 128 columns:
 // cbuf[(slab * 2 n_v + 2 s + x) * kCap + column].
-__global__ void __launch_bounds__(256) k_compact3(const uint64_t *__restrict__ geno, int64_t n_f,
+// 128-thread CTAs with few registers: they fit beside a resident class-kernel
+// CTA (its warps leave under 2K registers on some SM sub-partitions), so the
+// next batch's preparation overlaps the current batch's tallies.
+constexpr int kPrepThreads = 128;
+
+__global__ void __launch_bounds__(kPrepThreads, 9) k_compact3(const uint64_t *__restrict__ geno, int64_t n_f,
                                                   int64_t n_v, int64_t ld, int64_t j0,
                                                   uint8_t *__restrict__ cbuf,
                                                   int32_t *__restrict__ missing, int snps_per_cta) {
   __shared__ int pos[kCap];
-  __shared__ int warp_tot[8];
+  constexpr int kWarps = kPrepThreads / 32;
+  __shared__ int warp_tot[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t j = j0 + blockIdx.x;
   const int64_t nw = (n_f + 31) / 32;
   int running = 0;
-  for (int64_t base = 0; base < nw; base += 256) {
+  for (int64_t base = 0; base < nw; base += kPrepThreads) {
     const int64_t wi = base + tid;
     uint64_t miss = 0;
     if (wi < nw) {
@@ -1080,7 +1087,7 @@ __global__ void __launch_bounds__(256) k_compact3(const uint64_t *__restrict__ g
     __syncthreads();
     int before = 0, tot = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < kWarps; ++q) {
       before += q < warp ? warp_tot[q] : 0;
       tot += warp_tot[q];
     }
@@ -1098,7 +1105,7 @@ __global__ void __launch_bounds__(256) k_compact3(const uint64_t *__restrict__ g
   const int ncols = (running + kBK - 1) / kBK * kBK;
   const int64_t s_lo = static_cast<int64_t>(blockIdx.y) * snps_per_cta;
   const int64_t s_hi = s_lo + snps_per_cta < n_v ? s_lo + snps_per_cta : n_v;
-  for (int64_t s = s_lo + warp; s < s_hi; s += 8) {
+  for (int64_t s = s_lo + warp; s < s_hi; s += kWarps) {
     uint8_t *row0 = cbuf + (static_cast<int64_t>(blockIdx.x) * 2 * n_v + 2 * s) * kCap;
     for (int idx = lane; idx < ncols; idx += 32) {
       uint32_t code = 2u;  // missing: both counts 0
@@ -1122,7 +1129,7 @@ __global__ void __launch_bounds__(256) k_compact3(const uint64_t *__restrict__ g
 //                                                          more than kCap missing)
 // in the operand buffer op (rows of kpad bytes; R occupies the first rows).
 // A CTA takes every gridDim.x-th row of its slab; a thread 16 bytes at a time.
-__global__ void __launch_bounds__(256) k_mask3c(const uint64_t *__restrict__ geno, int64_t n_f,
+__global__ void __launch_bounds__(kPrepThreads, 9) k_mask3c(const uint64_t *__restrict__ geno, int64_t n_f,
                                                 int64_t n_v, int64_t ld, uint8_t *__restrict__ op,
                                                 int64_t kpad, int64_t mrow0, int64_t j0,
                                                 const int32_t *__restrict__ missing) {
@@ -1189,7 +1196,7 @@ int launch_compact3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, 
   if (j1 <= j0) return CCC_OK;
   const int snps_per_cta = 64;
   const dim3 grid(static_cast<unsigned>(j1 - j0), static_cast<unsigned>(cdiv(n_v, snps_per_cta)), 1);
-  k_compact3<<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, j0, cbuf, missing, snps_per_cta);
+  k_compact3<<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, j0, cbuf, missing, snps_per_cta);
   return note_launch();
 }
 
@@ -1197,12 +1204,12 @@ int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, ui
                   int64_t kpad, int64_t mrow0, const int32_t *missing, int64_t j0, int64_t j1,
                   cudaStream_t s) {
   if (j1 <= j0) return CCC_OK;
-  // About 4 CTAs per SM in total; each slab's rows are spread over bx CTAs.
-  int64_t bx = cdiv(4 * 160, j1 - j0);
+  // About 8 CTAs per SM in total; each slab's rows are spread over bx CTAs.
+  int64_t bx = cdiv(8 * 160, j1 - j0);
   if (bx < 2) bx = 2;
   if (bx > 256) bx = 256;
   const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(j1 - j0), 1);
-  k_mask3c<<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, op, kpad, mrow0, j0, missing);
+  k_mask3c<<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, op, kpad, mrow0, j0, missing);
   return note_launch();
 }
 
