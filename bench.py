@@ -401,9 +401,9 @@ class Runner:
         """
         torch, ccc, w = self.torch, self.ccc, self.w
         if mode == "auto":
-            mode = "stream" if (w["kind"] == 2 and not self.filter) else "copy"
+            mode = "stream" if not self.filter else "copy"
         self.e2e_mode = mode if not self.filter else "copy"
-        streamed = mode == "stream" and w["kind"] == 2 and not self.filter
+        streamed = mode == "stream" and not self.filter
         direct = mode == "direct" and not self.filter
         if direct:
             host = [torch.empty(self.tally.shape, dtype=torch.int32, pin_memory=True),
@@ -419,9 +419,9 @@ class Runner:
             dev = []
             del self.tally, self.out, self.ws
             o0 = ccc.ccc_opts_default(path=self.path, tile=self.tile)
-            self.ws_stream = torch.empty(
-                ccc.ccc2_stream_workspace_size(self.geno, w["n_f"], phases, o0), dtype=torch.uint8,
-                device=self.dev)
+            size = (ccc.ccc2_stream_workspace_size if w["kind"] == 2 else
+                    ccc.ccc3_stream_workspace_size)(self.geno, w["n_f"], phases, o0)
+            self.ws_stream = torch.empty(size, dtype=torch.uint8, device=self.dev)
             self.opts = ccc.ccc_opts_default(path=self.path, workspace=self.ws_stream,
                                              tile=self.tile)
         else:
@@ -432,7 +432,8 @@ class Runner:
         def one():
             self.geno.copy_(self.host_geno, non_blocking=True)
             if streamed:
-                ccc.ccc2_stream(self.geno, w["n_f"], phases, host[0], host[1], self.opts, stream)
+                (ccc.ccc2_stream if w["kind"] == 2 else ccc.ccc3_stream)(
+                    self.geno, w["n_f"], phases, host[0], host[1], self.opts, stream)
             else:
                 self.step(stream)
             for h, d in zip(host, dev):
@@ -699,9 +700,9 @@ def main():
         result["e2e"] = {"value": cmp_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
                          "mode": run.e2e_mode,
-                         "note": {"stream": "pinned host panel -> device, ccc2_stream (8 phases: "
-                                            "results of each phase copied to pinned host memory "
-                                            "while the next computes)",
+                         "note": {"stream": "pinned host panel -> device, "
+                                            f"ccc{w['kind']}_stream (8 phases: results of each phase "
+                                            "copied to pinned host memory while the next computes)",
                                   "direct": "pinned host panel -> device, the same C ABI call with "
                                             "its output arrays in pinned host memory (the kernel "
                                             "epilogues store over the host link)",

@@ -237,6 +237,29 @@ int ccc2_stream(const ccc_panel *panel, int n_phases, int32_t *host_tally, float
                 const ccc_opts *opts, void *stream);
 
 /*
+ * Host helper: split the slabs [0, n_v) into n_phases contiguous ranges,
+ * bounds[0] = 0 <= ... <= bounds[n_phases] = n_v, with about equal triple
+ * counts (Sec. 8 item 3 emits the result in phases).  bounds: host
+ * int64[n_phases + 1].
+ */
+int ccc3_phase_bounds(int64_t n_v, int n_phases, int64_t *bounds);
+
+/*
+ * Phased 3-way output to host memory: all triples as ccc3_tally_metric over
+ * [0, n_v) computes them, slab range by slab range (ccc3_phase_bounds), into
+ * two staging buffers in the workspace; each finished range is copied to the
+ * caller's host arrays while the next one computes.  host_tally, host_ccc:
+ * host memory [ntriples][8] (pinned, or the copies do not overlap; host_ccc
+ * may be NULL for tallies only).  Workspace: ccc3_stream_workspace_size().
+ * The copies run on the two internal streams of ccc2_stream; the caller's
+ * stream is made to wait for them.  n_phases >= 2.
+ */
+int ccc3_stream_workspace_size(const ccc_panel *panel, int n_phases, const ccc_opts *opts,
+                               size_t *bytes);
+int ccc3_stream(const ccc_panel *panel, int n_phases, int32_t *host_tally, float *host_ccc,
+                const ccc_opts *opts, void *stream);
+
+/*
  * Batched 2-way over independent panels (many SNP panels of uneven n_v and n_f,
  * as in a multi-study run): for every panel k, the tallies and CCC values that
  * ccc2_tally_metric would write to tally[k] and ccc[k].  On the tensor-core

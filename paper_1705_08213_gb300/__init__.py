@@ -30,6 +30,7 @@ __all__ = [
     "ccc2_tally_metric_noalloc", "ccc_hit", "ccc2_filter", "ccc2_batched_workspace_size",
     "ccc2_batched", "ccc2_batched_tune", "ccc2_tally_metric_rows", "ccc2_rows_count",
     "ccc2_phase_bounds", "ccc2_stream_workspace_size", "ccc2_stream",
+    "ccc3_phase_bounds", "ccc3_stream_workspace_size", "ccc3_stream",
 ]
 
 CCC_OK = 0
@@ -119,6 +120,13 @@ def load():
     lib.ccc2_stream_workspace_size.restype = ctypes.c_int
     lib.ccc2_stream.argtypes = [P(ccc_panel), ctypes.c_int, vp, vp, P(ccc_opts), vp]
     lib.ccc2_stream.restype = ctypes.c_int
+    lib.ccc3_phase_bounds.argtypes = [i64, ctypes.c_int, P(i64)]
+    lib.ccc3_phase_bounds.restype = ctypes.c_int
+    lib.ccc3_stream_workspace_size.argtypes = [P(ccc_panel), ctypes.c_int, P(ccc_opts),
+                                               P(ctypes.c_size_t)]
+    lib.ccc3_stream_workspace_size.restype = ctypes.c_int
+    lib.ccc3_stream.argtypes = [P(ccc_panel), ctypes.c_int, vp, vp, P(ccc_opts), vp]
+    lib.ccc3_stream.restype = ctypes.c_int
     lib.ccc2_filter.argtypes = [P(ccc_panel), ctypes.c_float, vp, i64, vp, P(ccc_opts), vp]
     lib.ccc2_filter.restype = ctypes.c_int
     lib.ccc2_tally_metric_noalloc.argtypes = [P(ccc_panel), vp, vp, vp, P(ccc_opts), vp]
@@ -292,6 +300,32 @@ def ccc2_stream(geno, n_f, n_phases, host_tally, host_ccc, opts, stream=None):
     """Phased 2-way output into host tensors (pinned for overlap)."""
     p = _panel(geno, n_f)
     _check("ccc2_stream", load().ccc2_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally),
+                                             _ptr(host_ccc), ctypes.byref(opts), _stream(stream)))
+
+
+def ccc3_phase_bounds(n_v, n_phases):
+    b = (ctypes.c_int64 * (n_phases + 1))()
+    _check("ccc3_phase_bounds", load().ccc3_phase_bounds(int(n_v), int(n_phases), b))
+    return [int(x) for x in b]
+
+
+def ccc3_stream_workspace_size(geno_or_shape, n_f, n_phases, opts):
+    if hasattr(geno_or_shape, "data_ptr"):
+        p = _panel(geno_or_shape, n_f)
+    else:
+        n_v, ld = geno_or_shape
+        p = ccc_panel(None, int(n_f), int(n_v), int(ld))
+    out = ctypes.c_size_t(0)
+    _check("ccc3_stream_workspace_size",
+           load().ccc3_stream_workspace_size(ctypes.byref(p), int(n_phases), ctypes.byref(opts),
+                                             ctypes.byref(out)))
+    return int(out.value)
+
+
+def ccc3_stream(geno, n_f, n_phases, host_tally, host_ccc, opts, stream=None):
+    """Phased 3-way output (all triples) into host tensors (pinned for overlap)."""
+    p = _panel(geno, n_f)
+    _check("ccc3_stream", load().ccc3_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally),
                                              _ptr(host_ccc), ctypes.byref(opts), _stream(stream)))
 
 

@@ -373,68 +373,100 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   return rc;
 }
 
-// The 3-way sequence over slabs [j_begin, j_end): counts (+ factors), operand
-// preparation, then per batch of slabs the masked operands and the tally kernel
-// (tensor cores), or one popcount kernel over all slabs.
-static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t *tally,
-                    float *out_ccc, const ccc_opts *o, cudaStream_t s) {
+// A 3-way call after its checks: panel, options, stream, workspace layout and
+// the kernel arguments (j_begin, j_end, tally, ccc set per slab range).
+struct Run3 {
+  const ccc_panel *p;
+  const ccc_opts *o;
+  cudaStream_t s;
+  Layout L;
+  DeviceInfo dev;
+  Tally3Args a;
+};
+
+static int begin_3way(Run3 &R, const ccc_panel *p, const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_panel(p));
   CCC_TRY(check_opts(o));
-  if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
-  if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
-  if (j_begin < 0 || j_end < j_begin || j_end > p->n_v) return CCC_EINVAL;
   if (p->n_v > 65535) return CCC_ERANGE;
-  DeviceInfo dev;
-  CCC_TRY(query_device(&dev));
-  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY, o->tile);
-  CCC_TRY(check_workspace(o, L));
-  CCC_TRY(clear_status(o, L, s));
-  if (slab_offset(j_end, p->n_v) == slab_offset(j_begin, p->n_v)) return CCC_OK;
-  float *w = at<float>(o, L.w);
-  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
-    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
-  Tally3Args a;
-  a.n_v = p->n_v;
-  a.n_f = p->n_f;
-  a.j_begin = j_begin;
-  a.j_end = j_end;
-  a.w = w;
-  a.tally = tally;
-  a.ccc = out_ccc;
-  a.status = at<int32_t>(o, L.status);
-  a.gamma = static_cast<float>(o->gamma);
-  a.norm = o->norm;
-  if (o->path == CCC_PATH_TC && (o->tile == 0 || o->tile == 3)) {
-    // Genotype classes of v_j: 2-way tallies r_ik of the pairs i < k with
-    // i < j_end - 1, then per batch of slabs the compacted rows of the
-    // individuals with v_j missing and the class kernel.
+  CCC_TRY(query_device(&R.dev));
+  R.p = p;
+  R.o = o;
+  R.s = s;
+  R.L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY, o->tile);
+  CCC_TRY(check_workspace(o, R.L));
+  CCC_TRY(clear_status(o, R.L, s));
+  R.a.n_v = p->n_v;
+  R.a.n_f = p->n_f;
+  R.a.w = at<float>(o, R.L.w);
+  R.a.status = at<int32_t>(o, R.L.status);
+  R.a.gamma = static_cast<float>(o->gamma);
+  R.a.norm = o->norm;
+  return CCC_OK;
+}
+
+static bool class_route(const ccc_opts *o) {
+  return o->path == CCC_PATH_TC && (o->tile == 0 || o->tile == 3);
+}
+
+// Preparation shared by every slab range of a call: per-SNP factors, the e4m3
+// operands (tensor cores) or bit planes (popcount), and for the genotype-class
+// route the 2-way tallies r_ik of the pairs i < k with i < j_last - 1.
+static int prep_3way(Run3 &R, bool want_ccc, int64_t j_last) {
+  const ccc_panel *p = R.p;
+  const ccc_opts *o = R.o;
+  cudaStream_t s = R.s;
+  if (want_ccc && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, at<float>(o, R.L.w),
+                                 o->gamma, s));
+  if (o->path != CCC_PATH_TC)
+    return launch_planes(p->geno, p->n_f, p->n_v, p->ld, at<uint64_t>(o, R.L.planes), R.L.w64, s);
+  uint8_t *op = at<uint8_t>(o, R.L.op);
+  CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s));
+  if (!class_route(o)) return CCC_OK;
+  const int64_t je = j_last < p->n_v - 1 ? j_last : p->n_v - 1;
+  if (je < 2) return CCC_OK;
+  Tally2Args a2;
+  a2.n_v = p->n_v;
+  a2.n_f = p->n_f;
+  a2.w = nullptr;
+  a2.tally = at<int32_t>(o, R.L.rtab);
+  a2.ccc = nullptr;
+  a2.status = R.a.status;
+  a2.gamma = R.a.gamma;
+  a2.norm = R.a.norm;
+  a2.i_begin = 0;
+  a2.i_end = je - 1;
+  a2.pair0 = 0;
+  return launch_tally2_tc_pair(a2, op, R.L.rows_pad, R.L.kpad, R.dev.sms, s);
+}
+
+// Tallies (and CCC values) of the slabs [R.a.j_begin, R.a.j_end) into
+// R.a.tally / R.a.ccc (first triple = slab j_begin's first).
+static int slabs_3way(Run3 &R) {
+  const ccc_panel *p = R.p;
+  const ccc_opts *o = R.o;
+  const Layout &L = R.L;
+  cudaStream_t s = R.s;
+  const Tally3Args &a = R.a;
+  if (slab_offset(a.j_end, p->n_v) == slab_offset(a.j_begin, p->n_v)) return CCC_OK;
+  // Slab 0 has no i < j and slab n_v - 1 no k > j.
+  const int64_t jb = a.j_begin > 1 ? a.j_begin : 1;
+  const int64_t je = a.j_end < p->n_v - 1 ? a.j_end : p->n_v - 1;
+  if (class_route(o)) {
+    // Per batch of slabs: the compacted rows of the individuals with v_j
+    // missing, the masked rows, the class kernel.  Batches alternate between
+    // L.halves buffers; with two, batch b + 1 is prepared on a side stream
+    // (which first waits for everything already queued on s) while batch b's
+    // tally kernel runs.
+    if (jb >= je) return CCC_OK;
     uint8_t *op = at<uint8_t>(o, L.op);
     int32_t *rtab = at<int32_t>(o, L.rtab);
     uint8_t *cbuf = at<uint8_t>(o, L.cbuf);
     int32_t *missing = at<int32_t>(o, L.missing);
-    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
-    const int64_t jb = j_begin > 1 ? j_begin : 1;
-    const int64_t je = j_end < p->n_v - 1 ? j_end : p->n_v - 1;
-    if (jb >= je) return CCC_OK;
-    Tally2Args a2;
-    a2.n_v = p->n_v;
-    a2.n_f = p->n_f;
-    a2.w = nullptr;
-    a2.tally = rtab;
-    a2.ccc = nullptr;
-    a2.status = a.status;
-    a2.gamma = a.gamma;
-    a2.norm = a.norm;
-    a2.i_begin = 0;
-    a2.i_end = je - 1;
-    a2.pair0 = 0;
-    CCC_TRY(launch_tally2_tc_pair(a2, op, L.rows_pad, L.kpad, dev.sms, s));
-    // Batches of slabs alternate between L.halves buffers; with two, batch
-    // b + 1 is prepared on the side stream while batch b's tally kernel runs.
     PrepRes *P = nullptr;
     cudaStream_t ps = s;
     if (L.halves == 2) {
-      CCC_TRY(prep_res(dev.device, &P));
+      CCC_TRY(prep_res(R.dev.device, &P));
       ps = P->side;
       if (cudaEventRecord(P->fork, s) != cudaSuccess || cudaStreamWaitEvent(ps, P->fork, 0) != cudaSuccess)
         return CCC_ECUDA;
@@ -462,7 +494,7 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
         return CCC_ECUDA;
       const int slot = timing_begin(s);
       const int rc = launch_tally3_class(a, op, op_rows, mrow0, L.kpad, rtab, cb, ms,
-                                         at<uint32_t>(o, L.dscratch), j0, j1, dev.sms, s);
+                                         at<uint32_t>(o, L.dscratch), j0, j1, R.dev.sms, s);
       timing_end(slot, s);
       if (rc != CCC_OK) return rc;
       if (P != nullptr && cudaEventRecord(P->consumed[h], s) != cudaSuccess) return CCC_ECUDA;
@@ -474,20 +506,15 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
     // Masked operands formed inside the tally kernel from the packed codes
     // (slower on GB300: 45.9 ms against 36.7 ms for the 1,536 x 8,192 panel,
     // because every k-block tile of a slab forms the same i-block operand again).
-    uint8_t *op = at<uint8_t>(o, L.op);
-    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
     const int slot = timing_begin(s);
-    const int rc = launch_tally3_fused(a, p->geno, p->ld, op, L.rows_pad, L.kpad, dev.sms, s);
+    const int rc = launch_tally3_fused(a, p->geno, p->ld, at<uint8_t>(o, L.op), L.rows_pad, L.kpad,
+                                       R.dev.sms, s);
     timing_end(slot, s);
     return rc;
   }
   if (o->path == CCC_PATH_TC) {
     uint8_t *op = at<uint8_t>(o, L.op);
     uint8_t *lop = at<uint8_t>(o, L.lop);
-    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
-    // Slab 0 has no i < j and slab n_v - 1 no k > j.
-    const int64_t jb = j_begin > 1 ? j_begin : 1;
-    const int64_t je = j_end < p->n_v - 1 ? j_end : p->n_v - 1;
     int64_t j0 = jb;
     while (j0 < je) {
       int64_t j1 = j0 + 1;
@@ -495,19 +522,35 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
       if (tc3_lop_rows(j0, j1) > L.lop_rows) return CCC_ERANGE;
       CCC_TRY(launch_mask3(p->geno, p->n_f, p->n_v, p->ld, lop, L.kpad, j0, j1, s));
       const int slot = timing_begin(s);
-      const int rc = launch_tally3_tc(a, op, L.rows_pad, L.kpad, lop, L.lop_rows, j0, j1, dev.sms, s);
+      const int rc = launch_tally3_tc(a, op, L.rows_pad, L.kpad, lop, L.lop_rows, j0, j1, R.dev.sms, s);
       timing_end(slot, s);
       if (rc != CCC_OK) return rc;
       j0 = j1;
     }
     return CCC_OK;
   }
-  uint64_t *planes = at<uint64_t>(o, L.planes);
-  CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
   const int slot = timing_begin(s);
-  const int rc = launch_tally3_popc(a, planes, L.w64, s);
+  const int rc = launch_tally3_popc(a, at<uint64_t>(o, L.planes), L.w64, s);
   timing_end(slot, s);
   return rc;
+}
+
+// The 3-way sequence over slabs [j_begin, j_end): preparation, then the slabs.
+static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t *tally,
+                    float *out_ccc, const ccc_opts *o, cudaStream_t s) {
+  if (p == nullptr) return CCC_EINVAL;
+  if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
+  if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
+  if (j_begin < 0 || j_end < j_begin || j_end > p->n_v) return CCC_EINVAL;
+  Run3 R;
+  CCC_TRY(begin_3way(R, p, o, s));
+  if (slab_offset(j_end, p->n_v) == slab_offset(j_begin, p->n_v)) return CCC_OK;
+  CCC_TRY(prep_3way(R, out_ccc != nullptr, j_end));
+  R.a.j_begin = j_begin;
+  R.a.j_end = j_end;
+  R.a.tally = tally;
+  R.a.ccc = out_ccc;
+  return slabs_3way(R);
 }
 
 // Workspace of a batch: [status][per panel: factors, operands (or bit planes)].
@@ -834,6 +877,114 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
         cudaEventRecord(R->copied[k][1], R->copy[1]) != cudaSuccess ||
         cudaStreamWaitEvent(s, R->copied[k][0], 0) != cudaSuccess ||
         cudaStreamWaitEvent(s, R->copied[k][1], 0) != cudaSuccess)
+      return CCC_ECUDA;
+  return CCC_OK;
+}
+
+namespace {
+
+// Slab bounds with about equal triple counts.
+void phase_bounds3(int64_t n_v, int n_phases, int64_t *bounds) {
+  const int64_t total = slab_offset(n_v, n_v);
+  bounds[0] = 0;
+  int64_t j = 0;
+  for (int p = 1; p < n_phases; ++p) {
+    const double target = static_cast<double>(total) * p / n_phases;
+    while (j < n_v && static_cast<double>(slab_offset(j, n_v)) < target) ++j;
+    bounds[p] = j < bounds[p - 1] ? bounds[p - 1] : j;
+  }
+  bounds[n_phases] = n_v;
+}
+
+int64_t max_phase_triples(int64_t n_v, int n_phases) {
+  int64_t b[1025];
+  if (n_phases > 1024) return -1;
+  phase_bounds3(n_v, n_phases, b);
+  int64_t m = 0;
+  for (int k = 0; k < n_phases; ++k) {
+    const int64_t c = slab_offset(b[k + 1], n_v) - slab_offset(b[k], n_v);
+    if (c > m) m = c;
+  }
+  return m;
+}
+
+}  // namespace
+
+int ccc3_phase_bounds(int64_t n_v, int n_phases, int64_t *bounds) {
+  if (bounds == nullptr || n_v < 1 || n_phases < 1 || n_phases > 1 << 20) return CCC_EINVAL;
+  phase_bounds3(n_v, n_phases, bounds);
+  return CCC_OK;
+}
+
+int ccc3_stream_workspace_size(const ccc_panel *panel, int n_phases, const ccc_opts *opts,
+                               size_t *bytes) {
+  if (bytes == nullptr || panel == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
+  size_t base = 0;
+  CCC_TRY(ccc_workspace_size(panel, opts, CCC_OP_3WAY, &base));
+  const int64_t m = max_phase_triples(panel->n_v, n_phases);
+  *bytes = align_up(base, 1024) + 2 * align_up(static_cast<size_t>(m) * 64, 1024);
+  return CCC_OK;
+}
+
+int ccc3_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *host_ccc,
+                const ccc_opts *o, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p == nullptr || host_tally == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
+  size_t need = 0;
+  CCC_TRY(ccc3_stream_workspace_size(p, n_phases, o, &need));
+  if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
+  if (o->workspace_bytes < need) return CCC_ENOSPACE;
+  Run3 R;
+  CCC_TRY(begin_3way(R, p, o, s));
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return CCC_ECUDA;
+  StreamRes *S = nullptr;
+  CCC_TRY(stream_res(d, &S));
+  if (p->n_v < 3) return CCC_OK;
+  const bool want_ccc = host_ccc != nullptr;
+  CCC_TRY(prep_3way(R, want_ccc, p->n_v));
+  const int64_t slot_trip = max_phase_triples(p->n_v, n_phases);
+  const size_t slot_bytes = align_up(static_cast<size_t>(slot_trip) * 64, 1024);
+  const size_t slot0 = align_up(R.L.total, 1024);
+  int64_t bounds[1025];
+  phase_bounds3(p->n_v, n_phases, bounds);
+  for (int ph = 0; ph < n_phases; ++ph) {
+    const int64_t j0 = bounds[ph], j1 = bounds[ph + 1];
+    const int64_t t0 = slab_offset(j0, p->n_v);
+    const int64_t cnt = slab_offset(j1, p->n_v) - t0;
+    if (cnt == 0) continue;
+    const int k = ph & 1;
+    int32_t *st = at<int32_t>(o, slot0 + k * slot_bytes);
+    float *sc = reinterpret_cast<float *>(st + 8 * slot_trip);
+    if (ph >= 2) {  // the slot's previous copies must have finished
+      if (cudaStreamWaitEvent(s, S->copied[k][0], 0) != cudaSuccess ||
+          cudaStreamWaitEvent(s, S->copied[k][1], 0) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    R.a.j_begin = j0;
+    R.a.j_end = j1;
+    R.a.tally = st;
+    R.a.ccc = want_ccc ? sc : nullptr;
+    CCC_TRY(slabs_3way(R));
+    if (cudaEventRecord(S->computed[k], s) != cudaSuccess) return CCC_ECUDA;
+    if (cudaStreamWaitEvent(S->copy[0], S->computed[k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_tally + 8 * t0, st, static_cast<size_t>(cnt) * 32,
+                        cudaMemcpyDeviceToHost, S->copy[0]) != cudaSuccess ||
+        cudaEventRecord(S->copied[k][0], S->copy[0]) != cudaSuccess)
+      return CCC_ECUDA;
+    if (want_ccc) {
+      if (cudaStreamWaitEvent(S->copy[1], S->computed[k], 0) != cudaSuccess ||
+          cudaMemcpyAsync(host_ccc + 8 * t0, sc, static_cast<size_t>(cnt) * 32,
+                          cudaMemcpyDeviceToHost, S->copy[1]) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    if (cudaEventRecord(S->copied[k][1], S->copy[1]) != cudaSuccess) return CCC_ECUDA;
+  }
+  for (int k = 0; k < 2; ++k)
+    if (cudaEventRecord(S->copied[k][0], S->copy[0]) != cudaSuccess ||
+        cudaEventRecord(S->copied[k][1], S->copy[1]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, S->copied[k][0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s, S->copied[k][1], 0) != cudaSuccess)
       return CCC_ECUDA;
   return CCC_OK;
 }

@@ -173,3 +173,21 @@ def test_phase_bounds_and_row_counts(lib):
     o = ccc.ccc_opts_default()
     a = ccc.ccc2_stream_workspace_size((20000, 512), 16384, 8, o)
     assert a > ccc.ccc_workspace_size((20000, 512), 16384, o, ccc.CCC_OP_2WAY)
+
+
+def test_phase_bounds_3way(lib):
+    """Slab ranges of ccc3_stream: contiguous, covering, about equal triple counts."""
+    for n_v in (1, 2, 3, 40, 1536, 5000):
+        total = ccc.ccc3_count(n_v, 0, n_v)
+        for n_ph in (1, 2, 5, 8, 64):
+            b = ccc.ccc3_phase_bounds(n_v, n_ph)
+            assert b[0] == 0 and b[-1] == n_v and all(x <= y for x, y in zip(b, b[1:]))
+            counts = [ccc.ccc3_count(n_v, x, y) for x, y in zip(b, b[1:])]
+            assert sum(counts) == total
+            if n_v >= 1536:  # within one slab of the even split
+                assert max(counts) - total / n_ph <= n_v * n_v / 4 + 1
+    o = ccc.ccc_opts_default()
+    base = ccc.ccc_workspace_size((1536, 256), 8192, o, ccc.CCC_OP_3WAY)
+    ws = ccc.ccc3_stream_workspace_size((1536, 256), 8192, 8, o)
+    # two staging slots of the largest phase, 64 bytes per triple
+    assert ws >= base + 2 * 64 * (ccc.ccc3_count(1536, 0, 1536) // 8)

@@ -74,3 +74,36 @@ def test_stream_to_pinned_host(path, n_phases):
         ccc.ccc2_stream(g, n_f, n_phases, ht2, None, opts, stream=s)
     s.synchronize()
     assert_tally_equal(ht2.numpy(), et, "streamed tallies only")
+
+
+@pytest.mark.parametrize("path", [(0, 0), (0, 1), (1, 0)])
+@pytest.mark.parametrize("n_phases", [2, 5])
+def test_stream3_to_pinned_host(path, n_phases):
+    """ccc3_stream: all triples phase by phase into pinned host arrays equal the oracle
+    (tensor cores by genotype classes and by masked operands, popcount)."""
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    path, tile = path
+    n_v, n_f = 150, 700
+    geno = synth.panel_hwe(n_v, n_f, seed=63, p_missing=0.02)
+    et, ec = oracle.ccc3_slabs(geno, n_f)
+    g = to_device(geno)
+    opts = ccc.ccc_opts_default(path=path, tile=tile)
+    ws = workspace(ccc.ccc3_stream_workspace_size(g, n_f, n_phases, opts))
+    opts = ccc.ccc_opts_default(path=path, workspace=ws, tile=tile)
+    nt = ccc.ccc3_count(n_v, 0, n_v)
+    ht = torch.full((nt, 8), -7, dtype=torch.int32).pin_memory()
+    hc = torch.full((nt, 8), -7.0, dtype=torch.float32).pin_memory()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ccc.ccc3_stream(g, n_f, n_phases, ht, hc, opts, stream=s)
+    s.synchronize()
+    assert ccc.ccc_status(opts, stream=s) == ccc.CCC_OK
+    assert_tally_equal(ht.numpy(), et, "streamed 3-way tallies")
+    assert_ccc_close(hc.numpy(), ec, what="streamed 3-way CCC")
+    ht2 = torch.zeros((nt, 8), dtype=torch.int32).pin_memory()
+    with torch.cuda.stream(s):
+        ccc.ccc3_stream(g, n_f, n_phases, ht2, None, opts, stream=s)
+    s.synchronize()
+    assert_tally_equal(ht2.numpy(), et, "streamed 3-way tallies only")
