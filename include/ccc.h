@@ -263,9 +263,10 @@ int ccc3_stream(const ccc_panel *panel, int n_phases, int32_t *host_tally, float
  * Batched 2-way over independent panels (many SNP panels of uneven n_v and n_f,
  * as in a multi-study run): for every panel k, the tallies and CCC values that
  * ccc2_tally_metric would write to tally[k] and ccc[k].  On the tensor-core
- * path all tiles of up to 64 panels run in one persistent launch, so small
- * panels fill the SMs that large ones leave idle; opts->order and opts->group
- * choose the schedule (see ccc2_batched_tune).  panels: host array of
+ * path a panel with at least 1024 SM-pair tiles (n_v >= 5,633) runs as its
+ * own launch, and all tiles of up to 64 smaller panels run in one persistent
+ * launch, so small panels fill the SMs that large ones leave idle;
+ * opts->order and opts->group choose the schedule (see ccc2_batched_tune).  panels: host array of
  * n_panels panels; tally, ccc: host arrays of n_panels device pointers (ccc
  * may be NULL for tallies only).  Workspace: ccc2_batched_workspace_size().
  * The call queues only stream work (memsets and kernels), so it can be

@@ -60,6 +60,8 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
                                   const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                                   int num_sms, cudaStream_t s);
 
+// Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
+int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1);
 // 256 x 256 tiles on SM pairs (cta_group::2); same arguments as launch_tally2_tc.
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                           int num_sms, cudaStream_t s);
