@@ -6,9 +6,9 @@
 //   JOINT  factor w = (n - gamma R) / n         gamma's own rounding (amplified at most 2x,
 //                                               i.e. <= u) + fma + division = 3u
 //   products f * w_i * w_j (* w_k)              2 (3) roundings
-//   3-way PERSNP evaluates ((r * (1/n)) * (w_i w_j)) * w_k: 1/n, r * (1/n),
-//   w_i w_j and two products, 5 roundings besides the three factors'.
-// Worst case: 2-way 5u (PERSNP) / 9u (JOINT); 3-way 8u / 13u = 7.8e-7 < 1e-6.
+//   PERSNP evaluates (r * (1/n)) * w_i * w_j (2-way) and
+//   ((r * (1/n)) * (w_i w_j)) * w_k (3-way): 1/n and r * (1/n) are 2 roundings.
+// Worst case: 2-way 6u (PERSNP) / 9u (JOINT); 3-way 8u / 13u = 7.8e-7 < 1e-6.
 // There is no cancellation: every factor is at least 1 - gamma >= 1/3 for gamma <= 2/3.
 #pragma once
 
@@ -34,6 +34,14 @@ __device__ __forceinline__ float4 ccc2_values(int32_t r00, int32_t r01, int32_t 
     wj1 = joint_factor(r01 + r11, d, gamma);
   }
   float4 c;
+  if (norm != CCC_NORM_JOINT) {
+    const float inv = __frcp_rn(d);
+    c.x = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r00), inv), wi0), wj0);
+    c.y = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r01), inv), wi0), wj1);
+    c.z = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r10), inv), wi1), wj0);
+    c.w = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r11), inv), wi1), wj1);
+    return c;
+  }
   c.x = __fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r00), d), wi0), wj0);
   c.y = __fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r01), d), wi0), wj1);
   c.z = __fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r10), d), wi1), wj0);
@@ -80,6 +88,19 @@ __device__ __forceinline__ void ccc3_values(const int32_t (&r)[8], float wi0, fl
     const float f = __fdiv_rn(static_cast<float>(r[t]), d);
     out[t] = __fmul_rn(__fmul_rn(__fmul_rn(f, wi[t >> 2]), wj[(t >> 1) & 1]), wk[t & 1]);
   }
+}
+
+// PERSNP thresholding without division: false only when every CCC value of the
+// pair is certainly at most the threshold, i.e. max_ab r_ab w_i(a) w_j(b) is
+// below threshold * n by more than 2^-18 relative (the exact values carry at
+// most 6u + 3u of rounding here, u = 2^-24).
+__device__ __forceinline__ bool may_exceed(int32_t r00, int32_t r01, int32_t r10, int32_t r11,
+                                           float wi0, float wi1, float wj0, float wj1, float threshold) {
+  const int32_t n4 = r00 + r01 + r10 + r11;
+  if (n4 == 0) return threshold < 0.f;
+  const float m = fmaxf(fmaxf(static_cast<float>(r00) * wi0 * wj0, static_cast<float>(r01) * wi0 * wj1),
+                        fmaxf(static_cast<float>(r10) * wi1 * wj0, static_cast<float>(r11) * wi1 * wj1));
+  return m * (1.f + 0x1p-18f) >= threshold * static_cast<float>(n4);
 }
 
 // Append pair (i, j) to the hit list when its largest CCC value exceeds the threshold.

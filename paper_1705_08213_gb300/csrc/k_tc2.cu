@@ -174,13 +174,18 @@ struct Epi2 {
               wj0 = wj.x;
               wj1 = wj.y;
             }
-            const float4 cv =
-                ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
-            if (filter)
-              filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10,
-                          r11, cv);
-            else
-              __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
+            // Thresholded output: most pairs are ruled out without a division.
+            const bool skip = filter && args.norm == CCC_NORM_PERSNP &&
+                              !may_exceed(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.threshold);
+            if (!skip) {
+              const float4 cv =
+                  ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
+              if (filter)
+                filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10,
+                            r11, cv);
+              else
+                __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
+            }
           }
         }
       }
