@@ -117,10 +117,11 @@ def parse():
             print(k, source_hash(k))
         raise SystemExit(0)
     w = dict(WORKLOADS[a.workload])
-    if a.n_v is not None:
-        w["n_v"] = a.n_v
-    if a.n_f is not None:
-        w["n_f"] = a.n_f
+    if a.n_v is not None or a.n_f is not None:
+        w["n_v"] = a.n_v if a.n_v is not None else w["n_v"]
+        w["n_f"] = a.n_f if a.n_f is not None else w["n_f"]
+        w["text"] = (f"reduced case of the {a.workload} workload: n_v={w['n_v']} x n_f={w['n_f']}, "
+                     f"same generator and seed (not the bench line's configuration)")
     if a.steps is None:
         a.steps = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10}[a.workload]
     if a.workload == "batched":

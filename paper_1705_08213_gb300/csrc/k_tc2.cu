@@ -289,9 +289,7 @@ struct BatchSchedT {
 };
 using BatchSched = BatchSchedT<TriSched>;
 
-struct BatchSchedPair : BatchSchedT<TriSchedPair> {
-  __device__ int I() const { return t.I; }
-};
+struct BatchSchedPair : BatchSchedT<TriSchedPair> {};
 
 struct EpiBatchPair {
   using Params = BatchParams;

@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
     } else if (lane == 0) {
       // ---------------- follower: forward the epilogue's releases to the leader
       int dcount = 0;
-      Sched sc, pv;
+      Sched sc;
       sc.init(sp, cstart);
       for (int u = 0;; ++u) {
         if (sc.valid) {
