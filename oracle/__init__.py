@@ -4,7 +4,12 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package smoke check
 and by the benchmark's CPU-baseline leg, never by the CUDA path.  It shares no
 code with the CUDA path.
 
-Two routes are provided:
+Markers with s allele states (Sec. 8, the multi-allelic extension) have
+:func:`multi_counts`, :func:`ccc2_multi_rows`, :func:`ccc2_multi_all` and
+:func:`ccc2_multi_pairs` (C, ``oracle/ccc_oracle_multi.c``), cross-checked by the
+numpy route :mod:`oracle.multi_np`.
+
+Two routes are provided for biallelic SNPs:
 
 * :mod:`oracle.ccc_oracle` (C, loaded here through ctypes) -- the direct
   definitions, Eqs. 1-5, one loop over individuals per pair or triple;
@@ -57,6 +62,15 @@ def _load():
                                             ctypes.c_double, ctypes.c_int, i64p, f64p]
         lib.oracle_ccc3_triples.restype = ctypes.c_int
         lib.oracle_threads.restype = ctypes.c_int
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.oracle_multi_counts.argtypes = [u8p, I64, I64, I64, ctypes.c_int, i64p]
+        lib.oracle_multi_counts.restype = None
+        lib.oracle_multi_rows.argtypes = [u8p, I64, I64, I64, ctypes.c_int, i64p, I64,
+                                          ctypes.c_double, ctypes.c_int, i64p, f64p]
+        lib.oracle_multi_rows.restype = ctypes.c_int
+        lib.oracle_multi_pairs.argtypes = [u8p, I64, I64, I64, ctypes.c_int, i64p, i64p, I64,
+                                           ctypes.c_double, ctypes.c_int, i64p, f64p]
+        lib.oracle_multi_pairs.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -215,3 +229,71 @@ def triple_index(i, j, k, n_v):
     j = np.asarray(j, dtype=np.int64)
     k = np.asarray(k, dtype=np.int64)
     return slab_offset(j, n_v) + i * (n_v - 1 - j) + (k - j - 1)
+
+
+# ---------------------------------------------------------------- markers with s states
+
+
+def _multi_geno(geno, s):
+    g = np.ascontiguousarray(geno, dtype=np.uint8)
+    if g.ndim != 2:
+        raise ValueError("geno must be [n_v, ld] uint8")
+    if not 2 <= s <= 15:
+        raise ValueError("s must be in [2, 15]")
+    return g
+
+
+def multi_counts(geno, n_f, s):
+    """Per SNP: s_i^a for a < s (allele-state sums) and n_i (non-missing count): int64 [n_v, s+1]."""
+    g = _multi_geno(geno, s)
+    n_v, ld = g.shape
+    out = np.zeros((n_v, s + 1), np.int64)
+    _load().oracle_multi_counts(_p(g, ctypes.c_uint8), n_f, n_v, ld, s, _p(out, ctypes.c_int64))
+    return out
+
+
+def ccc2_multi_rows(geno, n_f, s, rows, gamma=GAMMA, norm=NORM_PERSNP):
+    """Tallies and CCC of every listed row i against all j > i for markers with s states.
+
+    Returns (tally int64 [P, s*s], ccc float64 [P, s*s]), P = sum(n_v - 1 - i), values
+    (a, b) with a major, rows in the listed order and j increasing inside each row.
+    """
+    g = _multi_geno(geno, s)
+    n_v, ld = g.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    P = int(np.sum(n_v - 1 - rows)) if rows.size else 0
+    tally = np.zeros((max(P, 1), s * s), np.int64)
+    ccc = np.zeros((max(P, 1), s * s), np.float64)
+    rc = _load().oracle_multi_rows(_p(g, ctypes.c_uint8), n_f, n_v, ld, s, _p(rows, ctypes.c_int64),
+                                   rows.size, gamma, norm, _p(tally, ctypes.c_int64),
+                                   _p(ccc, ctypes.c_double))
+    if rc == 1:
+        raise ValueError("row out of range")
+    if rc:
+        raise MemoryError("oracle_multi_rows")
+    return tally[:P], ccc[:P]
+
+
+def ccc2_multi_all(geno, n_f, s, gamma=GAMMA, norm=NORM_PERSNP):
+    """All unique pairs i < j in the order of :func:`pair_index`."""
+    n_v = np.asarray(geno).shape[0]
+    return ccc2_multi_rows(geno, n_f, s, np.arange(n_v), gamma, norm)
+
+
+def ccc2_multi_pairs(geno, n_f, s, pi, pj, gamma=GAMMA, norm=NORM_PERSNP):
+    """Tallies and CCC of explicit pairs pi[t] < pj[t] for markers with s states."""
+    g = _multi_geno(geno, s)
+    n_v, ld = g.shape
+    pi = np.ascontiguousarray(pi, dtype=np.int64)
+    pj = np.ascontiguousarray(pj, dtype=np.int64)
+    if not (np.all(pi < pj) and np.all(pi >= 0) and np.all(pj < n_v)):
+        raise ValueError("pairs must satisfy 0 <= i < j < n_v")
+    n = pi.size
+    tally = np.zeros((max(n, 1), s * s), np.int64)
+    ccc = np.zeros((max(n, 1), s * s), np.float64)
+    rc = _load().oracle_multi_pairs(_p(g, ctypes.c_uint8), n_f, n_v, ld, s, _p(pi, ctypes.c_int64),
+                                    _p(pj, ctypes.c_int64), n, gamma, norm,
+                                    _p(tally, ctypes.c_int64), _p(ccc, ctypes.c_double))
+    if rc:
+        raise MemoryError("oracle_multi_pairs")
+    return tally[:n], ccc[:n]

@@ -11,19 +11,20 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "ccc_oracle.c")
+SRCS = [os.path.join(HERE, "ccc_oracle.c"), os.path.join(HERE, "ccc_oracle_multi.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libccc_oracle.so")
 
 
 def build(force: bool = False) -> str:
     """Build the oracle library if it is missing or older than its source; return its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(f)
+                                                  for f in SRCS):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wextra",
-           "-o", tmp, SRC]
+           "-o", tmp, *SRCS]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

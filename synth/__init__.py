@@ -39,7 +39,9 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "CODE_HOM0", "CODE_HET", "CODE_MISSING", "CODE_HOM1",
+    "CODE_HOM0", "CODE_HET", "CODE_MISSING", "CODE_HOM1", "MULTI_MISSING",
+    "multi_state_thresholds", "genotypes_multi", "panel_multi", "multi_default_ld",
+    "multi_from_biallelic",
     "mix64", "uniforms", "maf_beta_half", "genotypes_uniform", "genotypes_hwe",
     "genotypes_analytic", "codes_from_genotypes", "pack", "unpack", "words_per_snp", "fill_padding", "hwe_thresholds", "plant_near_duplicates",
     "panel_uniform", "panel_hwe", "panel_analytic", "default_ld",
@@ -238,6 +240,10 @@ def _fast_lib():
                                        ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, dp, dp,
                                        ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
             lib.synth_pack.restype = None
+            lib.synth_multi.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_uint64, ctypes.c_int64, dp, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_uint8)]
+            lib.synth_multi.restype = None
             _fast = lib
         except Exception:  # no compiler: the numpy definitions are used
             _fast = False
@@ -320,3 +326,114 @@ def plant_near_duplicates(geno: np.ndarray, n_f: int, n_pairs: int, seed: int, r
         codes[sel] = new
         pack(codes[None, :], ld=geno.shape[1], out=geno, row0=dst)
     return pairs.astype(np.int64)
+
+
+# ---------------------------------------------------------------- multi-allelic panels
+#
+# Markers with s allele states (the multi-allelic extension the paper sketches in
+# Sec. 8): every entry is an unordered pair of states (x, y), x, y in {0..s-1},
+# stored in one byte as x | (y << 4); an entry whose low or high nibble is >= s
+# is missing, 0xFF being the value written here.  SNP i occupies bytes
+# [i*ld, i*ld + n_f); bytes past n_f are padding that consumers must ignore.
+#
+# Draws (same SplitMix64 keys as above):
+#   per-SNP state weights  x_a = sin^2(pi u_a / 2), u_a = unit(mix(k' + (a+1) G)),
+#                          k' = mix(key(seed, p, i) ^ 0x5851F42D4C957F2D);
+#                          p_a = max(x_a, 0.01) / sum_b max(x_b, 0.01)
+#                          (Beta(1/2,1/2) weights floored at 0.01, normalised)
+#   per entry              um = u(3q + 1), u1 = u(3q + 2), u2 = u(3q + 3) with
+#                          u(c) = unit(mix(key(seed, p, i) + c G));
+#                          missing if um < p_missing, else x = state of u1 and
+#                          y = state of u2 under the cumulative weights
+#                          (two alleles drawn independently: Hardy-Weinberg).
+
+MULTI_MISSING = 0xFF
+_MULTI_SALT = np.uint64(0x5851F42D4C957F2D)
+
+
+def multi_default_ld(n_f: int) -> int:
+    """Row stride in bytes of a multi-allelic panel: n_f rounded up to 16."""
+    return max(16, (n_f + 15) // 16 * 16)
+
+
+def multi_state_thresholds(seed, panel, snps, s):
+    """Cumulative state weights c[r, a] = p_0 + .. + p_a of each listed SNP: float64 [len, s]."""
+    snps = np.asarray(snps, dtype=np.int64)
+    with np.errstate(over="ignore"):
+        k2 = mix64(_key(seed, panel, snps) ^ _MULTI_SALT)[:, None]
+        a = np.arange(s, dtype=np.uint64)[None, :]
+        u = _to_unit(mix64(k2 + (a + np.uint64(1)) * _G))
+    x = np.maximum(np.sin(0.5 * np.pi * u) ** 2, 0.01)
+    c = np.cumsum(x / x.sum(axis=1, keepdims=True), axis=1)
+    c[:, -1] = 1.0
+    return c
+
+
+def _entry_uniforms(seed, panel, snps, n_f, t):
+    snps = np.asarray(snps, dtype=np.int64)
+    k = _key(seed, panel, snps)[:, None]
+    q = np.arange(n_f, dtype=np.uint64)[None, :]
+    with np.errstate(over="ignore"):
+        return _to_unit(mix64(k + (np.uint64(3) * q + np.uint64(t + 1)) * _G))
+
+
+def genotypes_multi(seed, panel, snps, n_f, s, p_missing):
+    """Entry bytes x | (y << 4) of the listed SNPs (0xFF = missing): uint8 [len, n_f]."""
+    c = multi_state_thresholds(seed, panel, snps, s)
+    um = _entry_uniforms(seed, panel, snps, n_f, 0)
+    out = []
+    for t in (1, 2):
+        u = _entry_uniforms(seed, panel, snps, n_f, t)
+        st = (u[:, :, None] >= c[:, None, :]).sum(axis=2)
+        out.append(np.minimum(st, s - 1).astype(np.uint8))
+    g = out[0] | (out[1] << np.uint8(4))
+    g[um < p_missing] = MULTI_MISSING
+    return g
+
+
+def _multi_fill_padding(rows, n_f, pad_seed, row0=0):
+    n_v, ld = rows.shape
+    if ld <= n_f:
+        return
+    with np.errstate(over="ignore"):
+        idx = (np.arange(n_v, dtype=np.uint64)[:, None] + np.uint64(row0)) * np.uint64(ld) \
+            + np.arange(n_f, ld, dtype=np.uint64)[None, :]
+        rows[:, n_f:] = (mix64(idx + np.uint64(pad_seed) * _G) & np.uint64(0xFF)).astype(np.uint8)
+
+
+def panel_multi(n_v, n_f, s, seed=6, p_missing=0.01, panel=0, ld=None, pad_seed=None, fast=True):
+    """Multi-allelic panel with s states: uint8 [n_v, ld] (layout above)."""
+    if not 2 <= s <= 15:
+        raise ValueError("s must be in [2, 15]")
+    if ld is None:
+        ld = multi_default_ld(n_f)
+    if ld < n_f:
+        raise ValueError("ld must be at least n_f")
+    out = np.zeros((n_v, ld), dtype=np.uint8)
+    lib = _fast_lib() if fast else None
+    if lib is not None:
+        import ctypes
+        c = np.ascontiguousarray(multi_state_thresholds(seed, panel, np.arange(n_v), s))
+        lib.synth_multi(n_v, n_f, ld, s, seed & 0xFFFFFFFFFFFFFFFF, panel,
+                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(p_missing),
+                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    else:
+        chunk = max(1, (1 << 21) // max(n_f, 1))
+        for r0 in range(0, n_v, chunk):
+            r1 = min(n_v, r0 + chunk)
+            out[r0:r1, :n_f] = genotypes_multi(seed, panel, np.arange(r0, r1), n_f, s, p_missing)
+    if pad_seed is not None:
+        _multi_fill_padding(out, n_f, pad_seed)
+    return out
+
+
+def multi_from_biallelic(words, n_f, ld=None):
+    """A packed 2-bit panel as a 2-state multi-allelic panel: 00 -> (0,0), 01 -> (0,1),
+    11 -> (1,1), 10 (missing) -> 0xFF."""
+    codes = unpack(words, n_f)
+    lut = np.array([0x00, 0x10, MULTI_MISSING, 0x11], dtype=np.uint8)
+    if ld is None:
+        ld = multi_default_ld(n_f)
+    out = np.zeros((codes.shape[0], ld), dtype=np.uint8)
+    out[:, :n_f] = lut[codes]
+    return out

@@ -56,3 +56,34 @@ void synth_pack(int kind, int64_t n_rows, int64_t n_f, int64_t ld, uint64_t seed
     }
   }
 }
+
+/*
+ * Multi-allelic rows (the numpy definition in synth/__init__.py): entry byte
+ * x | (y << 4) with x, y drawn from the cumulative state weights c[r][0..s-1]
+ * (computed by the caller), 0xFF when missing; padding bytes zero.
+ */
+void synth_multi(int64_t n_rows, int64_t n_f, int64_t ld, int s, uint64_t seed, int64_t panel,
+                 const double *c, double p_missing, uint8_t *out) {
+  int64_t r;
+#pragma omp parallel for schedule(static)
+  for (r = 0; r < n_rows; ++r) {
+    const uint64_t key = snp_key(seed, panel, r);
+    const double *cr = c + r * s;
+    uint8_t *row = out + r * ld;
+    int64_t q;
+    for (q = n_f; q < ld; ++q) row[q] = 0;
+    for (q = 0; q < n_f; ++q) {
+      const double um = unit(mix64(key + (3u * (uint64_t)q + 1u) * G));
+      const double u1 = unit(mix64(key + (3u * (uint64_t)q + 2u) * G));
+      const double u2 = unit(mix64(key + (3u * (uint64_t)q + 3u) * G));
+      int x = 0, y = 0, a;
+      for (a = 0; a < s; ++a) {
+        x += u1 >= cr[a];
+        y += u2 >= cr[a];
+      }
+      if (x > s - 1) x = s - 1;
+      if (y > s - 1) y = s - 1;
+      row[q] = um < p_missing ? 0xFF : (uint8_t)(x | (y << 4));
+    }
+  }
+}
