@@ -78,6 +78,13 @@ WORKLOADS = {
         text=("2-way CCC batched: 64 independent panels, n_v uniform in [500,8000], n_f uniform in "
               "[2000,50000] (shape seed 2), Hardy-Weinberg genotypes, Beta(1/2,1/2) MAF floored at "
               "0.01, 1% missing; one persistent launch over all panels' tiles, CUDA-graph replay")),
+    "multi": dict(
+        kind=2, states=4, n_v=10000, n_f=16384, seed=6, model="multi", p_missing=0.01,
+        metric="2-way multi-allelic CCC elementwise comparisons/sec on 1 GB300",
+        text=("2-way CCC of markers with s=4 allele states: n_v=10000 markers x n_f=16384 "
+              "individuals, per-marker state weights Beta(1/2,1/2) floored at 0.01 and normalised, "
+              "two alleles drawn independently, 1% missing, seed 6; all 49,995,000 unique pairs, "
+              "16 int32 tallies + 16 fp32 CCC per pair")),
     "small": dict(
         kind=2, n_v=256, n_f=1024, seed=0, model="uniform", p_missing=0.02,
         metric="2-way CCC elementwise comparisons/sec on 1 GB300",
@@ -123,7 +130,8 @@ def parse():
         w["text"] = (f"reduced case of the {a.workload} workload: n_v={w['n_v']} x n_f={w['n_f']}, "
                      f"same generator and seed (not the bench line's configuration)")
     if a.steps is None:
-        a.steps = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10}[a.workload]
+        a.steps = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10,
+                   "multi": 60}[a.workload]
     if a.workload == "batched":
         rng = np.random.default_rng(w["seed"])
         w["shapes"] = [(int(rng.integers(500, 8001)), int(rng.integers(2000, 50001)))
@@ -139,6 +147,8 @@ def dist_env():
 
 def make_panel(w, rank=0):
     seed = w["seed"] + rank
+    if w["model"] == "multi":
+        return synth.panel_multi(w["n_v"], w["n_f"], w["states"], seed=seed, p_missing=w["p_missing"])
     if w["model"] == "uniform":
         g = synth.panel_uniform(w["n_v"], w["n_f"], seed=seed, p_missing=w["p_missing"])
     else:
@@ -159,9 +169,12 @@ def comparisons(w):
 
 # Device-code files of each tally kernel: a traffic figure stays valid while they are unchanged.
 KERNEL_SOURCES = {
-    "k_tally2_tc_pair": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "ccc_dev.cuh",
-                         "ccc_metric.cuh", "ccc_launch.h"],
-    "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
+                         "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_multi": ["k_multi.cuh", "k_multi.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
+                       "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh",
+                    "ccc_launch.h"],
     "k_tally3_tc": ["k_tc3.cu", "tc_pipeline.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally3_class": ["k_tc3c.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "ccc_dev.cuh",
                        "ccc_metric.cuh", "ccc_launch.h"],
@@ -296,7 +309,10 @@ def oracle_sample(geno, w, rng, budget):
     if w["kind"] == 2:
         i = rng.integers(0, n_v - 1, size=budget)
         j = i + 1 + (rng.random(budget) * (n_v - 1 - i)).astype(np.int64)
-        oracle.ccc2_pairs(geno, n_f, i, j)
+        if w.get("states"):
+            oracle.ccc2_multi_pairs(geno, n_f, w["states"], i, j)
+        else:
+            oracle.ccc2_pairs(geno, n_f, i, j)
         return budget * n_f
     j = rng.integers(1, n_v - 1, size=budget)
     i = (rng.random(budget) * j).astype(np.int64)
@@ -365,12 +381,15 @@ class Runner:
         self.ccc, self.torch, self.dev, self.w, self.path = ccc, torch, dev, w, path
         self.tile = tile
         n_v, n_f = w["n_v"], w["n_f"]
-        self.host_geno = torch.from_numpy(geno_np.view(np.int64)).pin_memory()
+        self.states = w.get("states")
+        self.host_geno = torch.from_numpy(geno_np if self.states else geno_np.view(np.int64))
+        self.host_geno = self.host_geno.pin_memory()
         self.geno = self.host_geno.to(dev)
         op = ccc.CCC_OP_2WAY if w["kind"] == 2 else ccc.CCC_OP_3WAY
         o0 = ccc.ccc_opts_default(path=path, tile=tile)
-        self.ws = torch.empty(ccc.ccc_workspace_size(self.geno, n_f, o0, op), dtype=torch.uint8,
-                              device=dev)
+        size = (ccc.ccc_multi_workspace_size(self.geno, n_f, self.states, o0) if self.states else
+                ccc.ccc_workspace_size(self.geno, n_f, o0, op))
+        self.ws = torch.empty(size, dtype=torch.uint8, device=dev)
         self.opts = ccc.ccc_opts_default(path=path, workspace=self.ws, tile=tile)
         self.filter = "threshold" in w
         if self.filter:
@@ -380,7 +399,7 @@ class Runner:
             self.out_bytes = 8
         else:
             rows = ccc.ccc2_count(n_v) if w["kind"] == 2 else ccc.ccc3_count(n_v, 0, n_v)
-            width = 4 if w["kind"] == 2 else 8
+            width = (self.states ** 2 if self.states else 4) if w["kind"] == 2 else 8
             self.tally = torch.empty((rows, width), dtype=torch.int32, device=dev)
             self.out = torch.empty((rows, width), dtype=torch.float32, device=dev)
             self.out_bytes = rows * width * 8
@@ -390,6 +409,9 @@ class Runner:
         if self.filter:
             ccc.ccc2_filter(self.geno, w["n_f"], w["threshold"], self.hits, self.cap, self.n_hits,
                             self.opts, stream)
+        elif self.states:
+            ccc.ccc2_multi_tally_metric(self.geno, w["n_f"], self.states, self.tally, self.out,
+                                        self.opts, stream)
         elif w["kind"] == 2:
             ccc.ccc2_tally_metric(self.geno, w["n_f"], self.tally, self.out, self.opts, stream)
         else:
@@ -407,7 +429,9 @@ class Runner:
         """
         torch, ccc, w = self.torch, self.ccc, self.w
         if mode == "auto":
-            mode = "stream" if not self.filter else "copy"
+            mode = "stream" if not (self.filter or self.states) else "copy"
+        if self.states and mode == "stream":
+            mode = "copy"  # the multi-allelic calls have no phased variant
         self.e2e_mode = mode if not self.filter else "copy"
         streamed = mode == "stream" and not self.filter
         direct = mode == "direct" and not self.filter
@@ -456,7 +480,8 @@ class Runner:
         torch.cuda.synchronize(self.dev)
         if self.filter:
             self.hit_count = int(host[0].item())
-        return e0.elapsed_time(e1) / steps, self.host_geno.numel() * 8, self.out_bytes
+        return (e0.elapsed_time(e1) / steps,
+                self.host_geno.numel() * self.host_geno.element_size(), self.out_bytes)
 
 
 def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
@@ -645,7 +670,8 @@ def main():
     # summed duration of its launches in the timed region / steps.
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
-    kname = {(2, True): "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc",
+    kname = {(2, True): ("k_tally2_multi" if w.get("states") else
+                         "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc"),
              (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(
                  args.tile, "k_tally3_class_w" if w["n_f"] <= 16383 else "k_tally3_class"),
              (2, False): "k_tally2_popc", (3, False): "k_tally3_popc"}[(w["kind"],
@@ -657,6 +683,8 @@ def main():
         # executes 4 MAC per comparison (plus the product over the individuals with v_j
         # missing), so its credited rate reads twice its executed one.
         per_cmp = 8.0 if w["kind"] == 2 else 16.0
+        if w.get("states"):
+            per_cmp = 2.0 * w["states"] ** 2  # s^2 MAC per comparison
         flops = per_cmp * cmp_per_step
         achieved = flops / (kernel_step_ms * 1e-3) / 1e12
         peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)
@@ -720,7 +748,7 @@ def main():
             result["config"]["hits_per_step"] = run.hit_count
 
     if (not args.skip_popc and rank == 0 and path == ccc.CCC_PATH_TC and w["kind"] == 2
-            and not run.filter):
+            and not run.filter and not w.get("states")):
         for name in ("ws", "ws_stream"):
             if hasattr(run, name):
                 delattr(run, name)

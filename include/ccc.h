@@ -343,6 +343,70 @@ int ccc3_tally_metric(const ccc_panel *panel, int64_t j_begin, int64_t j_end, in
 int ccc2_tally_metric_noalloc(const ccc_panel *panel, int32_t *tally, float *ccc,
                               int32_t *status, const ccc_opts *opts, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Markers with s allele states (Sec. 8: CCC extended from biallelic SNPs to
+ * markers with any number of states, a marker with s_1 states against one with
+ * s_2 states giving an s_1 x s_2 table of values).
+ *
+ * Input: one byte per entry, x | (y << 4) for the unordered pair of allele
+ * states (x, y) of individual q, 0 <= x, y < s; an entry with x >= s or
+ * y >= s is MISSING (0xFF by convention) and contributes nothing.  SNP i
+ * occupies bytes geno[i*ld .. i*ld + n_f - 1]; bytes past n_f are ignored.
+ * Requirements: 2 <= s <= 15, n_f >= 1, n_v >= 1, ld >= n_f, ld a multiple
+ * of 16, geno 16-byte aligned, device memory.  A panel whose markers have
+ * different state counts uses s = the largest; the states a marker never
+ * takes give zero tallies and zero values.
+ *
+ * Definitions: Eqs. 1-3 over S = {0..s-1}:
+ *   rho_{i,q}(a)  = [x == a] + [y == a]  (0 for a missing entry),
+ *   r_{ij}^{ab}   = sum_q rho_{i,q}(a) rho_{j,q}(b),
+ *   CCC_{ij}(a,b) = r/(4 n_ij) (1 - gamma f_i(a)) (1 - gamma f_j(b)),
+ * with n_ij, f_i and opts->norm as for the biallelic calls.  With s = 2 and
+ * 00 -> (0,0), 01 -> (0,1), 11 -> (1,1), 10 -> missing, every result equals
+ * the biallelic call's bit for bit.
+ *
+ * Output: pairs i < j in the order of ccc2_index, s*s values per pair, (a, b)
+ * with a (the state of SNP i) major: tally[ccc2_index(i, j, n_v)*s*s + a*s + b].
+ * Tensor-core path on SM pairs only: opts->path must be CCC_PATH_TC
+ * (CCC_PATH_POPC returns CCC_EUNSUPPORTED), opts->tile 0 or 2.  Tallies are
+ * exact; CCC values are within 1e-6 relative of exact arithmetic.
+ * --------------------------------------------------------------------------- */
+typedef struct ccc_panel_multi {
+  const uint8_t *geno; /* device pointer to n_v rows of ld bytes */
+  int64_t n_f;         /* individuals */
+  int64_t n_v;         /* markers */
+  int64_t ld;          /* row stride in bytes */
+  int32_t n_states;    /* s */
+  int32_t reserved;    /* zero */
+} ccc_panel_multi;
+
+/* Bytes of workspace the multi-allelic calls need (host only).  CCC_OK,
+ * CCC_EINVAL, CCC_ERANGE or CCC_EUNSUPPORTED (popcount path). */
+int ccc_multi_workspace_size(const ccc_panel_multi *panel, const ccc_opts *opts, size_t *bytes);
+
+/* Per-marker state sums and non-missing counts (Eq. 1 numerators):
+ * counts[i*(s+1) + a] = s_i^a for a < s, counts[i*(s+1) + s] = n_i.
+ * counts: device int32[n_v][s+1].  Needs no workspace. */
+int ccc_multi_counts(const ccc_panel_multi *panel, int32_t *counts, void *stream);
+
+/* Tallies of all pairs i < j (Eq. 2 numerators over S x S).  tally: device
+ * int32[npairs][s*s], 16-byte aligned.  Needs the workspace. */
+int ccc2_multi_tally(const ccc_panel_multi *panel, int32_t *tally, const ccc_opts *opts,
+                     void *stream);
+
+/* Fused: tallies and CCC values (Eqs. 1-3 over S x S), the values formed in
+ * the tally kernel's epilogue.  tally: device int32[npairs][s*s]; ccc: device
+ * float[npairs][s*s]; both 16-byte aligned.  Needs the workspace. */
+int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float *ccc,
+                            const ccc_opts *opts, void *stream);
+
+/* CCC values (Eq. 3 over S x S) from tallies of ccc2_multi_tally and counts of
+ * ccc_multi_counts.  tally: device int32[npairs][s*s]; counts: device
+ * int32[n_v][s+1]; ccc: device float[npairs][s*s].  Workspace: any that
+ * ccc_multi_workspace_size() accepts for a panel with the same n_v and s. */
+int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
+                      const ccc_opts *opts, float *ccc, void *stream);
+
 /*
  * Device-side status of the workspace: *status receives CCC_OK or the first
  * CCC_E* code a kernel recorded (CCC_ETIMEOUT when a bounded wait gave up).

@@ -31,6 +31,8 @@ __all__ = [
     "ccc2_batched", "ccc2_batched_tune", "ccc2_tally_metric_rows", "ccc2_rows_count",
     "ccc2_phase_bounds", "ccc2_stream_workspace_size", "ccc2_stream",
     "ccc3_phase_bounds", "ccc3_stream_workspace_size", "ccc3_stream",
+    "ccc_panel_multi", "ccc_multi_workspace_size", "ccc_multi_counts", "ccc2_multi_tally",
+    "ccc2_multi_tally_metric", "ccc2_multi_metric",
 ]
 
 CCC_OK = 0
@@ -66,6 +68,11 @@ class ccc_panel(ctypes.Structure):
                 ("ld", ctypes.c_int64)]
 
 
+class ccc_panel_multi(ctypes.Structure):
+    _fields_ = [("geno", ctypes.c_void_p), ("n_f", ctypes.c_int64), ("n_v", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("n_states", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class ccc_hit(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("tally", ctypes.c_int32 * 4),
                 ("ccc", ctypes.c_float * 4)]
@@ -93,6 +100,11 @@ def load():
     vp = ctypes.c_void_p
     i64 = ctypes.c_int64
     lib.ccc_opts_default.argtypes = [P(ccc_opts)]
+    lib.ccc_multi_workspace_size.argtypes = [P(ccc_panel_multi), P(ccc_opts), P(ctypes.c_size_t)]
+    lib.ccc_multi_counts.argtypes = [P(ccc_panel_multi), vp, vp]
+    lib.ccc2_multi_tally.argtypes = [P(ccc_panel_multi), vp, P(ccc_opts), vp]
+    lib.ccc2_multi_tally_metric.argtypes = [P(ccc_panel_multi), vp, vp, P(ccc_opts), vp]
+    lib.ccc2_multi_metric.argtypes = [vp, vp, i64, ctypes.c_int32, P(ccc_opts), vp, vp]
     lib.ccc_opts_default.restype = None
     lib.ccc_workspace_size.argtypes = [P(ccc_panel), P(ccc_opts), ctypes.c_int, P(ctypes.c_size_t)]
     lib.ccc_allele_counts.argtypes = [P(ccc_panel), vp, vp]
@@ -415,3 +427,53 @@ def ccc2_tally_metric_noalloc(geno, n_f, tally, ccc, opts, status=None, stream=N
     _check("ccc2_tally_metric_noalloc",
            load().ccc2_tally_metric_noalloc(ctypes.byref(p), _ptr(tally), _ptr(ccc), _ptr(status),
                                             ctypes.byref(opts), _stream(stream)))
+
+
+# ---------------------------------------------------------------- markers with s states
+#
+# Multi-allelic panels are torch uint8 tensors of shape [n_v, ld] (one byte per
+# entry, x | (y << 4); a nibble >= s marks a missing entry) on the GPU.
+
+
+def _panel_multi(geno, n_f, s):
+    if geno.dim() != 2 or not geno.is_contiguous() or geno.element_size() != 1:
+        raise CCCError("panel", CCC_EINVAL)
+    return ccc_panel_multi(geno.data_ptr(), int(n_f), int(geno.shape[0]), int(geno.shape[1]),
+                           int(s), 0)
+
+
+def ccc_multi_workspace_size(geno_or_shape, n_f, s, opts):
+    """Workspace bytes for a multi-allelic panel (tensor or (n_v, ld) shape) with s states."""
+    if hasattr(geno_or_shape, "shape") and hasattr(geno_or_shape, "data_ptr"):
+        p = _panel_multi(geno_or_shape, n_f, s)
+    else:
+        n_v, ld = geno_or_shape
+        p = ccc_panel_multi(None, int(n_f), int(n_v), int(ld), int(s), 0)
+    out = ctypes.c_size_t(0)
+    _check("ccc_multi_workspace_size",
+           load().ccc_multi_workspace_size(ctypes.byref(p), ctypes.byref(opts), ctypes.byref(out)))
+    return int(out.value)
+
+
+def ccc_multi_counts(geno, n_f, s, counts, stream=None):
+    p = _panel_multi(geno, n_f, s)
+    _check("ccc_multi_counts", load().ccc_multi_counts(ctypes.byref(p), _ptr(counts), _stream(stream)))
+
+
+def ccc2_multi_tally(geno, n_f, s, tally, opts, stream=None):
+    p = _panel_multi(geno, n_f, s)
+    _check("ccc2_multi_tally", load().ccc2_multi_tally(ctypes.byref(p), _ptr(tally),
+                                                       ctypes.byref(opts), _stream(stream)))
+
+
+def ccc2_multi_tally_metric(geno, n_f, s, tally, ccc, opts, stream=None):
+    p = _panel_multi(geno, n_f, s)
+    _check("ccc2_multi_tally_metric",
+           load().ccc2_multi_tally_metric(ctypes.byref(p), _ptr(tally), _ptr(ccc), ctypes.byref(opts),
+                                          _stream(stream)))
+
+
+def ccc2_multi_metric(tally, counts, n_v, s, opts, ccc, stream=None):
+    _check("ccc2_multi_metric",
+           load().ccc2_multi_metric(_ptr(tally), _ptr(counts), int(n_v), int(s), ctypes.byref(opts),
+                                    _ptr(ccc), _stream(stream)))

@@ -693,11 +693,133 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
   return CCC_OK;
 }
 
+// ---------------------------------------------------------------- markers with s states
+
+static int check_panel_multi(const ccc_panel_multi *p) {
+  if (p == nullptr || p->geno == nullptr) return CCC_EINVAL;
+  if (p->n_f < 1 || p->n_v < 1 || p->n_states < 2 || p->n_states > 15) return CCC_EINVAL;
+  if (p->ld < p->n_f || p->ld % 16 != 0 || !aligned(p->geno, 16)) return CCC_EINVAL;
+  if (p->n_f > CCC_MAX_NF || p->n_v > kMaxNV) return CCC_ERANGE;
+  return CCC_OK;
+}
+
+static int check_opts_multi(const ccc_opts *o) {
+  CCC_TRY(check_opts(o));
+  if (o->path != CCC_PATH_TC) return CCC_EUNSUPPORTED;
+  return (o->tile == 0 || o->tile == 2) ? CCC_OK : CCC_EINVAL;
+}
+
+// Workspace of the multi-allelic calls: [status][factors w[n_v][s]][operand rows].
+struct MultiLayout {
+  size_t status = 0, w = 0, op = 0, total = 0;
+  int64_t kpad = 0, rows_pad = 0;
+};
+
+static MultiLayout make_multi_layout(int64_t n_f, int64_t n_v, int s, bool with_op) {
+  MultiLayout L;
+  size_t off = kAlign;
+  L.w = off;
+  off = align_up(off + sizeof(float) * static_cast<size_t>(n_v) * static_cast<size_t>(s), kAlign);
+  if (with_op) {
+    L.kpad = round_up(n_f, 128);
+    L.rows_pad = multi_rows_pad(n_v, s);
+    off = align_up(off, 1024);
+    L.op = off;
+    off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(L.kpad), 1024);
+  }
+  L.total = off;
+  return L;
+}
+
+static int check_multi_workspace(const ccc_opts *o, const MultiLayout &L, cudaStream_t s) {
+  if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
+  if (o->workspace_bytes < L.total) return CCC_ENOSPACE;
+  return cudaMemsetAsync(at<int32_t>(o, L.status), 0, sizeof(int32_t), s) == cudaSuccess
+             ? CCC_OK
+             : CCC_ECUDA;
+}
+
+// The multi-allelic 2-way sequence: factors (PERSNP values), operand rows, tally kernel.
+static int run_multi(const ccc_panel_multi *p, int32_t *tally, float *out_ccc, const ccc_opts *o,
+                     cudaStream_t s) {
+  CCC_TRY(check_panel_multi(p));
+  CCC_TRY(check_opts_multi(o));
+  if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
+  if (out_ccc != nullptr && !aligned(out_ccc, 16)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  const int ns = p->n_states;
+  const MultiLayout L = make_multi_layout(p->n_f, p->n_v, ns, true);
+  CCC_TRY(check_multi_workspace(o, L, s));
+  if (p->n_v < 2) return CCC_OK;
+  float *w = at<float>(o, L.w);
+  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
+  uint8_t *op = at<uint8_t>(o, L.op);
+  CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s));
+  const int slot = timing_begin(s);
+  const int rc = launch_tally2_multi(ns, p->n_v, w, tally, out_ccc, at<int32_t>(o, L.status),
+                                     static_cast<float>(o->gamma), o->norm, o->group, op,
+                                     L.rows_pad, L.kpad, dev.sms, s);
+  timing_end(slot, s);
+  return rc;
+}
+
 }  // namespace ccc
 
 using namespace ccc;
 
 extern "C" {
+
+int ccc_multi_workspace_size(const ccc_panel_multi *panel, const ccc_opts *opts, size_t *bytes) {
+  if (bytes == nullptr || panel == nullptr) return CCC_EINVAL;
+  CCC_TRY(check_opts_multi(opts));
+  if (panel->n_f < 1 || panel->n_v < 1 || panel->n_states < 2 || panel->n_states > 15)
+    return CCC_EINVAL;
+  if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
+  *bytes = make_multi_layout(panel->n_f, panel->n_v, panel->n_states, true).total;
+  return CCC_OK;
+}
+
+int ccc_multi_counts(const ccc_panel_multi *panel, int32_t *counts, void *stream) {
+  CCC_TRY(check_panel_multi(panel));
+  if (counts == nullptr || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return launch_multi_counts(panel->geno, panel->n_f, panel->n_v, panel->ld, panel->n_states,
+                             counts, nullptr, 0.0, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_multi_tally(const ccc_panel_multi *panel, int32_t *tally, const ccc_opts *opts,
+                     void *stream) {
+  return run_multi(panel, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float *out_ccc,
+                            const ccc_opts *opts, void *stream) {
+  if (out_ccc == nullptr) return CCC_EINVAL;
+  return run_multi(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
+                      const ccc_opts *opts, float *out_ccc, void *stream) {
+  CCC_TRY(check_opts_multi(opts));
+  if (n_v < 1 || n_v > kMaxNV || n_states < 2 || n_states > 15) return CCC_EINVAL;
+  if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
+  if (!aligned(tally, 4) || !aligned(out_ccc, 4) || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const MultiLayout L = make_multi_layout(1, n_v, n_states, false);
+  CCC_TRY(check_multi_workspace(opts, L, s));
+  if (n_v < 2) return CCC_OK;
+  float *w = at<float>(opts, L.w);
+  if (opts->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_multi_factors(counts, n_v, n_states, w, opts->gamma, s));
+  return launch_metric2_multi(tally, w, n_v, n_states, static_cast<float>(opts->gamma), opts->norm,
+                              out_ccc, s);
+}
+
 
 void ccc_opts_default(ccc_opts *opts) {
   if (opts == nullptr) return;

@@ -131,6 +131,27 @@ int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64,
 int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
                    int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);
 
+// Markers with s allele states (k_multi.cu, k_multi_wide.cu).  Operand rows:
+// multi_rows_pad(n_v, s) rows of kpad bytes (32 rows per floor(32 / s) SNPs).
+int64_t multi_rows_pad(int64_t n_v, int s);
+// counts [n_v][s + 1] (s_i^a, then n_i) and/or PERSNP factors w [n_v][s]; either may be null.
+int launch_multi_counts(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t ld, int s,
+                        int32_t *counts, float *w, double gamma, cudaStream_t st);
+int launch_multi_factors(const int32_t *counts, int64_t n_v, int s, float *w, double gamma,
+                         cudaStream_t st);
+int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t ld, int s,
+                        uint8_t *op, int64_t kpad, int64_t rows_pad, cudaStream_t st);
+// Tallies [npairs][s*s] and, when out_ccc is set, CCC values of every pair.
+int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
+                        int32_t *status, float gamma, int32_t norm, int32_t group, const uint8_t *op,
+                        int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st);
+int launch_tally2_multi_wide(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
+                             int32_t *status, float gamma, int32_t norm, int32_t group,
+                             const uint8_t *op, int64_t rows_pad, int64_t kpad, int num_sms,
+                             cudaStream_t st);
+int launch_metric2_multi(const int32_t *tally, const float *w, int64_t n_v, int s, float gamma,
+                         int32_t norm, float *out_ccc, cudaStream_t st);
+
 // Host index helpers (also exported through the C ABI).
 int64_t pair_index(int64_t i, int64_t j, int64_t n_v);
 int64_t slab_offset(int64_t j, int64_t n_v);

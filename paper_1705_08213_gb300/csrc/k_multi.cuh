@@ -1,0 +1,191 @@
+// The multi-allelic 2-way tally kernel (k_multi.cu describes the method and
+// the operand layout), templated on the number of states s.  k_multi.cu
+// instantiates s = 2..8 and k_multi_wide.cu s = 9..15.
+#pragma once
+
+#include "ccc_launch.h"
+#include "ccc_metric.cuh"
+#include "tc_pipeline.cuh"
+#include "tc_pipeline_pair.cuh"
+#include "tc_sched.cuh"
+
+namespace ccc {
+namespace {
+
+constexpr int kMultiEpiWarps = 8;
+constexpr int kMultiThreads = 64 + 32 * kMultiEpiWarps;
+
+__host__ __device__ constexpr int snps_per_quarter(int s) { return 32 / s; }
+
+struct MultiArgs {
+  int64_t n_v;
+  const float *w;   // [n_v][s] PERSNP factors, or null
+  int32_t *tally;   // [npairs][s*s]
+  float *ccc;       // [npairs][s*s], or null
+  int32_t *status;
+  float gamma;
+  int32_t norm;
+};
+
+// s consecutive values from registers to global memory (streaming stores).
+template <int S>
+__device__ __forceinline__ void store_row(int32_t *dst, const int32_t (&v)[S]) {
+  if constexpr (S % 4 == 0) {
+#pragma unroll
+    for (int b = 0; b < S; b += 4)
+      __stcs(reinterpret_cast<int4 *>(dst + b), make_int4(v[b], v[b + 1], v[b + 2], v[b + 3]));
+  } else if constexpr (S % 2 == 0) {
+#pragma unroll
+    for (int b = 0; b < S; b += 2) __stcs(reinterpret_cast<int2 *>(dst + b), make_int2(v[b], v[b + 1]));
+  } else {
+#pragma unroll
+    for (int b = 0; b < S; ++b) __stcs(dst + b, v[b]);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void store_row(float *dst, const float (&v)[S]) {
+  if constexpr (S % 4 == 0) {
+#pragma unroll
+    for (int b = 0; b < S; b += 4)
+      __stcs(reinterpret_cast<float4 *>(dst + b), make_float4(v[b], v[b + 1], v[b + 2], v[b + 3]));
+  } else if constexpr (S % 2 == 0) {
+#pragma unroll
+    for (int b = 0; b < S; b += 2)
+      __stcs(reinterpret_cast<float2 *>(dst + b), make_float2(v[b], v[b + 1]));
+  } else {
+#pragma unroll
+    for (int b = 0; b < S; ++b) __stcs(dst + b, v[b]);
+  }
+}
+
+template <int S>
+struct EpiMulti {
+  using Params = MultiArgs;
+  static constexpr int PW = snps_per_quarter(S);
+
+  template <int NC>
+  __device__ static void tile(const Params &args, const TriSchedPair &sc, int rank, int quarter,
+                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0) {
+    const int u = lane / S;
+    const int a = lane - u * S;
+    const int64_t n_v = args.n_v;
+    // Accumulator lane = A row (i, a) of CTA `rank`'s 128 rows.
+    const int64_t i = ((2 * static_cast<int64_t>(sc.I) + rank) * 4 + quarter) * PW + u;
+    const bool row_ok = u < PW && i < n_v;
+    const bool want_ccc = args.ccc != nullptr;
+    const bool persnp = args.norm == CCC_NORM_PERSNP;
+    float wi = 1.f;
+    if (want_ccc && persnp && row_ok) wi = __ldg(args.w + i * S + a);
+    const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1;  // pair index = row_base + j
+    const int src0 = (u < PW ? u : 0) * S;                        // first lane of SNP i
+    for (int c = c0; c < c0 + NC; ++c) {
+      uint32_t v[32];
+      tmem_ld_32x32b_x32(t_base + c * 32, v);
+      tmem_ld_wait();
+      if (c == c0 + NC - 1) {
+        tc_fence_before();
+        mbar_arrive_cluster(release_cluster_bar);
+      }
+      // Column chunk c = 32 rows of the B block: quarter (c & 3) of half c >> 2.
+      const int64_t j0 = ((2 * static_cast<int64_t>(sc.J) + (c >> 2)) * 4 + (c & 3)) * PW;
+#pragma unroll
+      for (int jl = 0; jl < PW; ++jl) {
+        const int64_t j = j0 + jl;
+        int32_t r[S];
+        int32_t rs = 0;
+#pragma unroll
+        for (int b = 0; b < S; ++b) {
+          r[b] = __float2int_rn(__uint_as_float(v[jl * S + b]));
+          rs += r[b];
+        }
+        // 4 n_ij = sum over the pair's table: the row sums of SNP i's s lanes.
+        int32_t n4 = 0;
+#pragma unroll
+        for (int k = 0; k < S; ++k) n4 += __shfl_sync(0xffffffffu, rs, src0 + k);
+        int32_t colsum[S];
+        if (want_ccc && !persnp) {
+#pragma unroll
+          for (int b = 0; b < S; ++b) {
+            colsum[b] = 0;
+#pragma unroll
+            for (int k = 0; k < S; ++k) colsum[b] += __shfl_sync(0xffffffffu, r[b], src0 + k);
+          }
+        }
+        if (!(row_ok && i < j && j < n_v)) continue;
+        const int64_t base = (row_base + j) * (S * S) + a * S;
+        store_row<S>(args.tally + base, r);
+        if (!want_ccc) continue;
+        float cv[S];
+        if (n4 == 0) {
+#pragma unroll
+          for (int b = 0; b < S; ++b) cv[b] = 0.f;
+        } else if (persnp) {
+          const float inv = __frcp_rn(static_cast<float>(n4));
+#pragma unroll
+          for (int b = 0; b < S; ++b) {
+            const float wj = __ldg(args.w + j * S + b);
+            cv[b] = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r[b]), inv), wi), wj);
+          }
+        } else {
+          const float d = static_cast<float>(n4);
+          const float wia = joint_factor(rs, d, args.gamma);
+#pragma unroll
+          for (int b = 0; b < S; ++b) {
+            const float wjb = joint_factor(colsum[b], d, args.gamma);
+            cv[b] = __fmul_rn(__fmul_rn(__fdiv_rn(static_cast<float>(r[b]), d), wia), wjb);
+          }
+        }
+        store_row<S>(args.ccc + base, cv);
+      }
+    }
+  }
+};
+
+template <int S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
+    k_tally2_multi(const __grid_constant__ CUtensorMap tm, const MultiArgs args,
+                   TriSched::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<TriSchedPair, EpiMulti<S>, kMultiEpiWarps>(&tm, sp, args, nkb, args.status);
+}
+
+template <int S>
+int launch_tally2_multi_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB, int group, int nkb,
+                          int num_sms, cudaStream_t s) {
+  TriSched::Params sp;
+  sp.nI = static_cast<int>(nB);
+  sp.nJ = sp.nI;
+  sp.group = group > 0 ? group : 8;
+  sp.shift = 0;
+  sp.I0 = 0;
+  sp.I1 = sp.nI;
+  const int64_t tiles = nB * (nB + 1) / 2;
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    if (cudaFuncSetAttribute(k_tally2_multi<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+      return CCC_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(kMultiThreads, 1, 1);
+    cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tally2_multi<S>, &cfg) != cudaSuccess || n < 1)
+      return CCC_ECUDA;
+    max_clusters = n < num_sms / 2 ? n : num_sms / 2;
+  }
+  const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
+  k_tally2_multi<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, tcp::SMEM_BYTES, s>>>(tm, a, sp,
+                                                                                          nkb);
+  return note_launch();
+}
+
+}  // namespace
+}  // namespace ccc

@@ -18,6 +18,7 @@
 #include "ccc_metric.cuh"
 #include "tc_pipeline.cuh"
 #include "tc_pipeline_pair.cuh"
+#include "tc_sched.cuh"
 
 #include <string.h>
 
@@ -28,70 +29,6 @@ using namespace tc;
 
 constexpr int SNP_I = BM / 2;
 constexpr int SNP_J = BN / 2;
-
-// Upper-triangle tiles: I = 64-SNP row block, J = 128-SNP column block,
-// J >= I/2 (the first column block holding a j > every i of the row block),
-// in groups of `group` column blocks, rows inside a group in increasing order.
-struct TriSched {
-  struct Params {
-    int nI, nJ, group;
-    int I0, I1;  // row blocks [I0, I1) (a phase); 0, nI for the whole triangle
-    int shift;   // row block I needs column blocks J >= I >> shift (1: 64/128-SNP, 0: square)
-  };
-  int nI, nJ, nG, G, I0, sh;
-  int g, I, J, col_end, row_end;
-  bool valid;
-
-  __device__ void set_group() {
-    col_end = min((g + 1) * G, nJ);
-    row_end = min(nI, col_end << sh);
-  }
-  // From group g on, the first group holding a row >= I0; rows start at I0.
-  __device__ void enter_group() {
-    while (g < nG) {
-      set_group();
-      if (I0 < row_end) {
-        I = I0;
-        J = max(g * G, I >> sh);
-        return;
-      }
-      ++g;
-    }
-    valid = false;
-  }
-  __device__ void init(const Params &p, int64_t start) {
-    nI = min(p.nI, p.I1);
-    nJ = p.nJ;
-    G = p.group;
-    I0 = p.I0;
-    sh = p.shift;
-    nG = (nJ + G - 1) / G;
-    valid = nI > I0 && nJ > 0;
-    g = (I0 >> sh) / G;
-    if (valid) enter_group();
-    advance(start);
-  }
-  __device__ void advance(int64_t step) {
-    while (valid && step > 0) {
-      const int64_t rem = col_end - 1 - J;
-      if (step <= rem) {
-        J += static_cast<int>(step);
-        return;
-      }
-      step -= rem + 1;
-      if (++I >= row_end) {
-        ++g;
-        enter_group();
-      } else {
-        J = max(g * G, I >> sh);
-      }
-    }
-  }
-  __device__ int map_index() const { return 0; }
-  __device__ int k_blocks(int nkb) const { return nkb; }
-  __device__ int a_row() const { return I * BM; }
-  __device__ int b_row() const { return J * BN; }
-};
 
 // Row / column block of a tile as the 2-way epilogue sees it: I in 64-SNP
 // units (A rows 128 I ..), J in 128-SNP units (B rows 256 J ..).
@@ -201,12 +138,6 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1)
 }
 
 // ---------------------------------------------------------------- SM pairs
-
-// 256 x 256 tiles (128 SNPs i x 128 SNPs j) on pairs of SMs.
-struct TriSchedPair : TriSched {
-  __device__ int a_row() const { return I * 256; }
-  __device__ int b_row() const { return J * 256; }
-};
 
 struct Epi2Pair {
   using Params = Tally2Args;

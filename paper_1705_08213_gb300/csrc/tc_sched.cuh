@@ -1,0 +1,81 @@
+// Tile order over the upper triangle of a Gram product, shared by the 2-way
+// tally kernels (biallelic and multi-allelic).
+#pragma once
+
+#include "tc_pipeline.cuh"
+
+namespace ccc {
+namespace {
+
+// Upper-triangle tiles: I = 64-SNP row block, J = 128-SNP column block,
+// J >= I/2 (the first column block holding a j > every i of the row block),
+// in groups of `group` column blocks, rows inside a group in increasing order.
+struct TriSched {
+  struct Params {
+    int nI, nJ, group;
+    int I0, I1;  // row blocks [I0, I1) (a phase); 0, nI for the whole triangle
+    int shift;   // row block I needs column blocks J >= I >> shift (1: 64/128-SNP, 0: square)
+  };
+  int nI, nJ, nG, G, I0, sh;
+  int g, I, J, col_end, row_end;
+  bool valid;
+
+  __device__ void set_group() {
+    col_end = min((g + 1) * G, nJ);
+    row_end = min(nI, col_end << sh);
+  }
+  // From group g on, the first group holding a row >= I0; rows start at I0.
+  __device__ void enter_group() {
+    while (g < nG) {
+      set_group();
+      if (I0 < row_end) {
+        I = I0;
+        J = max(g * G, I >> sh);
+        return;
+      }
+      ++g;
+    }
+    valid = false;
+  }
+  __device__ void init(const Params &p, int64_t start) {
+    nI = min(p.nI, p.I1);
+    nJ = p.nJ;
+    G = p.group;
+    I0 = p.I0;
+    sh = p.shift;
+    nG = (nJ + G - 1) / G;
+    valid = nI > I0 && nJ > 0;
+    g = (I0 >> sh) / G;
+    if (valid) enter_group();
+    advance(start);
+  }
+  __device__ void advance(int64_t step) {
+    while (valid && step > 0) {
+      const int64_t rem = col_end - 1 - J;
+      if (step <= rem) {
+        J += static_cast<int>(step);
+        return;
+      }
+      step -= rem + 1;
+      if (++I >= row_end) {
+        ++g;
+        enter_group();
+      } else {
+        J = max(g * G, I >> sh);
+      }
+    }
+  }
+  __device__ int map_index() const { return 0; }
+  __device__ int k_blocks(int nkb) const { return nkb; }
+  __device__ int a_row() const { return I * tc::BM; }
+  __device__ int b_row() const { return J * tc::BN; }
+};
+
+// 256 x 256 tiles on pairs of SMs: I, J count 256-row blocks.
+struct TriSchedPair : TriSched {
+  __device__ int a_row() const { return I * 256; }
+  __device__ int b_row() const { return J * 256; }
+};
+
+}  // namespace
+}  // namespace ccc

@@ -95,3 +95,33 @@ def assert_tally_equal(got, expect, what=""):
         bad = np.argwhere(got != expect)[:5]
         raise AssertionError(f"{what}: {int((got != expect).sum())} tallies differ; first "
                              f"{[(tuple(i), got[tuple(i)], expect[tuple(i)]) for i in bad]}")
+
+
+def to_device_bytes(geno_np):
+    torch = torch_mod()
+    return torch.from_numpy(np.ascontiguousarray(geno_np, dtype=np.uint8)).cuda()
+
+
+def run_multi(geno_np, n_f, s, norm=0, gamma=2.0 / 3.0, fused=True, group=0):
+    """Multi-allelic tallies (int32 [npairs, s*s]) and CCC (float32 [npairs, s*s]) via the C ABI."""
+    import paper_1705_08213_gb300 as ccc
+    torch = torch_mod()
+    g = to_device_bytes(geno_np)
+    n_v = geno_np.shape[0]
+    npairs = ccc.ccc2_count(n_v)
+    opts = ccc.ccc_opts_default(norm=norm, gamma=gamma)
+    ws = workspace(ccc.ccc_multi_workspace_size(g, n_f, s, opts))
+    opts = ccc.ccc_opts_default(norm=norm, gamma=gamma, workspace=ws)
+    opts.group = group
+    tally = torch.full((max(npairs, 1), s * s), -7, dtype=torch.int32, device="cuda")
+    out = torch.full((max(npairs, 1), s * s), -7.0, dtype=torch.float32, device="cuda")
+    if fused:
+        ccc.ccc2_multi_tally_metric(g, n_f, s, tally, out, opts)
+    else:
+        counts = torch.zeros((n_v, s + 1), dtype=torch.int32, device="cuda")
+        ccc.ccc_multi_counts(g, n_f, s, counts)
+        ccc.ccc2_multi_tally(g, n_f, s, tally, opts)
+        ccc.ccc2_multi_metric(tally, counts, n_v, s, opts, out)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    return tally[:npairs].cpu().numpy(), out[:npairs].cpu().numpy()

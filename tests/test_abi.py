@@ -191,3 +191,52 @@ def test_phase_bounds_3way(lib):
     ws = ccc.ccc3_stream_workspace_size((1536, 256), 8192, 8, o)
     # two staging slots of the largest phase, 64 bytes per triple
     assert ws >= base + 2 * 64 * (ccc.ccc3_count(1536, 0, 1536) // 8)
+
+
+def test_multi_workspace_size(lib):
+    """Markers with s states: the operand holds 32 rows per floor(32 / s) markers, padded to
+    256-row blocks, of round_up(n_f, 128) bytes; the popcount path is not offered."""
+    o = ccc.ccc_opts_default()
+    n_v, n_f = 1000, 2000
+    for s, per_quarter in ((2, 16), (3, 10), (4, 8), (5, 6), (8, 4), (9, 3), (15, 2)):
+        rows = -(-n_v // per_quarter) * 32
+        rows = -(-rows // 256) * 256
+        size = ccc.ccc_multi_workspace_size((n_v, 2000), n_f, s, o)
+        assert rows * 2048 <= size < rows * 2048 + n_v * s * 4 + 4096, s
+    for bad_s in (1, 16):
+        with pytest.raises(ccc.CCCError) as e:
+            ccc.ccc_multi_workspace_size((n_v, 2000), n_f, bad_s, o)
+        assert e.value.status == ccc.CCC_EINVAL
+    o.path = ccc.CCC_PATH_POPC
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_multi_workspace_size((n_v, 2000), n_f, 4, o)
+    assert e.value.status == ccc.CCC_EUNSUPPORTED
+    o = ccc.ccc_opts_default(tile=1)
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_multi_workspace_size((n_v, 2000), n_f, 4, o)
+    assert e.value.status == ccc.CCC_EINVAL
+
+
+def test_multi_argument_errors_before_device_work(lib):
+    o = ccc.ccc_opts_default()
+    t = ctypes.c_void_p(256)
+    M = ccc.ccc_panel_multi
+    assert lib.ccc2_multi_tally(None, t, ctypes.byref(o), None) == ccc.CCC_EINVAL
+    for p in (M(16, 100, 10, 104, 4, 0),      # ld not a multiple of 16
+              M(16, 100, 10, 96, 4, 0),       # ld < n_f
+              M(8, 100, 10, 112, 4, 0),       # misaligned entries
+              M(16, 100, 10, 112, 1, 0),      # s < 2
+              M(16, 100, 10, 112, 16, 0),     # s > 15
+              M(16, 0, 10, 112, 4, 0)):       # no individuals
+        assert lib.ccc2_multi_tally(ctypes.byref(p), t, ctypes.byref(o), None) == ccc.CCC_EINVAL
+    p = M(16, ccc.CCC_MAX_NF + 1, 10, 1 << 22, 4, 0)
+    assert lib.ccc2_multi_tally(ctypes.byref(p), t, ctypes.byref(o), None) == ccc.CCC_ERANGE
+    p = M(16, 100, 10, 112, 4, 0)
+    assert lib.ccc2_multi_tally(ctypes.byref(p), ctypes.c_void_p(260), ctypes.byref(o), None) \
+        == ccc.CCC_EINVAL  # tally not 16-byte aligned
+    assert lib.ccc2_multi_tally_metric(ctypes.byref(p), t, None, ctypes.byref(o), None) == ccc.CCC_EINVAL
+    o.path = ccc.CCC_PATH_POPC
+    assert lib.ccc2_multi_tally(ctypes.byref(p), t, ctypes.byref(o), None) == ccc.CCC_EUNSUPPORTED
+    o = ccc.ccc_opts_default()
+    assert lib.ccc2_multi_metric(t, t, 10, 16, ctypes.byref(o), t, None) == ccc.CCC_EINVAL
+    assert lib.ccc2_multi_metric(None, t, 10, 4, ctypes.byref(o), t, None) == ccc.CCC_EINVAL
