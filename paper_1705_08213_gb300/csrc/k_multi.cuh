@@ -63,10 +63,12 @@ template <int S>
 struct EpiMulti {
   using Params = MultiArgs;
   static constexpr int PW = snps_per_quarter(S);
+  static constexpr int STAGE_BYTES_PER_WARP = 0;
 
   template <int NC>
   __device__ static void tile(const Params &args, const TriSchedPair &sc, int rank, int quarter,
-                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0) {
+                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
+                              float *) {
     const int u = lane / S;
     const int a = lane - u * S;
     const int64_t n_v = args.n_v;

@@ -39,6 +39,11 @@ constexpr int TMEM_COLS = 512;
 constexpr int NUM_BARS = 2 * STAGES + 5;
 constexpr uint32_t IDESC = idesc_e4m3_f32(256, 256);
 constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE_BYTES + NUM_BARS * 8 + 64;
+// Dynamic shared memory of a kernel whose epilogue warps each stage
+// `stage_bytes` (Epi::STAGE_BYTES_PER_WARP) after the barriers.
+constexpr size_t smem_bytes(int epi_warps, int stage_bytes) {
+  return SMEM_BYTES + (stage_bytes > 0 ? 16 + static_cast<size_t>(epi_warps) * stage_bytes : 0);
+}
 
 static_assert(SMEM_BYTES <= 232448, "dynamic shared memory limit");
 
@@ -111,7 +116,10 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
 // tile's tensor map in tm[].
 // Epi: template <int NC> static void tile(const Params&, const Sched&, int rank,
 //        int quarter, int lane, uint32_t t_base, uint32_t release_cluster_bar,
-//        int c0); the release arrives at a cluster address.
+//        int c0, float *stage); the release arrives at a cluster address;
+//        static constexpr int STAGE_BYTES_PER_WARP: shared memory each epilogue
+//        warp may use at `stage` (the kernel is launched with
+//        smem_bytes(EW, STAGE_BYTES_PER_WARP)).
 template <class Sched, class Epi, int EW>
 __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
                                                      const typename Sched::Params &sp,
@@ -125,6 +133,8 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
   uint64_t *bars = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NUM_BARS);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  float *const stage_base = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(tmem_slot) + 64 + 15) & ~static_cast<uintptr_t>(15));
 
   constexpr int EPI_THREADS = tc::Epilogue<EW>::THREADS;
   const int warp = threadIdx.x >> 5;
@@ -264,7 +274,8 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       const uint32_t t_base =
           tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * ACC_COLS;
       Epi::template tile<NC>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
-                             map_to_rank(tempty_bar(acc), 0), c0);
+                             map_to_rank(tempty_bar(acc), 0), c0,
+                             stage_base + (warp - 2) * (Epi::STAGE_BYTES_PER_WARP / 4));
     }
   }
 
