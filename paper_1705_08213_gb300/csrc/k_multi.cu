@@ -49,18 +49,20 @@ __device__ __forceinline__ uint32_t valid_bytes(int64_t q0, int64_t n_f) {
 //
 // One warp per SNP: s_i^a = sum_q rho_{i,q}(a) (Eq. 1 numerators), n_i, and the
 // PERSNP factors 1 - gamma s_i^a / (2 n_i) rounded once to fp32 (the formula of
-// the biallelic counts kernel).
+// the biallelic counts kernel).  Templated on the number of states S.
+template <int S>
 __global__ void __launch_bounds__(256) k_multi_counts(const uint8_t *__restrict__ geno, int64_t n_f,
-                                                      int64_t n_v, int64_t ld, int s,
+                                                      int64_t n_v, int64_t ld,
                                                       int32_t *__restrict__ counts,
                                                       float *__restrict__ w, double gamma) {
+  constexpr int s = S;
   const int lane = threadIdx.x & 31;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n_v) return;
   const uint8_t *row = geno + i * ld;
-  uint32_t c[15];
+  uint32_t c[S];
 #pragma unroll
-  for (int a = 0; a < 15; ++a) c[a] = 0;
+  for (int a = 0; a < S; ++a) c[a] = 0;
   uint32_t n = 0;
   const uint32_t us = static_cast<uint32_t>(s);
   for (int64_t q0 = 16 * static_cast<int64_t>(lane); q0 < n_f; q0 += 16 * 32) {
@@ -73,27 +75,25 @@ __global__ void __launch_bounds__(256) k_multi_counts(const uint8_t *__restrict_
           valid_bytes(q0 + 4 * k, n_f) & ~(nibble_ge(lo, us) | nibble_ge(hi, us));
       n += __popc(present);
 #pragma unroll
-      for (int a = 0; a < 15; ++a)
-        if (a < s)
-          c[a] += __popc(nibble_eq(lo, a) & present) + __popc(nibble_eq(hi, a) & present);
+      for (int a = 0; a < S; ++a)
+        c[a] += __popc(nibble_eq(lo, a) & present) + __popc(nibble_eq(hi, a) & present);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     n += __shfl_xor_sync(0xffffffffu, n, o);
 #pragma unroll
-    for (int a = 0; a < 15; ++a) c[a] += __shfl_xor_sync(0xffffffffu, c[a], o);
+    for (int a = 0; a < S; ++a) c[a] += __shfl_xor_sync(0xffffffffu, c[a], o);
   }
   if (lane == 0) {
 #pragma unroll
-    for (int a = 0; a < 15; ++a)
-      if (a < s) {
-        if (counts) counts[i * (s + 1) + a] = static_cast<int32_t>(c[a]);
-        if (w) {
-          const double f = n > 0 ? static_cast<double>(c[a]) / (2.0 * static_cast<double>(n)) : 0.0;
-          w[i * s + a] = static_cast<float>(1.0 - gamma * f);
-        }
+    for (int a = 0; a < S; ++a) {
+      if (counts) counts[i * (s + 1) + a] = static_cast<int32_t>(c[a]);
+      if (w) {
+        const double f = n > 0 ? static_cast<double>(c[a]) / (2.0 * static_cast<double>(n)) : 0.0;
+        w[i * s + a] = static_cast<float>(1.0 - gamma * f);
       }
+    }
     if (counts) counts[i * (s + 1) + s] = static_cast<int32_t>(n);
   }
 }
@@ -224,9 +224,20 @@ int64_t multi_rows_pad(int64_t n_v, int s) {
 int launch_multi_counts(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t ld, int s,
                         int32_t *counts, float *w, double gamma, cudaStream_t st) {
   if (n_v < 1) return CCC_OK;
-  const int64_t blocks = (n_v + 7) / 8;
-  k_multi_counts<<<static_cast<unsigned>(blocks), 256, 0, st>>>(geno, n_f, n_v, ld, s, counts, w,
-                                                               gamma);
+  const unsigned blocks = static_cast<unsigned>((n_v + 7) / 8);
+  switch (s) {
+#define CCC_MULTI_COUNTS(S)                                                                   \
+  case S:                                                                                    \
+    k_multi_counts<S><<<blocks, 256, 0, st>>>(geno, n_f, n_v, ld, counts, w, gamma);       \
+    break;
+    CCC_MULTI_COUNTS(2) CCC_MULTI_COUNTS(3) CCC_MULTI_COUNTS(4) CCC_MULTI_COUNTS(5)
+    CCC_MULTI_COUNTS(6) CCC_MULTI_COUNTS(7) CCC_MULTI_COUNTS(8) CCC_MULTI_COUNTS(9)
+    CCC_MULTI_COUNTS(10) CCC_MULTI_COUNTS(11) CCC_MULTI_COUNTS(12) CCC_MULTI_COUNTS(13)
+    CCC_MULTI_COUNTS(14) CCC_MULTI_COUNTS(15)
+#undef CCC_MULTI_COUNTS
+    default:
+      return CCC_EINVAL;
+  }
   return note_launch();
 }
 
