@@ -140,3 +140,62 @@ def test_full_size_workload_sampled_rows():
     it = torch.from_numpy(idx).cuda()
     assert_tally_equal(tally[it].cpu().numpy(), et, "full-size rows")
     assert_ccc_close(out[it].cpu().numpy(), ec, what="full-size rows")
+
+
+def test_tile_order_groups_agree():
+    s, n_v, n_f = 5, 400, 600
+    g = synth.panel_multi(n_v, n_f, s, seed=80, p_missing=0.02)
+    t0, c0 = run_multi(g, n_f, s)
+    for group in (1, 3, 16):
+        t1, c1 = run_multi(g, n_f, s, group=group)
+        np.testing.assert_array_equal(t1, t0)
+        np.testing.assert_array_equal(c1, c0)
+
+
+def test_workspace_too_small_is_refused():
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    s, n_v, n_f = 4, 50, 200
+    g = to_device_bytes(synth.panel_multi(n_v, n_f, s, seed=81))
+    opts = ccc.ccc_opts_default()
+    need = ccc.ccc_multi_workspace_size(g, n_f, s, opts)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    opts = ccc.ccc_opts_default(workspace=ws)
+    opts.workspace_bytes = need - 1
+    tally = torch.full((ccc.ccc2_count(n_v), s * s), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc2_multi_tally(g, n_f, s, tally, opts)
+    assert e.value.status == ccc.CCC_ENOSPACE
+    torch.cuda.synchronize()
+    assert bool((tally == -7).all())  # nothing was written
+
+
+def test_cuda_graph_capture_and_replay():
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    s, n_v, n_f = 3, 300, 500
+    gm = synth.panel_multi(n_v, n_f, s, seed=82, p_missing=0.03)
+    g = to_device_bytes(gm)
+    opts = ccc.ccc_opts_default()
+    ws = torch.empty(ccc.ccc_multi_workspace_size(g, n_f, s, opts), dtype=torch.uint8, device="cuda")
+    opts = ccc.ccc_opts_default(workspace=ws)
+    npairs = ccc.ccc2_count(n_v)
+    tally = torch.zeros((npairs, s * s), dtype=torch.int32, device="cuda")
+    out = torch.zeros((npairs, s * s), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        ccc.ccc2_multi_tally_metric(g, n_f, s, tally, out, opts, stream=st)  # first call outside
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        ccc.ccc2_multi_tally_metric(g, n_f, s, tally, out, opts, stream=st)
+    tally.zero_()
+    out.zero_()
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    et, ec = oracle.ccc2_multi_all(gm, n_f, s)
+    assert_tally_equal(tally.cpu().numpy(), et, "graph replay")
+    assert_ccc_close(out.cpu().numpy(), ec, what="graph replay")
