@@ -429,9 +429,7 @@ class Runner:
         """
         torch, ccc, w = self.torch, self.ccc, self.w
         if mode == "auto":
-            mode = "stream" if not (self.filter or self.states) else "copy"
-        if self.states and mode == "stream":
-            mode = "copy"  # the multi-allelic calls have no phased variant
+            mode = "stream" if not self.filter else "copy"
         self.e2e_mode = mode if not self.filter else "copy"
         streamed = mode == "stream" and not self.filter
         direct = mode == "direct" and not self.filter
@@ -449,8 +447,11 @@ class Runner:
             dev = []
             del self.tally, self.out, self.ws
             o0 = ccc.ccc_opts_default(path=self.path, tile=self.tile)
-            size = (ccc.ccc2_stream_workspace_size if w["kind"] == 2 else
-                    ccc.ccc3_stream_workspace_size)(self.geno, w["n_f"], phases, o0)
+            if self.states:
+                size = ccc.ccc2_multi_stream_workspace_size(self.geno, w["n_f"], self.states, phases, o0)
+            else:
+                size = (ccc.ccc2_stream_workspace_size if w["kind"] == 2 else
+                        ccc.ccc3_stream_workspace_size)(self.geno, w["n_f"], phases, o0)
             self.ws_stream = torch.empty(size, dtype=torch.uint8, device=self.dev)
             self.opts = ccc.ccc_opts_default(path=self.path, workspace=self.ws_stream,
                                              tile=self.tile)
@@ -461,7 +462,10 @@ class Runner:
 
         def one():
             self.geno.copy_(self.host_geno, non_blocking=True)
-            if streamed:
+            if streamed and self.states:
+                ccc.ccc2_multi_stream(self.geno, w["n_f"], self.states, phases, host[0], host[1],
+                                      self.opts, stream)
+            elif streamed:
                 (ccc.ccc2_stream if w["kind"] == 2 else ccc.ccc3_stream)(
                     self.geno, w["n_f"], phases, host[0], host[1], self.opts, stream)
             else:
@@ -737,8 +741,10 @@ def main():
                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
                          "mode": run.e2e_mode,
                          "note": {"stream": "pinned host panel -> device, "
-                                            f"ccc{w['kind']}_stream (8 phases: results of each phase "
-                                            "copied to pinned host memory while the next computes)",
+                                            + ("ccc2_multi_stream" if w.get("states") else
+                                               f"ccc{w['kind']}_stream")
+                                            + " (8 phases: results of each phase copied to pinned "
+                                              "host memory while the next computes)",
                                   "direct": "pinned host panel -> device, the same C ABI call with "
                                             "its output arrays in pinned host memory (the kernel "
                                             "epilogues store over the host link)",

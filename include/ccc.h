@@ -407,6 +407,32 @@ int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float 
 int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
                       const ccc_opts *opts, float *ccc, void *stream);
 
+/* One phase (Sec. 8 item 3) of ccc2_multi_tally_metric: the pairs with
+ * i_begin <= i < i_end and every j > i, stored from index
+ * ccc2_index(i_begin, i_begin + 1, n_v) on (s*s values per pair).  tally, ccc:
+ * device [ccc2_rows_count(n_v, i_begin, i_end)][s*s].  Workspace as for
+ * ccc2_multi_tally_metric.  0 <= i_begin <= i_end <= n_v; ranges on multiples
+ * of 8*floor(32/s) markers (ccc2_multi_phase_bounds) waste no tensor work. */
+int ccc2_multi_tally_metric_rows(const ccc_panel_multi *panel, int64_t i_begin, int64_t i_end,
+                                 int32_t *tally, float *ccc, const ccc_opts *opts, void *stream);
+
+/* Host helper: rows [0, n_v) split into n_phases ranges with about equal pair
+ * counts, inner bounds on multiples of 8*floor(32/s).  bounds: host
+ * int64[n_phases + 1]. */
+int ccc2_multi_phase_bounds(int64_t n_v, int32_t n_states, int n_phases, int64_t *bounds);
+
+/* Phased multi-allelic output to host memory, as ccc2_stream does for
+ * biallelic panels: every pair computed phase by phase into two staging
+ * buffers of the workspace, each finished phase copied to host_tally /
+ * host_ccc ([npairs][s*s], pinned host memory; host_ccc may be NULL) while the
+ * next one computes, on the two copy streams of ccc2_stream; the caller's
+ * stream waits for the copies.  Workspace: ccc2_multi_stream_workspace_size().
+ * n_phases >= 2. */
+int ccc2_multi_stream_workspace_size(const ccc_panel_multi *panel, int n_phases,
+                                     const ccc_opts *opts, size_t *bytes);
+int ccc2_multi_stream(const ccc_panel_multi *panel, int n_phases, int32_t *host_tally,
+                      float *host_ccc, const ccc_opts *opts, void *stream);
+
 /*
  * Device-side status of the workspace: *status receives CCC_OK or the first
  * CCC_E* code a kernel recorded (CCC_ETIMEOUT when a bounded wait gave up).

@@ -32,7 +32,8 @@ __all__ = [
     "ccc2_phase_bounds", "ccc2_stream_workspace_size", "ccc2_stream",
     "ccc3_phase_bounds", "ccc3_stream_workspace_size", "ccc3_stream",
     "ccc_panel_multi", "ccc_multi_workspace_size", "ccc_multi_counts", "ccc2_multi_tally",
-    "ccc2_multi_tally_metric", "ccc2_multi_metric",
+    "ccc2_multi_tally_metric", "ccc2_multi_metric", "ccc2_multi_tally_metric_rows",
+    "ccc2_multi_phase_bounds", "ccc2_multi_stream_workspace_size", "ccc2_multi_stream",
 ]
 
 CCC_OK = 0
@@ -105,6 +106,12 @@ def load():
     lib.ccc2_multi_tally.argtypes = [P(ccc_panel_multi), vp, P(ccc_opts), vp]
     lib.ccc2_multi_tally_metric.argtypes = [P(ccc_panel_multi), vp, vp, P(ccc_opts), vp]
     lib.ccc2_multi_metric.argtypes = [vp, vp, i64, ctypes.c_int32, P(ccc_opts), vp, vp]
+    lib.ccc2_multi_tally_metric_rows.argtypes = [P(ccc_panel_multi), i64, i64, vp, vp, P(ccc_opts),
+                                                 vp]
+    lib.ccc2_multi_phase_bounds.argtypes = [i64, ctypes.c_int32, ctypes.c_int, P(i64)]
+    lib.ccc2_multi_stream_workspace_size.argtypes = [P(ccc_panel_multi), ctypes.c_int, P(ccc_opts),
+                                                     P(ctypes.c_size_t)]
+    lib.ccc2_multi_stream.argtypes = [P(ccc_panel_multi), ctypes.c_int, vp, vp, P(ccc_opts), vp]
     lib.ccc_opts_default.restype = None
     lib.ccc_workspace_size.argtypes = [P(ccc_panel), P(ccc_opts), ctypes.c_int, P(ctypes.c_size_t)]
     lib.ccc_allele_counts.argtypes = [P(ccc_panel), vp, vp]
@@ -477,3 +484,36 @@ def ccc2_multi_metric(tally, counts, n_v, s, opts, ccc, stream=None):
     _check("ccc2_multi_metric",
            load().ccc2_multi_metric(_ptr(tally), _ptr(counts), int(n_v), int(s), ctypes.byref(opts),
                                     _ptr(ccc), _stream(stream)))
+
+
+def ccc2_multi_tally_metric_rows(geno, n_f, s, i_begin, i_end, tally, ccc, opts, stream=None):
+    p = _panel_multi(geno, n_f, s)
+    _check("ccc2_multi_tally_metric_rows",
+           load().ccc2_multi_tally_metric_rows(ctypes.byref(p), int(i_begin), int(i_end), _ptr(tally),
+                                               _ptr(ccc), ctypes.byref(opts), _stream(stream)))
+
+
+def ccc2_multi_phase_bounds(n_v, s, n_phases):
+    b = (ctypes.c_int64 * (n_phases + 1))()
+    _check("ccc2_multi_phase_bounds", load().ccc2_multi_phase_bounds(int(n_v), int(s), int(n_phases), b))
+    return list(b)
+
+
+def ccc2_multi_stream_workspace_size(geno_or_shape, n_f, s, n_phases, opts):
+    if hasattr(geno_or_shape, "shape") and hasattr(geno_or_shape, "data_ptr"):
+        p = _panel_multi(geno_or_shape, n_f, s)
+    else:
+        n_v, ld = geno_or_shape
+        p = ccc_panel_multi(None, int(n_f), int(n_v), int(ld), int(s), 0)
+    out = ctypes.c_size_t(0)
+    _check("ccc2_multi_stream_workspace_size",
+           load().ccc2_multi_stream_workspace_size(ctypes.byref(p), int(n_phases), ctypes.byref(opts),
+                                                   ctypes.byref(out)))
+    return int(out.value)
+
+
+def ccc2_multi_stream(geno, n_f, s, n_phases, host_tally, host_ccc, opts, stream=None):
+    p = _panel_multi(geno, n_f, s)
+    _check("ccc2_multi_stream",
+           load().ccc2_multi_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally), _ptr(host_ccc),
+                                    ctypes.byref(opts), _stream(stream)))

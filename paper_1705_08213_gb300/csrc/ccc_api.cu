@@ -249,14 +249,14 @@ int64_t rows_count(int64_t n_v, int64_t i_begin, int64_t i_end) {
   return pair_index(i_end, i_end + 1, n_v) - pair_index(i_begin, i_begin + 1, n_v);
 }
 
-// Balanced phase bounds on multiples of 64 rows.
-static void phase_bounds(int64_t n_v, int n_phases, int64_t *bounds) {
+// Balanced phase bounds on multiples of `step` rows.
+static void phase_bounds(int64_t n_v, int n_phases, int64_t *bounds, int64_t step = 64) {
   const int64_t total = rows_count(n_v, 0, n_v);
   bounds[0] = 0;
   int64_t r = 0;
   for (int p = 1; p < n_phases; ++p) {
     const double target = static_cast<double>(total) * p / n_phases;
-    while (r < n_v && static_cast<double>(rows_count(n_v, 0, r)) < target) r += 64;
+    while (r < n_v && static_cast<double>(rows_count(n_v, 0, r)) < target) r += step;
     if (r > n_v) r = n_v;
     if (r < bounds[p - 1]) r = bounds[p - 1];
     bounds[p] = r;
@@ -739,9 +739,13 @@ static int check_multi_workspace(const ccc_opts *o, const MultiLayout &L, cudaSt
              : CCC_ECUDA;
 }
 
-// The multi-allelic 2-way sequence: factors (PERSNP values), operand rows, tally kernel.
+// Markers per 256-row operand block: phases on multiples of it waste no tile.
+static int64_t multi_block_rows(int s) { return 8 * (32 / s); }
+
+// The multi-allelic 2-way sequence: factors (PERSNP values), operand rows, tally
+// kernel over the rows [i_begin, i_end) (all rows when i_end < 0).
 static int run_multi(const ccc_panel_multi *p, int32_t *tally, float *out_ccc, const ccc_opts *o,
-                     cudaStream_t s) {
+                     cudaStream_t s, int64_t i_begin = 0, int64_t i_end = -1) {
   CCC_TRY(check_panel_multi(p));
   CCC_TRY(check_opts_multi(o));
   if (tally == nullptr || !aligned(tally, 16)) return CCC_EINVAL;
@@ -757,12 +761,30 @@ static int run_multi(const ccc_panel_multi *p, int32_t *tally, float *out_ccc, c
     CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
   uint8_t *op = at<uint8_t>(o, L.op);
   CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s));
+  if (i_end < 0) {
+    i_begin = 0;
+    i_end = p->n_v;
+  }
   const int slot = timing_begin(s);
   const int rc = launch_tally2_multi(ns, p->n_v, w, tally, out_ccc, at<int32_t>(o, L.status),
                                      static_cast<float>(o->gamma), o->norm, o->group, op,
-                                     L.rows_pad, L.kpad, dev.sms, s);
+                                     L.rows_pad, L.kpad, dev.sms, s, i_begin, i_end,
+                                     pair_index(i_begin, i_begin + 1, p->n_v));
   timing_end(slot, s);
   return rc;
+}
+
+// Largest phase of a multi-allelic split, in pairs.
+static int64_t max_phase_pairs_multi(int64_t n_v, int s, int n_phases) {
+  int64_t b[1025];
+  if (n_phases > 1024) return -1;
+  phase_bounds(n_v, n_phases, b, multi_block_rows(s));
+  int64_t m = 0;
+  for (int k = 0; k < n_phases; ++k) {
+    const int64_t c = rows_count(n_v, b[k], b[k + 1]);
+    if (c > m) m = c;
+  }
+  return m;
 }
 
 }  // namespace ccc
@@ -771,54 +793,7 @@ using namespace ccc;
 
 extern "C" {
 
-int ccc_multi_workspace_size(const ccc_panel_multi *panel, const ccc_opts *opts, size_t *bytes) {
-  if (bytes == nullptr || panel == nullptr) return CCC_EINVAL;
-  CCC_TRY(check_opts_multi(opts));
-  if (panel->n_f < 1 || panel->n_v < 1 || panel->n_states < 2 || panel->n_states > 15)
-    return CCC_EINVAL;
-  if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
-  *bytes = make_multi_layout(panel->n_f, panel->n_v, panel->n_states, true).total;
-  return CCC_OK;
-}
 
-int ccc_multi_counts(const ccc_panel_multi *panel, int32_t *counts, void *stream) {
-  CCC_TRY(check_panel_multi(panel));
-  if (counts == nullptr || !aligned(counts, 4)) return CCC_EINVAL;
-  DeviceInfo dev;
-  CCC_TRY(query_device(&dev));
-  return launch_multi_counts(panel->geno, panel->n_f, panel->n_v, panel->ld, panel->n_states,
-                             counts, nullptr, 0.0, static_cast<cudaStream_t>(stream));
-}
-
-int ccc2_multi_tally(const ccc_panel_multi *panel, int32_t *tally, const ccc_opts *opts,
-                     void *stream) {
-  return run_multi(panel, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
-}
-
-int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float *out_ccc,
-                            const ccc_opts *opts, void *stream) {
-  if (out_ccc == nullptr) return CCC_EINVAL;
-  return run_multi(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
-}
-
-int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
-                      const ccc_opts *opts, float *out_ccc, void *stream) {
-  CCC_TRY(check_opts_multi(opts));
-  if (n_v < 1 || n_v > kMaxNV || n_states < 2 || n_states > 15) return CCC_EINVAL;
-  if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
-  if (!aligned(tally, 4) || !aligned(out_ccc, 4) || !aligned(counts, 4)) return CCC_EINVAL;
-  DeviceInfo dev;
-  CCC_TRY(query_device(&dev));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const MultiLayout L = make_multi_layout(1, n_v, n_states, false);
-  CCC_TRY(check_multi_workspace(opts, L, s));
-  if (n_v < 2) return CCC_OK;
-  float *w = at<float>(opts, L.w);
-  if (opts->norm == CCC_NORM_PERSNP)
-    CCC_TRY(launch_multi_factors(counts, n_v, n_states, w, opts->gamma, s));
-  return launch_metric2_multi(tally, w, n_v, n_states, static_cast<float>(opts->gamma), opts->norm,
-                              out_ccc, s);
-}
 
 
 void ccc_opts_default(ccc_opts *opts) {
@@ -1310,6 +1285,165 @@ int ccc_timing_read(double *total_ms, int64_t *launches) {
   *total_ms = sum;
   *launches = g_timing.used;
   g_timing.used = 0;
+  return CCC_OK;
+}
+
+int ccc_multi_workspace_size(const ccc_panel_multi *panel, const ccc_opts *opts, size_t *bytes) {
+  if (bytes == nullptr || panel == nullptr) return CCC_EINVAL;
+  CCC_TRY(check_opts_multi(opts));
+  if (panel->n_f < 1 || panel->n_v < 1 || panel->n_states < 2 || panel->n_states > 15)
+    return CCC_EINVAL;
+  if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
+  *bytes = make_multi_layout(panel->n_f, panel->n_v, panel->n_states, true).total;
+  return CCC_OK;
+}
+
+int ccc_multi_counts(const ccc_panel_multi *panel, int32_t *counts, void *stream) {
+  CCC_TRY(check_panel_multi(panel));
+  if (counts == nullptr || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return launch_multi_counts(panel->geno, panel->n_f, panel->n_v, panel->ld, panel->n_states,
+                             counts, nullptr, 0.0, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_multi_tally(const ccc_panel_multi *panel, int32_t *tally, const ccc_opts *opts,
+                     void *stream) {
+  return run_multi(panel, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float *out_ccc,
+                            const ccc_opts *opts, void *stream) {
+  if (out_ccc == nullptr) return CCC_EINVAL;
+  return run_multi(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
+}
+
+int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
+                      const ccc_opts *opts, float *out_ccc, void *stream) {
+  CCC_TRY(check_opts_multi(opts));
+  if (n_v < 1 || n_v > kMaxNV || n_states < 2 || n_states > 15) return CCC_EINVAL;
+  if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
+  if (!aligned(tally, 4) || !aligned(out_ccc, 4) || !aligned(counts, 4)) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const MultiLayout L = make_multi_layout(1, n_v, n_states, false);
+  CCC_TRY(check_multi_workspace(opts, L, s));
+  if (n_v < 2) return CCC_OK;
+  float *w = at<float>(opts, L.w);
+  if (opts->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_multi_factors(counts, n_v, n_states, w, opts->gamma, s));
+  return launch_metric2_multi(tally, w, n_v, n_states, static_cast<float>(opts->gamma), opts->norm,
+                              out_ccc, s);
+}
+
+int ccc2_multi_tally_metric_rows(const ccc_panel_multi *panel, int64_t i_begin, int64_t i_end,
+                                 int32_t *tally, float *out_ccc, const ccc_opts *opts, void *stream) {
+  if (panel == nullptr || i_begin < 0 || i_end < i_begin || i_end > panel->n_v) return CCC_EINVAL;
+  if (out_ccc == nullptr) return CCC_EINVAL;
+  if (i_begin == i_end || rows_count(panel->n_v, i_begin, i_end) == 0) {
+    CCC_TRY(check_panel_multi(panel));
+    CCC_TRY(check_opts_multi(opts));
+    return CCC_OK;
+  }
+  return run_multi(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream), i_begin, i_end);
+}
+
+int ccc2_multi_phase_bounds(int64_t n_v, int32_t n_states, int n_phases, int64_t *bounds) {
+  if (bounds == nullptr || n_v < 1 || n_states < 2 || n_states > 15 || n_phases < 1 ||
+      n_phases > 1 << 20)
+    return CCC_EINVAL;
+  phase_bounds(n_v, n_phases, bounds, multi_block_rows(n_states));
+  return CCC_OK;
+}
+
+int ccc2_multi_stream_workspace_size(const ccc_panel_multi *panel, int n_phases,
+                                     const ccc_opts *opts, size_t *bytes) {
+  if (bytes == nullptr || panel == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
+  size_t base = 0;
+  CCC_TRY(ccc_multi_workspace_size(panel, opts, &base));
+  const int64_t m = max_phase_pairs_multi(panel->n_v, panel->n_states, n_phases);
+  const size_t ss = static_cast<size_t>(panel->n_states) * static_cast<size_t>(panel->n_states);
+  *bytes = align_up(base, 1024) + 2 * align_up(static_cast<size_t>(m) * ss * 8, 1024);
+  return CCC_OK;
+}
+
+int ccc2_multi_stream(const ccc_panel_multi *p, int n_phases, int32_t *host_tally, float *host_ccc,
+                      const ccc_opts *o, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CCC_TRY(check_panel_multi(p));
+  CCC_TRY(check_opts_multi(o));
+  if (host_tally == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
+  size_t need = 0;
+  CCC_TRY(ccc2_multi_stream_workspace_size(p, n_phases, o, &need));
+  if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
+  if (o->workspace_bytes < need) return CCC_ENOSPACE;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return CCC_ECUDA;
+  StreamRes *R = nullptr;
+  CCC_TRY(stream_res(d, &R));
+  const int ns = p->n_states;
+  const int64_t ss = static_cast<int64_t>(ns) * ns;
+  const MultiLayout L = make_multi_layout(p->n_f, p->n_v, ns, true);
+  if (cudaMemsetAsync(at<int32_t>(o, L.status), 0, sizeof(int32_t), s) != cudaSuccess)
+    return CCC_ECUDA;
+  if (p->n_v < 2) return CCC_OK;
+  const bool want_ccc = host_ccc != nullptr;
+  const int64_t slot_pairs = max_phase_pairs_multi(p->n_v, ns, n_phases);
+  const size_t slot_bytes = align_up(static_cast<size_t>(slot_pairs * ss) * 8, 1024);
+  const size_t slot0 = align_up(L.total, 1024);
+  // Preparation once for all phases.
+  float *w = at<float>(o, L.w);
+  if (want_ccc && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
+  uint8_t *op = at<uint8_t>(o, L.op);
+  CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s));
+  int64_t bounds[1025];
+  phase_bounds(p->n_v, n_phases, bounds, multi_block_rows(ns));
+  for (int ph = 0; ph < n_phases; ++ph) {
+    const int64_t i0 = bounds[ph], i1 = bounds[ph + 1];
+    const int64_t cnt = rows_count(p->n_v, i0, i1);
+    if (cnt == 0) continue;
+    const int k = ph & 1;
+    int32_t *st = at<int32_t>(o, slot0 + k * slot_bytes);
+    float *sc = reinterpret_cast<float *>(st + ss * slot_pairs);
+    if (ph >= 2) {  // the slot's previous copies must have finished
+      if (cudaStreamWaitEvent(s, R->copied[k][0], 0) != cudaSuccess ||
+          cudaStreamWaitEvent(s, R->copied[k][1], 0) != cudaSuccess)
+        return CCC_ECUDA;
+    }
+    const int64_t pair0 = pair_index(i0, i0 + 1, p->n_v);
+    const int slot = timing_begin(s);
+    const int rc = launch_tally2_multi(ns, p->n_v, w, st, want_ccc ? sc : nullptr,
+                                       at<int32_t>(o, L.status), static_cast<float>(o->gamma),
+                                       o->norm, o->group, op, L.rows_pad, L.kpad, dev.sms, s, i0, i1,
+                                       pair0);
+    timing_end(slot, s);
+    if (rc != CCC_OK) return rc;
+    if (cudaEventRecord(R->computed[k], s) != cudaSuccess) return CCC_ECUDA;
+    // Tallies on one copy stream, CCC values on the other.
+    const size_t bytes = static_cast<size_t>(cnt * ss) * 4;
+    if (cudaStreamWaitEvent(R->copy[0], R->computed[k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_tally + ss * pair0, st, bytes, cudaMemcpyDeviceToHost, R->copy[0]) !=
+            cudaSuccess ||
+        cudaEventRecord(R->copied[k][0], R->copy[0]) != cudaSuccess)
+      return CCC_ECUDA;
+    if (want_ccc) {
+      if (cudaStreamWaitEvent(R->copy[1], R->computed[k], 0) != cudaSuccess ||
+          cudaMemcpyAsync(host_ccc + ss * pair0, sc, bytes, cudaMemcpyDeviceToHost, R->copy[1]) !=
+              cudaSuccess)
+        return CCC_ECUDA;
+    }
+    if (cudaEventRecord(R->copied[k][1], R->copy[1]) != cudaSuccess) return CCC_ECUDA;
+  }
+  for (int k = 0; k < 2; ++k)
+    if (cudaEventRecord(R->copied[k][0], R->copy[0]) != cudaSuccess ||
+        cudaEventRecord(R->copied[k][1], R->copy[1]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, R->copied[k][0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s, R->copied[k][1], 0) != cudaSuccess)
+      return CCC_ECUDA;
   return CCC_OK;
 }
 

@@ -262,13 +262,14 @@ int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t l
 
 int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                         int32_t *status, float gamma, int32_t norm, int32_t group, const uint8_t *op,
-                        int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st) {
+                        int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st,
+                        int64_t i_begin, int64_t i_end, int64_t pair0) {
   if (n_v < 2) return CCC_OK;
   if (s > 8) return launch_tally2_multi_wide(s, n_v, w, tally, out_ccc, status, gamma, norm, group,
-                                             op, rows_pad, kpad, num_sms, st);
+                                             op, rows_pad, kpad, num_sms, st, i_begin, i_end, pair0);
   CUtensorMap tm;
   if (!tc::make_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
-  MultiArgs a{n_v, w, tally, out_ccc, status, gamma, norm};
+  MultiArgs a{n_v, w, tally, out_ccc, status, gamma, norm, i_begin, i_end, pair0};
   // 256-row blocks holding a SNP (rows_pad has exactly these).
   const int64_t nB = rows_pad / 256;
   const int nkb = static_cast<int>(kpad / tcp::BK);

@@ -25,6 +25,9 @@ struct MultiArgs {
   int32_t *status;
   float gamma;
   int32_t norm;
+  // Row range of a phase: only pairs with i_begin <= i < i_end, stored at
+  // pair_index(i, j) - pair0.
+  int64_t i_begin, i_end, pair0;
 };
 
 // s consecutive values from registers to global memory (streaming stores).
@@ -114,8 +117,8 @@ struct EpiMulti {
             for (int k = 0; k < S; ++k) colsum[b] += __shfl_sync(0xffffffffu, r[b], src0 + k);
           }
         }
-        if (!(row_ok && i < j && j < n_v)) continue;
-        const int64_t base = (row_base + j) * (S * S) + a * S;
+        if (!(row_ok && i < j && j < n_v && i >= args.i_begin && i < args.i_end)) continue;
+        const int64_t base = (row_base + j - args.pair0) * (S * S) + a * S;
         store_row<S>(args.tally + base, r);
         if (!want_ccc) continue;
         float cv[S];
@@ -154,14 +157,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
 template <int S>
 int launch_tally2_multi_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB, int group, int nkb,
                           int num_sms, cudaStream_t s) {
+  // Row blocks of 8 PW markers holding rows [i_begin, i_end).
+  const int64_t per_block = 8 * static_cast<int64_t>(snps_per_quarter(S));
+  const int64_t I0 = a.i_begin / per_block;
+  const int64_t I1 = (a.i_end < a.n_v ? a.i_end : a.n_v) + per_block - 1;
   TriSched::Params sp;
   sp.nI = static_cast<int>(nB);
   sp.nJ = sp.nI;
   sp.group = group > 0 ? group : 8;
   sp.shift = 0;
-  sp.I0 = 0;
-  sp.I1 = sp.nI;
-  const int64_t tiles = nB * (nB + 1) / 2;
+  sp.I0 = static_cast<int>(I0);
+  sp.I1 = static_cast<int>(I1 / per_block < nB ? I1 / per_block : nB);
+  // Tiles of rows [I0, I1): sum of nB - I.
+  const int64_t rows = sp.I1 > sp.I0 ? sp.I1 - sp.I0 : 0;
+  const int64_t tiles = rows * nB - (static_cast<int64_t>(sp.I0) + sp.I1 - 1) * rows / 2;
+  if (tiles <= 0) return CCC_OK;
   static int max_clusters = 0;
   if (max_clusters == 0) {
     if (cudaFuncSetAttribute(k_tally2_multi<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

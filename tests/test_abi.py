@@ -240,3 +240,20 @@ def test_multi_argument_errors_before_device_work(lib):
     o = ccc.ccc_opts_default()
     assert lib.ccc2_multi_metric(t, t, 10, 16, ctypes.byref(o), t, None) == ccc.CCC_EINVAL
     assert lib.ccc2_multi_metric(None, t, 10, 4, ctypes.byref(o), t, None) == ccc.CCC_EINVAL
+
+
+def test_multi_phase_bounds(lib):
+    """Phase bounds for markers with s states: cover [0, n_v], inner bounds on multiples of
+    8 floor(32 / s) markers (a 256-row operand block), pair counts about equal."""
+    for s, n_v, n_phases in ((4, 10000, 8), (3, 777, 5), (15, 100, 3), (2, 5, 4)):
+        b = ccc.ccc2_multi_phase_bounds(n_v, s, n_phases)
+        assert b[0] == 0 and b[-1] == n_v
+        assert all(x <= y for x, y in zip(b, b[1:]))
+        step = 8 * (32 // s)
+        assert all(x % step == 0 for x in b[1:-1] if x < n_v)
+        counts = [ccc.ccc2_rows_count(n_v, x, y) for x, y in zip(b, b[1:])]
+        assert sum(counts) == n_v * (n_v - 1) // 2
+        if n_v >= 1000:
+            assert max(counts) <= 1.6 * (sum(counts) / n_phases)
+    with pytest.raises(ccc.CCCError):
+        ccc.ccc2_multi_phase_bounds(10, 16, 2)

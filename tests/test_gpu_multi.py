@@ -199,3 +199,57 @@ def test_cuda_graph_capture_and_replay():
     et, ec = oracle.ccc2_multi_all(gm, n_f, s)
     assert_tally_equal(tally.cpu().numpy(), et, "graph replay")
     assert_ccc_close(out.cpu().numpy(), ec, what="graph replay")
+
+
+@pytest.mark.parametrize("s", [3, 4, 11])
+def test_row_ranges_equal_slices_of_the_full_call(s):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    n_v, n_f = 260, 700
+    gm = synth.panel_multi(n_v, n_f, s, seed=90 + s, p_missing=0.03)
+    t_full, c_full = run_multi(gm, n_f, s)
+    g = to_device_bytes(gm)
+    opts = ccc.ccc_opts_default()
+    ws = torch.empty(ccc.ccc_multi_workspace_size(g, n_f, s, opts), dtype=torch.uint8, device="cuda")
+    opts = ccc.ccc_opts_default(workspace=ws)
+    step = 8 * (32 // s)
+    for i0, i1 in ((0, step), (step, 3 * step), (5, 77), (n_v - 3, n_v), (100, 100)):
+        i1 = min(i1, n_v)
+        cnt = ccc.ccc2_rows_count(n_v, i0, i1)
+        t = torch.full((max(cnt, 1), s * s), -7, dtype=torch.int32, device="cuda")
+        c = torch.full((max(cnt, 1), s * s), -7.0, dtype=torch.float32, device="cuda")
+        ccc.ccc2_multi_tally_metric_rows(g, n_f, s, i0, i1, t, c, opts)
+        torch.cuda.synchronize()
+        assert ccc.ccc_status(opts) == ccc.CCC_OK
+        p0 = ccc.ccc2_index(i0, i0 + 1, n_v) if cnt else 0
+        np.testing.assert_array_equal(t[:cnt].cpu().numpy(), t_full[p0:p0 + cnt])
+        np.testing.assert_array_equal(c[:cnt].cpu().numpy(), c_full[p0:p0 + cnt])
+
+
+@pytest.mark.parametrize("n_phases", [2, 5])
+def test_stream_to_pinned_host(n_phases):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    s, n_v, n_f = 4, 700, 900
+    gm = synth.panel_multi(n_v, n_f, s, seed=95, p_missing=0.02)
+    t_full, c_full = run_multi(gm, n_f, s)
+    g = to_device_bytes(gm)
+    opts = ccc.ccc_opts_default()
+    ws = torch.empty(ccc.ccc2_multi_stream_workspace_size(g, n_f, s, n_phases, opts),
+                     dtype=torch.uint8, device="cuda")
+    opts = ccc.ccc_opts_default(workspace=ws)
+    npairs = ccc.ccc2_count(n_v)
+    ht = torch.full((npairs, s * s), -7, dtype=torch.int32, pin_memory=True)
+    hc = torch.full((npairs, s * s), -7.0, dtype=torch.float32, pin_memory=True)
+    ccc.ccc2_multi_stream(g, n_f, s, n_phases, ht, hc, opts)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    np.testing.assert_array_equal(ht.numpy(), t_full)
+    np.testing.assert_array_equal(hc.numpy(), c_full)
+    # tallies only
+    ht2 = torch.full((npairs, s * s), -7, dtype=torch.int32, pin_memory=True)
+    ccc.ccc2_multi_stream(g, n_f, s, n_phases, ht2, None, opts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ht2.numpy(), t_full)
