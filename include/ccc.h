@@ -441,6 +441,17 @@ int ccc2_multi_stream(const ccc_panel_multi *panel, int n_phases, int32_t *host_
  */
 int ccc_status(const ccc_opts *opts, int32_t *status, void *stream);
 
+/*
+ * Self-test of the device-side bounded waits (every pipeline of the library
+ * waits on mbarriers through the same bounded loop).  Queues one small kernel
+ * whose wait cannot complete: after limit_ns nanoseconds of device time
+ * (1e6 <= limit_ns <= 2e9) it gives up, writes CCC_ETIMEOUT to *status
+ * (device int32 owned by the caller; written only on a timeout) and exits; the
+ * CUDA context stays usable.  Returns CCC_OK once queued, CCC_EINVAL for a
+ * bad argument.
+ */
+int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream);
+
 /* Index helpers (host): positions defined in the header comment; -1 if out of range. */
 int64_t ccc2_index(int64_t i, int64_t j, int64_t n_v);
 int64_t ccc3_index(int64_t i, int64_t j, int64_t k, int64_t n_v);

@@ -34,6 +34,7 @@ __all__ = [
     "ccc_panel_multi", "ccc_multi_workspace_size", "ccc_multi_counts", "ccc2_multi_tally",
     "ccc2_multi_tally_metric", "ccc2_multi_metric", "ccc2_multi_tally_metric_rows",
     "ccc2_multi_phase_bounds", "ccc2_multi_stream_workspace_size", "ccc2_multi_stream",
+    "ccc_check_bounded_wait",
 ]
 
 CCC_OK = 0
@@ -103,6 +104,7 @@ def load():
     lib.ccc_opts_default.argtypes = [P(ccc_opts)]
     lib.ccc_multi_workspace_size.argtypes = [P(ccc_panel_multi), P(ccc_opts), P(ctypes.c_size_t)]
     lib.ccc_multi_counts.argtypes = [P(ccc_panel_multi), vp, vp]
+    lib.ccc_check_bounded_wait.argtypes = [vp, i64, vp]
     lib.ccc2_multi_tally.argtypes = [P(ccc_panel_multi), vp, P(ccc_opts), vp]
     lib.ccc2_multi_tally_metric.argtypes = [P(ccc_panel_multi), vp, vp, P(ccc_opts), vp]
     lib.ccc2_multi_metric.argtypes = [vp, vp, i64, ctypes.c_int32, P(ccc_opts), vp, vp]
@@ -517,3 +519,9 @@ def ccc2_multi_stream(geno, n_f, s, n_phases, host_tally, host_ccc, opts, stream
     _check("ccc2_multi_stream",
            load().ccc2_multi_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally), _ptr(host_ccc),
                                     ctypes.byref(opts), _stream(stream)))
+
+
+def ccc_check_bounded_wait(status, limit_ns, stream=None):
+    """Queue the bounded-wait self-test; *status (device int32) receives CCC_ETIMEOUT."""
+    _check("ccc_check_bounded_wait", load().ccc_check_bounded_wait(_ptr(status), int(limit_ns),
+                                                                   _stream(stream)))

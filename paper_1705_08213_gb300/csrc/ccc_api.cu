@@ -257,9 +257,18 @@ static void phase_bounds(int64_t n_v, int n_phases, int64_t *bounds, int64_t ste
   for (int p = 1; p < n_phases; ++p) {
     const double target = static_cast<double>(total) * p / n_phases;
     while (r < n_v && static_cast<double>(rows_count(n_v, 0, r)) < target) r += step;
-    if (r > n_v) r = n_v;
-    if (r < bounds[p - 1]) r = bounds[p - 1];
-    bounds[p] = r;
+    // The nearer of the two step multiples around the target (the upper one
+    // clamped to n_v).
+    const int64_t hi = r < n_v ? r : n_v;
+    const int64_t lo = r - step;
+    int64_t pick = hi;
+    if (lo > 0 && lo >= bounds[p - 1] &&
+        target - static_cast<double>(rows_count(n_v, 0, lo)) <
+            static_cast<double>(rows_count(n_v, 0, hi)) - target) {
+      pick = lo;
+      r = lo;
+    }
+    bounds[p] = pick < bounds[p - 1] ? bounds[p - 1] : pick;
   }
   bounds[n_phases] = n_v;
 }
@@ -1222,6 +1231,15 @@ int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_
   if (opts->norm == CCC_NORM_PERSNP) CCC_TRY(launch_factors_from_counts(counts, n_v, w, opts->gamma, s));
   return launch_metric3(tally, w, n_v, j_begin, j_end, static_cast<float>(opts->gamma), opts->norm,
                         out_ccc, s);
+}
+
+int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream) {
+  if (status == nullptr || !aligned(status, 4)) return CCC_EINVAL;
+  if (limit_ns < 1000000 || limit_ns > 2000000000) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return launch_wait_selftest(status, static_cast<uint64_t>(limit_ns),
+                              static_cast<cudaStream_t>(stream));
 }
 
 int ccc_status(const ccc_opts *opts, int32_t *status, void *stream) {

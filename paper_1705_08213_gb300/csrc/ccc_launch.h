@@ -154,6 +154,9 @@ int launch_tally2_multi_wide(int s, int64_t n_v, const float *w, int32_t *tally,
 int launch_metric2_multi(const int32_t *tally, const float *w, int64_t n_v, int s, float gamma,
                          int32_t norm, float *out_ccc, cudaStream_t st);
 
+// Bounded-wait self-test (k_selftest.cu): one CTA whose mbarrier wait cannot complete.
+int launch_wait_selftest(int32_t *status, uint64_t limit_ns, cudaStream_t s);
+
 // Host index helpers (also exported through the C ABI).
 int64_t pair_index(int64_t i, int64_t j, int64_t n_v);
 int64_t slab_offset(int64_t j, int64_t n_v);

@@ -257,3 +257,9 @@ def test_multi_phase_bounds(lib):
             assert max(counts) <= 1.6 * (sum(counts) / n_phases)
     with pytest.raises(ccc.CCCError):
         ccc.ccc2_multi_phase_bounds(10, 16, 2)
+
+
+def test_bounded_wait_selftest_arguments(lib):
+    assert lib.ccc_check_bounded_wait(None, 10000000, None) == ccc.CCC_EINVAL
+    for bad in (0, 999999, 2000000001):
+        assert lib.ccc_check_bounded_wait(ctypes.c_void_p(256), bad, None) == ccc.CCC_EINVAL

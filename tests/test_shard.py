@@ -1,0 +1,133 @@
+"""The rank partition of paper_1705_08213_gb300.shard, on CPU ranks.
+
+* Index level, for many shapes and world sizes: the ranges of all ranks are
+  contiguous, cover the triangle (tetrahedron) exactly once and balance work.
+* Two gloo processes (world size 2): each computes its shard of one panel with
+  the oracle (2-way rows, 3-way slabs, multi-allelic rows), the shards are
+  gathered, and rank 0 checks that their concatenation in rank order is the
+  full result, with no pair or triple twice; the max-over-ranks timing
+  reduction of the benchmark runs over the same process group.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_1705_08213_gb300 import build as cbuild
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    cbuild.build()
+
+
+def _pairs(n_v, i0, i1):
+    return sum(n_v - 1 - i for i in range(i0, i1))
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_ranges_cover_once_and_balance(world):
+    from paper_1705_08213_gb300 import shard
+    for n_v in (1, 2, 3, 65, 300, 4096, 20000):
+        r2 = [shard.pair_range(n_v, world, r) for r in range(world)]
+        assert r2[0][0] == 0 and r2[-1][1] == n_v
+        assert all(a[1] == b[0] for a, b in zip(r2, r2[1:]))
+        counts = [_pairs(n_v, a, b) for a, b in r2]
+        assert sum(counts) == n_v * (n_v - 1) // 2
+        offs = [shard.pair_offset(n_v, a) for a, _ in r2]
+        assert offs == list(np.cumsum([0] + counts[:-1]))
+        if n_v >= 4096:
+            assert max(counts) <= 1.15 * sum(counts) / world
+        r3 = [shard.slab_range(n_v, world, r) for r in range(world)]
+        assert r3[0][0] == 0 and r3[-1][1] == n_v
+        assert all(a[1] == b[0] for a, b in zip(r3, r3[1:]))
+        t3 = [shard.triple_offset(n_v, b) - shard.triple_offset(n_v, a) for a, b in r3]
+        assert sum(t3) == n_v * (n_v - 1) * (n_v - 2) // 6
+        if n_v >= 4096:
+            assert max(t3) <= 1.05 * sum(t3) / world
+        for s in (2, 4, 7):
+            rm = [shard.multi_pair_range(n_v, s, world, r) for r in range(world)]
+            assert rm[0][0] == 0 and rm[-1][1] == n_v
+            assert all(a[1] == b[0] for a, b in zip(rm, rm[1:]))
+            assert all(a % (8 * (32 // s)) == 0 for a, _ in rm[1:] if a < n_v)
+
+
+def _worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_1705_08213_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n_v, n_f = 90, 200
+        geno = synth.panel_hwe(n_v, n_f, seed=3, p_missing=0.02)
+        i0, i1 = shard.pair_range(n_v, world, rank)
+        t2, c2 = oracle.ccc2_rows(geno, n_f, np.arange(i0, i1))
+        ii = np.concatenate([np.full(n_v - 1 - i, i) for i in range(i0, i1)] or [np.zeros(0, int)])
+        jj = np.concatenate([np.arange(i + 1, n_v) for i in range(i0, i1)] or [np.zeros(0, int)])
+        n3 = 30
+        g3 = np.ascontiguousarray(geno[:n3])
+        j0, j1 = shard.slab_range(n3, world, rank)
+        t3, c3 = oracle.ccc3_slabs(g3, n_f, j0, j1)
+        s, nm = 4, 70
+        gm = synth.panel_multi(nm, n_f, s, seed=4, p_missing=0.02)
+        m0, m1 = shard.multi_pair_range(nm, s, world, rank)
+        tm, cm = oracle.ccc2_multi_rows(gm, n_f, s, np.arange(m0, m1))
+        mine = {"rank": rank, "t2": t2, "c2": c2, "ij": (ii, jj), "off2": shard.pair_offset(n_v, i0),
+                "t3": t3, "c3": c3, "off3": shard.triple_offset(n3, j0), "tm": tm, "cm": cm}
+        gathered = [None] * world
+        dist.all_gather_object(gathered, mine)
+        import torch
+        t = torch.tensor([10.0 + rank])  # per-rank step time
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            full2 = oracle.ccc2_all(geno, n_f)
+            full3 = oracle.ccc3_slabs(g3, n_f)
+            fullm = oracle.ccc2_multi_all(gm, n_f, s)
+            res = {
+                "t2": np.concatenate([g["t2"] for g in gathered]),
+                "c2": np.concatenate([g["c2"] for g in gathered]),
+                "off2": [g["off2"] for g in gathered],
+                "pairs": np.concatenate([np.stack(g["ij"], 1) for g in gathered]),
+                "t3": np.concatenate([g["t3"] for g in gathered]),
+                "c3": np.concatenate([g["c3"] for g in gathered]),
+                "off3": [g["off3"] for g in gathered],
+                "tm": np.concatenate([g["tm"] for g in gathered]),
+                "cm": np.concatenate([g["cm"] for g in gathered]),
+                "full2": full2, "full3": full3, "fullm": fullm, "tmax": float(t.item()),
+                "n_v": n_v,
+            }
+            np.save(os.path.join(out_dir, "res.npy"), np.array([res], dtype=object), allow_pickle=True)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reassemble_the_full_result(tmp_path):
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    world = 2
+    mp.start_processes(_worker, args=(world, port, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = np.load(tmp_path / "res.npy", allow_pickle=True)[0]
+    t2, c2 = res["full2"]
+    np.testing.assert_array_equal(res["t2"], t2)
+    np.testing.assert_array_equal(res["c2"], c2)
+    n_v = res["n_v"]
+    pairs = res["pairs"]
+    assert len({(int(i), int(j)) for i, j in pairs}) == len(pairs) == n_v * (n_v - 1) // 2
+    assert res["off2"][0] == 0 and res["off2"][1] == len(res["t2"]) - (len(t2) - res["off2"][1])
+    t3, c3 = res["full3"]
+    np.testing.assert_array_equal(res["t3"], t3)
+    np.testing.assert_array_equal(res["c3"], c3)
+    tm, cm = res["fullm"]
+    np.testing.assert_array_equal(res["tm"], tm)
+    np.testing.assert_array_equal(res["cm"], cm)
+    assert res["tmax"] == 11.0
