@@ -9,7 +9,7 @@
  *
  * ---------------------------------------------------------------------------
  * Input: the packed genotype panel (Sec. 2.1 vector model; Sec. 3.1 packing;
- * Sec. 8 item 1 missing-value marker)
+ * Sec. 7 item 1 missing-value marker)
  *
  *   Every entry v_{i,q} of SNP vector i (0 <= i < n_v) for individual q
  *   (0 <= q < n_f) is a pair of allele bits ((v)_1, (v)_2), stored as the
@@ -183,7 +183,7 @@ typedef struct ccc_hit {
 } ccc_hit;
 
 /*
- * 2-way with thresholded output (Sec. 8 item 6: in practice only the few
+ * 2-way with thresholded output (Sec. 7 item 6: in practice only the few
  * values above a threshold are wanted).  Computes the tallies and CCC values
  * of every pair i < j exactly as ccc2_tally_metric does, but stores only the
  * pairs whose largest CCC value exceeds `threshold`: they are appended in no
@@ -196,7 +196,7 @@ int ccc2_filter(const ccc_panel *panel, float threshold, ccc_hit *hits, int64_t 
                 int64_t *n_hits, const ccc_opts *opts, void *stream);
 
 /*
- * 2-way over a row range -- one "phase" in the sense of Sec. 8 item 3, where a
+ * 2-way over a row range -- one "phase" in the sense of Sec. 7 item 3, where a
  * run computes and stores only part of the results when all of them do not fit
  * in memory at once: the pairs (i, j) with i_begin <= i < i_end and every
  * j > i, with tallies and CCC values as ccc2_tally_metric computes them,
@@ -239,7 +239,7 @@ int ccc2_stream(const ccc_panel *panel, int n_phases, int32_t *host_tally, float
 /*
  * Host helper: split the slabs [0, n_v) into n_phases contiguous ranges,
  * bounds[0] = 0 <= ... <= bounds[n_phases] = n_v, with about equal triple
- * counts (Sec. 8 item 3 emits the result in phases).  bounds: host
+ * counts (Sec. 7 item 3 emits the result in phases).  bounds: host
  * int64[n_phases + 1].
  */
 int ccc3_phase_bounds(int64_t n_v, int n_phases, int64_t *bounds);
@@ -344,7 +344,7 @@ int ccc2_tally_metric_noalloc(const ccc_panel *panel, int32_t *tally, float *ccc
                               int32_t *status, const ccc_opts *opts, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Markers with s allele states (Sec. 8: CCC extended from biallelic SNPs to
+ * Markers with s allele states (Sec. 7 item 2: CCC extended from biallelic SNPs to
  * markers with any number of states, a marker with s_1 states against one with
  * s_2 states giving an s_1 x s_2 table of values).
  *
@@ -407,7 +407,7 @@ int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float 
 int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
                       const ccc_opts *opts, float *ccc, void *stream);
 
-/* One phase (Sec. 8 item 3) of ccc2_multi_tally_metric: the pairs with
+/* One phase (Sec. 7 item 3) of ccc2_multi_tally_metric: the pairs with
  * i_begin <= i < i_end and every j > i, stored from index
  * ccc2_index(i_begin, i_begin + 1, n_v) on (s*s values per pair).  tally, ccc:
  * device [ccc2_rows_count(n_v, i_begin, i_end)][s*s].  Workspace as for
@@ -440,6 +440,20 @@ int ccc2_multi_stream(const ccc_panel_multi *panel, int n_phases, int32_t *host_
  * first, so this reports on the calls since the last workspace call began.
  */
 int ccc_status(const ccc_opts *opts, int32_t *status, void *stream);
+
+/*
+ * Exact checksum of results (the paper's extended-precision integer checksum,
+ * Sec. 5, used to check results bit for bit):
+ *   C = sum_e h(base + e) * words[e]  (mod 2^128),
+ * words[e] = the e-th 32-bit word of an output array taken as unsigned (a
+ * tally, or the bit pattern of a CCC value); h(x) = the SplitMix64 finaliser
+ * of (x + 1) * 0x9E3779B97F4A7C15.  Linear, so the checksums of the phases or
+ * shards of an output, each with base = its first word's global index, add up
+ * (mod 2^128) to the whole's.  words: device, 4-byte aligned, count words;
+ * out: device uint64[2] = (low, high), 16-byte aligned, cleared and written
+ * by the call.  Needs no workspace.
+ */
+int ccc_checksum(const void *words, int64_t count, int64_t base, uint64_t *out, void *stream);
 
 /*
  * Self-test of the device-side bounded waits (every pipeline of the library

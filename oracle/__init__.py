@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package smoke check
 and by the benchmark's CPU-baseline leg, never by the CUDA path.  It shares no
 code with the CUDA path.
 
-Markers with s allele states (Sec. 8, the multi-allelic extension) have
+Markers with s allele states (Sec. 7 item 2, the multi-allelic extension) have
 :func:`multi_counts`, :func:`ccc2_multi_rows`, :func:`ccc2_multi_all` and
 :func:`ccc2_multi_pairs` (C, ``oracle/ccc_oracle_multi.c``), cross-checked by the
 numpy route :mod:`oracle.multi_np`.
@@ -62,6 +62,9 @@ def _load():
                                             ctypes.c_double, ctypes.c_int, i64p, f64p]
         lib.oracle_ccc3_triples.restype = ctypes.c_int
         lib.oracle_threads.restype = ctypes.c_int
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.oracle_checksum.argtypes = [u32p, I64, I64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.oracle_checksum.restype = None
         u8p = ctypes.POINTER(ctypes.c_uint8)
         lib.oracle_multi_counts.argtypes = [u8p, I64, I64, I64, ctypes.c_int, i64p]
         lib.oracle_multi_counts.restype = None
@@ -297,3 +300,18 @@ def ccc2_multi_pairs(geno, n_f, s, pi, pj, gamma=GAMMA, norm=NORM_PERSNP):
     if rc:
         raise MemoryError("oracle_multi_pairs")
     return tally[:n], ccc[:n]
+
+
+def checksum(values, base=0):
+    """Exact 128-bit checksum of an integer array's entries as 32-bit words (int64 tallies
+    below 2^31 give the same words as the library's int32 output), global offset `base`."""
+    v = np.asarray(values)
+    if v.dtype == np.float32:
+        w = np.ascontiguousarray(v).view(np.uint32).ravel()
+    else:
+        if v.size and (v.min() < 0 or v.max() >= 1 << 31):
+            raise ValueError("tallies must lie in [0, 2^31)")
+        w = np.ascontiguousarray(v.astype(np.uint32)).ravel()
+    out = np.zeros(2, np.uint64)
+    _load().oracle_checksum(_p(w, ctypes.c_uint32), w.size, int(base), _p(out, ctypes.c_uint64))
+    return int(out[0]) | (int(out[1]) << 64)

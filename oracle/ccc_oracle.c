@@ -21,7 +21,7 @@
  *   Eq. 3     CCC_{i,j}(a,b) = f_{i,j}(a,b) (1 - g f_i(a)) (1 - g f_j(b)), g = 2/3
  *   Eq. 5     f_{i,j,k}(a,b,c) = (1/(8 n_f)) sum_q rho_i(a) rho_j(b) rho_k(c)
  *   Eq. 4     CCC_{i,j,k}(a,b,c) = f_{i,j,k}(a,b,c) (1-g f_i(a))(1-g f_j(b))(1-g f_k(c))
- *   Sec. 8 item 1: the allele pair (1,0) is reserved to mark a missing entry,
+ *   Sec. 7 item 1: the allele pair (1,0) is reserved to mark a missing entry,
  *             and missing entries are skipped.
  *
  * Readings where the paper is silent (each is also listed in the design notes):
@@ -59,7 +59,7 @@ static int entry_code(const uint64_t *geno, int64_t ld, int64_t i, int64_t q) {
 static int allele_1(int code) { return (code >> 1) & 1; }
 static int allele_2(int code) { return code & 1; }
 
-/* Sec. 8 item 1: the pair (1,0) marks a missing entry. */
+/* Sec. 7 item 1: the pair (1,0) marks a missing entry. */
 static int is_missing(int code) { return allele_1(code) == 1 && allele_2(code) == 0; }
 
 /* rho_{i,q}(a) = sum_r chi_a((v_{i,q})_r), Sec. 2.1; 0 for a missing entry. */
@@ -292,4 +292,33 @@ int oracle_ccc3_triples(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t 
                   tally + 8 * t, ccc + 8 * t);
   counts_free(&sc);
   return 0;
+}
+
+/*
+ * Host twin of the library's result checksum (the paper's extended-precision
+ * integer checksum, Sec. 5): C = sum_e h(base + e) * words[e] mod 2^128 over
+ * 32-bit words taken as unsigned, h(x) = the SplitMix64 finaliser of
+ * (x + 1) * 0x9E3779B97F4A7C15.  out[0] = low 64 bits, out[1] = high.
+ */
+static uint64_t checksum_hash(uint64_t x) {
+  uint64_t z = (x + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void oracle_checksum(const uint32_t *words, int64_t count, int64_t base, uint64_t *out) {
+  unsigned __int128 total = 0;
+#pragma omp parallel
+  {
+    unsigned __int128 part = 0;
+    int64_t e;
+#pragma omp for schedule(static)
+    for (e = 0; e < count; ++e)
+      part += (unsigned __int128)checksum_hash((uint64_t)(base + e)) * words[e];
+#pragma omp critical
+    total += part;
+  }
+  out[0] = (uint64_t)total;
+  out[1] = (uint64_t)(total >> 64);
 }

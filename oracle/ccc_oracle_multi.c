@@ -5,7 +5,7 @@
  * library): loaded only by the tests, the package's smoke check and the
  * benchmark's CPU baseline; it shares nothing with the CUDA path.
  *
- * Sec. 8 of the paper names the extension of CCC from biallelic SNPs to
+ * Sec. 7 item 2 of the paper names the extension of CCC from biallelic SNPs to
  * markers with an arbitrary number of states: a marker with s_1 states against
  * one with s_2 states gives an s_1 x s_2 table of values.  It is written here
  * with the definitions of Sec. 2.1 and Eqs. 1-3 unchanged except for the

@@ -9,7 +9,7 @@ TEST INFRASTRUCTURE ONLY (see :mod:`oracle`).  Used to cross-check the direct
    (1,1) for xi = 1, 2, 3 respectively, and the null marker (1,0) otherwise;
 2. form B_{j,xi} = X_{j,xi}^T o_3 V, the 2-way pairing tally that discards
    null entries of X (and, with missing data, missing entries of V, following
-   Sec. 8 item 1 which reuses the skip for the missing marker);
+   Sec. 7 item 1 which reuses the skip for the missing marker);
 3. reconstruct the 3-way table from the three 2-way tables:
        r_{ijk}(0,b,c) = 2 (B_{j,1})_{(i,k)}(b,c) + (B_{j,2})_{(i,k)}(b,c)
        r_{ijk}(1,b,c) = 2 (B_{j,3})_{(i,k)}(b,c) + (B_{j,2})_{(i,k)}(b,c)

@@ -34,7 +34,7 @@ __all__ = [
     "ccc_panel_multi", "ccc_multi_workspace_size", "ccc_multi_counts", "ccc2_multi_tally",
     "ccc2_multi_tally_metric", "ccc2_multi_metric", "ccc2_multi_tally_metric_rows",
     "ccc2_multi_phase_bounds", "ccc2_multi_stream_workspace_size", "ccc2_multi_stream",
-    "ccc_check_bounded_wait",
+    "ccc_check_bounded_wait", "ccc_checksum",
 ]
 
 CCC_OK = 0
@@ -105,6 +105,7 @@ def load():
     lib.ccc_multi_workspace_size.argtypes = [P(ccc_panel_multi), P(ccc_opts), P(ctypes.c_size_t)]
     lib.ccc_multi_counts.argtypes = [P(ccc_panel_multi), vp, vp]
     lib.ccc_check_bounded_wait.argtypes = [vp, i64, vp]
+    lib.ccc_checksum.argtypes = [vp, i64, i64, vp, vp]
     lib.ccc2_multi_tally.argtypes = [P(ccc_panel_multi), vp, P(ccc_opts), vp]
     lib.ccc2_multi_tally_metric.argtypes = [P(ccc_panel_multi), vp, vp, P(ccc_opts), vp]
     lib.ccc2_multi_metric.argtypes = [vp, vp, i64, ctypes.c_int32, P(ccc_opts), vp, vp]
@@ -525,3 +526,17 @@ def ccc_check_bounded_wait(status, limit_ns, stream=None):
     """Queue the bounded-wait self-test; *status (device int32) receives CCC_ETIMEOUT."""
     _check("ccc_check_bounded_wait", load().ccc_check_bounded_wait(_ptr(status), int(limit_ns),
                                                                    _stream(stream)))
+
+
+def ccc_checksum(words, base=0, out=None, stream=None):
+    """128-bit checksum of a device tensor of 32-bit words (int32 tallies or float32 values)
+    whose first word has global index `base`; returns it as a Python int (synchronises)."""
+    import torch
+    if words.element_size() != 4 or not words.is_contiguous():
+        raise CCCError("ccc_checksum", CCC_EINVAL)
+    if out is None:
+        out = torch.zeros(2, dtype=torch.int64, device=words.device)
+    _check("ccc_checksum", load().ccc_checksum(_ptr(words), int(words.numel()), int(base), _ptr(out),
+                                               _stream(stream)))
+    lo, hi = (int(x) & 0xFFFFFFFFFFFFFFFF for x in out.cpu().tolist())
+    return lo | (hi << 64)

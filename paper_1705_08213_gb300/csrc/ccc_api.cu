@@ -1233,6 +1233,15 @@ int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_
                         out_ccc, s);
 }
 
+int ccc_checksum(const void *words, int64_t count, int64_t base, uint64_t *out, void *stream) {
+  if (out == nullptr || !aligned(out, 16) || count < 0 || base < 0) return CCC_EINVAL;
+  if (count > 0 && (words == nullptr || !aligned(words, 4))) return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  return launch_checksum(static_cast<const uint32_t *>(words), count, base, out,
+                         static_cast<cudaStream_t>(stream));
+}
+
 int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream) {
   if (status == nullptr || !aligned(status, 4)) return CCC_EINVAL;
   if (limit_ns < 1000000 || limit_ns > 2000000000) return CCC_EINVAL;

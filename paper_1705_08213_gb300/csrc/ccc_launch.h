@@ -154,6 +154,10 @@ int launch_tally2_multi_wide(int s, int64_t n_v, const float *w, int32_t *tally,
 int launch_metric2_multi(const int32_t *tally, const float *w, int64_t n_v, int s, float gamma,
                          int32_t norm, float *out_ccc, cudaStream_t st);
 
+// Exact 128-bit checksum of `count` 32-bit words with global offset `base` into out[2].
+int launch_checksum(const uint32_t *words, int64_t count, int64_t base, uint64_t *out,
+                    cudaStream_t s);
+
 // Bounded-wait self-test (k_selftest.cu): one CTA whose mbarrier wait cannot complete.
 int launch_wait_selftest(int32_t *status, uint64_t limit_ns, cudaStream_t s);
 

@@ -1,6 +1,6 @@
 // 2-way CCC of markers with s allele states on the tcgen05 tensor cores.
 //
-// Sec. 8 extends CCC from biallelic SNPs to markers with any number of
+// Sec. 7 item 2 extends CCC from biallelic SNPs to markers with any number of
 // states: a pair of markers gets an s x s table.  Written with the state set
 // S = {0..s-1}, Eqs. 1-3 keep their form, and the tally table is again a block
 // of a Gram product (Sec. 3.1): with s count rows rho_i(a) per SNP,

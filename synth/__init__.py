@@ -5,7 +5,7 @@ benchmark.  It holds no part of the CCC arithmetic: it only draws genotypes and
 packs/unpacks the storage format.
 
 Storage format (the vector model of Sec. 2.1, with the missing-value marker of
-Sec. 8 item 1):
+Sec. 7 item 1):
 
 * every entry ``v_{i,q}`` is a pair of allele bits ``((v)_1, (v)_2)``; it is
   stored as the 2-bit code ``2*(v)_1 + (v)_2``;
@@ -331,7 +331,7 @@ def plant_near_duplicates(geno: np.ndarray, n_f: int, n_pairs: int, seed: int, r
 # ---------------------------------------------------------------- multi-allelic panels
 #
 # Markers with s allele states (the multi-allelic extension the paper sketches in
-# Sec. 8): every entry is an unordered pair of states (x, y), x, y in {0..s-1},
+# Sec. 7 item 2): every entry is an unordered pair of states (x, y), x, y in {0..s-1},
 # stored in one byte as x | (y << 4); an entry whose low or high nibble is >= s
 # is missing, 0xFF being the value written here.  SNP i occupies bytes
 # [i*ld, i*ld + n_f); bytes past n_f are padding that consumers must ignore.

@@ -394,3 +394,37 @@ def test_padding_bits_ignored():
     b, cb = oracle.ccc2_all(dirty, 45)
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(ca, cb)
+
+
+# ---------------------------------------------------------------- result checksum
+
+def _splitmix_finaliser(x):
+    m = (1 << 64) - 1
+    z = ((x + 1) * 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def test_checksum_against_big_integer_arithmetic():
+    rng = np.random.default_rng(5)
+    for n, base in ((1, 0), (1000, 0), (777, 123456789), (5000, (1 << 40) + 3)):
+        v = rng.integers(0, 1 << 31, size=n, dtype=np.int64)
+        want = sum(_splitmix_finaliser(base + e) * int(x) for e, x in enumerate(v)) % (1 << 128)
+        assert oracle.checksum(v, base) == want
+    # float32 words: the bit patterns
+    f = rng.random(300).astype(np.float32)
+    bits = f.view(np.uint32).astype(np.int64)
+    want = sum(_splitmix_finaliser(7 + e) * int(x) for e, x in enumerate(bits)) % (1 << 128)
+    assert oracle.checksum(f, 7) == want
+
+
+def test_checksum_is_additive_over_pieces():
+    rng = np.random.default_rng(6)
+    v = rng.integers(0, 1 << 24, size=10000, dtype=np.int64)
+    whole = oracle.checksum(v)
+    parts = sum(oracle.checksum(v[a:b], a) for a, b in ((0, 17), (17, 5000), (5000, 10000)))
+    assert parts % (1 << 128) == whole
+    v2 = v.copy()
+    v2[4321] += 1  # one changed value changes the checksum by h(4321)
+    assert (oracle.checksum(v2) - whole) % (1 << 128) == _splitmix_finaliser(4321)

@@ -1,4 +1,4 @@
-"""Pins of the oracle for markers with s allele states (Sec. 8 extension of Eqs. 1-3).
+"""Pins of the oracle for markers with s allele states (Sec. 7 item 2 extension of Eqs. 1-3).
 
 Each check ties the oracle to something other than its own code:
 
