@@ -26,7 +26,10 @@ Workloads (``--workload``):
 
 Prints ONE JSON line (rank 0).  Under torchrun with N ranks every rank runs an
 independent panel of the same shape (seed + rank); there is no data-path
-collective (weak scaling), only a barrier around the timed region.
+collective (weak scaling), only a barrier around the timed region.  With
+--scaling strong every rank holds the same panel and computes its own range of
+rows (2-way) or slabs (3-way) from paper_1705_08213_gb300.shard; value = the
+whole panel's comparisons / the slowest rank's time.
 
 --impl reference times the CPU oracle (oracle/, all host cores) on a bounded
 random sample of the same workload in every step.
@@ -107,6 +110,8 @@ def parse():
                     help="tensor-core variant (0 automatic). 2-way: 1 one SM, 2 SM pairs; 3-way: "
                          "1 masked operands in HBM, 2 masked operands in shared memory, "
                          "3 genotype classes of v_j")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: an independent panel per rank; strong: one panel split by rows/slabs")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--skip-e2e", action="store_true", help="no host-buffer end-to-end timing")
     ap.add_argument("--skip-popc", action="store_true", help="no popcount-path comparison")
@@ -377,10 +382,12 @@ def run_reference(args, w):
 class Runner:
     """Device buffers and one step of the chosen workload through the C ABI."""
 
-    def __init__(self, ccc, torch, dev, w, path, geno_np, tile=0):
+    def __init__(self, ccc, torch, dev, w, path, geno_np, tile=0, shard=None):
         self.ccc, self.torch, self.dev, self.w, self.path = ccc, torch, dev, w, path
         self.tile = tile
         n_v, n_f = w["n_v"], w["n_f"]
+        # Rows (2-way) or slabs (3-way) [lo, hi) of this rank; None = the whole panel.
+        self.shard = shard
         self.states = w.get("states")
         self.host_geno = torch.from_numpy(geno_np if self.states else geno_np.view(np.int64))
         self.host_geno = self.host_geno.pin_memory()
@@ -398,7 +405,9 @@ class Runner:
             self.n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
             self.out_bytes = 8
         else:
-            rows = ccc.ccc2_count(n_v) if w["kind"] == 2 else ccc.ccc3_count(n_v, 0, n_v)
+            lo, hi = shard if shard is not None else (0, n_v)
+            rows = ccc.ccc2_rows_count(n_v, lo, hi) if w["kind"] == 2 else ccc.ccc3_count(n_v, lo, hi)
+            rows = max(rows, 1)
             width = (self.states ** 2 if self.states else 4) if w["kind"] == 2 else 8
             self.tally = torch.empty((rows, width), dtype=torch.int32, device=dev)
             self.out = torch.empty((rows, width), dtype=torch.float32, device=dev)
@@ -409,13 +418,22 @@ class Runner:
         if self.filter:
             ccc.ccc2_filter(self.geno, w["n_f"], w["threshold"], self.hits, self.cap, self.n_hits,
                             self.opts, stream)
+        elif self.shard is not None and w["kind"] == 2:
+            lo, hi = self.shard
+            if self.states:
+                ccc.ccc2_multi_tally_metric_rows(self.geno, w["n_f"], self.states, lo, hi, self.tally,
+                                                 self.out, self.opts, stream)
+            else:
+                ccc.ccc2_tally_metric_rows(self.geno, w["n_f"], lo, hi, self.tally, self.out,
+                                           self.opts, stream)
         elif self.states:
             ccc.ccc2_multi_tally_metric(self.geno, w["n_f"], self.states, self.tally, self.out,
                                         self.opts, stream)
         elif w["kind"] == 2:
             ccc.ccc2_tally_metric(self.geno, w["n_f"], self.tally, self.out, self.opts, stream)
         else:
-            ccc.ccc3_tally_metric(self.geno, w["n_f"], 0, w["n_v"], self.tally, self.out, self.opts,
+            lo, hi = self.shard if self.shard is not None else (0, w["n_v"])
+            ccc.ccc3_tally_metric(self.geno, w["n_f"], lo, hi, self.tally, self.out, self.opts,
                                   stream)
 
     def e2e(self, stream, steps, phases=8, mode="auto"):
@@ -624,8 +642,24 @@ def main():
             return run_batched(args, w, ccc, torch, dev, side, rank, world, pg)
     path = ccc.CCC_PATH_TC if args.path == "tc" else ccc.CCC_PATH_POPC
     cmp_per_step = comparisons(w)
-    geno_np = make_panel(w, rank)
-    run = Runner(ccc, torch, dev, w, path, geno_np, tile=args.tile)
+    strong = args.scaling == "strong"
+    shard_range = None
+    cmp_rank = cmp_per_step  # comparisons this rank computes per step
+    if strong:
+        if "threshold" in w:
+            raise SystemExit("--scaling strong covers the 2way, 3way, small and multi workloads")
+        from paper_1705_08213_gb300 import shard as sh
+        n_v = w["n_v"]
+        if w["kind"] == 3:
+            shard_range = sh.slab_range(n_v, world, rank)
+            cmp_rank = ccc.ccc3_count(n_v, *shard_range) * w["n_f"]
+        else:
+            shard_range = (sh.multi_pair_range(n_v, w["states"], world, rank) if w.get("states")
+                           else sh.pair_range(n_v, world, rank))
+            cmp_rank = ccc.ccc2_rows_count(n_v, *shard_range) * w["n_f"]
+    geno_np = make_panel(w, 0 if strong else rank)
+    run = Runner(ccc, torch, dev, w, path, geno_np, tile=args.tile,
+                 shard=shard_range if strong else None)
     stream = torch.cuda.current_stream(dev)
 
     sampler = ClockSampler(gpu_id_for(torch, dev)) if local == 0 else None
@@ -668,7 +702,7 @@ def main():
         ms_per_step = float(t.item())
     if ccc.ccc_status(run.opts) != ccc.CCC_OK:
         raise RuntimeError("device status not ok after the timed region")
-    value = world * cmp_per_step / (ms_per_step * 1e-3)
+    value = (1 if strong else world) * cmp_per_step / (ms_per_step * 1e-3)
 
     # Roofline of the dominant kernel (the tally kernel), from its own events:
     # summed duration of its launches in the timed region / steps.
@@ -689,7 +723,7 @@ def main():
         per_cmp = 8.0 if w["kind"] == 2 else 16.0
         if w.get("states"):
             per_cmp = 2.0 * w["states"] ** 2  # s^2 MAC per comparison
-        flops = per_cmp * cmp_per_step
+        flops = per_cmp * cmp_rank
         achieved = flops / (kernel_step_ms * 1e-3) / 1e12
         peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -700,13 +734,13 @@ def main():
                 "peak_note": f"e4m3 dense peak = 2 x {peak_src} bf16 burst {bf16_peak:.0f} TFLOP/s "
                              "(kind::i8 is not available on sm_103a)"}
         if kname.startswith("k_tally3_class"):
-            ex = 8.0 * cmp_per_step / (kernel_step_ms * 1e-3) / 1e12
+            ex = 8.0 * cmp_rank / (kernel_step_ms * 1e-3) / 1e12
             roof["executed"] = {"per_unit": "8 flops per comparison (T product; the D product "
                                             "over individuals with v_j missing not counted)",
                                 "achieved": ex, "frac": ex / peak}
     else:
         per = 9.0 / 64.0 if w["kind"] == 2 else 27.0 / 64.0
-        achieved = per * cmp_per_step / (kernel_step_ms * 1e-3) / 1e12
+        achieved = per * cmp_rank / (kernel_step_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": POPC64_PEAK_T, "unit": "T popc64/s",
                 "frac": achieved / POPC64_PEAK_T, "traffic": None, "kernel": kname,
                 "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n,
@@ -716,7 +750,7 @@ def main():
     result = {
         "metric": w["metric"], "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
         "dtype": "e4m3 operands, fp32 accumulate" if path == ccc.CCC_PATH_TC else "u64 bit planes",
         "data": "synthetic",
         "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"], "path": args.path,
@@ -725,7 +759,10 @@ def main():
                             {0: "automatic (genotype classes of v_j on SM pairs)",
                              1: "masked operands L_j formed in HBM", 2: "L_j formed in shared memory",
                              3: "genotype classes of v_j on SM pairs"})[args.tile],
-                   "parallelism": (f"{world} independent panels (one per GPU)" if world > 1
+                   "parallelism": ((f"one panel over {world} GPUs, rank 0 computing "
+                                    f"{'slabs' if w['kind'] == 3 else 'rows'} {list(shard_range)}")
+                                   if strong and world > 1 else
+                                   f"{world} independent panels (one per GPU)" if world > 1
                                    else "1 GPU"),
                    "l2": ("inputs larger than L2 (operand matrix and outputs exceed the 129 MB L2)"
                           if w["n_v"] * w["n_f"] * 2 > 129e6 else
@@ -735,7 +772,7 @@ def main():
         "clocks": clocks,
     }
 
-    if not args.skip_e2e and rank == 0:
+    if not args.skip_e2e and rank == 0 and not (strong and world > 1):
         e2e_ms, bi, bo = run.e2e(stream, max(1, min(args.steps, 5)), mode=args.e2e_mode)
         result["e2e"] = {"value": cmp_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
