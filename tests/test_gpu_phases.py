@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import assert_ccc_close, assert_tally_equal, run_2way, to_device, workspace
+from tests.gpu_util import assert_ccc_close, assert_tally_equal, run_2way, run_3way, to_device, workspace
 
 pytestmark = pytest.mark.gpu
 
@@ -107,3 +107,47 @@ def test_stream3_to_pinned_host(path, n_phases):
         ccc.ccc3_stream(g, n_f, n_phases, ht2, None, opts, stream=s)
     s.synchronize()
     assert_tally_equal(ht2.numpy(), et, "streamed 3-way tallies only")
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+def test_field_slices_sum_to_the_full_tallies(kind):
+    """The n_pf split on one device: tallies over slices of the individuals (views of the packed
+    panel) sum to the full tallies; CCC values from the summed tallies and the whole panel's
+    counts equal the fused call's bit for bit."""
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    from paper_1705_08213_gb300 import shard
+    n_v, n_f = (700, 3000) if kind == 2 else (120, 1500)
+    geno = synth.panel_hwe(n_v, n_f, seed=77, p_missing=0.02)
+    g = to_device(geno)
+    op = ccc.CCC_OP_2WAY if kind == 2 else ccc.CCC_OP_3WAY
+    opts = ccc.ccc_opts_default()
+    ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, op))
+    opts = ccc.ccc_opts_default(workspace=ws)
+    rows = ccc.ccc2_count(n_v) if kind == 2 else ccc.ccc3_count(n_v, 0, n_v)
+    width = 4 if kind == 2 else 8
+    total = torch.zeros((rows, width), dtype=torch.int32, device="cuda")
+    part = torch.empty_like(total)
+    for r in range(3):
+        q0, q1 = shard.field_range(n_f, 3, r)
+        if q0 == q1:
+            continue
+        if kind == 2:
+            shard.field_tally2(g, n_f, q0, q1, part, opts)
+        else:
+            shard.field_tally3(g, n_f, q0, q1, 0, n_v, part, opts)
+        total += part
+    t_full, c_full = (run_2way(geno, n_f, 0) if kind == 2 else run_3way(geno, n_f, 0))
+    np.testing.assert_array_equal(total.cpu().numpy(), t_full)
+    counts = torch.zeros((n_v, 3), dtype=torch.int32, device="cuda")
+    ccc.ccc_allele_counts(g, n_f, counts)
+    wsm = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_METRIC))
+    optm = ccc.ccc_opts_default(workspace=wsm)
+    out = torch.empty((rows, width), dtype=torch.float32, device="cuda")
+    if kind == 2:
+        ccc.ccc2_metric(total, counts, n_v, optm, out)
+    else:
+        ccc.ccc3_metric(total, counts, n_v, 0, n_v, optm, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), c_full)

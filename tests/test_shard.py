@@ -7,6 +7,9 @@
   gathered, and rank 0 checks that their concatenation in rank order is the
   full result, with no pair or triple twice; the max-over-ranks timing
   reduction of the benchmark runs over the same process group.
+* The individuals axis (n_pf, Sec. 4): two gloo ranks tally their slices of
+  the individuals and an all-reduce sums the partial tallies; the sum equals
+  the tallies over all individuals.
 """
 
 import os
@@ -131,3 +134,63 @@ def test_two_gloo_ranks_reassemble_the_full_result(tmp_path):
     np.testing.assert_array_equal(res["tm"], tm)
     np.testing.assert_array_equal(res["cm"], cm)
     assert res["tmax"] == 11.0
+
+
+def test_field_ranges_cover_the_individuals():
+    from paper_1705_08213_gb300 import shard
+    for n_f in (1, 63, 64, 65, 1000, 16384, 100000):
+        for world in (1, 2, 3, 8):
+            r = [shard.field_range(n_f, world, k) for k in range(world)]
+            assert r[0][0] == 0 and r[-1][1] == n_f
+            assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
+            assert all(a % 64 == 0 for a, _ in r)
+            sizes = [b - a for a, b in r]
+            assert max(sizes) - min(sizes) <= 64 + (n_f % 64)
+
+
+def _field_worker(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_1705_08213_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n_v, n_f = 60, 1000
+        geno = synth.panel_hwe(n_v, n_f, seed=8, p_missing=0.03)
+        q0, q1 = shard.field_range(n_f, world, rank)
+        # this rank's individuals: whole words from q0 (a multiple of 64) on
+        sl = np.ascontiguousarray(geno[:, q0 // 32:])
+        t2, _ = oracle.ccc2_all(sl, q1 - q0)
+        t3, _ = oracle.ccc3_slabs(np.ascontiguousarray(sl[:25]), q1 - q0)
+        p2 = torch.from_numpy(t2.copy())
+        p3 = torch.from_numpy(t3.copy())
+        shard.allreduce_tallies(p2)
+        shard.allreduce_tallies(p3)
+        if rank == 0:
+            np.save(os.path.join(out_dir, "field.npy"),
+                    np.array([{"t2": p2.numpy(), "t3": p3.numpy(),
+                               "full2": oracle.ccc2_all(geno, n_f)[0],
+                               "full3": oracle.ccc3_slabs(np.ascontiguousarray(geno[:25]), n_f)[0]}],
+                             dtype=object), allow_pickle=True)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sum_field_slices(tmp_path):
+    """The n_pf axis: each rank tallies its slice of the individuals, an all-reduce sums the
+    partial tallies; the sum equals the tallies over all individuals (2-way and 3-way)."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    mp.start_processes(_field_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    res = np.load(tmp_path / "field.npy", allow_pickle=True)[0]
+    np.testing.assert_array_equal(res["t2"], res["full2"])
+    np.testing.assert_array_equal(res["t3"], res["full3"])
