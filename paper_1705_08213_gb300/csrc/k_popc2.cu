@@ -10,7 +10,9 @@
 //   Y   = sum_q m_i rho_1,j     = |Mi&P1j| + |Mi&P2j|
 //   Z   = sum_q m_i m_j         = |Mi&Mj|
 //   r10 = 2X - r11,  r01 = 2Y - r11,  r00 = 4Z - 2X - 2Y + r11.
-// Nine AND+POPC per 64 entries per pair; four accumulators per pair.
+// P2 is a subset of P1 (hom 1 implies a first copy), so of the four r11 terms
+// the last three take two population counts (see the inner loop): eight
+// POPC per 64 entries per pair; four accumulators per pair.
 //
 // Block tile: 64 x 64 SNPs of the upper triangle (J >= I), 256 threads, each
 // thread 4 x 4 pairs; the planes of both tiles are staged in shared memory 8
@@ -104,8 +106,10 @@ __global__ void __launch_bounds__(THREADS)
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          acc[x][y][0] += __popcll(a1[x] & b1[y]) + __popcll(a1[x] & b2[y]) +
-                          __popcll(a2[x] & b1[y]) + __popcll(a2[x] & b2[y]);
+          // P2 is a subset of P1, so (P1i & P2j) & (P2i & P1j) = P2i & P2j and
+          // |P1i&P2j| + |P2i&P1j| + |P2i&P2j| = |p ^ q| + 3 |p & q|.
+          const uint64_t p = a1[x] & b2[y], q = a2[x] & b1[y];
+          acc[x][y][0] += __popcll(a1[x] & b1[y]) + __popcll(p ^ q) + 3 * __popcll(p & q);
           acc[x][y][1] += __popcll(a1[x] & bm[y]) + __popcll(a2[x] & bm[y]);
           acc[x][y][2] += __popcll(am[x] & b1[y]) + __popcll(am[x] & b2[y]);
           acc[x][y][3] += __popcll(am[x] & bm[y]);
