@@ -739,7 +739,7 @@ def main():
                                             "over individuals with v_j missing not counted)",
                                 "achieved": ex, "frac": ex / peak}
     else:
-        per = 8.0 / 64.0 if w["kind"] == 2 else 27.0 / 64.0
+        per = 8.0 / 64.0 if w["kind"] == 2 else 24.0 / 64.0
         achieved = per * cmp_rank / (kernel_step_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": POPC64_PEAK_T, "unit": "T popc64/s",
                 "frac": achieved / POPC64_PEAK_T, "traffic": None, "kernel": kname,

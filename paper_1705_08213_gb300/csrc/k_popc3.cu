@@ -4,13 +4,16 @@
 // With the bit planes of k_planes (P1, P2 = the two copies of allele 1,
 // M = present), rho_1 = P1 + P2 and m = M.  For each triple the eight sums
 //     T[x y z] = sum_q X_i Y_j Z_k,  X, Y, Z in {rho_1, m}
-// come from the 27 AND+POPC of the plane triples (P1|P2|M)^3, and the tallies
-// follow from rho_0 = 2m - rho_1:
+// come from AND+POPC of plane triples, and the tallies follow from
+// rho_0 = 2m - rho_1:
 //     r^{abc} = sum_{x,y,z} C_a(x) C_b(y) C_c(z) T[x y z],
 //     C_1(rho_1) = 1, C_1(m) = 0, C_0(rho_1) = -1, C_0(m) = 2.
-// The nine (i, j) plane products are formed once per staged word and shared by
-// all k.  Block: one slab j (blockIdx.y), a tile of 32 SNPs i < j by 64 SNPs
-// k > j, 256 threads, 2 x 4 triples per thread.
+// The (i, j) plane products are formed once per staged word and shared by all
+// k.  P2 is a subset of P1, so of the four (rho_1, rho_1) products the cross
+// terms p = P1i & P2j, q = P2i & P1j satisfy p & q = P2i & P2j and enter as
+// p ^ q and 3 (p & q): eight (i, j) products, 24 POPC per 64 comparisons
+// instead of 27.  Block: one slab j (blockIdx.y), a tile of 32 SNPs i < j by
+// 64 SNPs k > j, 256 threads, 2 x 4 triples per thread.
 #include "ccc_launch.h"
 #include "ccc_metric.cuh"
 
@@ -36,7 +39,8 @@ __device__ __forceinline__ void planes_of(const uint64_t *__restrict__ planes, i
 
 __global__ void __launch_bounds__(THREADS)
     k_tally3_popc(const uint64_t *__restrict__ planes, int64_t w64, const Tally3Args args) {
-  __shared__ uint64_t sIJ[9][KC][TI + 1];
+  constexpr int NIJ = 8;
+  __shared__ uint64_t sIJ[NIJ][KC][TI + 1];
   __shared__ uint64_t sK[3][KC][TK + 1];
   const int64_t n_v = args.n_v;
   const int64_t j = args.j_begin + blockIdx.y;
@@ -56,7 +60,9 @@ __global__ void __launch_bounds__(THREADS)
       for (int z = 0; z < 8; ++z) T[x][y][z] = 0u;
 
   for (int64_t kw0 = 0; kw0 < w64; kw0 += KC) {
-    // i side: 32 SNPs x KC words -> nine plane products with v_j.
+    // i side: 32 SNPs x KC words -> eight plane products with v_j:
+    // (rho_1, rho_1): P1P1, p ^ q, p & q (weight 3); (rho_1, m): P1M, P2M;
+    // (m, rho_1): MP1, MP2; (m, m): MM.
     for (int l = threadIdx.x; l < TI * KC; l += THREADS) {
       const int word = l % KC;
       const int si = l / KC;
@@ -67,10 +73,15 @@ __global__ void __launch_bounds__(THREADS)
         planes_of(planes, w64, i, k, a[0], a[1], a[2]);
         planes_of(planes, w64, j, k, b[0], b[1], b[2]);
       }
-#pragma unroll
-      for (int pi = 0; pi < 3; ++pi)
-#pragma unroll
-        for (int pj = 0; pj < 3; ++pj) sIJ[3 * pi + pj][word][si] = a[pi] & b[pj];
+      const uint64_t p = a[0] & b[1], q = a[1] & b[0];
+      sIJ[0][word][si] = a[0] & b[0];
+      sIJ[1][word][si] = p ^ q;
+      sIJ[2][word][si] = p & q;
+      sIJ[3][word][si] = a[0] & b[2];
+      sIJ[4][word][si] = a[1] & b[2];
+      sIJ[5][word][si] = a[2] & b[0];
+      sIJ[6][word][si] = a[2] & b[1];
+      sIJ[7][word][si] = a[2] & b[2];
     }
     // k side: 64 SNPs x KC words.
     for (int l = threadIdx.x; l < TK * KC; l += THREADS) {
@@ -94,15 +105,16 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
       for (int x = 0; x < 2; ++x) {
 #pragma unroll
-        for (int pij = 0; pij < 9; ++pij) {
+        for (int pij = 0; pij < NIJ; ++pij) {
           const uint64_t ij = sIJ[pij][w][ty + 16 * x];
-          // plane type: P1, P2 -> rho_1 (0); M -> m (1)
-          const int tI = (pij / 3) == 2 ? 1 : 0;
-          const int tJ = (pij % 3) == 2 ? 1 : 0;
+          // plane type of the i and j factors: rho_1 (0) or m (1)
+          const int tI = pij >= 5 ? 1 : 0;
+          const int tJ = (pij == 3 || pij == 4 || pij == 7) ? 1 : 0;
+          const uint32_t wt = pij == 2 ? 3u : 1u;
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
-            T[x][y][4 * tI + 2 * tJ + 0] += __popcll(ij & kp[y][0]) + __popcll(ij & kp[y][1]);
-            T[x][y][4 * tI + 2 * tJ + 1] += __popcll(ij & kp[y][2]);
+            T[x][y][4 * tI + 2 * tJ + 0] += wt * (__popcll(ij & kp[y][0]) + __popcll(ij & kp[y][1]));
+            T[x][y][4 * tI + 2 * tJ + 1] += wt * __popcll(ij & kp[y][2]);
           }
         }
       }
