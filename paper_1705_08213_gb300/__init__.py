@@ -84,7 +84,7 @@ class ccc_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("norm", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("group", ctypes.c_int32), ("order", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("split", ctypes.c_int32)]
 
 
 _lib = None

@@ -72,6 +72,7 @@ int check_opts(const ccc_opts *o) {
   if (!(o->gamma >= 0.0 && o->gamma <= 1.0)) return CCC_EINVAL;
   if (o->group < 0 || o->group > 4096 || (o->order != 0 && o->order != 1)) return CCC_EINVAL;
   if (o->tile < 0 || o->tile > 3) return CCC_EINVAL;
+  if (o->split < 0 || o->split > 4096) return CCC_EINVAL;
   return CCC_OK;
 }
 
@@ -308,6 +309,30 @@ static int launch_tally2_tc_auto(const Tally2Args &a, const ccc_opts *o, const u
               : launch_tally2_tc(a, op, rows_pad, kpad, sms, s);
 }
 
+static bool on_device(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice;
+}
+
+// K parts of a 2-way tensor-core call: opts->split when set (at most the K
+// stages), else automatic: a panel whose triangle has at most half as many
+// tiles as there are SM pairs, with at least 32 K stages, is split so that the
+// parts fill the SM pairs (each part keeping at least 16 K stages).
+static int k_split(int requested, int64_t n_v, int64_t kpad, int sms) {
+  const int64_t nkb = kpad / 128;
+  if (requested >= 1) return static_cast<int>(requested < nkb ? requested : nkb);
+  const int64_t tiles = tc2_pair_tiles(n_v, 0, (n_v + 127) / 128);
+  const int64_t clusters = sms / 2;
+  if (tiles < 1 || 2 * tiles > clusters || nkb < 32) return 1;
+  int64_t split = clusters / tiles;
+  if (split > nkb / 16) split = nkb / 16;
+  return split > 1 ? static_cast<int>(split) : 1;
+}
+
 // Thresholded output of a 2-way call (ccc2_filter); null for plain output.
 struct FilterSpec {
   ccc_hit *hits;
@@ -369,6 +394,20 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   if (o->path == CCC_PATH_TC) {
     uint8_t *op = at<uint8_t>(o, L.op);
     CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    const int split = (filter == nullptr && i_end < 0 && o->tile != 1 && on_device(tally))
+                          ? k_split(o->split, p->n_v, L.kpad, dev.sms)
+                          : 1;
+    if (split > 1) {
+      // Partial tallies of the K parts are summed into the zeroed output; the
+      // CCC values follow from the complete tallies.
+      const size_t bytes = 16 * static_cast<size_t>(p->n_v) * static_cast<size_t>(p->n_v - 1) / 2;
+      if (cudaMemsetAsync(tally, 0, bytes, s) != cudaSuccess) return CCC_ECUDA;
+      const int slot = timing_begin(s);
+      rc = launch_tally2_tc_pair_split(a, op, L.rows_pad, L.kpad, split, dev.sms, s);
+      timing_end(slot, s);
+      if (rc != CCC_OK || out_ccc == nullptr) return rc;
+      return launch_metric2(tally, w, p->n_v, a.gamma, a.norm, out_ccc, s);
+    }
     const int slot = timing_begin(s);
     rc = launch_tally2_tc_auto(a, o, op, L.rows_pad, L.kpad, dev.sms, s);
     timing_end(slot, s);

@@ -65,6 +65,11 @@ int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1);
 // 256 x 256 tiles on SM pairs (cta_group::2); same arguments as launch_tally2_tc.
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                           int num_sms, cudaStream_t s);
+// The same with the K dimension split into `split` parts (1 <= split <= kpad /
+// 128) whose partial tallies are added into a.tally with integer reductions
+// (a.tally must be zero; no CCC values, no thresholded output).
+int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t rows_pad,
+                                int64_t kpad, int split, int num_sms, cudaStream_t s);
 // Tensor-core 2-way tallies over the e4m3 operand matrix op[rows_pad][kpad].
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      int num_sms, cudaStream_t s);

@@ -239,6 +239,93 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
   tcp::persistent_gemm_pair<TriSchedPair, Epi2Pair, EW>(&tm, sp, args, nkb, args.status);
 }
 
+// ---------------------------------------------------------------- split K
+
+// Units of a K-split launch: unit u = (tile u / split, part u % split); part p
+// takes the K stages [p nkb / split, (p + 1) nkb / split) of its tile (the host
+// keeps split <= nkb, so no part is empty).
+struct SplitSchedPair {
+  struct Params {
+    TriSched::Params tri;
+    int split, nkb;
+  };
+  TriSchedPair t;
+  int split, nkb, part, I, J;
+  int64_t u;
+  bool valid;
+
+  __device__ void sync() {
+    valid = t.valid;
+    I = t.I;
+    J = t.J;
+    part = static_cast<int>(u % split);
+  }
+  __device__ void init(const Params &p, int64_t start) {
+    split = p.split;
+    nkb = p.nkb;
+    u = start;
+    t.init(p.tri, start / split);
+    sync();
+  }
+  __device__ void advance(int64_t step) {
+    const int64_t u2 = u + step;
+    t.advance(u2 / split - u / split);
+    u = u2;
+    sync();
+  }
+  __device__ int map_index() const { return 0; }
+  __device__ int k_begin() const {
+    return static_cast<int>(static_cast<int64_t>(part) * nkb / split);
+  }
+  __device__ int k_blocks(int) const {
+    return static_cast<int>(static_cast<int64_t>(part + 1) * nkb / split) - k_begin();
+  }
+  __device__ int a_row() const { return t.a_row(); }
+  __device__ int b_row() const { return t.b_row(); }
+};
+
+// Partial tallies of one K part, added into the zeroed tally array with
+// integer reductions (exact in any order); CCC values follow from the summed
+// tallies in a separate pass.
+struct Epi2Split {
+  using Params = Tally2Args;
+  static constexpr int STAGE_BYTES_PER_WARP = 0;
+  template <int NC>
+  __device__ static void tile(const Params &args, const SplitSchedPair &sc, int rank, int quarter,
+                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
+                              float *) {
+    const int row = quarter * 32 + lane;
+    const int a = row & 1;
+    const int64_t n_v = args.n_v;
+    const int64_t i = static_cast<int64_t>(2 * sc.I + rank) * SNP_I + (row >> 1);
+    const bool row_ok = i < n_v && i >= args.i_begin && i < args.i_end;
+    const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1 - args.pair0;
+    for (int c = c0; c < c0 + NC; ++c) {
+      uint32_t v[32];
+      tmem_ld_32x32b_x32(t_base + c * 32, v);
+      tmem_ld_wait();
+      if (c == c0 + NC - 1) {
+        tc_fence_before();
+        mbar_arrive_cluster(release_cluster_bar);
+      }
+#pragma unroll
+      for (int col = 0; col < 32; ++col) {
+        const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + (col >> 1);
+        const int32_t r = __float2int_rn(__uint_as_float(v[col]));
+        if (row_ok && i < j && j < n_v && r != 0)
+          atomicAdd(args.tally + (row_base + j) * 4 + 2 * a + (col & 1), r);
+      }
+    }
+  }
+};
+
+template <int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
+    k_tally2_tc_pair_split(const __grid_constant__ CUtensorMap tm, const Tally2Args args,
+                           SplitSchedPair::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<SplitSchedPair, Epi2Split, EW>(&tm, sp, args, nkb, args.status);
+}
+
 // ---------------------------------------------------------------- batched panels
 
 struct BatchPanel {
@@ -298,6 +385,7 @@ struct BatchSchedT {
   }
   __device__ int map_index() const { return p; }
   __device__ int k_blocks(int) const { return bp->p[p].nkb; }
+  __device__ int k_begin() const { return 0; }
   __device__ int a_row() const { return t.a_row(); }
   __device__ int b_row() const { return t.b_row(); }
 };
@@ -556,6 +644,50 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
     k_tally2_tc_pair<4><<<grid, 64 + 32 * 4, pair_smem(4), s>>>(tm, a, sp, nkb);
   else
     k_tally2_tc_pair<8><<<grid, 64 + 32 * 8, pair_smem(8), s>>>(tm, a, sp, nkb);
+  return note_launch();
+}
+
+int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t rows_pad,
+                                int64_t kpad, int split, int num_sms, cudaStream_t s) {
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    if (cudaFuncSetAttribute(k_tally2_tc_pair_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+      return CCC_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(64 + 32 * 4, 1, 1);
+    cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair_split<4>, &cfg) != cudaSuccess || n < 1)
+      return CCC_ECUDA;
+    max_clusters = n < num_sms / 2 ? n : num_sms / 2;
+  }
+  const int nkb = static_cast<int>(kpad / BK);
+  if (split < 1 || split > nkb) return CCC_EINVAL;
+  CUtensorMap tm;
+  if (!make_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
+  SplitSchedPair::Params sp;
+  sp.tri.nI = static_cast<int>((a.n_v + 127) / 128);
+  sp.tri.nJ = sp.tri.nI;
+  sp.tri.group = a.group > 0 ? a.group : 8;
+  sp.tri.shift = 0;
+  sp.tri.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / 128);
+  sp.tri.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.tri.nI);
+  sp.split = split;
+  sp.nkb = nkb;
+  const int64_t units = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1) * split;
+  if (units == 0) return CCC_OK;
+  const int64_t clusters = units < max_clusters ? units : max_clusters;
+  k_tally2_tc_pair_split<4><<<static_cast<unsigned>(2 * clusters), 64 + 32 * 4, tcp::SMEM_BYTES, s>>>(
+      tm, a, sp, nkb);
   return note_launch();
 }
 

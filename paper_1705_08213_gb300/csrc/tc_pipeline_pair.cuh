@@ -113,7 +113,8 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
 
 // Sched: as for tc::persistent_gemm, in units of 256-row tiles; a_row/b_row
 // give the first row of the tile (the CTA adds 128 r); map_index() selects the
-// tile's tensor map in tm[].
+// tile's tensor map in tm[]; the tile's K stages are k_begin() ..
+// k_begin() + k_blocks(nkb) - 1.
 // Epi: template <int NC> static void tile(const Params&, const Sched&, int rank,
 //        int quarter, int lane, uint32_t t_base, uint32_t release_cluster_bar,
 //        int c0, float *stage); the release arrives at a cluster address;
@@ -188,6 +189,7 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
         const int yb = sc.b_row() + BNH * static_cast<int>(rank);
         const CUtensorMap *m = tm + sc.map_index();
         const int kbs = sc.k_blocks(nkb);
+        const int kb0 = sc.k_begin();
         for (int kb = 0; kb < kbs; ++kb) {
           if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, status, abort_flag)) {
             ok = false;
@@ -195,8 +197,8 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
           }
           if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * STAGE_BYTES);
           const uint32_t fb = map_to_rank(full_bar(stage), 0);
-          tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), m, kb * BK, ya, fb);
-          tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), m, kb * BK, yb, fb);
+          tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), m, (kb0 + kb) * BK, ya, fb);
+          tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), m, (kb0 + kb) * BK, yb, fb);
           last_parity[stage] = static_cast<int>(phase);
           if (++stage == STAGES) {
             stage = 0;

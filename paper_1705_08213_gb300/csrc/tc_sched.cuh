@@ -67,6 +67,7 @@ struct TriSched {
   }
   __device__ int map_index() const { return 0; }
   __device__ int k_blocks(int nkb) const { return nkb; }
+  __device__ int k_begin() const { return 0; }
   __device__ int a_row() const { return I * tc::BM; }
   __device__ int b_row() const { return J * tc::BN; }
 };

@@ -1,0 +1,118 @@
+"""K-split 2-way calls (ccc_opts.split): panels with few SNP tiles and long vectors.
+
+The individuals are split into parts whose partial tallies are summed on the
+device (the n_pf axis of Sec. 4 on one GPU); CCC values then come from the
+summed tallies.  Results must equal the unsplit call bit for bit and the
+oracle exactly (tallies) / within 1e-6 (CCC), for forced and automatic splits,
+both normalisations, tally-only calls, and outputs in pinned host memory
+(which the split does not use).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import assert_ccc_close, assert_tally_equal, to_device, workspace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_08213_gb300 import build
+    build.build()
+
+
+def _run(geno, n_f, split, norm=0, tally_only=False, host=False):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    g = to_device(geno)
+    n_v = geno.shape[0]
+    opts = ccc.ccc_opts_default(norm=norm)
+    ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
+    opts = ccc.ccc_opts_default(norm=norm, workspace=ws)
+    opts.split = split
+    npairs = ccc.ccc2_count(n_v)
+    kw = dict(dtype=torch.int32, pin_memory=True) if host else dict(dtype=torch.int32, device="cuda")
+    tally = torch.full((npairs, 4), -7, **kw)
+    kwf = dict(kw, dtype=torch.float32)
+    out = torch.full((npairs, 4), -7.0, **kwf)
+    if tally_only:
+        ccc.ccc2_tally(g, n_f, tally, opts)
+    else:
+        ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    return tally.cpu().numpy(), out.cpu().numpy()
+
+
+@pytest.mark.parametrize("norm", [0, 1])
+def test_forced_splits_equal_unsplit_and_oracle(norm):
+    n_v, n_f = 300, 5000  # 40 K stages
+    geno = synth.panel_hwe(n_v, n_f, seed=71, p_missing=0.02)
+    t1, c1 = _run(geno, n_f, 1, norm)
+    et, ec = oracle.ccc2_all(geno, n_f, norm=norm)
+    assert_tally_equal(t1, et, "unsplit")
+    assert_ccc_close(c1, ec, what="unsplit")
+    for split in (2, 3, 7, 40, 4096):  # 4096 is clamped to the 40 K stages
+        t, c = _run(geno, n_f, split, norm)
+        np.testing.assert_array_equal(t, t1)
+        np.testing.assert_array_equal(c, c1)
+
+
+def test_automatic_split_on_a_long_panel():
+    n_v, n_f = 500, 100000
+    geno = synth.panel_hwe(n_v, n_f, seed=72, p_missing=0.01)
+    t, c = _run(geno, n_f, 0)
+    et, ec = oracle.ccc2_all(geno, n_f)
+    assert_tally_equal(t, et, "auto split")
+    assert_ccc_close(c, ec, what="auto split")
+    t1, c1 = _run(geno, n_f, 1)
+    np.testing.assert_array_equal(t, t1)
+    np.testing.assert_array_equal(c, c1)
+
+
+def test_tally_only_and_host_outputs():
+    n_v, n_f = 200, 9000
+    geno = synth.panel_hwe(n_v, n_f, seed=73, p_missing=0.02)
+    et, ec = oracle.ccc2_all(geno, n_f)
+    t, _ = _run(geno, n_f, 5, tally_only=True)
+    assert_tally_equal(t, et, "tally only")
+    t, c = _run(geno, n_f, 5, host=True)  # pinned host outputs: computed unsplit
+    assert_tally_equal(t, et, "host outputs")
+    assert_ccc_close(c, ec, what="host outputs")
+
+
+def test_split_is_faster_on_few_tiles():
+    """512 SNPs (10 SM-pair tiles) x 600,000 individuals: the automatic split fills the SM
+    pairs that the unsplit call leaves idle."""
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    n_v, n_f = 512, 600000
+    geno = synth.panel_hwe(n_v, n_f, seed=74, p_missing=0.01)
+    g = to_device(geno)
+    npairs = ccc.ccc2_count(n_v)
+    tally = torch.empty((npairs, 4), dtype=torch.int32, device="cuda")
+    out = torch.empty((npairs, 4), dtype=torch.float32, device="cuda")
+    times = {}
+    for split in (1, 0):
+        opts = ccc.ccc_opts_default()
+        ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
+        opts = ccc.ccc_opts_default(workspace=ws)
+        opts.split = split
+        ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        times[split] = e0.elapsed_time(e1) / 3
+    assert times[0] < 0.5 * times[1], times
