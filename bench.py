@@ -88,6 +88,12 @@ WORKLOADS = {
               "individuals, per-marker state weights Beta(1/2,1/2) floored at 0.01 and normalised, "
               "two alleles drawn independently, 1% missing, seed 6; all 49,995,000 unique pairs, "
               "16 int32 tallies + 16 fp32 CCC per pair")),
+    "long": dict(
+        kind=2, n_v=512, n_f=1000000, seed=7, model="hwe", p_missing=0.01, split_compare=True,
+        metric="2-way CCC elementwise comparisons/sec on 1 GB300",
+        text=("2-way CCC, few SNPs with long vectors: n_v=512 x n_f=1,000,000, Hardy-Weinberg "
+              "genotypes, Beta(1/2,1/2) MAF floored at 0.01, 1% missing, seed 7; all 130,816 pairs "
+              "(10 SM-pair tiles: the individuals are split into K parts, ccc_opts.split automatic)")),
     "small": dict(
         kind=2, n_v=256, n_f=1024, seed=0, model="uniform", p_missing=0.02,
         metric="2-way CCC elementwise comparisons/sec on 1 GB300",
@@ -136,7 +142,7 @@ def parse():
                      f"same generator and seed (not the bench line's configuration)")
     if a.steps is None:
         a.steps = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10,
-                   "multi": 60}[a.workload]
+                   "multi": 60, "long": 20}[a.workload]
     if a.workload == "batched":
         rng = np.random.default_rng(w["seed"])
         w["shapes"] = [(int(rng.integers(500, 8001)), int(rng.integers(2000, 50001)))
@@ -709,6 +715,7 @@ def main():
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
     kname = {(2, True): ("k_tally2_multi" if w.get("states") else
+                         "k_tally2_tc_pair_split" if w.get("split_compare") else
                          "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc"),
              (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(
                  args.tile, "k_tally3_class_w" if w["n_f"] <= 16383 else "k_tally3_class"),
@@ -771,6 +778,24 @@ def main():
         "roofline": roof,
         "clocks": clocks,
     }
+
+    if w.get("split_compare") and rank == 0:
+        # The same call with the K split turned off (ccc_opts.split = 1).
+        run.opts.split = 1
+        run.step(stream)
+        torch.cuda.synchronize(dev)
+        u0 = torch.cuda.Event(enable_timing=True)
+        u1 = torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        for _ in range(3):
+            run.step(stream)
+        u1.record(stream)
+        torch.cuda.synchronize(dev)
+        ums = u0.elapsed_time(u1) / 3
+        run.opts.split = 0
+        result["unsplit"] = {"value": cmp_per_step / (ums * 1e-3), "unit": UNIT, "ms_per_step": ums,
+                             "split_speedup": ums / ms_per_step,
+                             "note": "ccc_opts.split = 1: one K part per tile"}
 
     if not args.skip_e2e and rank == 0 and not (strong and world > 1):
         e2e_ms, bi, bo = run.e2e(stream, max(1, min(args.steps, 5)), mode=args.e2e_mode)
