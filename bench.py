@@ -453,7 +453,9 @@ class Runner:
         """
         torch, ccc, w = self.torch, self.ccc, self.w
         if mode == "auto":
-            mode = "stream" if not self.filter else "copy"
+            # Phases split the rows; a panel of few tiles is better served by one
+            # K-split call and a copy of its small output.
+            mode = "stream" if not (self.filter or w.get("split_compare")) else "copy"
         self.e2e_mode = mode if not self.filter else "copy"
         streamed = mode == "stream" and not self.filter
         direct = mode == "direct" and not self.filter
