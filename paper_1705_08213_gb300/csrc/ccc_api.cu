@@ -322,15 +322,18 @@ static bool on_device(const void *p) {
 // stages), else automatic: a panel whose triangle has at most half as many
 // tiles as there are SM pairs, with at least 32 K stages, is split so that the
 // parts fill the SM pairs (each part keeping at least 16 K stages).
-static int k_split(int requested, int64_t n_v, int64_t kpad, int sms) {
+static int k_split_tiles(int requested, int64_t tiles, int64_t kpad, int sms) {
   const int64_t nkb = kpad / 128;
   if (requested >= 1) return static_cast<int>(requested < nkb ? requested : nkb);
-  const int64_t tiles = tc2_pair_tiles(n_v, 0, (n_v + 127) / 128);
   const int64_t clusters = sms / 2;
   if (tiles < 1 || 2 * tiles > clusters || nkb < 32) return 1;
   int64_t split = clusters / tiles;
   if (split > nkb / 16) split = nkb / 16;
   return split > 1 ? static_cast<int>(split) : 1;
+}
+
+static int k_split(int requested, int64_t n_v, int64_t kpad, int sms) {
+  return k_split_tiles(requested, tc2_pair_tiles(n_v, 0, (n_v + 127) / 128), kpad, sms);
 }
 
 // Thresholded output of a 2-way call (ccc2_filter); null for plain output.
@@ -809,9 +812,29 @@ static int run_multi(const ccc_panel_multi *p, int32_t *tally, float *out_ccc, c
     CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
   uint8_t *op = at<uint8_t>(o, L.op);
   CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s));
-  if (i_end < 0) {
+  const bool whole = i_end < 0;
+  if (whole) {
     i_begin = 0;
     i_end = p->n_v;
+  }
+  const int split = whole && on_device(tally)
+                        ? k_split_tiles(o->split, (L.rows_pad / 256) * (L.rows_pad / 256 + 1) / 2,
+                                        L.kpad, dev.sms)
+                        : 1;
+  if (split > 1) {
+    // Partial tallies of the K parts summed into the zeroed output; CCC values
+    // from the complete tallies.
+    const size_t bytes = 4 * static_cast<size_t>(ns) * ns * static_cast<size_t>(p->n_v) *
+                         static_cast<size_t>(p->n_v - 1) / 2;
+    if (cudaMemsetAsync(tally, 0, bytes, s) != cudaSuccess) return CCC_ECUDA;
+    const int slot = timing_begin(s);
+    const int rc = launch_tally2_multi(ns, p->n_v, w, tally, nullptr, at<int32_t>(o, L.status),
+                                       static_cast<float>(o->gamma), o->norm, o->group, op,
+                                       L.rows_pad, L.kpad, dev.sms, s, 0, p->n_v, 0, split);
+    timing_end(slot, s);
+    if (rc != CCC_OK || out_ccc == nullptr) return rc;
+    return launch_metric2_multi(tally, w, p->n_v, ns, static_cast<float>(o->gamma), o->norm,
+                                out_ccc, s);
   }
   const int slot = timing_begin(s);
   const int rc = launch_tally2_multi(ns, p->n_v, w, tally, out_ccc, at<int32_t>(o, L.status),

@@ -148,14 +148,17 @@ int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t l
                         uint8_t *op, int64_t kpad, int64_t rows_pad, cudaStream_t st);
 // Tallies and, when out_ccc is set, CCC values of the pairs with
 // i_begin <= i < i_end (s*s each), pair (i, j) at pair_index(i, j) - pair0.
+// split > 1 (whole triangle only): the K stages in `split` parts whose partial
+// tallies are added into the zeroed tally array, no CCC values.
 int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                         int32_t *status, float gamma, int32_t norm, int32_t group, const uint8_t *op,
                         int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st,
-                        int64_t i_begin, int64_t i_end, int64_t pair0);
+                        int64_t i_begin, int64_t i_end, int64_t pair0, int split = 1);
 int launch_tally2_multi_wide(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                              int32_t *status, float gamma, int32_t norm, int32_t group,
                              const uint8_t *op, int64_t rows_pad, int64_t kpad, int num_sms,
-                             cudaStream_t st, int64_t i_begin, int64_t i_end, int64_t pair0);
+                             cudaStream_t st, int64_t i_begin, int64_t i_end, int64_t pair0,
+                             int split);
 int launch_metric2_multi(const int32_t *tally, const float *w, int64_t n_v, int s, float gamma,
                          int32_t norm, float *out_ccc, cudaStream_t st);
 

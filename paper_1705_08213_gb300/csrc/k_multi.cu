@@ -263,16 +263,29 @@ int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t l
 int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                         int32_t *status, float gamma, int32_t norm, int32_t group, const uint8_t *op,
                         int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st,
-                        int64_t i_begin, int64_t i_end, int64_t pair0) {
+                        int64_t i_begin, int64_t i_end, int64_t pair0, int split) {
   if (n_v < 2) return CCC_OK;
   if (s > 8) return launch_tally2_multi_wide(s, n_v, w, tally, out_ccc, status, gamma, norm, group,
-                                             op, rows_pad, kpad, num_sms, st, i_begin, i_end, pair0);
+                                             op, rows_pad, kpad, num_sms, st, i_begin, i_end, pair0,
+                                             split);
   CUtensorMap tm;
   if (!tc::make_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
   MultiArgs a{n_v, w, tally, out_ccc, status, gamma, norm, i_begin, i_end, pair0};
   // 256-row blocks holding a SNP (rows_pad has exactly these).
   const int64_t nB = rows_pad / 256;
   const int nkb = static_cast<int>(kpad / tcp::BK);
+  if (split > 1) {
+    switch (s) {
+      case 2: return launch_tally2_multi_split_s<2>(tm, a, nB, group, nkb, split, num_sms, st);
+      case 3: return launch_tally2_multi_split_s<3>(tm, a, nB, group, nkb, split, num_sms, st);
+      case 4: return launch_tally2_multi_split_s<4>(tm, a, nB, group, nkb, split, num_sms, st);
+      case 5: return launch_tally2_multi_split_s<5>(tm, a, nB, group, nkb, split, num_sms, st);
+      case 6: return launch_tally2_multi_split_s<6>(tm, a, nB, group, nkb, split, num_sms, st);
+      case 7: return launch_tally2_multi_split_s<7>(tm, a, nB, group, nkb, split, num_sms, st);
+      case 8: return launch_tally2_multi_split_s<8>(tm, a, nB, group, nkb, split, num_sms, st);
+      default: return CCC_EINVAL;
+    }
+  }
   switch (s) {
     case 2: return launch_tally2_multi_s<2>(tm, a, nB, group, nkb, num_sms, st);
     case 3: return launch_tally2_multi_s<3>(tm, a, nB, group, nkb, num_sms, st);

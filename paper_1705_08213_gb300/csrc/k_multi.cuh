@@ -147,11 +147,108 @@ struct EpiMulti {
   }
 };
 
+// Partial tallies of one K part (K split): each accumulator element is added
+// into the zeroed tally array with an integer reduction.
+template <int S>
+struct EpiMultiSplit {
+  using Params = MultiArgs;
+  static constexpr int PW = snps_per_quarter(S);
+  static constexpr int STAGE_BYTES_PER_WARP = 0;
+
+  template <int NC>
+  __device__ static void tile(const Params &args, const SplitSchedPair &sc, int rank, int quarter,
+                              int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
+                              float *) {
+    const int u = lane / S;
+    const int a = lane - u * S;
+    const int64_t n_v = args.n_v;
+    const int64_t i = ((2 * static_cast<int64_t>(sc.I) + rank) * 4 + quarter) * PW + u;
+    const bool row_ok = u < PW && i < n_v && i >= args.i_begin && i < args.i_end;
+    const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1 - args.pair0;
+    for (int c = c0; c < c0 + NC; ++c) {
+      uint32_t v[32];
+      tmem_ld_32x32b_x32(t_base + c * 32, v);
+      tmem_ld_wait();
+      if (c == c0 + NC - 1) {
+        tc_fence_before();
+        mbar_arrive_cluster(release_cluster_bar);
+      }
+      const int64_t j0 = ((2 * static_cast<int64_t>(sc.J) + (c >> 2)) * 4 + (c & 3)) * PW;
+#pragma unroll
+      for (int jl = 0; jl < PW; ++jl) {
+        const int64_t j = j0 + jl;
+        if (!(row_ok && i < j && j < n_v)) continue;
+        int32_t *dst = args.tally + (row_base + j) * (S * S) + a * S;
+#pragma unroll
+        for (int b = 0; b < S; ++b) {
+          const int32_t r = __float2int_rn(__uint_as_float(v[jl * S + b]));
+          if (r != 0) atomicAdd(dst + b, r);
+        }
+      }
+    }
+  }
+};
+
+template <int S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
+    k_tally2_multi_split(const __grid_constant__ CUtensorMap tm, const MultiArgs args,
+                         SplitSchedPair::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<SplitSchedPair, EpiMultiSplit<S>, kMultiEpiWarps>(&tm, sp, args, nkb,
+                                                                               args.status);
+}
+
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
     k_tally2_multi(const __grid_constant__ CUtensorMap tm, const MultiArgs args,
                    TriSched::Params sp, int nkb) {
   tcp::persistent_gemm_pair<TriSchedPair, EpiMulti<S>, kMultiEpiWarps>(&tm, sp, args, nkb, args.status);
+}
+
+// Persistent grid size for a pair kernel of kMultiThreads threads.
+template <typename K>
+int multi_max_clusters(K kernel, int num_sms) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 2;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+  cfg.blockDim = dim3(kMultiThreads, 1, 1);
+  cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) return 0;
+  return n < num_sms / 2 ? n : num_sms / 2;
+}
+
+// K-split launch over the whole triangle of nB row blocks (split <= nkb).
+template <int S>
+int launch_tally2_multi_split_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB, int group,
+                                int nkb, int split, int num_sms, cudaStream_t s) {
+  static int max_clusters = 0;
+  if (max_clusters == 0) max_clusters = multi_max_clusters(k_tally2_multi_split<S>, num_sms);
+  if (max_clusters == 0) return CCC_ECUDA;
+  if (split < 1 || split > nkb) return CCC_EINVAL;
+  SplitSchedPair::Params sp;
+  sp.tri.nI = static_cast<int>(nB);
+  sp.tri.nJ = sp.tri.nI;
+  sp.tri.group = group > 0 ? group : 8;
+  sp.tri.shift = 0;
+  sp.tri.I0 = 0;
+  sp.tri.I1 = sp.tri.nI;
+  sp.split = split;
+  sp.nkb = nkb;
+  const int64_t units = nB * (nB + 1) / 2 * split;
+  if (units == 0) return CCC_OK;
+  const int64_t clusters = units < max_clusters ? units : max_clusters;
+  k_tally2_multi_split<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, tcp::SMEM_BYTES,
+                            s>>>(tm, a, sp, nkb);
+  return note_launch();
 }
 
 template <int S>

@@ -1,5 +1,5 @@
 // Tile order over the upper triangle of a Gram product, shared by the 2-way
-// tally kernels (biallelic and multi-allelic).
+// tally kernels (biallelic and multi-allelic), and its K-split form.
 #pragma once
 
 #include "tc_pipeline.cuh"
@@ -76,6 +76,49 @@ struct TriSched {
 struct TriSchedPair : TriSched {
   __device__ int a_row() const { return I * 256; }
   __device__ int b_row() const { return J * 256; }
+};
+
+// Units of a K-split launch: unit u = (tile u / split, part u % split); part p
+// takes the K stages [p nkb / split, (p + 1) nkb / split) of its tile (the host
+// keeps split <= nkb, so no part is empty).
+struct SplitSchedPair {
+  struct Params {
+    TriSched::Params tri;
+    int split, nkb;
+  };
+  TriSchedPair t;
+  int split, nkb, part, I, J;
+  int64_t u;
+  bool valid;
+
+  __device__ void sync() {
+    valid = t.valid;
+    I = t.I;
+    J = t.J;
+    part = static_cast<int>(u % split);
+  }
+  __device__ void init(const Params &p, int64_t start) {
+    split = p.split;
+    nkb = p.nkb;
+    u = start;
+    t.init(p.tri, start / split);
+    sync();
+  }
+  __device__ void advance(int64_t step) {
+    const int64_t u2 = u + step;
+    t.advance(u2 / split - u / split);
+    u = u2;
+    sync();
+  }
+  __device__ int map_index() const { return 0; }
+  __device__ int k_begin() const {
+    return static_cast<int>(static_cast<int64_t>(part) * nkb / split);
+  }
+  __device__ int k_blocks(int) const {
+    return static_cast<int>(static_cast<int64_t>(part + 1) * nkb / split) - k_begin();
+  }
+  __device__ int a_row() const { return t.a_row(); }
+  __device__ int b_row() const { return t.b_row(); }
 };
 
 }  // namespace

@@ -116,3 +116,33 @@ def test_split_is_faster_on_few_tiles():
         torch.cuda.synchronize()
         times[split] = e0.elapsed_time(e1) / 3
     assert times[0] < 0.5 * times[1], times
+
+
+@pytest.mark.parametrize("s", [3, 4, 11])
+def test_multi_split_equals_unsplit_and_oracle(s):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    from tests.gpu_util import to_device_bytes
+    n_v, n_f = 90, 20000
+    gm = synth.panel_multi(n_v, n_f, s, seed=75 + s, p_missing=0.02)
+    g = to_device_bytes(gm)
+    res = {}
+    for split in (1, 0, 6):
+        opts = ccc.ccc_opts_default()
+        ws = workspace(ccc.ccc_multi_workspace_size(g, n_f, s, opts))
+        opts = ccc.ccc_opts_default(workspace=ws)
+        opts.split = split
+        npairs = ccc.ccc2_count(n_v)
+        t = torch.full((npairs, s * s), -7, dtype=torch.int32, device="cuda")
+        c = torch.full((npairs, s * s), -7.0, dtype=torch.float32, device="cuda")
+        ccc.ccc2_multi_tally_metric(g, n_f, s, t, c, opts)
+        torch.cuda.synchronize()
+        assert ccc.ccc_status(opts) == ccc.CCC_OK
+        res[split] = (t.cpu().numpy(), c.cpu().numpy())
+    et, ec = oracle.ccc2_multi_all(gm, n_f, s)
+    assert_tally_equal(res[1][0], et, "multi unsplit")
+    assert_ccc_close(res[1][1], ec, what="multi unsplit")
+    for split in (0, 6):
+        np.testing.assert_array_equal(res[split][0], res[1][0])
+        np.testing.assert_array_equal(res[split][1], res[1][1])
