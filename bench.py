@@ -182,6 +182,8 @@ def comparisons(w):
 KERNEL_SOURCES = {
     "k_tally2_tc_pair": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
                          "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_split": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
+                               "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_multi": ["k_multi.cuh", "k_multi.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
                        "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh",
