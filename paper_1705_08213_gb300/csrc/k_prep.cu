@@ -20,32 +20,67 @@ __device__ __forceinline__ uint64_t valid_even_mask(int64_t w, int64_t n_f) {
   return kEven & ((1ull << (2 * tail)) - 1ull);
 }
 
-// One warp per SNP.  For every word: l = (v)_2 bits, h = (v)_1 bits; the
-// missing marker is h & ~l; rho_1 = l + (h & l) for present entries.
-__global__ void k_allele_counts(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
-                                int64_t ld, int32_t *__restrict__ counts, float *__restrict__ w,
-                                double gamma) {
-  const int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n_v) return;
+// WPS warps per SNP (256-thread blocks hold 8 / WPS SNPs).  For every word:
+// l = (v)_2 bits, h = (v)_1 bits; the missing marker is h & ~l; rho_1 = l + (h & l)
+// for present entries.  Several warps per SNP keep enough loads in flight when
+// a panel has few SNPs with long vectors.
+template <int WPS>
+__global__ void __launch_bounds__(256) k_allele_counts(const uint64_t *__restrict__ geno,
+                                                       int64_t n_f, int64_t n_v, int64_t ld,
+                                                       int32_t *__restrict__ counts,
+                                                       float *__restrict__ w, double gamma) {
+  constexpr int kSnpsPerBlock = 8 / WPS;
+  __shared__ long long part[8][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = warp / WPS, sub = warp % WPS;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kSnpsPerBlock + slot;
   const int64_t words = (n_f + 31) / 32;
-  const uint64_t *row = geno + i * ld;
   int64_t n = 0, s1 = 0;
-  for (int64_t k = lane; k < words; k += 32) {
-    const uint64_t v = row[k];
-    const uint64_t valid = valid_even_mask(k, n_f);
-    const uint64_t l = v & valid;
-    const uint64_t h = (v >> 1) & valid;
-    const uint64_t present = valid & ~(h & ~l);
-    n += __popcll(present);
-    s1 += __popcll(l) + __popcll(h & l);
+  if (i < n_v) {
+    const uint64_t *row = geno + i * ld;
+    const int64_t step = 32 * WPS;
+    int64_t k = sub * 32 + lane;
+    // Four independent loads per iteration.
+    for (; k + 3 * step < words; k += 4 * step) {
+      uint64_t v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(row + k + u * step);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint64_t valid = valid_even_mask(k + u * step, n_f);
+        const uint64_t l = v[u] & valid;
+        const uint64_t h = (v[u] >> 1) & valid;
+        n += __popcll(valid & ~(h & ~l));
+        s1 += __popcll(l) + __popcll(h & l);
+      }
+    }
+    for (; k < words; k += step) {
+      const uint64_t v = __ldg(row + k);
+      const uint64_t valid = valid_even_mask(k, n_f);
+      const uint64_t l = v & valid;
+      const uint64_t h = (v >> 1) & valid;
+      n += __popcll(valid & ~(h & ~l));
+      s1 += __popcll(l) + __popcll(h & l);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     n += __shfl_xor_sync(0xffffffffu, n, o);
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
   }
-  if (lane == 0) {
+  if (WPS > 1) {
+    if (lane == 0) {
+      part[warp][0] = n;
+      part[warp][1] = s1;
+    }
+    __syncthreads();
+    if (sub != 0) return;
+    for (int u = 1; u < WPS; ++u) {
+      n += part[warp + u][0];
+      s1 += part[warp + u][1];
+    }
+  }
+  if (lane == 0 && i < n_v) {
     const int64_t s0 = 2 * n - s1;
     if (counts) {
       counts[3 * i + 0] = static_cast<int32_t>(s0);
@@ -86,34 +121,34 @@ constexpr uint32_t kRho1E4M3 = 0x40003800u;
 
 // Operand rows for SNP i: row 2i holds rho_{i,q}(0), row 2i+1 holds rho_{i,q}(1),
 // q = 0 .. kpad-1 (zero past n_f).  Rows past 2 n_v are zero.  One thread per
-// packed word (32 entries -> 32 bytes in each of the two rows).
+// half of a packed word (16 entries -> 16 bytes in each of the two rows), so
+// that each warp store covers 512 contiguous bytes of a row.
 __global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
                               int64_t ld, uint8_t *__restrict__ op, int64_t kpad,
                               int64_t snps_pad) {
-  const int64_t wpr = kpad / 32;  // words per operand row
+  const int64_t hpr = kpad / 16;  // 16-entry chunks per operand row
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= wpr * snps_pad) return;
-  const int64_t i = t / wpr;
-  const int64_t k = t - i * wpr;
+  if (t >= hpr * snps_pad) return;
+  const int64_t i = t / hpr;
+  const int64_t c = t - i * hpr;
+  const int64_t k = c >> 1;
   uint64_t v = 0xAAAAAAAAAAAAAAAAull;  // all entries "missing" -> zero operands
   if (i < n_v && k * 32 < n_f) {
     const uint64_t valid = valid_even_mask(k, n_f);
     const uint64_t vm = valid | (valid << 1);
-    v = (geno[i * ld + k] & vm) | (0xAAAAAAAAAAAAAAAAull & ~vm);
+    v = (__ldg(geno + i * ld + k) & vm) | (0xAAAAAAAAAAAAAAAAull & ~vm);
   }
-  uint32_t r0[8], r1[8];
+  const uint32_t h = static_cast<uint32_t>(v >> (32 * (c & 1)));
+  uint32_t r0[4], r1[4];
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const uint32_t sel = code_nibbles(static_cast<uint32_t>(v >> (8 * b)) & 0xFFu);
+  for (int b = 0; b < 4; ++b) {
+    const uint32_t sel = code_nibbles((h >> (8 * b)) & 0xFFu);
     r0[b] = __byte_perm(kRho0E4M3, 0u, sel);
     r1[b] = __byte_perm(kRho1E4M3, 0u, sel);
   }
-  uint4 *d0 = reinterpret_cast<uint4 *>(op + (2 * i) * kpad + k * 32);
-  uint4 *d1 = reinterpret_cast<uint4 *>(op + (2 * i + 1) * kpad + k * 32);
-  d0[0] = make_uint4(r0[0], r0[1], r0[2], r0[3]);
-  d0[1] = make_uint4(r0[4], r0[5], r0[6], r0[7]);
-  d1[0] = make_uint4(r1[0], r1[1], r1[2], r1[3]);
-  d1[1] = make_uint4(r1[4], r1[5], r1[6], r1[7]);
+  *reinterpret_cast<uint4 *>(op + (2 * i) * kpad + c * 16) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+  *reinterpret_cast<uint4 *>(op + (2 * i + 1) * kpad + c * 16) =
+      make_uint4(r1[0], r1[1], r1[2], r1[3]);
 }
 
 // Gather the 32 even-position bits of x into the low 32 bits.
@@ -161,10 +196,28 @@ __global__ void k_planes(const uint64_t *__restrict__ geno, int64_t n_f, int64_t
 
 int launch_allele_counts(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld,
                          int32_t *counts, float *w, double gamma, cudaStream_t s) {
-  const int threads = 256;
-  const int64_t blocks = (n_v * 32 + threads - 1) / threads;
-  k_allele_counts<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, counts,
-                                                                     w, gamma);
+  if (n_v < 1) return CCC_OK;
+  // Warps per SNP: double while the grid holds under 32 warps per SM and every
+  // lane still gets at least two words.
+  const int64_t words = (n_f + 31) / 32;
+  int wps = 1;
+  while (wps < 8 && n_v * wps < 152 * 32 && words >= 64 * 2 * wps) wps *= 2;
+  const int64_t per_block = 8 / wps;
+  const unsigned blocks = static_cast<unsigned>((n_v + per_block - 1) / per_block);
+  switch (wps) {
+    case 1:
+      k_allele_counts<1><<<blocks, 256, 0, s>>>(geno, n_f, n_v, ld, counts, w, gamma);
+      break;
+    case 2:
+      k_allele_counts<2><<<blocks, 256, 0, s>>>(geno, n_f, n_v, ld, counts, w, gamma);
+      break;
+    case 4:
+      k_allele_counts<4><<<blocks, 256, 0, s>>>(geno, n_f, n_v, ld, counts, w, gamma);
+      break;
+    default:
+      k_allele_counts<8><<<blocks, 256, 0, s>>>(geno, n_f, n_v, ld, counts, w, gamma);
+      break;
+  }
   return note_launch();
 }
 
@@ -179,7 +232,7 @@ int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, dou
 int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                        int64_t kpad, int64_t snps_pad, cudaStream_t s) {
   const int threads = 256;
-  const int64_t total = (kpad / 32) * snps_pad;
+  const int64_t total = (kpad / 16) * snps_pad;
   const int64_t blocks = (total + threads - 1) / threads;
   k_unpack_e4m3<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
                                                                    snps_pad);
