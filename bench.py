@@ -184,6 +184,10 @@ KERNEL_SOURCES = {
                          "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_split": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
                                "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_packed": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
+                                "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_split_packed": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
+                                      "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_multi": ["k_multi.cuh", "k_multi.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
                        "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh",
@@ -718,9 +722,10 @@ def main():
     # summed duration of its launches in the timed region / steps.
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
+    packed = "_packed" if args.tile == 3 else ""
     kname = {(2, True): ("k_tally2_multi" if w.get("states") else
-                         "k_tally2_tc_pair_split" if w.get("split_compare") else
-                         "k_tally2_tc_pair" if args.tile != 1 else "k_tally2_tc"),
+                         "k_tally2_tc_pair_split" + packed if w.get("split_compare") else
+                         "k_tally2_tc_pair" + packed if args.tile != 1 else "k_tally2_tc"),
              (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(
                  args.tile, "k_tally3_class_w" if w["n_f"] <= 16383 else "k_tally3_class"),
              (2, False): "k_tally2_popc", (3, False): "k_tally3_popc"}[(w["kind"],
@@ -766,7 +771,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"], "path": args.path,
                    "tile": ({0: "automatic (256x256 on an SM pair)", 1: "128x256 on one SM",
-                             2: "256x256 on an SM pair"} if w["kind"] == 2 else
+                             2: "256x256 on an SM pair",
+                             3: "256x256 on an SM pair, 2-bit codes expanded in shared memory"}
+                            if w["kind"] == 2 else
                             {0: "automatic (genotype classes of v_j on SM pairs)",
                              1: "masked operands L_j formed in HBM", 2: "L_j formed in shared memory",
                              3: "genotype classes of v_j on SM pairs"})[args.tile],

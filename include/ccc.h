@@ -115,7 +115,11 @@ typedef struct ccc_opts {
   int32_t group;          /* tensor-core tile order: column blocks per L2 group; 0 = 8 */
   int32_t order;          /* ccc2_batched panel order: 0 = most tile work first, 1 = as given */
   int32_t tile;           /* tensor-core variant.  2-way: 1 = 128 x 256 tiles on one SM,
-                             2 = 256 x 256 tiles on a pair of SMs (cta_group::2); automatic = 2.
+                             2 = 256 x 256 tiles on a pair of SMs (cta_group::2), 3 = as 2 with
+                             the 2-bit codes expanded into count rows in shared memory inside the
+                             tally kernel (the unpack of Sec. 3.1 fused; no operand matrix in the
+                             workspace, for panels whose 2-bytes-per-entry operands would not fit;
+                             slower on GB300); automatic = 2.  ccc2_batched rejects 3.
                              3-way: 1 = masked operands L_j formed in HBM by a separate pass,
                              2 = L_j formed in shared memory inside the tally kernel (repeated
                              for every k-block, slower), 3 = genotype classes of v_j on SM

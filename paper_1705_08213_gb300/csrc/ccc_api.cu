@@ -79,7 +79,7 @@ int check_opts(const ccc_opts *o) {
 // Options of a 2-way call: tile 3 names a 3-way variant only.
 int check_opts2(const ccc_opts *o) {
   CCC_TRY_INNER(check_opts(o));
-  return o->tile > 2 ? CCC_EINVAL : CCC_OK;
+  return o->tile > 3 ? CCC_EINVAL : CCC_OK;
 }
 
 // Workspace layout shared by the 2-way and 3-way calls.
@@ -120,7 +120,8 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
   if (op == CCC_OP_2WAY || op == CCC_OP_3WAY) {
     if (path == CCC_PATH_TC) {
       L.kpad = round_up(n_f, 128);
-      L.rows_pad = tc_rows_pad(n_v);
+      // 2-way tile 3 expands the codes in shared memory: no operand matrix.
+      L.rows_pad = (op == CCC_OP_2WAY && tile == 3) ? 0 : tc_rows_pad(n_v);
       off = align_up(off, 1024);
       L.op = off;
       if (op == CCC_OP_3WAY && (tile == 0 || tile == 3)) {
@@ -362,7 +363,7 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   }
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
-  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY);
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY, o->tile);
   CCC_TRY(check_workspace(o, L));
   CCC_TRY(clear_status(o, L, s));
   if (filter != nullptr &&
@@ -395,8 +396,12 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   a.norm = o->norm;
   int rc;
   if (o->path == CCC_PATH_TC) {
-    uint8_t *op = at<uint8_t>(o, L.op);
-    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    // tile 3: the tally kernel reads the packed panel and forms the count rows
+    // in shared memory; otherwise they are unpacked into the operand matrix.
+    const bool packed = o->tile == 3;
+    uint8_t *op = packed ? nullptr : at<uint8_t>(o, L.op);
+    if (!packed)
+      CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
     const int split = (filter == nullptr && i_end < 0 && o->tile != 1 && on_device(tally))
                           ? k_split(o->split, p->n_v, L.kpad, dev.sms)
                           : 1;
@@ -406,13 +411,15 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
       const size_t bytes = 16 * static_cast<size_t>(p->n_v) * static_cast<size_t>(p->n_v - 1) / 2;
       if (cudaMemsetAsync(tally, 0, bytes, s) != cudaSuccess) return CCC_ECUDA;
       const int slot = timing_begin(s);
-      rc = launch_tally2_tc_pair_split(a, op, L.rows_pad, L.kpad, split, dev.sms, s);
+      rc = packed ? launch_tally2_tc_pair_split_packed(a, p->geno, p->ld, split, dev.sms, s)
+                  : launch_tally2_tc_pair_split(a, op, L.rows_pad, L.kpad, split, dev.sms, s);
       timing_end(slot, s);
       if (rc != CCC_OK || out_ccc == nullptr) return rc;
       return launch_metric2(tally, w, p->n_v, a.gamma, a.norm, out_ccc, s);
     }
     const int slot = timing_begin(s);
-    rc = launch_tally2_tc_auto(a, o, op, L.rows_pad, L.kpad, dev.sms, s);
+    rc = packed ? launch_tally2_tc_pair_packed(a, p->geno, p->ld, dev.sms, s)
+                : launch_tally2_tc_auto(a, o, op, L.rows_pad, L.kpad, dev.sms, s);
     timing_end(slot, s);
     return rc;
   }
@@ -636,6 +643,7 @@ static int batch_layout(const ccc_panel *panels, int n, int path, BatchLayout *B
 static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, float *const *out_ccc,
                        const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_opts2(o));
+  if (o->tile == 3) return CCC_EINVAL;  // batched panels use the operand matrices
   if (panels == nullptr || tally == nullptr || n < 1 || n > kMaxPanelsPerCall) return CCC_EINVAL;
   for (int k = 0; k < n; ++k) {
     CCC_TRY(check_panel(&panels[k]));
@@ -881,7 +889,6 @@ int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, siz
   if (panel == nullptr || panel->n_f < 1 || panel->n_v < 1) return CCC_EINVAL;
   if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
   if (op != CCC_OP_2WAY && op != CCC_OP_3WAY && op != CCC_OP_METRIC) return CCC_EINVAL;
-  if (op != CCC_OP_3WAY && opts->tile > 2) return CCC_EINVAL;
   *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile).total;
   return CCC_OK;
 }
@@ -996,7 +1003,7 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
   if (cudaGetDevice(&d) != cudaSuccess) return CCC_ECUDA;
   StreamRes *R = nullptr;
   CCC_TRY(stream_res(d, &R));
-  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY);
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY, o->tile);
   CCC_TRY(clear_status(o, L, s));
   if (p->n_v < 2) return CCC_OK;
   const bool want_ccc = host_ccc != nullptr;
@@ -1009,10 +1016,11 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
     CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   uint8_t *op = nullptr;
   uint64_t *planes = nullptr;
-  if (o->path == CCC_PATH_TC) {
+  const bool packed = o->path == CCC_PATH_TC && o->tile == 3;
+  if (o->path == CCC_PATH_TC && !packed) {
     op = at<uint8_t>(o, L.op);
     CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
-  } else {
+  } else if (o->path != CCC_PATH_TC) {
     planes = at<uint64_t>(o, L.planes);
     CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
   }
@@ -1044,7 +1052,8 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
     a.i_end = i1;
     a.pair0 = pair_index(i0, i0 + 1, p->n_v);
     const int slot = timing_begin(s);
-    const int rc = o->path == CCC_PATH_TC
+    const int rc = packed ? launch_tally2_tc_pair_packed(a, p->geno, p->ld, dev.sms, s)
+                   : o->path == CCC_PATH_TC
                        ? launch_tally2_tc_auto(a, o, op, L.rows_pad, L.kpad, dev.sms, s)
                        : launch_tally2_popc(a, planes, L.w64, s);
     timing_end(slot, s);

@@ -70,6 +70,13 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
 // (a.tally must be zero; no CCC values, no thresholded output).
 int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t rows_pad,
                                 int64_t kpad, int split, int num_sms, cudaStream_t s);
+// The two launches above with the operand preparation fused in: the kernel
+// reads the packed panel geno (row stride ld words, even; 16-byte aligned)
+// and expands the codes into count rows in shared memory.
+int launch_tally2_tc_pair_packed(const Tally2Args &a, const uint64_t *geno, int64_t ld,
+                                 int num_sms, cudaStream_t s);
+int launch_tally2_tc_pair_split_packed(const Tally2Args &a, const uint64_t *geno, int64_t ld,
+                                       int split, int num_sms, cudaStream_t s);
 // Tensor-core 2-way tallies over the e4m3 operand matrix op[rows_pad][kpad].
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      int num_sms, cudaStream_t s);

@@ -283,6 +283,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
   tcp::persistent_gemm_pair<SplitSchedPair, Epi2Split, EW>(&tm, sp, args, nkb, args.status);
 }
 
+// ---------------------------------------------------------------- packed operands
+
+// The pair kernels with the 2-bit codes expanded into count rows in shared
+// memory (tcp::persistent_gemm_pair_packed): no operand matrix in HBM.
+template <int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW + 32 * tcp::pk::CW, 1)
+    k_tally2_tc_pair_packed(const __grid_constant__ CUtensorMap tmP, const Tally2Args args,
+                            TriSched::Params sp, int nkb) {
+  tcp::persistent_gemm_pair_packed<TriSchedPair, Epi2Pair, EW>(&tmP, sp, args, nkb, args.n_v,
+                                                               args.n_f, args.status);
+}
+
+template <int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW + 32 * tcp::pk::CW, 1)
+    k_tally2_tc_pair_split_packed(const __grid_constant__ CUtensorMap tmP, const Tally2Args args,
+                                  SplitSchedPair::Params sp, int nkb) {
+  tcp::persistent_gemm_pair_packed<SplitSchedPair, Epi2Split, EW>(&tmP, sp, args, nkb, args.n_v,
+                                                                  args.n_f, args.status);
+}
+
+constexpr size_t packed_smem(int ew) {
+  return tcp::pk::smem_bytes(ew, Epi2Staged::STAGE_BYTES_PER_WARP);
+}
+static_assert(packed_smem(8) <= 232448, "dynamic shared memory limit");
+
 // ---------------------------------------------------------------- batched panels
 
 struct BatchPanel {
@@ -645,6 +670,107 @@ int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t 
   const int64_t clusters = units < max_clusters ? units : max_clusters;
   k_tally2_tc_pair_split<4><<<static_cast<unsigned>(2 * clusters), 64 + 32 * 4, tcp::SMEM_BYTES, s>>>(
       tm, a, sp, nkb);
+  return note_launch();
+}
+
+// Tensor map over the packed panel for the packed kernels: uint64 words,
+// [n_v][ceil(n_f / 32)] with row stride ld, box 4 words (one 128-entry K
+// stage) x 64 SNPs, no swizzle; boxes past the panel read zeros, which the
+// converters mask.
+static bool make_packed_map(CUtensorMap *map, const uint64_t *geno, int64_t n_f, int64_t n_v,
+                            int64_t ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>((n_f + 31) / 32),
+                              static_cast<cuuint64_t>(n_v)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 8u};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK / 32),
+                             static_cast<cuuint32_t>(tcp::pk::SNPS)};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t *>(geno), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class K>
+static int pair_clusters(K kernel, int threads, size_t smem, int num_sms, int *cache) {
+  if (*cache == 0) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return -1;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(static_cast<unsigned>(threads), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) return -1;
+    *cache = n < num_sms / 2 ? n : num_sms / 2;
+  }
+  return *cache;
+}
+
+static TriSched::Params pair_params(const Tally2Args &a) {
+  TriSched::Params sp;
+  sp.nI = static_cast<int>((a.n_v + 127) / 128);
+  sp.nJ = sp.nI;
+  sp.group = a.group > 0 ? a.group : 8;
+  sp.shift = 0;
+  sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / 128);
+  sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.nI);
+  return sp;
+}
+
+int launch_tally2_tc_pair_packed(const Tally2Args &a, const uint64_t *geno, int64_t ld,
+                                 int num_sms, cudaStream_t s) {
+  constexpr int CT = 32 * tcp::pk::CW;
+  CUtensorMap tm;
+  if (!make_packed_map(&tm, geno, a.n_f, a.n_v, ld)) return CCC_ECUDA;
+  const TriSched::Params sp = pair_params(a);
+  const int nkb = static_cast<int>((a.n_f + BK - 1) / BK);
+  const int64_t tiles = tc2_pair_tiles(a.n_v, sp.I0, sp.I1);
+  if (tiles == 0) return CCC_OK;
+  const int ew = epilogue_warps(nkb);
+  static int cache[2] = {0, 0};
+  const int mc = ew == 4 ? pair_clusters(k_tally2_tc_pair_packed<4>, 64 + 32 * 4 + CT,
+                                         packed_smem(4), num_sms, &cache[0])
+                         : pair_clusters(k_tally2_tc_pair_packed<8>, 64 + 32 * 8 + CT,
+                                         packed_smem(8), num_sms, &cache[1]);
+  if (mc < 1) return CCC_ECUDA;
+  const int grid = static_cast<int>(2 * (tiles < mc ? tiles : mc));
+  if (ew == 4)
+    k_tally2_tc_pair_packed<4><<<grid, 64 + 32 * 4 + CT, packed_smem(4), s>>>(tm, a, sp, nkb);
+  else
+    k_tally2_tc_pair_packed<8><<<grid, 64 + 32 * 8 + CT, packed_smem(8), s>>>(tm, a, sp, nkb);
+  return note_launch();
+}
+
+int launch_tally2_tc_pair_split_packed(const Tally2Args &a, const uint64_t *geno, int64_t ld,
+                                       int split, int num_sms, cudaStream_t s) {
+  constexpr int CT = 32 * tcp::pk::CW;
+  const int nkb = static_cast<int>((a.n_f + BK - 1) / BK);
+  if (split < 1 || split > nkb) return CCC_EINVAL;
+  CUtensorMap tm;
+  if (!make_packed_map(&tm, geno, a.n_f, a.n_v, ld)) return CCC_ECUDA;
+  SplitSchedPair::Params sp;
+  sp.tri = pair_params(a);
+  sp.split = split;
+  sp.nkb = nkb;
+  const int64_t units = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1) * split;
+  if (units == 0) return CCC_OK;
+  static int cache = 0;
+  const int mc = pair_clusters(k_tally2_tc_pair_split_packed<4>, 64 + 32 * 4 + CT,
+                               tcp::pk::SMEM_BYTES, num_sms, &cache);
+  if (mc < 1) return CCC_ECUDA;
+  const int64_t clusters = units < mc ? units : mc;
+  k_tally2_tc_pair_split_packed<4><<<static_cast<unsigned>(2 * clusters), 64 + 32 * 4 + CT,
+                                     tcp::pk::SMEM_BYTES, s>>>(tm, a, sp, nkb);
   return note_launch();
 }
 

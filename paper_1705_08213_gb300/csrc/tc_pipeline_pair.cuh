@@ -288,5 +288,352 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
   if (warp == 1) tmem_dealloc_pair(tmem_base, TMEM_COLS);
 }
 
+// ---------------------------------------------------------------- packed operands
+//
+// The same SM-pair GEMM with the operand preparation fused in (the unpack of
+// Sec. 3.1 done in shared memory).  TMA brings the 2-bit genotype codes of the
+// tile's SNPs, 64 SNPs x 128 entries = 2 KB per operand, CTA and K stage, into
+// a ring of packed stages; CW converter warps expand them into the e4m3 count
+// rows rho(0), rho(1) in the 128-byte-swizzled K-major layout a TMA load of
+// those rows would have written, mask entries past n_f and SNPs past n_v,
+// fence the writes for the async proxy and arrive on the leader's conv[]
+// barrier.  No operand matrix exists in HBM; the kernel reads 1/8 of its bytes.
+// The converter warps form TEAMS teams that take the K stages in turn, so that
+// several stages are converted at once.
+//   pfull[p]   (both)    the CTA's packed TMA loads complete on it;
+//   pempty[p]  (both)    the converting team's warps arrive once they have read it
+//                        (one team of WPT warps converts each K stage);
+//   lconv[o]   (both)    the converting team's warps arrive (CTA scope) once
+//                        operand stage o is written and fenced;
+//   rconv[o]   (leader)  the follower's relay thread (its idle MMA warp)
+//                        arrives, at cluster scope, once the follower's lconv[o]
+//                        completed; the MMA waits on lconv[o] and rconv[o];
+//   oempty[o]  (both)    the MMA commit is multicast: operand stage o is free;
+//   tfull, tempty, drain as above.
+namespace pk {
+constexpr int OP_STAGES = 5;
+constexpr int P_STAGES = 8;
+constexpr int CW = 8;                          // converter warps
+constexpr int TEAMS = 4;                       // teams taking the K stages in turn
+constexpr int WPT = CW / TEAMS;                // warps per team
+constexpr int SNPS = BMH / 2;                  // SNPs per CTA and operand
+constexpr int P_SIDE_BYTES = SNPS * (BK / 4);  // 32 bytes of codes per SNP and K stage
+constexpr int P_BYTES = 2 * P_SIDE_BYTES;
+constexpr int NUM_BARS = 2 * P_STAGES + 3 * OP_STAGES + 5;
+constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(OP_STAGES) * STAGE_BYTES +
+                              static_cast<size_t>(P_STAGES) * P_BYTES + NUM_BARS * 8 + 64;
+constexpr size_t smem_bytes(int epi_warps, int stage_bytes) {
+  return SMEM_BYTES + (stage_bytes > 0 ? 16 + static_cast<size_t>(epi_warps) * stage_bytes : 0);
+}
+static_assert(A_BYTES == B_BYTES, "one operand stage size");
+static_assert((2 * SNPS * (BK / 16)) % (WPT * 32) == 0, "converter tasks per stage");
+
+// e4m3 rho(0) and rho(1) indexed by code: 00 -> (2, 0), 01 -> (1, 1),
+// 10 (missing) -> (0, 0), 11 -> (0, 2); 1.0 = 0x38, 2.0 = 0x40.
+constexpr uint32_t kRho0 = 0x00003840u;
+constexpr uint32_t kRho1 = 0x40003800u;
+
+__device__ __forceinline__ bool try_wait_acq_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      "selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// mbar_wait_bounded with cluster-scope acquire (arrivals from the peer CTA
+// release writes to its shared memory that the MMA then reads).
+__device__ __forceinline__ bool wait_bounded_cluster(uint32_t bar, uint32_t parity,
+                                                     int32_t *status, volatile int *abort_flag) {
+  if (try_wait_acq_cluster(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  uint32_t spins = 0;
+  while (true) {
+    if (try_wait_acq_cluster(bar, parity)) return true;
+    if (((++spins) & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (global_timer_ns() - t0 > 2000000000ull) {
+        record_error(status, CCC_ETIMEOUT);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+}  // namespace pk
+
+// tmP: tensor map over the packed panel (uint64 words [n_v][ld], box 4 words x
+// 64 SNPs, no swizzle).  Sched and Epi as for persistent_gemm_pair; the kernel
+// runs 64 + 32 EW + 32 CW threads with pk::smem_bytes(EW, Epi::STAGE_BYTES_PER_WARP).
+template <class Sched, class Epi, int EW>
+__device__ __forceinline__ void persistent_gemm_pair_packed(const CUtensorMap *tmP,
+                                                            const typename Sched::Params &sp,
+                                                            const typename Epi::Params &ep,
+                                                            int nkb, int64_t n_v, int64_t n_f,
+                                                            int32_t *status) {
+  using pk::OP_STAGES;
+  using pk::TEAMS;
+  using pk::WPT;
+  using pk::P_BYTES;
+  using pk::P_SIDE_BYTES;
+  using pk::P_STAGES;
+  using pk::SNPS;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + OP_STAGES * A_BYTES;
+  uint8_t *sP = sB + OP_STAGES * B_BYTES;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sP + P_STAGES * P_BYTES);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + pk::NUM_BARS);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  float *const stage_base = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(tmem_slot) + 64 + 15) & ~static_cast<uintptr_t>(15));
+
+  constexpr int EPI_THREADS = tc::Epilogue<EW>::THREADS;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t bar0 = smem_u32(bars);
+  auto pfull_bar = [&](int p) { return bar0 + 8u * p; };
+  auto pempty_bar = [&](int p) { return bar0 + 8u * (P_STAGES + p); };
+  auto lconv_bar = [&](int o) { return bar0 + 8u * (2 * P_STAGES + o); };
+  auto rconv_bar = [&](int o) { return bar0 + 8u * (2 * P_STAGES + OP_STAGES + o); };
+  auto oempty_bar = [&](int o) { return bar0 + 8u * (2 * P_STAGES + 2 * OP_STAGES + o); };
+  constexpr int TB = 2 * P_STAGES + 3 * OP_STAGES;
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (TB + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (TB + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (TB + 4);
+
+  if (threadIdx.x == 0) {
+    for (int p = 0; p < P_STAGES; ++p) {
+      mbar_init(pfull_bar(p), 1);
+      mbar_init(pempty_bar(p), WPT);
+    }
+    for (int o = 0; o < OP_STAGES; ++o) {
+      mbar_init(lconv_bar(o), WPT);
+      mbar_init(rconv_bar(o), 1);
+      mbar_init(oempty_bar(o), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 2 * EPI_THREADS);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) tma_prefetch_desc(tmP);
+  if (warp == 1) {
+    tmem_alloc_pair(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the peer's barriers are initialised before any remote use
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int64_t cstart = blockIdx.x >> 1;
+  const int64_t cstep = gridDim.x >> 1;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer of packed codes (both CTAs)
+      int n = 0;
+      int last_parity[P_STAGES];
+      for (int p = 0; p < P_STAGES; ++p) last_parity[p] = -1;
+      bool ok = true;
+      Sched sc;
+      for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep)) {
+        const int ya = sc.a_row() / 2 + SNPS * static_cast<int>(rank);
+        const int yb = sc.b_row() / 2 + SNPS * static_cast<int>(rank);
+        const int kbs = sc.k_blocks(nkb);
+        const int kb0 = sc.k_begin();
+        for (int kb = 0; kb < kbs; ++kb, ++n) {
+          const int p = n % P_STAGES;
+          const uint32_t ph = static_cast<uint32_t>(n / P_STAGES) & 1u;
+          if (!mbar_wait_bounded(pempty_bar(p), ph ^ 1u, status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(pfull_bar(p), P_BYTES);
+          const uint32_t dst = smem_u32(sP + p * P_BYTES);
+          tma_load_2d(dst, tmP, (kb0 + kb) * (BK / 32), ya, pfull_bar(p));
+          tma_load_2d(dst + P_SIDE_BYTES, tmP, (kb0 + kb) * (BK / 32), yb, pfull_bar(p));
+          last_parity[p] = static_cast<int>(ph);
+        }
+      }
+      if (!ok) {
+        // Let the copies already issued land before the CTA's memory goes away.
+        for (int p = 0; p < P_STAGES; ++p)
+          if (last_parity[p] >= 0) mbar_wait_timeout(pfull_bar(p), static_cast<uint32_t>(last_parity[p]));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      // ---------------- MMA issuer (leader CTA)
+      int n = 0;
+      int lt = 0;
+      bool ok = true;
+      Sched sc;
+      for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep), ++lt) {
+        const int acc = lt & 1;
+        const uint32_t acc_phase = (lt >> 1) & 1;
+        if (!mbar_wait_bounded(tempty_bar(acc), acc_phase ^ 1u, status, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
+        const int kbs = sc.k_blocks(nkb);
+        for (int kb = 0; kb < kbs; ++kb, ++n) {
+          const int o = n % OP_STAGES;
+          const uint32_t ph = static_cast<uint32_t>(n / OP_STAGES) & 1u;
+          if (!mbar_wait_bounded(lconv_bar(o), ph, status, abort_flag) ||
+              !pk::wait_bounded_cluster(rconv_bar(o), ph, status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + o * A_BYTES);
+          const uint32_t b0 = smem_u32(sB + o * B_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / UK; ++k)
+            mma_f8f6f4_pair(d_tmem, smem_desc_sw128(a0 + k * UK), smem_desc_sw128(b0 + k * UK),
+                            IDESC, (kb | k) != 0 ? 1u : 0u);
+          mma_commit_pair(oempty_bar(o), 0x3);
+        }
+        if (!ok) break;
+        mma_commit_pair(tfull_bar(acc), 0x3);
+      }
+      mma_commit_pair(drain_bar, 0x1);
+      mbar_wait_timeout(drain_bar, 0);
+    } else if (lane == 0) {
+      // ---------------- relay (follower CTA): its operand stages are ready
+      int n = 0;
+      bool ok = true;
+      Sched sc;
+      for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep)) {
+        const int kbs = sc.k_blocks(nkb);
+        for (int kb = 0; kb < kbs; ++kb, ++n) {
+          const int o = n % OP_STAGES;
+          const uint32_t ph = static_cast<uint32_t>(n / OP_STAGES) & 1u;
+          if (!mbar_wait_bounded(lconv_bar(o), ph, status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_cluster(map_to_rank(rconv_bar(o), 0));
+        }
+      }
+    }
+  } else if (warp < 2 + EW) {
+    // ---------------- epilogue (both CTAs)
+    const int quarter = warp & 3;
+    constexpr int NC = tc::Epilogue<EW>::CHUNKS_PER_WARP;
+    const int c0 = ((warp - 2) >> 2) * NC;
+    int lt = 0;
+    Sched sc;
+    for (sc.init(sp, cstart); sc.valid; sc.advance(cstep), ++lt) {
+      const int acc = lt & 1;
+      const uint32_t acc_phase = (lt >> 1) & 1;
+      const bool ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, status, abort_flag);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const uint32_t t_base =
+          tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * ACC_COLS;
+      Epi::template tile<NC>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
+                             map_to_rank(tempty_bar(acc), 0), c0,
+                             stage_base + (warp - 2) * (Epi::STAGE_BYTES_PER_WARP / 4));
+    }
+  } else {
+    // ---------------- converters (both CTAs)
+    // Per K stage, 32 groups of 4 SNPs x 8 chunks of 16 entries: group g is
+    // operand g / 16 (A, B), SNPs 4 (g % 16) .. + 3; warp cw takes groups
+    // cw, cw + CW, ...  Lane = (SNP 4 (g % 16) + lane / 8, chunk lane % 8): a
+    // warp reads 128 contiguous bytes of codes and writes four whole pairs of
+    // 128-byte rows.  Rows 2 s and 2 s + 1 of SNP s have (row & 7) = 2 (lane /
+    // 8) and 2 (lane / 8) + 1, so each lane's swizzled 16-byte offsets are fixed.
+    const int cw = warp - 2 - EW;
+    const int team = cw / WPT;
+    const int member = cw % WPT;
+    const int c = lane & 7;
+    const int rr = lane >> 3;
+    const uint32_t off0 = static_cast<uint32_t>((c ^ (2 * rr)) << 4);
+    const uint32_t off1 = 128u + static_cast<uint32_t>((c ^ (2 * rr + 1)) << 4);
+    constexpr int GROUPS = 2 * SNPS / 4;
+    static_assert(GROUPS % WPT == 0, "whole groups per converter warp");
+    int n = 0;
+    Sched sc;
+    bool ok = true;
+    for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep)) {
+      // SNPs of the CTA's A and B halves that exist (the rest read as missing).
+      const int64_t ra = n_v - (sc.a_row() / 2 + SNPS * static_cast<int64_t>(rank));
+      const int64_t rb = n_v - (sc.b_row() / 2 + SNPS * static_cast<int64_t>(rank));
+      const int va = ra < 0 ? 0 : (ra > SNPS ? SNPS : static_cast<int>(ra));
+      const int vb = rb < 0 ? 0 : (rb > SNPS ? SNPS : static_cast<int>(rb));
+      const int kbs = sc.k_blocks(nkb);
+      const int kb0 = sc.k_begin();
+      for (int kb = 0; kb < kbs; ++kb, ++n) {
+        if (n % TEAMS != team) continue;
+        const int p = n % P_STAGES;
+        const uint32_t pph = static_cast<uint32_t>(n / P_STAGES) & 1u;
+        const int o = n % OP_STAGES;
+        const uint32_t oph = static_cast<uint32_t>(n / OP_STAGES) & 1u;
+        const bool got = mbar_wait_bounded(pfull_bar(p), pph, status, abort_flag) &&
+                         mbar_wait_bounded(oempty_bar(o), oph ^ 1u, status, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        // Entries of this lane's chunk inside the panel (2 bits each).
+        const int64_t left = n_f - (static_cast<int64_t>(kb0 + kb) * BK + 16 * c);
+        const uint32_t mq = left >= 16 ? 0xFFFFFFFFu
+                                       : (left <= 0 ? 0u : (1u << (2 * static_cast<int>(left))) - 1u);
+        const uint8_t *src = sP + p * P_BYTES + rr * 32 + c * 4;
+        uint8_t *dA = sA + o * A_BYTES + rr * 256;
+        uint8_t *dB = sB + o * B_BYTES + rr * 256;
+#pragma unroll
+        for (int it = 0; it < GROUPS / WPT; ++it) {
+          const int g = it * WPT + member;
+          const int side = g / (GROUPS / 2);
+          const int s4 = 4 * (g % (GROUPS / 2));  // first SNP of the group
+          const uint32_t m = s4 + rr < (side ? vb : va) ? mq : 0u;
+          uint32_t x = *reinterpret_cast<const uint32_t *>(src + side * P_SIDE_BYTES + s4 * 32);
+          x = (x & m) | (0xAAAAAAAAu & ~m);  // masked entries read as missing
+          // 2-bit codes -> 4-bit byte selectors: lo for entries 0-7, hi for 8-15.
+          uint32_t lo = x & 0xFFFFu, hi = x >> 16;
+          lo = (lo | (lo << 8)) & 0x00FF00FFu;
+          hi = (hi | (hi << 8)) & 0x00FF00FFu;
+          lo = (lo | (lo << 4)) & 0x0F0F0F0Fu;
+          hi = (hi | (hi << 4)) & 0x0F0F0F0Fu;
+          lo = (lo | (lo << 2)) & 0x33333333u;
+          hi = (hi | (hi << 2)) & 0x33333333u;
+          const uint4 v0 = make_uint4(__byte_perm(pk::kRho0, 0u, lo), __byte_perm(pk::kRho0, 0u, lo >> 16),
+                                      __byte_perm(pk::kRho0, 0u, hi), __byte_perm(pk::kRho0, 0u, hi >> 16));
+          const uint4 v1 = make_uint4(__byte_perm(pk::kRho1, 0u, lo), __byte_perm(pk::kRho1, 0u, lo >> 16),
+                                      __byte_perm(pk::kRho1, 0u, hi), __byte_perm(pk::kRho1, 0u, hi >> 16));
+          uint8_t *d = (side ? dB : dA) + s4 * 256;
+          *reinterpret_cast<uint4 *>(d + off0) = v0;
+          *reinterpret_cast<uint4 *>(d + off1) = v1;
+        }
+        fence_proxy_async_smem();  // the MMA (async proxy) reads what was written
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(pempty_bar(p));
+          mbar_arrive(lconv_bar(o));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // no remote arrive or load is still aimed at either CTA
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc_pair(tmem_base, TMEM_COLS);
+}
+
 }  // namespace tcp
 }  // namespace ccc
