@@ -86,6 +86,8 @@ extern "C" {
 #define CCC_ECUDA (-4)        /* a CUDA call failed */
 #define CCC_ETIMEOUT (-5)     /* a device-side bounded wait gave up (ccc_status) */
 #define CCC_ENOSPACE (-6)     /* workspace smaller than ccc_workspace_size() */
+#define CCC_EBOUNDS (-7)      /* a library built with CCC_BOUNDS_CHECK found an index outside its
+                                 buffer on the device and skipped the access (ccc_status) */
 
 /* Tally paths. */
 #define CCC_PATH_TC 0   /* tcgen05 tensor cores, e4m3 count operands, FP32 accumulate */

@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "CCCError", "load", "lib_path",
     "CCC_OK", "CCC_EINVAL", "CCC_ERANGE", "CCC_EUNSUPPORTED", "CCC_ECUDA", "CCC_ETIMEOUT",
-    "CCC_ENOSPACE", "CCC_PATH_TC", "CCC_PATH_POPC", "CCC_NORM_PERSNP", "CCC_NORM_JOINT",
+    "CCC_ENOSPACE", "CCC_EBOUNDS", "CCC_PATH_TC", "CCC_PATH_POPC", "CCC_NORM_PERSNP", "CCC_NORM_JOINT",
     "CCC_OP_METRIC", "CCC_OP_2WAY", "CCC_OP_3WAY", "CCC_MAX_NF",
     "ccc_panel", "ccc_opts", "ccc_opts_default", "ccc_workspace_size", "ccc_allele_counts",
     "ccc2_tally", "ccc2_metric", "ccc2_tally_metric", "ccc3_tally", "ccc3_metric",
@@ -35,6 +35,7 @@ __all__ = [
     "ccc2_multi_tally_metric", "ccc2_multi_metric", "ccc2_multi_tally_metric_rows",
     "ccc2_multi_phase_bounds", "ccc2_multi_stream_workspace_size", "ccc2_multi_stream",
     "ccc_check_bounded_wait", "ccc_checksum",
+    "ccc_checked_shrink_outputs",
 ]
 
 CCC_OK = 0
@@ -44,6 +45,7 @@ CCC_EUNSUPPORTED = -3
 CCC_ECUDA = -4
 CCC_ETIMEOUT = -5
 CCC_ENOSPACE = -6
+CCC_EBOUNDS = -7  # checked build: an index outside its buffer (include/ccc_checked.h)
 CCC_PATH_TC = 0
 CCC_PATH_POPC = 1
 CCC_NORM_PERSNP = 0
@@ -53,7 +55,9 @@ CCC_OP_2WAY = 2
 CCC_OP_3WAY = 3
 CCC_MAX_NF = 2097151
 
-lib_path = _build.LIB
+# CCC_LIBRARY selects another build of the library (the bounds-checking one,
+# paper_1705_08213_gb300/_build_checked/libccc_checked.so, in tests).
+lib_path = os.environ.get("CCC_LIBRARY") or _build.LIB
 
 
 class CCCError(RuntimeError):
@@ -520,6 +524,16 @@ def ccc2_multi_stream(geno, n_f, s, n_phases, host_tally, host_ccc, opts, stream
     _check("ccc2_multi_stream",
            load().ccc2_multi_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally), _ptr(host_ccc),
                                     ctypes.byref(opts), _stream(stream)))
+
+
+def ccc_checked_shrink_outputs(n):
+    """Checked build only (include/ccc_checked.h): later calls tell their kernels that the
+    output arrays hold n fewer entries, so the last n stores must be caught (CCC_EBOUNDS)."""
+    lib = load()
+    if not hasattr(lib, "ccc_checked_shrink_outputs"):
+        raise CCCError("ccc_checked_shrink_outputs", "not the bounds-checking build of the library")
+    lib.ccc_checked_shrink_outputs.argtypes = [ctypes.c_int64]
+    _check("ccc_checked_shrink_outputs", lib.ccc_checked_shrink_outputs(int(n)))
 
 
 def ccc_check_bounded_wait(status, limit_ns, stream=None):

@@ -19,6 +19,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libccc.so")
+# The checked build (-DCCC_BOUNDS_CHECK): every output index of the tally
+# kernels and the shared-memory stores of the code expansion are tested on the
+# device; a violation records CCC_EBOUNDS and skips the access.  Tests select
+# it with the environment variable CCC_LIBRARY.
+CHECKED_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libccc_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
@@ -39,45 +45,49 @@ def _deps():
         + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def _up_to_date(lib: str) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str) -> tuple[str, str]:
-    obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, out_dir: str, extra: tuple = ()) -> tuple[str, str]:
+    obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{p.stdout}\n{p.stderr}")
     return obj, p.stderr
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every kernel translation unit and link libccc.so; return its path."""
-    if not force and _up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every kernel translation unit and link libccc.so (checked: the
+    bounds-checking libccc_checked.so); return its path."""
+    out_dir, lib = (CHECKED_DIR, CHECKED_LIB) if checked else (OUT_DIR, LIB)
+    extra = ("-DCCC_BOUNDS_CHECK",) if checked else ()
+    if not force and _up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(_compile, srcs))
+        results = list(ex.map(lambda src: _compile(src, out_dir, extra), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for o, log in results:
             print(f"--- {os.path.basename(o)}\n{log}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")
-    os.replace(tmp, LIB)
-    with open(os.path.join(OUT_DIR, "ptxas.log"), "w") as f:
+    os.replace(tmp, lib)
+    with open(os.path.join(out_dir, "ptxas.log"), "w") as f:
         for o, log in results:
             f.write(f"--- {os.path.basename(o)}\n{log}\n")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -6,6 +6,7 @@
 
 #include <atomic>
 
+#include "../../include/ccc_checked.h"
 #include "ccc_launch.h"
 
 namespace ccc {
@@ -13,6 +14,8 @@ namespace ccc {
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+// Checked build: output entries hidden from the kernels' index checks.
+std::atomic<int64_t> g_checked_shrink{0};
 
 constexpr size_t kAlign = 256;
 
@@ -247,6 +250,14 @@ int64_t slab_offset(int64_t j, int64_t n_v) {
   return s1 * (n_v - 1) - s2;
 }
 
+int64_t checked_out_len(int64_t len) {
+#ifdef CCC_BOUNDS_CHECK
+  return len - g_checked_shrink.load(std::memory_order_relaxed);
+#else
+  return len;
+#endif
+}
+
 int64_t rows_count(int64_t n_v, int64_t i_begin, int64_t i_end) {
   return pair_index(i_end, i_end + 1, n_v) - pair_index(i_begin, i_begin + 1, n_v);
 }
@@ -394,6 +405,9 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   a.status = at<int32_t>(o, L.status);
   a.gamma = static_cast<float>(o->gamma);
   a.norm = o->norm;
+  if (filter == nullptr)
+    a.out_len = checked_out_len(i_end >= 0 ? pairs_in_rows(p->n_v, i_begin, i_end)
+                                           : pairs_in_rows(p->n_v, 0, p->n_v));
   int rc;
   if (o->path == CCC_PATH_TC) {
     // tile 3: the tally kernel reads the packed panel and forms the count rows
@@ -495,6 +509,7 @@ static int prep_3way(Run3 &R, bool want_ccc, int64_t j_last) {
   a2.i_begin = 0;
   a2.i_end = je - 1;
   a2.pair0 = 0;
+  a2.out_len = pairs_in_rows(p->n_v, 0, p->n_v);  // the table holds every pair
   return launch_tally2_tc_pair(a2, op, R.L.rows_pad, R.L.kpad, R.dev.sms, s);
 }
 
@@ -608,6 +623,7 @@ static int run_3way(const ccc_panel *p, int64_t j_begin, int64_t j_end, int32_t 
   R.a.j_end = j_end;
   R.a.tally = tally;
   R.a.ccc = out_ccc;
+  R.a.out_len = checked_out_len(slab_offset(j_end, p->n_v) - slab_offset(j_begin, p->n_v));
   return slabs_3way(R);
 }
 
@@ -676,6 +692,7 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
     a.gamma = static_cast<float>(o->gamma);
     a.norm = o->norm;
     a.group = o->group;
+    a.out_len = checked_out_len(pairs_in_rows(p.n_v, 0, p.n_v));
     args[k] = a;
     if (p.n_v < 2) continue;
     if (o->path == CCC_PATH_TC) {
@@ -1051,6 +1068,7 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
     a.i_begin = i0;
     a.i_end = i1;
     a.pair0 = pair_index(i0, i0 + 1, p->n_v);
+    a.out_len = checked_out_len(cnt);
     const int slot = timing_begin(s);
     const int rc = packed ? launch_tally2_tc_pair_packed(a, p->geno, p->ld, dev.sms, s)
                    : o->path == CCC_PATH_TC
@@ -1166,6 +1184,7 @@ int ccc3_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
     R.a.j_end = j1;
     R.a.tally = st;
     R.a.ccc = want_ccc ? sc : nullptr;
+    R.a.out_len = checked_out_len(cnt);
     CCC_TRY(slabs_3way(R));
     if (cudaEventRecord(S->computed[k], s) != cudaSuccess) return CCC_ECUDA;
     if (cudaStreamWaitEvent(S->copy[0], S->computed[k], 0) != cudaSuccess ||
@@ -1359,11 +1378,20 @@ const char *ccc_strerror(int status) {
     case CCC_ECUDA: return "CUDA call failed";
     case CCC_ETIMEOUT: return "device-side wait timed out";
     case CCC_ENOSPACE: return "workspace too small";
+    case CCC_EBOUNDS: return "index out of bounds on the device (checked build)";
     default: return "unknown status";
   }
 }
 
 uint64_t ccc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+#ifdef CCC_BOUNDS_CHECK
+int ccc_checked_shrink_outputs(int64_t n) {
+  if (n < 0) return CCC_EINVAL;
+  g_checked_shrink.store(n, std::memory_order_relaxed);
+  return CCC_OK;
+}
+#endif
 
 int ccc_timing_enable(int enable) {
   g_timing.on = enable != 0;

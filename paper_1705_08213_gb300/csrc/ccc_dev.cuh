@@ -21,6 +21,20 @@ __device__ __forceinline__ void record_error(int32_t *status, int32_t code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Index checks of the checked build (compiled with -DCCC_BOUNDS_CHECK): an
+// index outside [0, n) records CCC_EBOUNDS and the caller skips the access.
+// In the normal build the check is the constant true and costs nothing.
+__device__ __forceinline__ bool in_bounds_check(int64_t idx, int64_t n, int32_t *status) {
+  if (idx >= 0 && idx < n) return true;
+  record_error(status, CCC_EBOUNDS);
+  return false;
+}
+#ifdef CCC_BOUNDS_CHECK
+#define CCC_IN_BOUNDS(idx, n, status) ::ccc::in_bounds_check((idx), (n), (status))
+#else
+#define CCC_IN_BOUNDS(idx, n, status) true
+#endif
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -22,6 +22,20 @@ int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
 int launch_planes(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint64_t *planes,
                   int64_t w64, cudaStream_t s);
 
+// Pairs (i, j), i < j < n_v, with i_begin <= i < i_end: the length of the
+// output of a row range (a phase), the whole triangle for [0, n_v).
+inline int64_t pairs_in_rows(int64_t n_v, int64_t i_begin, int64_t i_end) {
+  if (i_begin < 0) i_begin = 0;
+  if (i_end > n_v) i_end = n_v;
+  if (i_end <= i_begin) return 0;
+  return (i_end - i_begin) * (2 * n_v - i_begin - i_end - 1) / 2;
+}
+
+// The output length a launch passes to its kernels: len, or, in the checked
+// build after ccc_checked_shrink_outputs(n), len - n (so that the last n
+// stores of a call must be caught by the index checks).
+int64_t checked_out_len(int64_t len);
+
 // Shared description of a 2-way tally launch.
 struct Tally2Args {
   int64_t n_v;
@@ -45,6 +59,8 @@ struct Tally2Args {
   int64_t i_begin = 0;
   int64_t i_end = int64_t(1) << 62;
   int64_t pair0 = 0;
+  // Pairs the tally / ccc arrays hold (checked builds test every store index).
+  int64_t out_len = int64_t(1) << 62;
 };
 
 // Panels per batched tensor-core launch (kernel parameter space).
@@ -97,6 +113,8 @@ struct Tally3Args {
   int32_t *status;
   float gamma;
   int32_t norm;
+  // Triples the tally / ccc arrays hold (checked builds test every store index).
+  int64_t out_len = int64_t(1) << 62;
 };
 
 // Masked 3-way operands L_j for the slabs [j0, j1) into lop (rows as tc3_lop_rows).

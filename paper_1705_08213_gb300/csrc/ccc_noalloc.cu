@@ -105,6 +105,7 @@ extern "C" int ccc2_tally_metric_noalloc(const ccc_panel *p, int32_t *tally, flo
   a.status = st;
   a.gamma = static_cast<float>(o->gamma);
   a.norm = o->norm;
+  a.out_len = pairs_in_rows(p->n_v, 0, p->n_v);
   rc = launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s);
   if (rc != CCC_OK) return rc;
   return launch_tally2_tc(a, op, rows_pad, kpad, sms, s);

@@ -271,6 +271,7 @@ int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, floa
   CUtensorMap tm;
   if (!tc::make_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
   MultiArgs a{n_v, w, tally, out_ccc, status, gamma, norm, i_begin, i_end, pair0};
+  a.out_len = checked_out_len(pairs_in_rows(n_v, i_begin, i_end));
   // 256-row blocks holding a SNP (rows_pad has exactly these).
   const int64_t nB = rows_pad / 256;
   const int nkb = static_cast<int>(kpad / tcp::BK);

@@ -28,6 +28,8 @@ struct MultiArgs {
   // Row range of a phase: only pairs with i_begin <= i < i_end, stored at
   // pair_index(i, j) - pair0.
   int64_t i_begin, i_end, pair0;
+  // Pairs the tally / ccc arrays hold (checked builds test every store index).
+  int64_t out_len = int64_t(1) << 62;
 };
 
 // s consecutive values from registers to global memory (streaming stores).
@@ -118,6 +120,7 @@ struct EpiMulti {
           }
         }
         if (!(row_ok && i < j && j < n_v && i >= args.i_begin && i < args.i_end)) continue;
+        if (!CCC_IN_BOUNDS(row_base + j - args.pair0, args.out_len, args.status)) continue;
         const int64_t base = (row_base + j - args.pair0) * (S * S) + a * S;
         store_row<S>(args.tally + base, r);
         if (!want_ccc) continue;
@@ -178,6 +181,7 @@ struct EpiMultiSplit {
       for (int jl = 0; jl < PW; ++jl) {
         const int64_t j = j0 + jl;
         if (!(row_ok && i < j && j < n_v)) continue;
+        if (!CCC_IN_BOUNDS(row_base + j, args.out_len, args.status)) continue;
         int32_t *dst = args.tally + (row_base + j) * (S * S) + a * S;
 #pragma unroll
         for (int b = 0; b < S; ++b) {

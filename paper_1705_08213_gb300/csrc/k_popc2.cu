@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(THREADS)
       const int32_t r01 = 2 * Y - r11;
       const int32_t r00 = 4 * Z - 2 * X - 2 * Y + r11;
       const int64_t pidx = row_base + j;
+      if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
       if (!filter) reinterpret_cast<int4 *>(args.tally)[pidx] = make_int4(r00, r01, r10, r11);
       if (want_ccc) {
         float wj0 = 1.f, wj1 = 1.f;

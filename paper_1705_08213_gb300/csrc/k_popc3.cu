@@ -15,6 +15,7 @@
 // instead of 27.  Block: one slab j (blockIdx.y), a tile of 32 SNPs i < j by
 // 64 SNPs k > j, 256 threads, 2 x 4 triples per thread.
 #include "ccc_launch.h"
+#include "ccc_dev.cuh"
 #include "ccc_metric.cuh"
 
 namespace ccc {
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(THREADS)
         r[abc] = sum;
       }
       const int64_t t = s0 + i * span + (k - j - 1);
+      if (!CCC_IN_BOUNDS(t, args.out_len, args.status)) continue;
       int4 *td = reinterpret_cast<int4 *>(args.tally) + 2 * t;
       td[0] = make_int4(r[0], r[1], r[2], r[3]);
       td[1] = make_int4(r[4], r[5], r[6], r[7]);

@@ -101,6 +101,7 @@ struct Epi2 {
         const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + 2 * p + a;
         if (i < j && j < n_v && i >= args.i_begin && i < args.i_end) {
           const int64_t pidx = row_base + j - args.pair0;
+          if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
           // Streaming stores: the output passes through L2 once and should not
           // evict the operand blocks that other tiles still read.
           if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
@@ -183,6 +184,7 @@ struct Epi2Staged {
         const int32_t r11 = __float2int_rn(r1[1]);
         if (!(i < j && j < n_v && i >= args.i_begin && i < args.i_end)) continue;
         const int64_t pidx = i * (2 * n_v - i - 1) / 2 - i - 1 + j - args.pair0;
+        if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
         if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
         if (!want_ccc) continue;
         float wi0 = 1.f, wi1 = 1.f;
@@ -269,7 +271,8 @@ struct Epi2Split {
       for (int col = 0; col < 32; ++col) {
         const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + (col >> 1);
         const int32_t r = __float2int_rn(__uint_as_float(v[col]));
-        if (row_ok && i < j && j < n_v && r != 0)
+        if (row_ok && i < j && j < n_v && r != 0 &&
+            CCC_IN_BOUNDS(row_base + j, args.out_len, args.status))
           atomicAdd(args.tally + (row_base + j) * 4 + 2 * a + (col & 1), r);
       }
     }

@@ -146,7 +146,7 @@ struct Epi3 {
         const int32_t ra = own + __shfl_xor_sync(0xffffffffu, own, 1);  // sum over b, c (fixed a)
         const int32_t rb = own + __shfl_xor_sync(0xffffffffu, own, 2);  // sum over a, c (fixed b)
         const int64_t k = k0 + c * 16 + kk;
-        if (row_ok && k < n_v) {
+        if (row_ok && k < n_v && CCC_IN_BOUNDS(base + (k - j - 1), args.out_len, args.status)) {
           const int64_t t = base + (k - j - 1);
           __stcs(reinterpret_cast<int2 *>(args.tally) + 4 * t + ab, make_int2(r0, r1));
           if (want_ccc) {

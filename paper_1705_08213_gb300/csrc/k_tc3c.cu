@@ -492,7 +492,8 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const int64_t k = kc + kk;
-          const bool ok = row_ok && k < n_v;
+          const bool ok = row_ok && k < n_v &&
+                          CCC_IN_BOUNDS(pbase + k, n_v * (n_v - 1) / 2, args.t.status);
           r[kk] = ok ? __ldg(reinterpret_cast<const int2 *>(rtab + 4 * (pbase + k)) + a)
                      : make_int2(0, 0);
           wk[kk] = (ok && want_ccc && persnp) ? __ldg(reinterpret_cast<const float2 *>(wv) + k)
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const int64_t k = kc + kk;
-          const bool ok = row_ok && k < n_v;
+          const bool ok = row_ok && k < n_v && CCC_IN_BOUNDS(base + k, args.t.out_len, args.t.status);
           const int32_t t0 = __float2int_rn(__uint_as_float(x[2 * kk]));
           const int32_t t1 = __float2int_rn(__uint_as_float(x[2 * kk + 1]));
           const int32_t d0 = __float2int_rn(__uint_as_float(d[2 * kk]));
@@ -961,7 +962,8 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
 #pragma unroll
           for (int kk = 0; kk < KC; ++kk) {
             const int64_t k = kc + kk;
-            const bool ok = row_ok && k < n_v;
+            const bool ok = row_ok && k < n_v &&
+                            CCC_IN_BOUNDS(pbase + k, n_v * (n_v - 1) / 2, args.t.status);
             r[kk] = ok ? __ldg(reinterpret_cast<const int2 *>(rtab + 4 * (pbase + k)) + a)
                        : make_int2(0, 0);
             wk[kk] = (ok && want_ccc && persnp) ? __ldg(reinterpret_cast<const float2 *>(wv) + k)
@@ -977,7 +979,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
 #pragma unroll
           for (int kk = 0; kk < KC; ++kk) {
             const int64_t k = kc + kk;
-            const bool ok = row_ok && k < n_v;
+            const bool ok = row_ok && k < n_v && CCC_IN_BOUNDS(base + k, args.t.out_len, args.t.status);
             const int32_t t0 = __float2int_rn(__uint_as_float(x[2 * kk]));
             const int32_t t1 = __float2int_rn(__uint_as_float(x[2 * kk + 1]));
             const int32_t d0 = static_cast<int32_t>(dd[kk] & 0xFFFFu);

@@ -615,6 +615,7 @@ __device__ __forceinline__ void persistent_gemm_pair_packed(const CUtensorMap *t
           const uint4 v1 = make_uint4(__byte_perm(pk::kRho1, 0u, lo), __byte_perm(pk::kRho1, 0u, lo >> 16),
                                       __byte_perm(pk::kRho1, 0u, hi), __byte_perm(pk::kRho1, 0u, hi >> 16));
           uint8_t *d = (side ? dB : dA) + s4 * 256;
+          if (!CCC_IN_BOUNDS(rr * 256 + s4 * 256 + off1 + 15, A_BYTES, status)) continue;
           *reinterpret_cast<uint4 *>(d + off0) = v0;
           *reinterpret_cast<uint4 *>(d + off1) = v1;
         }

@@ -264,3 +264,27 @@ def test_bounded_wait_selftest_arguments(lib):
     assert lib.ccc_check_bounded_wait(None, 10000000, None) == ccc.CCC_EINVAL
     for bad in (0, 999999, 2000000001):
         assert lib.ccc_check_bounded_wait(ctypes.c_void_p(256), bad, None) == ccc.CCC_EINVAL
+
+
+def test_checked_build_exports_the_same_entry_points_and_its_hook(lib):
+    """The bounds-checking build (-DCCC_BOUNDS_CHECK, include/ccc_checked.h) exports every
+    entry point of include/ccc.h plus ccc_checked_shrink_outputs; the normal build lacks
+    the hook."""
+    checked = cbuild.build(checked=True)
+
+    def exported(path):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                             check=True).stdout
+        return {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+
+    names = exported(checked)
+    for n in declared_functions():
+        assert n in names, n
+    assert "ccc_checked_shrink_outputs" in names
+    assert "ccc_checked_shrink_outputs" not in exported(ccc.lib_path)
+    hook = ctypes.CDLL(checked).ccc_checked_shrink_outputs
+    hook.argtypes = [ctypes.c_int64]
+    assert hook(-1) == ccc.CCC_EINVAL
+    assert hook(0) == ccc.CCC_OK
+    with pytest.raises(ccc.CCCError):
+        ccc.ccc_checked_shrink_outputs(3)  # this process loaded the normal build
