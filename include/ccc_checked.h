@@ -7,7 +7,8 @@
  * 3-way genotype-class route and the shared-memory stores of the code
  * expansion (ccc_opts.tile = 3).  An index outside its buffer records
  * CCC_EBOUNDS in the status word (ccc_status) and the access is skipped.  The
- * normal build neither checks nor exports this header's symbol.
+ * normal build has no checks; there this header's call returns
+ * CCC_EUNSUPPORTED.
  */
 #ifndef CCC_CHECKED_H
 #define CCC_CHECKED_H
@@ -22,7 +23,8 @@ extern "C" {
  * hold n fewer entries (pairs or triples) than they do, so the stores of the
  * last n entries must be caught: the call records CCC_EBOUNDS and leaves
  * those entries untouched, while every real access stays inside the arrays.
- * n = 0 restores the true lengths.  Returns CCC_OK, or CCC_EINVAL for n < 0.
+ * n = 0 restores the true lengths.  Returns CCC_OK, CCC_EINVAL for n < 0, or
+ * CCC_EUNSUPPORTED from the normal build.
  * Host state of the process, not thread-safe against concurrent calls. */
 int ccc_checked_shrink_outputs(int64_t n);
 

@@ -530,8 +530,6 @@ def ccc_checked_shrink_outputs(n):
     """Checked build only (include/ccc_checked.h): later calls tell their kernels that the
     output arrays hold n fewer entries, so the last n stores must be caught (CCC_EBOUNDS)."""
     lib = load()
-    if not hasattr(lib, "ccc_checked_shrink_outputs"):
-        raise CCCError("ccc_checked_shrink_outputs", "not the bounds-checking build of the library")
     lib.ccc_checked_shrink_outputs.argtypes = [ctypes.c_int64]
     _check("ccc_checked_shrink_outputs", lib.ccc_checked_shrink_outputs(int(n)))
 

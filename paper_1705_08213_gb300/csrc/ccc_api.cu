@@ -1385,13 +1385,16 @@ const char *ccc_strerror(int status) {
 
 uint64_t ccc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
-#ifdef CCC_BOUNDS_CHECK
 int ccc_checked_shrink_outputs(int64_t n) {
+#ifdef CCC_BOUNDS_CHECK
   if (n < 0) return CCC_EINVAL;
   g_checked_shrink.store(n, std::memory_order_relaxed);
   return CCC_OK;
-}
+#else
+  (void)n;
+  return CCC_EUNSUPPORTED;  // the normal build has no index checks
 #endif
+}
 
 int ccc_timing_enable(int enable) {
   g_timing.on = enable != 0;

@@ -16,6 +16,8 @@ from paper_1705_08213_gb300 import build as cbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ccc.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -24,8 +26,8 @@ def lib():
     return ccc.load()
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(headers=(HEADER,)):
+    text = "".join(open(h).read() for h in headers)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
                        text, flags=re.M)
@@ -44,14 +46,14 @@ def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", ccc.lib_path], capture_output=True,
                          text=True, check=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
-    missing = [n for n in declared_functions() if n not in exported]
+    missing = [n for n in declared_functions(HEADERS) if n not in exported]
     assert not missing, missing
     for n in declared_functions():
         assert hasattr(lib, n)
 
 
 def test_python_binding_names_match_header():
-    for n in declared_functions():
+    for n in declared_functions(HEADERS):
         assert hasattr(ccc, n), n
 
 
@@ -268,8 +270,8 @@ def test_bounded_wait_selftest_arguments(lib):
 
 def test_checked_build_exports_the_same_entry_points_and_its_hook(lib):
     """The bounds-checking build (-DCCC_BOUNDS_CHECK, include/ccc_checked.h) exports every
-    entry point of include/ccc.h plus ccc_checked_shrink_outputs; the normal build lacks
-    the hook."""
+    entry point of include/*.h; its hook works there and returns CCC_EUNSUPPORTED from the
+    normal build."""
     checked = cbuild.build(checked=True)
 
     def exported(path):
@@ -280,11 +282,12 @@ def test_checked_build_exports_the_same_entry_points_and_its_hook(lib):
     names = exported(checked)
     for n in declared_functions():
         assert n in names, n
-    assert "ccc_checked_shrink_outputs" in names
-    assert "ccc_checked_shrink_outputs" not in exported(ccc.lib_path)
+    for n in declared_functions(HEADERS):
+        assert n in names, n
     hook = ctypes.CDLL(checked).ccc_checked_shrink_outputs
     hook.argtypes = [ctypes.c_int64]
     assert hook(-1) == ccc.CCC_EINVAL
     assert hook(0) == ccc.CCC_OK
-    with pytest.raises(ccc.CCCError):
+    with pytest.raises(ccc.CCCError) as e:
         ccc.ccc_checked_shrink_outputs(3)  # this process loaded the normal build
+    assert e.value.status == ccc.CCC_EUNSUPPORTED
