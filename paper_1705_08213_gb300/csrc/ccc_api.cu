@@ -6,6 +6,8 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ccc_checked.h"
 #include "ccc_launch.h"
 
@@ -14,6 +16,16 @@ namespace ccc {
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+
+// An NVTX range named after the C-ABI call for its lifetime, so that a
+// timeline (Nsight Systems, ncu --nvtx) shows each call around its kernels.
+// Without a tool attached NVTX calls return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // Checked build: output entries hidden from the kernels' index checks.
 std::atomic<int64_t> g_checked_shrink{0};
 
@@ -911,6 +923,7 @@ int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, siz
 }
 
 int ccc_allele_counts(const ccc_panel *panel, int32_t *counts, void *stream) {
+  const NvtxRange nvtx_range("ccc_allele_counts");
   CCC_TRY(check_panel(panel));
   if (counts == nullptr || !aligned(counts, 4)) return CCC_EINVAL;
   DeviceInfo dev;
@@ -920,17 +933,20 @@ int ccc_allele_counts(const ccc_panel *panel, int32_t *counts, void *stream) {
 }
 
 int ccc2_tally(const ccc_panel *panel, int32_t *tally, const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_tally");
   return run_2way(panel, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc2_tally_metric(const ccc_panel *panel, int32_t *tally, float *out_ccc, const ccc_opts *opts,
                       void *stream) {
+  const NvtxRange nvtx_range("ccc2_tally_metric");
   if (out_ccc == nullptr) return CCC_EINVAL;
   return run_2way(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc2_tally_metric_rows(const ccc_panel *panel, int64_t i_begin, int64_t i_end,
                            int32_t *tally, float *out_ccc, const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_tally_metric_rows");
   if (panel == nullptr || i_begin < 0 || i_end < i_begin || i_end > panel->n_v) return CCC_EINVAL;
   if (out_ccc == nullptr) return CCC_EINVAL;
   if (i_begin == i_end || rows_count(panel->n_v, i_begin, i_end) == 0) {
@@ -1006,6 +1022,7 @@ int ccc2_stream_workspace_size(const ccc_panel *panel, int n_phases, const ccc_o
 
 int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *host_ccc,
                 const ccc_opts *o, void *stream) {
+  const NvtxRange nvtx_range("ccc2_stream");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CCC_TRY(check_panel(p));
   CCC_TRY(check_opts2(o));
@@ -1147,6 +1164,7 @@ int ccc3_stream_workspace_size(const ccc_panel *panel, int n_phases, const ccc_o
 
 int ccc3_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *host_ccc,
                 const ccc_opts *o, void *stream) {
+  const NvtxRange nvtx_range("ccc3_stream");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p == nullptr || host_tally == nullptr || n_phases < 2 || n_phases > 1024) return CCC_EINVAL;
   size_t need = 0;
@@ -1226,11 +1244,13 @@ int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc
 
 int ccc2_batched(const ccc_panel *panels, int n_panels, int32_t *const *tally, float *const *ccc,
                  const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_batched");
   return run_batched(panels, n_panels, tally, ccc, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tally, float *const *ccc,
                       ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_batched_tune");
   if (opts == nullptr) return CCC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int groups[3] = {4, 8, 16};
@@ -1271,12 +1291,14 @@ int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tal
 
 int ccc2_filter(const ccc_panel *panel, float threshold, ccc_hit *hits, int64_t cap,
                 int64_t *n_hits, const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_filter");
   FilterSpec f{hits, cap, n_hits, threshold};
   return run_2way(panel, nullptr, nullptr, opts, static_cast<cudaStream_t>(stream), &f);
 }
 
 int ccc2_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, const ccc_opts *opts,
                 float *out_ccc, void *stream) {
+  const NvtxRange nvtx_range("ccc2_metric");
   CCC_TRY(check_opts(opts));
   if (n_v < 1 || n_v > kMaxNV) return CCC_EINVAL;
   if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
@@ -1295,17 +1317,20 @@ int ccc2_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, const 
 
 int ccc3_tally(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
                const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc3_tally");
   return run_3way(panel, j_begin, j_end, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc3_tally_metric(const ccc_panel *panel, int64_t j_begin, int64_t j_end, int32_t *tally,
                       float *out_ccc, const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc3_tally_metric");
   if (out_ccc == nullptr) return CCC_EINVAL;
   return run_3way(panel, j_begin, j_end, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_t j_begin,
                 int64_t j_end, const ccc_opts *opts, float *out_ccc, void *stream) {
+  const NvtxRange nvtx_range("ccc3_metric");
   CCC_TRY(check_opts(opts));
   if (n_v < 1 || n_v > kMaxNV || j_begin < 0 || j_end < j_begin || j_end > n_v) return CCC_EINVAL;
   if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
@@ -1324,6 +1349,7 @@ int ccc3_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int64_
 }
 
 int ccc_checksum(const void *words, int64_t count, int64_t base, uint64_t *out, void *stream) {
+  const NvtxRange nvtx_range("ccc_checksum");
   if (out == nullptr || !aligned(out, 16) || count < 0 || base < 0) return CCC_EINVAL;
   if (count > 0 && (words == nullptr || !aligned(words, 4))) return CCC_EINVAL;
   DeviceInfo dev;
@@ -1428,6 +1454,7 @@ int ccc_multi_workspace_size(const ccc_panel_multi *panel, const ccc_opts *opts,
 }
 
 int ccc_multi_counts(const ccc_panel_multi *panel, int32_t *counts, void *stream) {
+  const NvtxRange nvtx_range("ccc_multi_counts");
   CCC_TRY(check_panel_multi(panel));
   if (counts == nullptr || !aligned(counts, 4)) return CCC_EINVAL;
   DeviceInfo dev;
@@ -1438,17 +1465,20 @@ int ccc_multi_counts(const ccc_panel_multi *panel, int32_t *counts, void *stream
 
 int ccc2_multi_tally(const ccc_panel_multi *panel, int32_t *tally, const ccc_opts *opts,
                      void *stream) {
+  const NvtxRange nvtx_range("ccc2_multi_tally");
   return run_multi(panel, tally, nullptr, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc2_multi_tally_metric(const ccc_panel_multi *panel, int32_t *tally, float *out_ccc,
                             const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_multi_tally_metric");
   if (out_ccc == nullptr) return CCC_EINVAL;
   return run_multi(panel, tally, out_ccc, opts, static_cast<cudaStream_t>(stream));
 }
 
 int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, int32_t n_states,
                       const ccc_opts *opts, float *out_ccc, void *stream) {
+  const NvtxRange nvtx_range("ccc2_multi_metric");
   CCC_TRY(check_opts_multi(opts));
   if (n_v < 1 || n_v > kMaxNV || n_states < 2 || n_states > 15) return CCC_EINVAL;
   if (tally == nullptr || counts == nullptr || out_ccc == nullptr) return CCC_EINVAL;
@@ -1468,6 +1498,7 @@ int ccc2_multi_metric(const int32_t *tally, const int32_t *counts, int64_t n_v, 
 
 int ccc2_multi_tally_metric_rows(const ccc_panel_multi *panel, int64_t i_begin, int64_t i_end,
                                  int32_t *tally, float *out_ccc, const ccc_opts *opts, void *stream) {
+  const NvtxRange nvtx_range("ccc2_multi_tally_metric_rows");
   if (panel == nullptr || i_begin < 0 || i_end < i_begin || i_end > panel->n_v) return CCC_EINVAL;
   if (out_ccc == nullptr) return CCC_EINVAL;
   if (i_begin == i_end || rows_count(panel->n_v, i_begin, i_end) == 0) {
@@ -1499,6 +1530,7 @@ int ccc2_multi_stream_workspace_size(const ccc_panel_multi *panel, int n_phases,
 
 int ccc2_multi_stream(const ccc_panel_multi *p, int n_phases, int32_t *host_tally, float *host_ccc,
                       const ccc_opts *o, void *stream) {
+  const NvtxRange nvtx_range("ccc2_multi_stream");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CCC_TRY(check_panel_multi(p));
   CCC_TRY(check_opts_multi(o));
