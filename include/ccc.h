@@ -294,9 +294,21 @@ int ccc2_batched(const ccc_panel *panels, int n_panels, int32_t *const *tally,
  * (group 4, 8, 16 x order 0, 1), timing each with CUDA events on the stream
  * (synchronising it), and stores the fastest group and order in *opts.  The
  * outputs hold a correct result afterwards.
+ * The choice is cached under the batch's shape: the multiset of its panels'
+ * (n_v, n_f) power-of-two buckets (bucket(x) = bit length of x - 1), with
+ * opts->path, opts->tile and the device's SM count.  A later call whose batch
+ * has the same key takes the cached choice and runs the batch once, without
+ * the timing runs.  The cache lives in the process; when the environment
+ * variable CCC_TUNE_CACHE names a file, choices are also appended to it (one
+ * text line each) and read back by later processes.  CCC_EINVAL for a null
+ * opts or panels or n_panels outside 1 .. 1024.
  */
 int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tally,
                       float *const *ccc, ccc_opts *opts, void *stream);
+
+/* Forget the tuning choices the process holds (the CCC_TUNE_CACHE file is left
+ * alone and read again by the next ccc2_batched_tune).  Returns CCC_OK. */
+int ccc_tune_cache_clear(void);
 
 /*
  * 3-way tallies of all triples i < j < k with j in [j_begin, j_end) (Eq. 5

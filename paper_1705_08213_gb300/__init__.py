@@ -36,6 +36,7 @@ __all__ = [
     "ccc2_multi_phase_bounds", "ccc2_multi_stream_workspace_size", "ccc2_multi_stream",
     "ccc_check_bounded_wait", "ccc_checksum",
     "ccc_checked_shrink_outputs",
+    "ccc_tune_cache_clear",
 ]
 
 CCC_OK = 0
@@ -524,6 +525,11 @@ def ccc2_multi_stream(geno, n_f, s, n_phases, host_tally, host_ccc, opts, stream
     _check("ccc2_multi_stream",
            load().ccc2_multi_stream(ctypes.byref(p), int(n_phases), _ptr(host_tally), _ptr(host_ccc),
                                     ctypes.byref(opts), _stream(stream)))
+
+
+def ccc_tune_cache_clear():
+    """Forget the batched-schedule choices this process cached (see ccc2_batched_tune)."""
+    _check("ccc_tune_cache_clear", load().ccc_tune_cache_clear())
 
 
 def ccc_checked_shrink_outputs(n):

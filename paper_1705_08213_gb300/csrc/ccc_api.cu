@@ -10,6 +10,7 @@
 
 #include "../../include/ccc_checked.h"
 #include "ccc_launch.h"
+#include "tune_cache.h"
 
 namespace ccc {
 
@@ -1251,8 +1252,20 @@ int ccc2_batched(const ccc_panel *panels, int n_panels, int32_t *const *tally, f
 int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tally, float *const *ccc,
                       ccc_opts *opts, void *stream) {
   const NvtxRange nvtx_range("ccc2_batched_tune");
-  if (opts == nullptr) return CCC_EINVAL;
+  if (opts == nullptr || panels == nullptr || n_panels < 1 || n_panels > kMaxPanelsPerCall)
+    return CCC_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  // A batch whose panel sizes fall in already-tuned buckets takes the cached
+  // schedule without the timing runs.
+  const uint64_t key = tune_key(panels, n_panels, opts->path, opts->tile, dev.sms);
+  TuneChoice cached;
+  if (tune_lookup(key, &cached)) {
+    opts->group = cached.group;
+    opts->order = cached.order;
+    return run_batched(panels, n_panels, tally, ccc, opts, s);
+  }
   const int groups[3] = {4, 8, 16};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return CCC_ECUDA;
@@ -1285,6 +1298,7 @@ int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tal
   if (rc != CCC_OK) return rc;
   opts->group = best_g;
   opts->order = best_o;
+  tune_store(key, TuneChoice{best_g, best_o}, best);
   // Leave the outputs as the chosen schedule writes them (all schedules agree).
   return run_batched(panels, n_panels, tally, ccc, opts, s);
 }
@@ -1420,6 +1434,11 @@ int ccc_checked_shrink_outputs(int64_t n) {
   (void)n;
   return CCC_EUNSUPPORTED;  // the normal build has no index checks
 #endif
+}
+
+int ccc_tune_cache_clear(void) {
+  tune_clear();
+  return CCC_OK;
 }
 
 int ccc_timing_enable(int enable) {

@@ -166,3 +166,46 @@ def test_batched_full_size_workload():
         it = torch.from_numpy(idx).cuda()
         assert_tally_equal(tallies[k][it].cpu().numpy(), et, f"panel {k}")
         assert_ccc_close(cccs[k][it].cpu().numpy(), ec, what=f"panel {k}")
+
+
+def _tune_launches(genos_np, shapes):
+    """Launches of one ccc2_batched_tune call, its choice and its results."""
+    import paper_1705_08213_gb300 as ccc
+    n0 = ccc.ccc_launch_count()
+    t, c = _run_batched(genos_np, shapes, tune=True)
+    return ccc.ccc_launch_count() - n0, t, c
+
+
+def test_tune_cache_by_shape_buckets_and_file(tmp_path, monkeypatch):
+    """ccc2_batched_tune times six schedules and runs the chosen one: seven identical runs
+    of the batch.  A batch whose panel sizes fall in the same (n_v, n_f) power-of-two
+    buckets then takes the cached choice and runs once; with CCC_TUNE_CACHE set the choice
+    goes to a file that a cleared cache reads back.  Results stay those of the plain
+    call."""
+    import paper_1705_08213_gb300 as ccc
+    shapes = [(300, 1000), (700, 2100), (1500, 600)]
+    same_buckets = [(400, 1020), (600, 2050), (1100, 700)]
+    genos = _batch(shapes, seed=31)
+    genos_b = _batch(same_buckets, seed=32)
+    ref_t, ref_c = _run_batched(genos, shapes)
+    ccc.ccc_tune_cache_clear()
+    first, t, c = _tune_launches(genos, shapes)
+    for a, b in zip(t + c, ref_t + ref_c):
+        np.testing.assert_array_equal(a, b)
+    hit, _, _ = _tune_launches(genos, shapes)
+    assert first == 7 * hit and hit > 0, (first, hit)
+    hit_b, t_b, _ = _tune_launches(genos_b, same_buckets)
+    assert hit_b < first / 2, (first, hit_b)
+    et, _ = oracle.ccc2_all(genos_b[0], same_buckets[0][1])
+    assert_tally_equal(t_b[0], et, "cached schedule")
+    # the same through a file
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("CCC_TUNE_CACHE", str(path))
+    ccc.ccc_tune_cache_clear()
+    assert _tune_launches(genos, shapes)[0] == first
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("ccc-tune-v1 ")
+    ccc.ccc_tune_cache_clear()  # forget the process's copy: the file answers
+    assert _tune_launches(genos, shapes)[0] == hit
+    monkeypatch.delenv("CCC_TUNE_CACHE")
+    ccc.ccc_tune_cache_clear()
