@@ -184,3 +184,18 @@ def test_packed_at_the_length_limit():
     et, ec = oracle.ccc2_all(geno, n_f)
     assert_tally_equal(t, et, "packed n_f limit")
     assert_ccc_close(c, ec, what="packed n_f limit")
+
+
+def test_packed_degenerate_snps():
+    """An all-missing SNP, identical SNPs and a half-missing SNP (codes built on the host)."""
+    n_v, n_f = 70, 300
+    codes = synth.unpack(synth.panel_hwe(n_v, n_f, seed=97, p_missing=0.02), n_f)
+    codes[5] = 2          # all missing
+    codes[7] = codes[8]   # identical
+    codes[11, :100] = 2   # first 100 entries missing
+    geno = synth.pack(codes, pad_seed=9)
+    for norm in (0, 1):
+        t, c = run_2way(geno, n_f, 0, norm=norm, tile=PACKED)
+        et, ec = oracle.ccc2_all(geno, n_f, norm=norm)
+        assert_tally_equal(t, et, "packed degenerate SNPs")
+        assert_ccc_close(c, ec, what="packed degenerate SNPs")
