@@ -129,13 +129,16 @@ typedef struct ccc_opts {
                              over all individuals and a product over those with v_j missing
                              (half the tensor work of 1 and 2); automatic = 3.  0 = automatic.
                              The workspace size depends on it. */
-  int32_t split;          /* 2-way tensor-core calls over the whole triangle (biallelic and s-state,
-                             outputs in device memory): K (individuals) split into this many parts
-                             whose partial tallies are summed (the n_pf axis of Sec. 4 on one GPU),
-                             for panels with few SNP tiles and long vectors.  0 = automatic (when
-                             the triangle has at most half as many tiles as SM pairs and
-                             n_f >= 4,096), 1 = off, n >= 2 = n parts (at most n_f / 128).  Same
-                             results; the CCC values then come from the summed tallies. */
+  int32_t split;          /* 2-way calls over the whole triangle (tensor cores, biallelic and
+                             s-state, and the biallelic popcount path; outputs in device memory):
+                             K (individuals) split into this many parts whose partial tallies
+                             are summed (the n_pf axis of Sec. 4 on one GPU), for panels with few
+                             SNP tiles and long vectors.  0 = automatic (tensor cores: when the
+                             triangle has at most half as many tiles as SM pairs and n_f >= 4,096;
+                             popcount: fewer 64-SNP tiles than two per SM, at least 4,096
+                             individuals per part), 1 = off, n >= 2 = n parts (at most n_f / 128
+                             on the tensor cores, n_f / 512 on the popcount path).  Same results;
+                             the CCC values then come from the summed tallies. */
 } ccc_opts;
 
 /* Operations, for ccc_workspace_size(). */

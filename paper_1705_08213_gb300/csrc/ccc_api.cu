@@ -375,6 +375,20 @@ static int k_split_tiles(int requested, int64_t tiles, int64_t kpad, int sms) {
   return best > 1 ? static_cast<int>(best) : 1;
 }
 
+// K parts of a 2-way popcount call: opts->split when set (at most the 8-word
+// stages), else automatic: a triangle of fewer 64-SNP tiles than two per SM is
+// split so that about two blocks per SM run, each part keeping at least 64
+// words (4,096 individuals).
+static int popc_split(int requested, int64_t n_v, int64_t w64, int sms) {
+  const int64_t stages = (w64 + 7) / 8;
+  if (requested >= 1) return static_cast<int>(requested < stages ? requested : stages);
+  const int64_t tiles = popc2_tiles(n_v);
+  if (tiles < 1 || tiles >= 2 * static_cast<int64_t>(sms)) return 1;
+  int64_t split = (2 * static_cast<int64_t>(sms) + tiles - 1) / tiles;
+  if (split > stages / 8) split = stages / 8;
+  return split > 1 ? static_cast<int>(split) : 1;
+}
+
 static int k_split(int requested, int64_t n_v, int64_t kpad, int sms) {
   return k_split_tiles(requested, tc2_pair_tiles(n_v, 0, (n_v + 127) / 128), kpad, sms);
 }
@@ -470,10 +484,18 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   }
   uint64_t *planes = at<uint64_t>(o, L.planes);
   CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
+  const int psplit = (filter == nullptr && i_end < 0 && on_device(tally))
+                         ? popc_split(o->split, p->n_v, L.w64, dev.sms)
+                         : 1;
+  if (psplit > 1) {
+    const size_t bytes = 16 * static_cast<size_t>(p->n_v) * static_cast<size_t>(p->n_v - 1) / 2;
+    if (cudaMemsetAsync(tally, 0, bytes, s) != cudaSuccess) return CCC_ECUDA;
+  }
   const int slot = timing_begin(s);
-  rc = launch_tally2_popc(a, planes, L.w64, s);
+  rc = launch_tally2_popc(a, planes, L.w64, s, psplit);
   timing_end(slot, s);
-  return rc;
+  if (rc != CCC_OK || psplit == 1 || out_ccc == nullptr) return rc;
+  return launch_metric2(tally, w, p->n_v, a.gamma, a.norm, out_ccc, s);
 }
 
 // A 3-way call after its checks: panel, options, stream, workspace layout and

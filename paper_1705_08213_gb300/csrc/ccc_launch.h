@@ -97,7 +97,12 @@ int launch_tally2_tc_pair_split_packed(const Tally2Args &a, const uint64_t *geno
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      int num_sms, cudaStream_t s);
 // Popcount 2-way tallies over planes[n_v][w64][4].
-int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
+// split > 1: the 64-entry words in that many parts whose partial tallies are
+// added into a.tally, which must be zero (no CCC values, no thresholded output).
+int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s,
+                       int split = 1);
+// 64 x 64-SNP tiles of the popcount kernel over the whole triangle.
+int64_t popc2_tiles(int64_t n_v);
 // CCC values from stored tallies.
 int launch_metric2(const int32_t *tally, const float *w, int64_t n_v, float gamma, int32_t norm,
                    float *ccc, cudaStream_t s);

@@ -16,7 +16,10 @@
 //
 // Block tile: 64 x 64 SNPs of the upper triangle (J >= I), 256 threads, each
 // thread 4 x 4 pairs; the planes of both tiles are staged in shared memory 8
-// words (512 entries) at a time.
+// words (512 entries) at a time.  A K split (gridDim.y parts) gives each block
+// a range of words; since the four tallies are linear in the four sums, the
+// parts add their partial tallies into the zeroed output with integer
+// reductions, and the CCC values follow from the summed tallies (k_metric2).
 #include "ccc_dev.cuh"
 #include "ccc_launch.h"
 #include "ccc_metric.cuh"
@@ -43,7 +46,7 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t nB, int64_t &I, i
 }
 
 __device__ __forceinline__ void load_stage(const uint64_t *__restrict__ planes, int64_t w64,
-                                           int64_t n_v, int64_t snp0, int64_t k0,
+                                           int64_t kend, int64_t n_v, int64_t snp0, int64_t k0,
                                            uint64_t (*s)[KC][LDS]) {
   // 64 SNPs x KC words x 2 halves of 16 bytes.
   for (int l = threadIdx.x; l < TS * KC * 2; l += THREADS) {
@@ -53,7 +56,7 @@ __device__ __forceinline__ void load_stage(const uint64_t *__restrict__ planes, 
     const int64_t i = snp0 + snp;
     const int64_t k = k0 + word;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (i < n_v && k < w64) v = __ldg(reinterpret_cast<const uint4 *>(planes + (i * w64 + k) * 4) + half);
+    if (i < n_v && k < kend) v = __ldg(reinterpret_cast<const uint4 *>(planes + (i * w64 + k) * 4) + half);
     const uint64_t lo = (static_cast<uint64_t>(v.y) << 32) | v.x;
     const uint64_t hi = (static_cast<uint64_t>(v.w) << 32) | v.z;
     if (half == 0) {
@@ -67,7 +70,7 @@ __device__ __forceinline__ void load_stage(const uint64_t *__restrict__ planes, 
 
 __global__ void __launch_bounds__(THREADS)
     k_tally2_popc(const uint64_t *__restrict__ planes, int64_t w64, const Tally2Args args,
-                  int64_t nB, int64_t t0) {
+                  int64_t nB, int64_t t0, int64_t part_words) {
   __shared__ uint64_t sI[3][KC][LDS];
   __shared__ uint64_t sJ[3][KC][LDS];
   int64_t I, J;
@@ -83,9 +86,11 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[x][y][c] = 0u;
 
-  for (int64_t k0 = 0; k0 < w64; k0 += KC) {
-    load_stage(planes, w64, n_v, I * TS, k0, sI);
-    load_stage(planes, w64, n_v, J * TS, k0, sJ);
+  const int64_t kbeg = static_cast<int64_t>(blockIdx.y) * part_words;
+  const int64_t kend = kbeg + part_words < w64 ? kbeg + part_words : w64;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += KC) {
+    load_stage(planes, w64, kend, n_v, I * TS, k0, sI);
+    load_stage(planes, w64, kend, n_v, J * TS, k0, sJ);
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < KC; ++k) {
@@ -123,7 +128,8 @@ __global__ void __launch_bounds__(THREADS)
     const int64_t i = I * TS + ty + 16 * x;
     if (i >= n_v || i < args.i_begin || i >= args.i_end) continue;
     const bool filter = args.hits != nullptr;
-    const bool want_ccc = filter || args.ccc != nullptr;
+    const bool partial = gridDim.y > 1;  // K split: partial tallies, no CCC here
+    const bool want_ccc = !partial && (filter || args.ccc != nullptr);
     float wi0 = 1.f, wi1 = 1.f;
     if (want_ccc && args.norm == CCC_NORM_PERSNP) {
       wi0 = __ldg(args.w + 2 * i);
@@ -143,6 +149,14 @@ __global__ void __launch_bounds__(THREADS)
       const int32_t r00 = 4 * Z - 2 * X - 2 * Y + r11;
       const int64_t pidx = row_base + j;
       if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
+      if (partial) {
+        int32_t *t = args.tally + 4 * pidx;
+        if (r00 != 0) atomicAdd(t + 0, r00);
+        if (r01 != 0) atomicAdd(t + 1, r01);
+        if (r10 != 0) atomicAdd(t + 2, r10);
+        if (r11 != 0) atomicAdd(t + 3, r11);
+        continue;
+      }
       if (!filter) reinterpret_cast<int4 *>(args.tally)[pidx] = make_int4(r00, r01, r10, r11);
       if (want_ccc) {
         float wj0 = 1.f, wj1 = 1.f;
@@ -189,7 +203,13 @@ __global__ void k_metric2(const int32_t *__restrict__ tally, const float *__rest
 
 }  // namespace
 
-int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s) {
+int64_t popc2_tiles(int64_t n_v) {
+  const int64_t nB = (n_v + TS - 1) / TS;
+  return nB * (nB + 1) / 2;
+}
+
+int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s,
+                       int split) {
   const int64_t nB = (a.n_v + TS - 1) / TS;
   // Row blocks [B0, B1) of the phase; tiles before row B are B nB - B (B - 1) / 2.
   const int64_t B0 = (a.i_begin > 0 ? a.i_begin : 0) / TS;
@@ -199,7 +219,15 @@ int launch_tally2_popc(const Tally2Args &a, const uint64_t *planes, int64_t w64,
   const int64_t tiles = start(B1) - t0;
   if (tiles <= 0) return CCC_OK;
   if (tiles > 0x7fffffffLL) return CCC_ERANGE;
-  k_tally2_popc<<<static_cast<unsigned>(tiles), THREADS, 0, s>>>(planes, w64, a, nB, t0);
+  // Parts of whole KC-word stages; split > 1 only with a.tally zeroed, no
+  // thresholded output and the CCC values formed afterwards.
+  const int64_t stages = (w64 + KC - 1) / KC;
+  if (split < 1 || split > 65535 || (split > 1 && a.hits != nullptr)) return CCC_EINVAL;
+  if (split > stages) split = static_cast<int>(stages);
+  const int64_t part_words = (stages + split - 1) / split * KC;
+  const int parts = static_cast<int>((w64 + part_words - 1) / part_words);
+  const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(parts > 0 ? parts : 1), 1);
+  k_tally2_popc<<<grid, THREADS, 0, s>>>(planes, w64, a, nB, t0, parts > 1 ? part_words : w64);
   return note_launch();
 }
 

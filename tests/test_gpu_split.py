@@ -5,7 +5,8 @@ device (the n_pf axis of Sec. 4 on one GPU); CCC values then come from the
 summed tallies.  Results must equal the unsplit call bit for bit and the
 oracle exactly (tallies) / within 1e-6 (CCC), for forced and automatic splits,
 both normalisations, tally-only calls, and outputs in pinned host memory
-(which the split does not use).
+(which the split does not use); on the tensor cores (biallelic and s-state) and
+on the popcount path.
 """
 
 import numpy as np
@@ -146,3 +147,53 @@ def test_multi_split_equals_unsplit_and_oracle(s):
     for split in (0, 6):
         np.testing.assert_array_equal(res[split][0], res[1][0])
         np.testing.assert_array_equal(res[split][1], res[1][1])
+
+
+
+def _run_path(geno, n_f, split, path, norm=0):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    g = to_device(geno)
+    n_v = geno.shape[0]
+    opts = ccc.ccc_opts_default(path=path, norm=norm)
+    ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
+    opts = ccc.ccc_opts_default(path=path, norm=norm, workspace=ws)
+    opts.split = split
+    npairs = ccc.ccc2_count(n_v)
+    tally = torch.full((npairs, 4), -7, dtype=torch.int32, device="cuda")
+    out = torch.full((npairs, 4), -7.0, dtype=torch.float32, device="cuda")
+    ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    return tally.cpu().numpy(), out.cpu().numpy()
+
+
+@pytest.mark.parametrize("norm", [0, 1])
+def test_popc_forced_splits_equal_unsplit_and_oracle(norm):
+    """The popcount path's K split: parts of whole 8-word stages whose partial tallies are
+    summed with integer reductions, CCC values from the sums."""
+    n_v, n_f = 150, 9000 + 37  # 18 stages of 512 individuals, ragged
+    geno = synth.panel_hwe(n_v, n_f, seed=76, p_missing=0.02, pad_seed=3)
+    et, ec = oracle.ccc2_all(geno, n_f, norm=norm)
+    t1, c1 = _run_path(geno, n_f, 1, 1, norm)
+    assert_tally_equal(t1, et, "popc unsplit")
+    assert_ccc_close(c1, ec, what="popc unsplit")
+    for split in (2, 5, 18, 4096):  # 4096 is clamped to the 18 stages
+        t, c = _run_path(geno, n_f, split, 1, norm)
+        np.testing.assert_array_equal(t, t1)
+        np.testing.assert_array_equal(c, c1)
+
+
+def test_popc_automatic_split_on_a_long_panel():
+    n_v, n_f = 300, 200000 + 5
+    geno = synth.panel_hwe(n_v, n_f, seed=77, p_missing=0.01, pad_seed=4)
+    t, c = _run_path(geno, n_f, 0, 1)
+    t_tc, c_tc = _run_path(geno, n_f, 0, 0)
+    np.testing.assert_array_equal(t, t_tc)
+    np.testing.assert_array_equal(c, c_tc)
+    rows = np.array([0, 150, 298])
+    et, ec = oracle.ccc2_rows(geno, n_f, rows)
+    idx = np.concatenate([oracle.pair_index(i, np.arange(i + 1, n_v), n_v) for i in rows])
+    assert_tally_equal(t[idx], et, "popc auto split rows")
+    assert_ccc_close(c[idx], ec, what="popc auto split rows")
