@@ -135,7 +135,7 @@ typedef struct ccc_opts {
                              are summed (the n_pf axis of Sec. 4 on one GPU), for panels with few
                              SNP tiles and long vectors.  0 = automatic (tensor cores: when the
                              triangle has at most half as many tiles as SM pairs and n_f >= 4,096;
-                             popcount: fewer 64-SNP tiles than two per SM, at least 4,096
+                             popcount: fewer 64-SNP tiles than four per SM, at least 4,096
                              individuals per part), 1 = off, n >= 2 = n parts (at most n_f / 128
                              on the tensor cores, n_f / 512 on the popcount path).  Same results;
                              the CCC values then come from the summed tallies. */

@@ -376,15 +376,16 @@ static int k_split_tiles(int requested, int64_t tiles, int64_t kpad, int sms) {
 }
 
 // K parts of a 2-way popcount call: opts->split when set (at most the 8-word
-// stages), else automatic: a triangle of fewer 64-SNP tiles than two per SM is
-// split so that about two blocks per SM run, each part keeping at least 64
-// words (4,096 individuals).
+// stages), else automatic: a triangle of fewer 64-SNP tiles than four per SM is
+// split into about 16 blocks per SM, each part keeping at least 64 words (4,096
+// individuals).  Measured on GB300, 512 SNPs (36 tiles) x 1,000,000: 9 parts
+// 12.3 ms, 18 parts 10.3, 36 parts 9.4, 72 parts 9.1.
 static int popc_split(int requested, int64_t n_v, int64_t w64, int sms) {
   const int64_t stages = (w64 + 7) / 8;
   if (requested >= 1) return static_cast<int>(requested < stages ? requested : stages);
   const int64_t tiles = popc2_tiles(n_v);
-  if (tiles < 1 || tiles >= 2 * static_cast<int64_t>(sms)) return 1;
-  int64_t split = (2 * static_cast<int64_t>(sms) + tiles - 1) / tiles;
+  if (tiles < 1 || tiles >= 4 * static_cast<int64_t>(sms)) return 1;
+  int64_t split = (16 * static_cast<int64_t>(sms) + tiles - 1) / tiles;
   if (split > stages / 8) split = stages / 8;
   return split > 1 ? static_cast<int>(split) : 1;
 }
