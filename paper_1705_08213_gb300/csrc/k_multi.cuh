@@ -247,7 +247,8 @@ int launch_tally2_multi_split_s(const CUtensorMap &tm, const MultiArgs &a, int64
   sp.tri.I1 = sp.tri.nI;
   sp.split = split;
   sp.nkb = nkb;
-  const int64_t units = nB * (nB + 1) / 2 * split;
+  sp.tiles = nB * (nB + 1) / 2;
+  const int64_t units = sp.tiles * split;
   if (units == 0) return CCC_OK;
   const int64_t clusters = units < max_clusters ? units : max_clusters;
   k_tally2_multi_split<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, tcp::SMEM_BYTES,

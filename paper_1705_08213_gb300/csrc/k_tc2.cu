@@ -668,7 +668,8 @@ int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t 
   sp.tri.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.tri.nI);
   sp.split = split;
   sp.nkb = nkb;
-  const int64_t units = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1) * split;
+  sp.tiles = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1);
+  const int64_t units = sp.tiles * split;
   if (units == 0) return CCC_OK;
   const int64_t clusters = units < max_clusters ? units : max_clusters;
   k_tally2_tc_pair_split<4><<<static_cast<unsigned>(2 * clusters), 64 + 32 * 4, tcp::SMEM_BYTES, s>>>(
@@ -765,7 +766,8 @@ int launch_tally2_tc_pair_split_packed(const Tally2Args &a, const uint64_t *geno
   sp.tri = pair_params(a);
   sp.split = split;
   sp.nkb = nkb;
-  const int64_t units = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1) * split;
+  sp.tiles = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1);
+  const int64_t units = sp.tiles * split;
   if (units == 0) return CCC_OK;
   static int cache = 0;
   const int mc = pair_clusters(k_tally2_tc_pair_split_packed<4>, 64 + 32 * 4 + CT,

@@ -78,37 +78,45 @@ struct TriSchedPair : TriSched {
   __device__ int b_row() const { return J * 256; }
 };
 
-// Units of a K-split launch: unit u = (tile u / split, part u % split); part p
-// takes the K stages [p nkb / split, (p + 1) nkb / split) of its tile (the host
-// keeps split <= nkb, so no part is empty).
+// Units of a K-split launch, part-major: unit u = (tile u % tiles, part
+// u / tiles); part p takes the K stages [p nkb / split, (p + 1) nkb / split)
+// of its tile (the host keeps split <= nkb, so no part is empty).  A wave of
+// units then covers every tile of a few parts: the tiles that share a row
+// block read the same K range at the same time, so its operand blocks come
+// from L2 after the first read (tile-major order ran the parts of one tile
+// side by side, which share nothing).
 struct SplitSchedPair {
   struct Params {
     TriSched::Params tri;
     int split, nkb;
+    int64_t tiles;  // tiles of the triangle (or of the row range)
   };
+  TriSched::Params tri;
   TriSchedPair t;
   int split, nkb, part, I, J;
-  int64_t u;
+  int64_t u, tiles;
   bool valid;
 
-  __device__ void sync() {
+  __device__ void set_unit() {
+    valid = u < tiles * split;
+    if (!valid) return;
+    part = static_cast<int>(u / tiles);
+    t.init(tri, u % tiles);
     valid = t.valid;
     I = t.I;
     J = t.J;
-    part = static_cast<int>(u % split);
   }
   __device__ void init(const Params &p, int64_t start) {
+    tri = p.tri;
     split = p.split;
     nkb = p.nkb;
+    tiles = p.tiles;
     u = start;
-    t.init(p.tri, start / split);
-    sync();
+    set_unit();
   }
   __device__ void advance(int64_t step) {
-    const int64_t u2 = u + step;
-    t.advance(u2 / split - u / split);
-    u = u2;
-    sync();
+    u += step;
+    set_unit();
   }
   __device__ int map_index() const { return 0; }
   __device__ int k_begin() const {
