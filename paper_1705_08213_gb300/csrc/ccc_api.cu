@@ -460,11 +460,13 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
     // in shared memory; otherwise they are unpacked into the operand matrix.
     const bool packed = o->tile == 3;
     uint8_t *op = packed ? nullptr : at<uint8_t>(o, L.op);
-    if (!packed)
-      CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
     const int split = (filter == nullptr && i_end < 0 && o->tile != 1 && on_device(tally))
                           ? k_split(o->split, p->n_v, L.kpad, dev.sms)
                           : 1;
+    // The K-split kernel reads its operand K-block-major.
+    if (!packed)
+      CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s,
+                                 split > 1));
     if (split > 1) {
       // Partial tallies of the K parts are summed into the zeroed output; the
       // CCC values follow from the complete tallies.

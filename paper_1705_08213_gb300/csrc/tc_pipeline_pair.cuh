@@ -76,6 +76,16 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void *tmap,
       : "memory");
 }
 
+// The same for a 3-D tensor map (an operand stored K-block-major).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const void *tmap, int32_t x, int32_t y,
+                                                 int32_t z, uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
                "r"(ncols)
@@ -121,7 +131,10 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
 //        static constexpr int STAGE_BYTES_PER_WARP: shared memory each epilogue
 //        warp may use at `stage` (the kernel is launched with
 //        smem_bytes(EW, STAGE_BYTES_PER_WARP)).
-template <class Sched, class Epi, int EW>
+// KBLK: the operand is stored K-block-major, [nkb][rows][128 bytes], behind a
+// 3-D tensor map (x = byte, y = row, z = K block), so that each 128-row box is
+// one contiguous 16 KB run.
+template <class Sched, class Epi, int EW, bool KBLK = false>
 __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
                                                      const typename Sched::Params &sp,
                                                      const typename Epi::Params &ep, int nkb,
@@ -197,8 +210,13 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
           }
           if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * STAGE_BYTES);
           const uint32_t fb = map_to_rank(full_bar(stage), 0);
-          tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), m, (kb0 + kb) * BK, ya, fb);
-          tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), m, (kb0 + kb) * BK, yb, fb);
+          if (KBLK) {
+            tma_load_3d_pair(smem_u32(sA + stage * A_BYTES), m, 0, ya, kb0 + kb, fb);
+            tma_load_3d_pair(smem_u32(sB + stage * B_BYTES), m, 0, yb, kb0 + kb, fb);
+          } else {
+            tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), m, (kb0 + kb) * BK, ya, fb);
+            tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), m, (kb0 + kb) * BK, yb, fb);
+          }
           last_parity[stage] = static_cast<int>(phase);
           if (++stage == STAGES) {
             stage = 0;
