@@ -466,7 +466,7 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
     // The K-split kernel reads its operand K-block-major.
     if (!packed)
       CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s,
-                                 split > 1));
+                                 split > 1 ? L.rows_pad : 0));
     if (split > 1) {
       // Partial tallies of the K parts are summed into the zeroed output; the
       // CCC values follow from the complete tallies.

@@ -17,10 +17,11 @@ int launch_allele_counts(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t
                          int32_t *counts, float *w, double gamma, cudaStream_t s);
 int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, double gamma,
                                cudaStream_t s);
-// blocked: K-block-major layout [kpad / 128][2 snps_pad][128] (the K-split
-// kernel's operand), else row-major [2 snps_pad][kpad].
+// blocked_rows > 0: K-block-major layout [kpad / 128][blocked_rows][128], the
+// operand buffer holding blocked_rows >= 2 snps_pad rows (the K-split kernel
+// reads it so); 0: row-major [2 snps_pad][kpad].
 int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
-                       int64_t kpad, int64_t snps_pad, cudaStream_t s, bool blocked = false);
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0);
 int launch_planes(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint64_t *planes,
                   int64_t w64, cudaStream_t s);
 

@@ -125,7 +125,7 @@ constexpr uint32_t kRho1E4M3 = 0x40003800u;
 // that each warp store covers 512 contiguous bytes of a row.
 __global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
                               int64_t ld, uint8_t *__restrict__ op, int64_t kpad,
-                              int64_t snps_pad, bool blocked) {
+                              int64_t snps_pad, int64_t blocked_rows) {
   const int64_t hpr = kpad / 16;  // 16-entry chunks per operand row
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= hpr * snps_pad) return;
@@ -146,10 +146,10 @@ __global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, in
     r0[b] = __byte_perm(kRho0E4M3, 0u, sel);
     r1[b] = __byte_perm(kRho1E4M3, 0u, sel);
   }
-  // Row-major [row][kpad], or K-block-major [kpad / 128][row][128] (blocked).
-  uint8_t *d0 = blocked ? op + ((c >> 3) * (2 * snps_pad) + 2 * i) * 128 + (c & 7) * 16
-                        : op + (2 * i) * kpad + c * 16;
-  uint8_t *d1 = blocked ? d0 + 128 : d0 + kpad;
+  // Row-major [row][kpad], or K-block-major [kpad / 128][blocked_rows][128].
+  uint8_t *d0 = blocked_rows > 0 ? op + ((c >> 3) * blocked_rows + 2 * i) * 128 + (c & 7) * 16
+                                 : op + (2 * i) * kpad + c * 16;
+  uint8_t *d1 = blocked_rows > 0 ? d0 + 128 : d0 + kpad;
   *reinterpret_cast<uint4 *>(d0) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
   *reinterpret_cast<uint4 *>(d1) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
 }
@@ -233,12 +233,13 @@ int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, dou
 }
 
 int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
-                       int64_t kpad, int64_t snps_pad, cudaStream_t s, bool blocked) {
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows) {
+  if (blocked_rows != 0 && blocked_rows < 2 * snps_pad) return CCC_EINVAL;
   const int threads = 256;
   const int64_t total = (kpad / 16) * snps_pad;
   const int64_t blocks = (total + threads - 1) / threads;
   k_unpack_e4m3<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
-                                                                   snps_pad, blocked);
+                                                                   snps_pad, blocked_rows);
   return note_launch();
 }
 

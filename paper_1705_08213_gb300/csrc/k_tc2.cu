@@ -452,6 +452,20 @@ bool make_operand_map(CUtensorMap *map, const uint8_t *op, int64_t rows, int64_t
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool make_blocked_operand_map(CUtensorMap *map, const uint8_t *op, int64_t rows, int64_t kpad,
+                              uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  const cuuint64_t dims[3] = {128u, static_cast<cuuint64_t>(rows),
+                              static_cast<cuuint64_t>(kpad / 128)};
+  const cuuint64_t strides[2] = {128u, static_cast<cuuint64_t>(rows) * 128u};
+  const cuuint32_t box[3] = {128u, box_rows, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(op), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace tc
 
 // Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
@@ -460,24 +474,6 @@ int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1) {
   int64_t t = 0;
   for (int64_t I = I0; I < nB && I < I1; ++I) t += nB - I;
   return t;
-}
-
-// 3-D tensor map over a K-block-major operand [kpad / 128][rows][128 bytes]
-// (x = byte in the block, y = row, z = K block), box 128 bytes x 128 rows x 1,
-// 128-byte swizzling: the same tiles as make_operand_map, each box one
-// contiguous 16 KB run.
-static bool make_blocked_operand_map(CUtensorMap *map, const uint8_t *op, int64_t rows,
-                                     int64_t kpad) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (enc == nullptr) return false;
-  const cuuint64_t dims[3] = {128u, static_cast<cuuint64_t>(rows),
-                              static_cast<cuuint64_t>(kpad / 128)};
-  const cuuint64_t strides[2] = {128u, static_cast<cuuint64_t>(rows) * 128u};
-  const cuuint32_t box[3] = {128u, static_cast<cuuint32_t>(tcp::BMH), 1u};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(op), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *ops,
@@ -676,7 +672,7 @@ int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t 
   const int nkb = static_cast<int>(kpad / BK);
   if (split < 1 || split > nkb) return CCC_EINVAL;
   CUtensorMap tm;
-  if (!make_blocked_operand_map(&tm, op, rows_pad, kpad)) return CCC_ECUDA;
+  if (!make_blocked_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
   SplitSchedPair::Params sp;
   sp.tri.nI = static_cast<int>((a.n_v + 127) / 128);
   sp.tri.nJ = sp.tri.nI;

@@ -218,6 +218,11 @@ __device__ __forceinline__ void persistent_gemm(const CUtensorMap *tmA, const CU
 // box of 128 bytes x box_rows and 128-byte swizzling (defined in k_tc2.cu).
 bool make_operand_map(CUtensorMap *map, const uint8_t *op, int64_t rows, int64_t kpad,
                       uint32_t box_rows);
+// The same tiles over an operand stored K-block-major, [kpad / 128][rows][128
+// bytes]: a 3-D map (x = byte in the block, y = row, z = K block) whose box of
+// 128 bytes x box_rows is one contiguous run (defined in k_tc2.cu).
+bool make_blocked_operand_map(CUtensorMap *map, const uint8_t *op, int64_t rows, int64_t kpad,
+                              uint32_t box_rows);
 
 }  // namespace tc
 }  // namespace ccc
