@@ -319,41 +319,41 @@ def gpu_id_for(torch, dev):
         return str(dev)
 
 
-def oracle_sample(geno, w, rng, budget):
+def oracle_sample(geno, w, rng, n_sample):
     """One oracle call on a random sample of the workload; returns comparisons done."""
     import oracle
     n_v, n_f = w["n_v"], w["n_f"]
     if w["kind"] == 2:
-        i = rng.integers(0, n_v - 1, size=budget)
-        j = i + 1 + (rng.random(budget) * (n_v - 1 - i)).astype(np.int64)
+        i = rng.integers(0, n_v - 1, size=n_sample)
+        j = i + 1 + (rng.random(n_sample) * (n_v - 1 - i)).astype(np.int64)
         if w.get("states"):
             oracle.ccc2_multi_pairs(geno, n_f, w["states"], i, j)
         else:
             oracle.ccc2_pairs(geno, n_f, i, j)
-        return budget * n_f
-    j = rng.integers(1, n_v - 1, size=budget)
-    i = (rng.random(budget) * j).astype(np.int64)
-    k = j + 1 + (rng.random(budget) * (n_v - 1 - j)).astype(np.int64)
+        return n_sample * n_f
+    j = rng.integers(1, n_v - 1, size=n_sample)
+    i = (rng.random(n_sample) * j).astype(np.int64)
+    k = j + 1 + (rng.random(n_sample) * (n_v - 1 - j)).astype(np.int64)
     oracle.ccc3_triples(geno, n_f, i, j, k)
-    return budget * n_f
+    return n_sample * n_f
 
 
 def cpu_baseline(geno, w, seconds, seed=7):
     """The oracle on host cores over random pairs (triples) of the same panel."""
     import oracle
     rng = np.random.default_rng(seed)
-    budget = max(64, int(4e8 // w["n_f"]))
+    n_sample = max(64, int(4e8 // w["n_f"]))
     done, calls = 0, 0
     t0 = time.perf_counter()
     while True:
-        done += oracle_sample(geno, w, rng, budget)
+        done += oracle_sample(geno, w, rng, n_sample)
         calls += 1
         el = time.perf_counter() - t0
         if el >= seconds or calls >= 200:
             break
     what = "pairs (i<j)" if w["kind"] == 2 else "triples (i<j<k)"
     return {"value": done / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{calls * budget} uniformly random {what} of the same panel, all "
+            "sample": f"{calls * n_sample} uniformly random {what} of the same panel, all "
                       f"{w['n_f']} individuals each, {el:.1f} s on the host cores"}
 
 
@@ -365,13 +365,13 @@ def run_reference(args, w):
     import oracle
     geno = make_panel(w)
     rng = np.random.default_rng(11)
-    budget = max(64, int(6e7 // w["n_f"]))
+    n_sample = max(64, int(6e7 // w["n_f"]))
     for _ in range(args.warmup):
-        oracle_sample(geno, w, rng, budget)
+        oracle_sample(geno, w, rng, n_sample)
     t0 = time.perf_counter()
     done = 0
     for _ in range(args.steps):
-        done += oracle_sample(geno, w, rng, budget)
+        done += oracle_sample(geno, w, rng, n_sample)
     el = time.perf_counter() - t0
     value = done / el
     what = "pairs" if w["kind"] == 2 else "triples"
@@ -381,9 +381,9 @@ def run_reference(args, w):
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
         "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"],
-                   "sample_per_step": f"{budget} random {what} x {w['n_f']} individuals"},
+                   "sample_per_step": f"{n_sample} random {what} x {w['n_f']} individuals"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                         "sample": f"{budget} uniformly random {what} per step, {args.steps} "
+                         "sample": f"{n_sample} uniformly random {what} per step, {args.steps} "
                                    "timed steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
