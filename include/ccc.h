@@ -64,8 +64,9 @@
  *   - Return value: CCC_OK, or a negative CCC_E* code for an argument error
  *     found before anything was queued (nothing is written then), or
  *     CCC_ECUDA when a launch was refused.  Errors found on the device (a
- *     bounded wait that timed out) are recorded in the workspace status word,
- *     read with ccc_status().
+ *     bounded wait that timed out; in the bounds-checking build, an index
+ *     outside its buffer) are recorded in the workspace status word, read
+ *     with ccc_status().
  * ---------------------------------------------------------------------------
  */
 #ifndef CCC_H_
@@ -462,7 +463,8 @@ int ccc2_multi_stream(const ccc_panel_multi *panel, int n_phases, int32_t *host_
 
 /*
  * Device-side status of the workspace: *status receives CCC_OK or the first
- * CCC_E* code a kernel recorded (CCC_ETIMEOUT when a bounded wait gave up).
+ * CCC_E* code a kernel recorded (CCC_ETIMEOUT when a bounded wait gave up;
+ * CCC_EBOUNDS from the bounds-checking build, include/ccc_checked.h).
  * Synchronises the stream.  Every call that takes a workspace clears the word
  * first, so this reports on the calls since the last workspace call began.
  */
