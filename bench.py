@@ -116,6 +116,9 @@ def parse():
                     help="tensor-core variant (0 automatic). 2-way: 1 one SM, 2 SM pairs; 3-way: "
                          "1 masked operands in HBM, 2 masked operands in shared memory, "
                          "3 genotype classes of v_j")
+    ap.add_argument("--operand", default="auto", choices=["auto", "e4m3", "e2m1"],
+                    help="tensor-core count operands (ccc_opts.operand): auto = e2m1 (FP4) on the "
+                         "2-way SM-pair tiles, e4m3 elsewhere")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak: an independent panel per rank; strong: one panel split by rows/slabs")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
@@ -127,6 +130,8 @@ def parse():
                     help="e2e leg: ccc2_stream phases (stream), results stored by the kernels "
                          "straight into pinned host memory (direct), or one copy per output "
                          "after the call (copy); auto = stream for 2-way, copy otherwise")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default 2-way line only: no 3way / batched / filter sub-records")
     ap.add_argument("--source-hash", action="store_true",
                     help="print the hash of the CUDA sources (for profiles/ncu_traffic.json) and exit")
     a = ap.parse_args()
@@ -134,21 +139,36 @@ def parse():
         for k in KERNEL_SOURCES:
             print(k, source_hash(k))
         raise SystemExit(0)
-    w = dict(WORKLOADS[a.workload])
-    if a.n_v is not None or a.n_f is not None:
-        w["n_v"] = a.n_v if a.n_v is not None else w["n_v"]
-        w["n_f"] = a.n_f if a.n_f is not None else w["n_f"]
-        w["text"] = (f"reduced case of the {a.workload} workload: n_v={w['n_v']} x n_f={w['n_f']}, "
-                     f"same generator and seed (not the bench line's configuration)")
+    w = workload_dict(a.workload, a.n_v, a.n_f)
     if a.steps is None:
-        a.steps = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10,
-                   "multi": 60, "long": 20}[a.workload]
-    if a.workload == "batched":
+        a.steps = DEFAULT_STEPS[a.workload]
+    return a, w
+
+
+DEFAULT_STEPS = {"2way": 60, "3way": 12, "filter": 3, "small": 200, "batched": 10, "multi": 60,
+                 "long": 20}
+# Workloads attached to the default 2-way line as sub-records (one GPU): timed steps and
+# warm-up of each, and the seconds of oracle time for its cpu_baseline.
+SUB_WORKLOADS = {"3way": (8, 3), "batched": (5, 3), "filter": (3, 3)}
+SUB_CPU_SECONDS = 8.0
+
+
+def workload_dict(name, n_v=None, n_f=None):
+    """The workload's description, with the optional reduced sizes and the batched shapes."""
+    w = dict(WORKLOADS[name])
+    w["name"] = name
+    if n_v is not None or n_f is not None:
+        w["n_v"] = n_v if n_v is not None else w["n_v"]
+        w["n_f"] = n_f if n_f is not None else w["n_f"]
+        w["text"] = (f"reduced case of the {name} workload: n_v={w['n_v']} x n_f={w['n_f']}, "
+                     f"same generator and seed (not the bench line's configuration)")
+        w["reduced"] = True
+    if name == "batched":
         rng = np.random.default_rng(w["seed"])
         w["shapes"] = [(int(rng.integers(500, 8001)), int(rng.integers(2000, 50001)))
                        for _ in range(w["n_panels"])]
         w["n_v"], w["n_f"] = max(v for v, _ in w["shapes"]), max(f for _, f in w["shapes"])
-    return a, w
+    return w
 
 
 def dist_env():
@@ -182,6 +202,10 @@ def comparisons(w):
 KERNEL_SOURCES = {
     "k_tally2_tc_pair": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
                          "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
+                             "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_split_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
+                                   "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_split": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
                                "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_packed": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
@@ -227,6 +251,42 @@ def ncu_traffic(kernel, workload):
 # 64-bit AND+POPC per second: 16 32-bit POPC per SM per clock (measured: 7.5 64-bit
 # AND+POPC per SM per clock in a register-only loop), 152 SMs at 2,070 MHz.
 POPC64_PEAK_T = 152 * 2.070e9 * 16 / 2 / 1e12
+
+
+_RATES = {}
+
+
+def probe_rates(ccc, torch, dev):
+    """Work per SM clock cycle of the tally kernels' execution units on this GPU, measured once
+    per process with the library's rate probes (ccc_mma_rate, ccc_popc_rate): back-to-back
+    M = 256 x N = 256 cta_group::2 MMAs on every SM pair, and register-only 64-bit AND+POPC."""
+    if _RATES:
+        return _RATES
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    _RATES["sms"] = sms
+    n_mma = 8192
+    for kind, name, k in ((ccc.CCC_MMA_E4M3, "e4m3", 32), (ccc.CCC_MMA_E2M1, "e2m1", 64)):
+        ccc.ccc_mma_rate(kind, 256, 256, sms // 2)
+        cycles, bad = ccc.ccc_mma_rate(kind, 256, n_mma, sms // 2)
+        med = statistics.median(cycles)
+        _RATES[name] = {"flops_per_sm_per_clock": 2.0 * 256 * 256 * k * n_mma / med / 2.0,
+                        "cycles_per_mma": med / n_mma, "bad": bad}
+    ccc.ccc_popc_rate(256, sms)
+    cyc = statistics.median(ccc.ccc_popc_rate(4096, sms))
+    _RATES["popc64_per_sm_per_clock"] = 8.0 * 1024 * 4096 / cyc
+    return _RATES
+
+
+def clock_normalised(achieved, per_clock, clocks, sms, what):
+    """Fraction of the peak at the SM clock the kernel ran at: achieved / (work per SM per
+    cycle x SMs x median SM MHz sampled during the timed region)."""
+    mhz = (clocks or {}).get("sm_mhz")
+    src = "median SM clock sampled during the timed region"
+    if not mhz:
+        mhz, src = 2070.0, "no clock samples: maximum SM clock 2,070 MHz"
+    peak = per_clock * sms * mhz * 1e6 / 1e12
+    return {"peak": peak, "frac": achieved / peak, "per_sm_per_clock": per_clock, "sms": sms,
+            "sm_mhz": mhz, "note": f"{what} x {sms} SMs x {mhz:.0f} MHz ({src})"}
 
 
 def measured_peaks():
@@ -394,9 +454,10 @@ def run_reference(args, w):
 class Runner:
     """Device buffers and one step of the chosen workload through the C ABI."""
 
-    def __init__(self, ccc, torch, dev, w, path, geno_np, tile=0, shard=None):
+    def __init__(self, ccc, torch, dev, w, path, geno_np, tile=0, shard=None, operand=0):
         self.ccc, self.torch, self.dev, self.w, self.path = ccc, torch, dev, w, path
         self.tile = tile
+        self.operand = operand
         n_v, n_f = w["n_v"], w["n_f"]
         # Rows (2-way) or slabs (3-way) [lo, hi) of this rank; None = the whole panel.
         self.shard = shard
@@ -405,11 +466,11 @@ class Runner:
         self.host_geno = self.host_geno.pin_memory()
         self.geno = self.host_geno.to(dev)
         op = ccc.CCC_OP_2WAY if w["kind"] == 2 else ccc.CCC_OP_3WAY
-        o0 = ccc.ccc_opts_default(path=path, tile=tile)
+        o0 = ccc.ccc_opts_default(path=path, tile=tile, operand=operand)
         size = (ccc.ccc_multi_workspace_size(self.geno, n_f, self.states, o0) if self.states else
                 ccc.ccc_workspace_size(self.geno, n_f, o0, op))
         self.ws = torch.empty(size, dtype=torch.uint8, device=dev)
-        self.opts = ccc.ccc_opts_default(path=path, workspace=self.ws, tile=tile)
+        self.opts = ccc.ccc_opts_default(path=path, workspace=self.ws, tile=tile, operand=operand)
         self.filter = "threshold" in w
         if self.filter:
             self.cap = 1 << 20
@@ -478,7 +539,7 @@ class Runner:
                     torch.empty(self.out.shape, dtype=torch.float32, pin_memory=True)]
             dev = []
             del self.tally, self.out, self.ws
-            o0 = ccc.ccc_opts_default(path=self.path, tile=self.tile)
+            o0 = ccc.ccc_opts_default(path=self.path, tile=self.tile, operand=self.operand)
             if self.states:
                 size = ccc.ccc2_multi_stream_workspace_size(self.geno, w["n_f"], self.states, phases, o0)
             else:
@@ -486,7 +547,7 @@ class Runner:
                         ccc.ccc3_stream_workspace_size)(self.geno, w["n_f"], phases, o0)
             self.ws_stream = torch.empty(size, dtype=torch.uint8, device=self.dev)
             self.opts = ccc.ccc_opts_default(path=self.path, workspace=self.ws_stream,
-                                             tile=self.tile)
+                                             tile=self.tile, operand=self.operand)
         else:
             host = [torch.empty(self.tally.shape, dtype=torch.int32, pin_memory=True),
                     torch.empty(self.out.shape, dtype=torch.float32, pin_memory=True)]
@@ -645,6 +706,10 @@ def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
         "sequential_64_calls": {"ms_per_step": ms_seq, "value": cmp_per_step / (ms_seq * 1e-3),
                                 "batched_speedup": ms_seq / ms_graph},
     }
+    rates = probe_rates(ccc, torch, dev)
+    result["roofline"]["clock_normalised"] = clock_normalised(
+        achieved, rates["e4m3"]["flops_per_sm_per_clock"], clocks, rates["sms"],
+        "e4m3 flops per SM per clock of the ccc_mma_rate probe")
     if e2e is not None:
         result["e2e"] = e2e
     if not args.skip_cpu:
@@ -652,8 +717,7 @@ def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
         wk = dict(kind=2, n_v=shapes[k][0], n_f=shapes[k][1])
         result["cpu_baseline"] = cpu_baseline(genos_np[k], wk, args.cpu_seconds)
         result["cpu_baseline"]["sample"] += f" (panel {k}, the largest)"
-    print(json.dumps(result), flush=True)
-    return 0
+    return result
 
 
 def main():
@@ -683,6 +747,35 @@ def main():
         pg.barrier()
     ccc.load()
 
+    result = run_workload(args, w, ccc, torch, dev, rank, world, local, pg)
+    if (rank == 0 and world == 1 and args.workload == "2way" and not w.get("reduced")
+            and not args.no_sub and args.path == "tc" and args.tile == 0):
+        # The other at-scale workloads, each timed in full as its own record.
+        result["workloads"] = {}
+        for name, (steps, warmup) in SUB_WORKLOADS.items():
+            torch.cuda.synchronize(dev)
+            torch.cuda.empty_cache()
+            sub = argparse.Namespace(**vars(args))
+            sub.workload, sub.steps, sub.warmup = name, steps, warmup
+            sub.cpu_seconds = SUB_CPU_SECONDS
+            sub.scaling = "weak"
+            try:
+                rec = run_workload(sub, workload_dict(name), ccc, torch, dev, rank, world, local,
+                                   pg)
+            except Exception as e:  # recorded, so one failing workload does not hide the others
+                rec = {"error": f"{type(e).__name__}: {e}"}
+            result["workloads"][name] = rec
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
+    """One workload's record (the bench line's keys) on this rank."""
     if args.workload == "batched":
         if world > 1:
             raise SystemExit("the batched workload runs on one GPU")
@@ -707,8 +800,13 @@ def main():
                            else sh.pair_range(n_v, world, rank))
             cmp_rank = ccc.ccc2_rows_count(n_v, *shard_range) * w["n_f"]
     geno_np = make_panel(w, 0 if strong else rank)
+    operand = {"auto": ccc.CCC_OPERAND_AUTO, "e4m3": ccc.CCC_OPERAND_E4M3,
+               "e2m1": ccc.CCC_OPERAND_E2M1}[args.operand]
+    # The library's automatic choice: e2m1 on the 2-way SM-pair tiles (not s states).
+    fp4 = (path == ccc.CCC_PATH_TC and w["kind"] == 2 and not w.get("states")
+           and args.tile in (0, 2) and operand != ccc.CCC_OPERAND_E4M3)
     run = Runner(ccc, torch, dev, w, path, geno_np, tile=args.tile,
-                 shard=shard_range if strong else None)
+                 shard=shard_range if strong else None, operand=operand)
     stream = torch.cuda.current_stream(dev)
 
     sampler = ClockSampler(gpu_id_for(torch, dev)) if local == 0 else None
@@ -757,7 +855,7 @@ def main():
     # summed duration of its launches in the timed region / steps.
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
-    packed = "_packed" if args.tile == 3 else ""
+    packed = "_packed" if args.tile == 3 else "_fp4" if fp4 else ""
     kname = {(2, True): ("k_tally2_multi" if w.get("states") else
                          "k_tally2_tc_pair_split" + packed if w.get("split_compare") else
                          "k_tally2_tc_pair" + packed if args.tile != 1 else "k_tally2_tc"),
@@ -776,19 +874,29 @@ def main():
             per_cmp = 2.0 * w["states"] ** 2  # s^2 MAC per comparison
         flops = per_cmp * cmp_rank
         achieved = flops / (kernel_step_ms * 1e-3) / 1e12
-        peak = 2.0 * bf16_peak  # e4m3 dense = 2x bf16 dense (nominal 4.5 / 2.25 PFLOP/s)
+        # The peak of the kernel's own operand type: the measured bf16 burst times the nominal
+        # dense ratio (e4m3 4.5 / 2.25 PFLOP/s; e2m1 13.5 / 2.25).
+        ratio = 6.0 if fp4 else 2.0
+        peak = ratio * bf16_peak
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kname, args.workload)
                 if (args.n_v is None and args.n_f is None) else None, "kernel": kname,
                 "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n,
                 "per_unit": f"{per_cmp:.0f} flops per comparison",
-                "peak_note": f"e4m3 dense peak = 2 x {peak_src} bf16 burst {bf16_peak:.0f} TFLOP/s "
-                             "(kind::i8 is not available on sm_103a)"}
+                "peak_note": (f"{'e2m1' if fp4 else 'e4m3'} dense peak = {ratio:.0f} x {peak_src} "
+                              f"bf16 burst {bf16_peak:.0f} TFLOP/s (nominal dense ratio; "
+                              "kind::i8 is not available on sm_103a)")}
+        rates = probe_rates(ccc, torch, dev)
+        kind = "e2m1" if fp4 else "e4m3"
+        roof["clock_normalised"] = clock_normalised(
+            achieved, rates[kind]["flops_per_sm_per_clock"], clocks, rates["sms"],
+            f"{kind} flops per SM per clock of the ccc_mma_rate probe")
         if kname.startswith("k_tally3_class"):
             ex = 8.0 * cmp_rank / (kernel_step_ms * 1e-3) / 1e12
             roof["executed"] = {"per_unit": "8 flops per comparison (T product; the D product "
                                             "over individuals with v_j missing not counted)",
-                                "achieved": ex, "frac": ex / peak}
+                                "achieved": ex, "frac": ex / peak,
+                                "frac_clock_normalised": ex / roof["clock_normalised"]["peak"]}
     else:
         per = 8.0 / 64.0 if w["kind"] == 2 else 24.0 / 64.0
         achieved = per * cmp_rank / (kernel_step_ms * 1e-3) / 1e12
@@ -797,12 +905,17 @@ def main():
                 "kernel_ms_per_step": kernel_step_ms, "kernel_launches": kernel_n,
                 "per_unit": f"{per * 64:.0f} 64-bit POPC per 64 comparisons",
                 "peak_note": "16 32-bit POPC per SM per clock x 152 SMs x 2,070 MHz / 2"}
+        rates = probe_rates(ccc, torch, dev)
+        roof["clock_normalised"] = clock_normalised(
+            achieved, rates["popc64_per_sm_per_clock"], clocks, rates["sms"],
+            "64-bit AND+POPC per SM per clock of the ccc_popc_rate probe")
 
     result = {
         "metric": w["metric"], "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
-        "dtype": "e4m3 operands, fp32 accumulate" if path == ccc.CCC_PATH_TC else "u64 bit planes",
+        "dtype": ("e2m1 operands (kind::mxf4, unit scale factors), fp32 accumulate" if fp4 else
+                  "e4m3 operands, fp32 accumulate" if path == ccc.CCC_PATH_TC else "u64 bit planes"),
         "data": "synthetic",
         "config": {"workload": w["text"], "n_v": w["n_v"], "n_f": w["n_f"], "path": args.path,
                    "tile": ({0: "automatic (256x256 on an SM pair)", 1: "128x256 on one SM",
@@ -861,6 +974,40 @@ def main():
         if run.filter:
             result["config"]["hits_per_step"] = run.hit_count
 
+    if fp4 and rank == 0 and not (strong and world > 1):
+        # The same call with e4m3 operands (ccc_opts.operand = E4M3), kernel time included.
+        for name in ("ws", "ws_stream"):
+            if hasattr(run, name):
+                delattr(run, name)
+        if not run.filter and not hasattr(run, "tally"):
+            rows = ccc.ccc2_count(w["n_v"])
+            run.tally = torch.empty((rows, 4), dtype=torch.int32, device=dev)
+            run.out = torch.empty((rows, 4), dtype=torch.float32, device=dev)
+        o8 = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3)
+        ws8 = torch.empty(ccc.ccc_workspace_size(run.geno, w["n_f"], o8, ccc.CCC_OP_2WAY),
+                          dtype=torch.uint8, device=dev)
+        run.opts = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3, workspace=ws8)
+        run.step(stream)
+        torch.cuda.synchronize(dev)
+        n8 = max(1, min(args.steps, 10))
+        ccc.ccc_timing_enable(True)
+        ccc.ccc_timing_read()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(n8):
+            run.step(stream)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        k8, _ = ccc.ccc_timing_read()
+        ccc.ccc_timing_enable(False)
+        ms8 = q0.elapsed_time(q1) / n8
+        result["e4m3_path"] = {"value": cmp_per_step / (ms8 * 1e-3), "unit": UNIT,
+                               "ms_per_step": ms8, "kernel_ms_per_step": k8 / n8,
+                               "fp4_speedup": ms8 / ms_per_step,
+                               "kernel_fp4_speedup": (k8 / n8) / kernel_step_ms,
+                               "note": "the same step with e4m3 count operands (kind::f8f6f4)"}
+        del ws8
+
     if (not args.skip_popc and rank == 0 and path == ccc.CCC_PATH_TC and w["kind"] == 2
             and not run.filter and not w.get("states")):
         for name in ("ws", "ws_stream"):
@@ -895,12 +1042,7 @@ def main():
     if not args.skip_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(geno_np, w, args.cpu_seconds)
 
-    if rank == 0:
-        print(json.dumps(result), flush=True)
-    if pg is not None:
-        pg.barrier()
-        pg.destroy_process_group()
-    return 0
+    return result
 
 
 if __name__ == "__main__":

@@ -140,7 +140,22 @@ typedef struct ccc_opts {
                              individuals per part), 1 = off, n >= 2 = n parts (at most n_f / 128
                              on the tensor cores, n_f / 512 on the popcount path).  Same results;
                              the CCC values then come from the summed tallies. */
+  int32_t operand;        /* encoding of the tensor-core count operands (CCC_OPERAND_*):
+                             E4M3 = one byte per count, kind::f8f6f4 MMAs; E2M1 = FP4, two counts
+                             per byte, block-scaled kind::mxf4 MMAs with every scale factor 1.0
+                             (half the operand bytes, a higher MMA rate).  Counts 0, 1, 2 are
+                             exact in both and the FP32 accumulation is exact below 2^24, so
+                             both give the same tallies and CCC values bit for bit.  E2M1 is
+                             built for the 2-way SM-pair tiles (opts->tile 0 or 2, with K split,
+                             row ranges, ccc2_stream and ccc2_filter); elsewhere an explicit
+                             E2M1 returns CCC_EUNSUPPORTED.  AUTO (0) = E2M1 where it is built,
+                             else E4M3.  The workspace size depends on it. */
 } ccc_opts;
+
+/* Operand encodings (ccc_opts.operand). */
+#define CCC_OPERAND_AUTO 0
+#define CCC_OPERAND_E4M3 1
+#define CCC_OPERAND_E2M1 2
 
 /* Operations, for ccc_workspace_size(). */
 #define CCC_OP_METRIC 1 /* ccc2_metric / ccc3_metric: status word and per-SNP factors */
@@ -344,14 +359,18 @@ int ccc3_tally_metric(const ccc_panel *panel, int64_t j_begin, int64_t j_end, in
  * and output buffers, or programs that may not allocate once they are running.
  * The paper has no counterpart; it is an interface convenience of this library.
  *
- * Computes exactly what ccc2_tally_metric computes with opts->path ==
- * CCC_PATH_TC (same kernels, same results), but keeps its scratch (status
- * word, per-SNP factors, e4m3 count operands) in a fixed 32 MiB device array
- * built into the library, which every GPU that loads the library holds until
- * the process exits.  The workspace fields of *opts are ignored; opts->path
- * must be CCC_PATH_TC.  Nothing is allocated: no cudaMalloc, no cudaFree.
+ * Computes what ccc2_tally_metric computes with opts->path == CCC_PATH_TC,
+ * bit for bit: the tile variant opts->tile selects (1 = one SM, 0 or 2 = SM
+ * pairs) and the tile order opts->group, with e4m3 operands and without the
+ * automatic K split (opts->split must be 0 or 1; tile 3 is rejected, an
+ * explicit opts->operand = CCC_OPERAND_E2M1 returns CCC_EUNSUPPORTED).  Its scratch (status
+ * word, per-SNP factors, e4m3 count operands) lives in a fixed 32 MiB device
+ * array built into the library, which every GPU that loads the library holds
+ * until the process exits.  The workspace fields of *opts are ignored.
+ * Nothing is allocated: no cudaMalloc, no cudaFree.
  *
- *   panel, tally, ccc, opts, stream: as for ccc2_tally_metric.
+ *   panel, tally, ccc, opts, stream: as for ccc2_tally_metric (ccc may be NULL:
+ *           tallies only); the argument checks are that call's.
  *   status: optional device int32 owned by the caller (NULL allowed); when
  *           given, it is cleared and receives CCC_ETIMEOUT if a device-side
  *           bounded wait gives up.  With NULL that word lives in the built-in
@@ -494,6 +513,45 @@ int ccc_checksum(const void *words, int64_t count, int64_t base, uint64_t *out, 
  * bad argument.
  */
 int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Rate probes.  Measurement only; the paper has no counterpart (its own peak
+ * figures, Sec. 6.1, are the vendor's).  They give the roofline denominators
+ * of the tensor-core and popcount paths as work per SM clock cycle on this
+ * device, so that a kernel's fraction of peak can be taken at the SM clock it
+ * ran at (peak = work per SM per cycle x SMs x clock).
+ *
+ * ccc_mma_rate: `clusters` clusters of two CTAs (one per SM pair, each CTA
+ * alone on its SM; 1 <= clusters <= SMs / 2) each issue n_mma
+ * (1 <= n_mma <= 65536) dense cta_group::2 MMAs of M = 256, N = n_cols
+ * (128 or 256) back to back from shared-memory operands into one TMEM
+ * accumulator, with operands of the given kind:
+ *   CCC_MMA_E4M3       kind::f8f6f4, e4m3 operands, K = 32 per MMA;
+ *   CCC_MMA_E2M1       kind::mxf4, e2m1 operands with UE8M0 scale factors per
+ *                      32 elements (all 1.0), K = 64 per MMA;
+ *   CCC_MMA_E2M1_NVF4  kind::mxf4nvf4, e2m1 operands with UE4M3 scale factors
+ *                      per 16 elements (all 1.0), K = 64 per MMA.
+ * cycles: device int64[clusters], receives the SM clock cycles from the first
+ * issue to the completion of the last MMA (-1 if the wait gave up).  bad:
+ * device int32, cleared by the call, receives the number of accumulator
+ * entries that differ from n_mma * K (operands are all 1.0), plus 2^20 per
+ * wait that gave up.  Flops per SM per cycle = 2 * 256 * n_cols * K * n_mma /
+ * (2 * cycles).  CCC_EINVAL for an argument outside these ranges.
+ *
+ * ccc_popc_rate: `blocks` blocks (1 <= blocks <= 65536) of 1024 threads, each
+ * thread running iters (1 <= iters <= 1 << 24) iterations of eight independent
+ * 64-bit AND + population counts over registers.  cycles: device
+ * int64[blocks], SM clock cycles of each block; sink: device uint64 (written
+ * only in a case that does not occur; it keeps the work from being removed).
+ * 64-bit AND + POPC per SM per cycle = 8 * 1024 * iters * (blocks resident on
+ * an SM) / cycles.
+ */
+#define CCC_MMA_E4M3 0
+#define CCC_MMA_E2M1 1
+#define CCC_MMA_E2M1_NVF4 2
+int ccc_mma_rate(int kind, int n_cols, int n_mma, int clusters, int64_t *cycles, int32_t *bad,
+                 void *stream);
+int ccc_popc_rate(int iters, int blocks, int64_t *cycles, uint64_t *sink, void *stream);
 
 /* Index helpers (host): positions defined in the header comment; -1 if out of range. */
 int64_t ccc2_index(int64_t i, int64_t j, int64_t n_v);

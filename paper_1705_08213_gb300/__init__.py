@@ -37,6 +37,8 @@ __all__ = [
     "ccc_check_bounded_wait", "ccc_checksum",
     "ccc_checked_shrink_outputs",
     "ccc_tune_cache_clear",
+    "CCC_MMA_E4M3", "CCC_MMA_E2M1", "CCC_MMA_E2M1_NVF4", "ccc_mma_rate", "ccc_popc_rate",
+    "CCC_OPERAND_AUTO", "CCC_OPERAND_E4M3", "CCC_OPERAND_E2M1",
 ]
 
 CCC_OK = 0
@@ -55,6 +57,12 @@ CCC_OP_METRIC = 1
 CCC_OP_2WAY = 2
 CCC_OP_3WAY = 3
 CCC_MAX_NF = 2097151
+CCC_MMA_E4M3 = 0
+CCC_MMA_E2M1 = 1
+CCC_MMA_E2M1_NVF4 = 2
+CCC_OPERAND_AUTO = 0
+CCC_OPERAND_E4M3 = 1
+CCC_OPERAND_E2M1 = 2
 
 # CCC_LIBRARY selects another build of the library (the bounds-checking one,
 # paper_1705_08213_gb300/_build_checked/libccc_checked.so, in tests).
@@ -89,7 +97,7 @@ class ccc_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("norm", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("group", ctypes.c_int32), ("order", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("split", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("operand", ctypes.c_int32)]
 
 
 _lib = None
@@ -213,13 +221,15 @@ def _panel(geno, n_f):
     return ccc_panel(geno.data_ptr(), int(n_f), int(geno.shape[0]), int(geno.shape[1]))
 
 
-def ccc_opts_default(path=CCC_PATH_TC, norm=CCC_NORM_PERSNP, gamma=None, workspace=None, tile=0):
+def ccc_opts_default(path=CCC_PATH_TC, norm=CCC_NORM_PERSNP, gamma=None, workspace=None, tile=0,
+                     operand=CCC_OPERAND_AUTO):
     """A ccc_opts filled by the library's defaults, then by the given fields."""
     o = ccc_opts()
     load().ccc_opts_default(ctypes.byref(o))
     o.path = int(path)
     o.norm = int(norm)
     o.tile = int(tile)
+    o.operand = int(operand)
     if gamma is not None:
         o.gamma = float(gamma)
     if workspace is not None:
@@ -558,3 +568,42 @@ def ccc_checksum(words, base=0, out=None, stream=None):
                                                _stream(stream)))
     lo, hi = (int(x) & 0xFFFFFFFFFFFFFFFF for x in out.cpu().tolist())
     return lo | (hi << 64)
+
+
+def ccc_mma_rate(kind, n_cols=256, n_mma=8192, clusters=None, stream=None):
+    """Tensor-core rate probe: (cycles per cluster as a list, bad-entry count).
+
+    `clusters` SM pairs (default: all) each issue n_mma M = 256 x N = n_cols MMAs of the kind
+    (CCC_MMA_E4M3, CCC_MMA_E2M1, CCC_MMA_E2M1_NVF4) back to back; synchronises the stream.
+    """
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if clusters is None:
+        clusters = torch.cuda.get_device_properties(dev).multi_processor_count // 2
+    cycles = torch.zeros(int(clusters), dtype=torch.int64, device=dev)
+    bad = torch.zeros(1, dtype=torch.int32, device=dev)
+    lib = load()
+    lib.ccc_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    s = _stream(stream)
+    _check("ccc_mma_rate", lib.ccc_mma_rate(int(kind), int(n_cols), int(n_mma), int(clusters),
+                                            _ptr(cycles), _ptr(bad), s))
+    torch.cuda.synchronize(dev)
+    return cycles.cpu().tolist(), int(bad.item())
+
+
+def ccc_popc_rate(iters=4096, blocks=None, stream=None):
+    """POPC rate probe: cycles of each 1024-thread block (one block per SM by default)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if blocks is None:
+        blocks = torch.cuda.get_device_properties(dev).multi_processor_count
+    cycles = torch.zeros(int(blocks), dtype=torch.int64, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    lib = load()
+    lib.ccc_popc_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+    _check("ccc_popc_rate", lib.ccc_popc_rate(int(iters), int(blocks), _ptr(cycles), _ptr(sink),
+                                              _stream(stream)))
+    torch.cuda.synchronize(dev)
+    return cycles.cpu().tolist()

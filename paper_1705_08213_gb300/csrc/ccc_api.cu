@@ -66,6 +66,9 @@ int query_device(DeviceInfo *info) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+}  // namespace
+
+// Argument checks shared with the allocation-free entry point (ccc_launch.h).
 int check_panel(const ccc_panel *p) {
   if (p == nullptr || p->geno == nullptr) return CCC_EINVAL;
   if (p->n_f < 1 || p->n_v < 1) return CCC_EINVAL;
@@ -89,14 +92,25 @@ int check_opts(const ccc_opts *o) {
   if (o->group < 0 || o->group > 4096 || (o->order != 0 && o->order != 1)) return CCC_EINVAL;
   if (o->tile < 0 || o->tile > 3) return CCC_EINVAL;
   if (o->split < 0 || o->split > 4096) return CCC_EINVAL;
+  if (o->operand < CCC_OPERAND_AUTO || o->operand > CCC_OPERAND_E2M1) return CCC_EINVAL;
   return CCC_OK;
+}
+
+// FP4 (e2m1) operands for a 2-way tensor-core call: built for the SM-pair
+// tiles (tile 0 or 2); automatic = FP4 there.
+bool fp4_2way(const ccc_opts *o) {
+  if (o->path != CCC_PATH_TC || o->operand == CCC_OPERAND_E4M3) return false;
+  return o->tile == 0 || o->tile == 2;
 }
 
 // Options of a 2-way call: tile 3 names a 3-way variant only.
 int check_opts2(const ccc_opts *o) {
   CCC_TRY_INNER(check_opts(o));
+  if (o->operand == CCC_OPERAND_E2M1 && !fp4_2way(o)) return CCC_EUNSUPPORTED;
   return o->tile > 3 ? CCC_EINVAL : CCC_OK;
 }
+
+namespace {
 
 // Workspace layout shared by the 2-way and 3-way calls.
 struct Layout {
@@ -124,7 +138,9 @@ constexpr int kMaxPanelsPerCall = 1024;
 // Bytes of masked 3-way operands staged per batch of slabs.
 constexpr size_t kLopBytes = size_t(2) << 30;
 
-Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
+// fp4: the 2-way operand matrix holds e2m1 counts, two per byte (K padded to
+// 256 entries, rows of kpad / 2 bytes).
+Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0, bool fp4 = false) {
   Layout L;
   size_t off = 0;
   L.status = off;
@@ -135,7 +151,7 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
   off = align_up(off + sizeof(int32_t) * 3 * static_cast<size_t>(n_v), kAlign);
   if (op == CCC_OP_2WAY || op == CCC_OP_3WAY) {
     if (path == CCC_PATH_TC) {
-      L.kpad = round_up(n_f, 128);
+      L.kpad = round_up(n_f, fp4 ? 256 : 128);
       // 2-way tile 3 expands the codes in shared memory: no operand matrix.
       L.rows_pad = (op == CCC_OP_2WAY && tile == 3) ? 0 : tc_rows_pad(n_v);
       off = align_up(off, 1024);
@@ -159,7 +175,7 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0) {
         L.halves = (all_rows > L.mask_rows || n_v > nb) ? 2 : 1;
       }
       off = align_up(off + static_cast<size_t>(L.rows_pad + L.halves * L.mask_rows) *
-                               static_cast<size_t>(L.kpad),
+                               static_cast<size_t>(fp4 ? L.kpad / 2 : L.kpad),
                      1024);
       if (op == CCC_OP_3WAY && (tile == 0 || tile == 3)) {
         // 2-way tallies of all pairs; compacted rows of cbuf_slabs slabs and
@@ -327,11 +343,23 @@ int prep_res(int dev, PrepRes **out) {
 // 2-way tensor-core tally launch with the tile shape chosen by opts->tile;
 // automatic = SM pairs (on GB300 the paired 256 x 256 tile ran the 20,000 x
 // 16,384 panel in 6.43 ms against 7.73 ms for one-SM 128 x 256 tiles).
+// FP4 operands (fp4_2way) run on the SM-pair tiles only.
 static int launch_tally2_tc_auto(const Tally2Args &a, const ccc_opts *o, const uint8_t *op,
                                  int64_t rows_pad, int64_t kpad, int sms, cudaStream_t s) {
   const bool pair = o->tile != 1;
-  return pair ? launch_tally2_tc_pair(a, op, rows_pad, kpad, sms, s)
+  return pair ? launch_tally2_tc_pair(a, op, rows_pad, kpad, sms, s, fp4_2way(o))
               : launch_tally2_tc(a, op, rows_pad, kpad, sms, s);
+}
+
+// Count operands of a 2-way tensor-core call: e2m1 or e4m3 rows, row-major or
+// (blocked_rows > 0) K-block-major.
+static int unpack_2way(const ccc_panel *p, const ccc_opts *o, uint8_t *op, int64_t kpad,
+                       int64_t rows_pad, cudaStream_t s, int64_t blocked_rows = 0) {
+  return fp4_2way(o)
+             ? launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
+                                  blocked_rows)
+             : launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
+                                  blocked_rows);
 }
 
 static bool on_device(const void *p) {
@@ -420,7 +448,8 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
   }
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
-  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY, o->tile);
+  const bool fp4 = fp4_2way(o);
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY, o->tile, fp4);
   CCC_TRY(check_workspace(o, L));
   CCC_TRY(clear_status(o, L, s));
   if (filter != nullptr &&
@@ -460,13 +489,12 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
     // in shared memory; otherwise they are unpacked into the operand matrix.
     const bool packed = o->tile == 3;
     uint8_t *op = packed ? nullptr : at<uint8_t>(o, L.op);
+    // K stages are 128-byte runs of a row: 128 e4m3 or 256 e2m1 entries.
     const int split = (filter == nullptr && i_end < 0 && o->tile != 1 && on_device(tally))
-                          ? k_split(o->split, p->n_v, L.kpad, dev.sms)
+                          ? k_split(o->split, p->n_v, fp4 ? L.kpad / 2 : L.kpad, dev.sms)
                           : 1;
     // The K-split kernel reads its operand K-block-major.
-    if (!packed)
-      CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s,
-                                 split > 1 ? L.rows_pad : 0));
+    if (!packed) CCC_TRY(unpack_2way(p, o, op, L.kpad, L.rows_pad, s, split > 1 ? L.rows_pad : 0));
     if (split > 1) {
       // Partial tallies of the K parts are summed into the zeroed output; the
       // CCC values follow from the complete tallies.
@@ -474,7 +502,7 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
       if (cudaMemsetAsync(tally, 0, bytes, s) != cudaSuccess) return CCC_ECUDA;
       const int slot = timing_begin(s);
       rc = packed ? launch_tally2_tc_pair_split_packed(a, p->geno, p->ld, split, dev.sms, s)
-                  : launch_tally2_tc_pair_split(a, op, L.rows_pad, L.kpad, split, dev.sms, s);
+                  : launch_tally2_tc_pair_split(a, op, L.rows_pad, L.kpad, split, dev.sms, s, fp4);
       timing_end(slot, s);
       if (rc != CCC_OK || out_ccc == nullptr) return rc;
       return launch_metric2(tally, w, p->n_v, a.gamma, a.norm, out_ccc, s);
@@ -515,6 +543,7 @@ struct Run3 {
 static int begin_3way(Run3 &R, const ccc_panel *p, const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_panel(p));
   CCC_TRY(check_opts(o));
+  if (o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;
   if (p->n_v > 65535) return CCC_ERANGE;
   CCC_TRY(query_device(&R.dev));
   R.p = p;
@@ -716,6 +745,7 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
                        const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_opts2(o));
   if (o->tile == 3) return CCC_EINVAL;  // batched panels use the operand matrices
+  if (o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;  // e4m3 operands only
   if (panels == nullptr || tally == nullptr || n < 1 || n > kMaxPanelsPerCall) return CCC_EINVAL;
   for (int k = 0; k < n; ++k) {
     CCC_TRY(check_panel(&panels[k]));
@@ -837,7 +867,7 @@ static int check_panel_multi(const ccc_panel_multi *p) {
 
 static int check_opts_multi(const ccc_opts *o) {
   CCC_TRY(check_opts(o));
-  if (o->path != CCC_PATH_TC) return CCC_EUNSUPPORTED;
+  if (o->path != CCC_PATH_TC || o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;
   return (o->tile == 0 || o->tile == 2) ? CCC_OK : CCC_EINVAL;
 }
 
@@ -962,7 +992,9 @@ int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, siz
   if (panel == nullptr || panel->n_f < 1 || panel->n_v < 1) return CCC_EINVAL;
   if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
   if (op != CCC_OP_2WAY && op != CCC_OP_3WAY && op != CCC_OP_METRIC) return CCC_EINVAL;
-  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile).total;
+  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile,
+                       op == CCC_OP_2WAY && fp4_2way(opts))
+               .total;
   return CCC_OK;
 }
 
@@ -1081,7 +1113,7 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
   if (cudaGetDevice(&d) != cudaSuccess) return CCC_ECUDA;
   StreamRes *R = nullptr;
   CCC_TRY(stream_res(d, &R));
-  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY, o->tile);
+  const Layout L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_2WAY, o->tile, fp4_2way(o));
   CCC_TRY(clear_status(o, L, s));
   if (p->n_v < 2) return CCC_OK;
   const bool want_ccc = host_ccc != nullptr;
@@ -1097,7 +1129,7 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
   const bool packed = o->path == CCC_PATH_TC && o->tile == 3;
   if (o->path == CCC_PATH_TC && !packed) {
     op = at<uint8_t>(o, L.op);
-    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, L.rows_pad / 2, s));
+    CCC_TRY(unpack_2way(p, o, op, L.kpad, L.rows_pad, s));
   } else if (o->path != CCC_PATH_TC) {
     planes = at<uint64_t>(o, L.planes);
     CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));
@@ -1422,6 +1454,32 @@ int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream) {
   CCC_TRY(query_device(&dev));
   return launch_wait_selftest(status, static_cast<uint64_t>(limit_ns),
                               static_cast<cudaStream_t>(stream));
+}
+
+int ccc_mma_rate(int kind, int n_cols, int n_mma, int clusters, int64_t *cycles, int32_t *bad,
+                 void *stream) {
+  if (kind < CCC_MMA_E4M3 || kind > CCC_MMA_E2M1_NVF4) return CCC_EINVAL;
+  if (n_cols != 128 && n_cols != 256) return CCC_EINVAL;
+  if (n_mma < 1 || n_mma > 65536) return CCC_EINVAL;
+  if (cycles == nullptr || !aligned(cycles, 8) || bad == nullptr || !aligned(bad, 4))
+    return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  if (clusters < 1 || clusters > dev.sms / 2) return CCC_EINVAL;
+  NvtxRange nvtx("ccc_mma_rate");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(bad, 0, sizeof(int32_t), s) != cudaSuccess) return CCC_ECUDA;
+  return launch_mma_rate(kind, n_cols, n_mma, clusters, cycles, bad, s);
+}
+
+int ccc_popc_rate(int iters, int blocks, int64_t *cycles, uint64_t *sink, void *stream) {
+  if (iters < 1 || iters > (1 << 24) || blocks < 1 || blocks > 65536) return CCC_EINVAL;
+  if (cycles == nullptr || !aligned(cycles, 8) || sink == nullptr || !aligned(sink, 8))
+    return CCC_EINVAL;
+  DeviceInfo dev;
+  CCC_TRY(query_device(&dev));
+  NvtxRange nvtx("ccc_popc_rate");
+  return launch_popc_rate(iters, blocks, cycles, sink, static_cast<cudaStream_t>(stream));
 }
 
 int ccc_status(const ccc_opts *opts, int32_t *status, void *stream) {

@@ -221,4 +221,32 @@ __host__ __device__ constexpr uint32_t idesc_e4m3_f32(uint32_t m, uint32_t n) {
   return (1u << 4) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
 
+// Instruction descriptor of the block-scaled kinds (kind::mxf4,
+// kind::mxf4nvf4) with A = B = E2M1 (value 1 in bits 7-9 and 10-12), both
+// K-major, dense with K = 64 per instruction (bit 31 = 0), N >> 3 at bits
+// 17-22, the scale-factor type at bit 23 (1 = UE8M0, 0 = UE4M3), M >> 7 at bits
+// 27-28, and scale-factor data ids 0 (bits 4-5 for B, 29-30 for A).  D is FP32.
+__host__ __device__ constexpr uint32_t idesc_e2m1_f32(uint32_t m, uint32_t n, bool ue8m0) {
+  return (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((ue8m0 ? 1u : 0u) << 23) | ((m >> 7) << 27);
+}
+
+// 32 lanes x 32 consecutive 32-bit columns of TMEM written from this thread's
+// registers (lane = the thread's lane of its warp's quarter).
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+      "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]),
+      "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]),
+      "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 }  // namespace ccc

@@ -13,6 +13,42 @@ namespace ccc {
 // Counts one kernel launch and converts a launch failure into CCC_ECUDA.
 int note_launch();
 
+// Launch set-up that the CUDA runtime keeps per device context (a kernel's
+// dynamic shared-memory limit, its cluster occupancy) is cached per device:
+// launchers index their caches with current_device(), which returns the
+// current device, or -1 when it cannot be read or is not below kMaxDevices.
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+  return d;
+}
+
+// Sets the dynamic shared-memory limit of `kernel` on the current device once.
+// Returns CCC_OK or CCC_ECUDA.
+template <class K>
+inline int set_smem_once(K kernel, size_t bytes, bool (&done)[kMaxDevices]) {
+  const int d = current_device();
+  if (d < 0) return CCC_ECUDA;
+  if (done[d]) return CCC_OK;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(bytes)) != cudaSuccess)
+    return CCC_ECUDA;
+  done[d] = true;
+  return CCC_OK;
+}
+
+// Argument checks of the C ABI (ccc_api.cu): a panel (pointer, sizes, stride,
+// alignment, CCC_MAX_NF) and the options of a 2-way call.  CCC_OK or the code
+// the entry point returns.
+int check_panel(const ccc_panel *p);
+int check_opts2(const ccc_opts *o);
+
+// Tensor-core and POPC rate probes (k_peak.cu); see ccc_mma_rate / ccc_popc_rate.
+int launch_mma_rate(int kind, int n_cols, int n_mma, int clusters, int64_t *cycles, int32_t *bad,
+                    cudaStream_t s);
+int launch_popc_rate(int iters, int blocks, int64_t *cycles, uint64_t *sink, cudaStream_t s);
+
 int launch_allele_counts(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld,
                          int32_t *counts, float *w, double gamma, cudaStream_t s);
 int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, double gamma,
@@ -21,6 +57,10 @@ int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, dou
 // operand buffer holding blocked_rows >= 2 snps_pad rows (the K-split kernel
 // reads it so); 0: row-major [2 snps_pad][kpad].
 int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0);
+// The same with e2m1 (FP4) counts, two entries per byte: rows of kpad / 2
+// bytes (kpad a multiple of 256); blocked: [kpad / 256][blocked_rows][128].
+int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                        int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0);
 int launch_planes(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint64_t *planes,
                   int64_t w64, cudaStream_t s);
@@ -82,13 +122,17 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
 // Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
 int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1);
 // 256 x 256 tiles on SM pairs (cta_group::2); same arguments as launch_tally2_tc.
+// fp4: op holds e2m1 rows of kpad / 2 bytes (launch_unpack_e2m1, kpad a
+// multiple of 256) and the tiles run on the block-scaled FP4 MMA.
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
-                          int num_sms, cudaStream_t s);
-// The same with the K dimension split into `split` parts (1 <= split <= kpad /
-// 128) whose partial tallies are added into a.tally with integer reductions
-// (a.tally must be zero; no CCC values, no thresholded output).
+                          int num_sms, cudaStream_t s, bool fp4 = false);
+// The same with the K dimension split into `split` parts (1 <= split <= the
+// 128-byte K stages of a row) whose partial tallies are added into a.tally
+// with integer reductions (a.tally must be zero; no CCC values, no thresholded
+// output).  The operand is K-block-major (launch_unpack_* with blocked_rows).
 int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t rows_pad,
-                                int64_t kpad, int split, int num_sms, cudaStream_t s);
+                                int64_t kpad, int split, int num_sms, cudaStream_t s,
+                                bool fp4 = false);
 // The two launches above with the operand preparation fused in: the kernel
 // reads the packed panel geno (row stride ld words, even; 16-byte aligned)
 // and expands the codes into count rows in shared memory.

@@ -11,9 +11,10 @@
 // file-scope device array of fixed size, which every GPU that loads the
 // library holds until the process exits.
 //
-// The computation is exactly that of ccc2_tally_metric with opts->path ==
-// CCC_PATH_TC: the same kernels, launched in the same order, on the same data
-// layout; only the scratch addresses differ.
+// The computation is that of ccc2_tally_metric with opts->path == CCC_PATH_TC
+// and the K split off: the tile variant opts->tile selects (the SM-pair
+// kernel unless it is 1), on the same data layout, with bit-identical results;
+// only the scratch addresses differ.
 #include <mutex>
 
 #include "ccc_launch.h"
@@ -26,7 +27,6 @@ constexpr size_t kScratchBytes = size_t(32) << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 
@@ -51,19 +51,19 @@ extern "C" int ccc2_tally_metric_noalloc(const ccc_panel *p, int32_t *tally, flo
                                          int32_t *status, const ccc_opts *o, void *stream) {
   using namespace ccc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Arguments: as for ccc2_tally_metric; the workspace fields of *o are ignored.
-  if (p == nullptr || p->geno == nullptr || o == nullptr || tally == nullptr || out_ccc == nullptr)
-    return CCC_EINVAL;
-  if (p->n_f < 1 || p->n_v < 1 || p->ld < (p->n_f + 31) / 32 || (p->ld & 1) != 0) return CCC_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(p->geno) & 15) != 0 ||
-      (reinterpret_cast<uintptr_t>(tally) & 15) != 0 ||
+  // Arguments: as for ccc2_tally_metric (the workspace fields of *o are
+  // ignored); the tensor-core path only, unsplit, with the operand matrix in the
+  // scratch (not tile 3).
+  int rc = check_panel(p);
+  if (rc != CCC_OK) return rc;
+  rc = check_opts2(o);
+  if (rc != CCC_OK) return rc;
+  if (o->path != CCC_PATH_TC || o->tile == 3 || o->split > 1) return CCC_EINVAL;
+  if (o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;  // e4m3 operands in the scratch
+  if (tally == nullptr || (reinterpret_cast<uintptr_t>(tally) & 15) != 0 ||
       (reinterpret_cast<uintptr_t>(out_ccc) & 15) != 0 ||
       (reinterpret_cast<uintptr_t>(status) & 3) != 0)
     return CCC_EINVAL;
-  if (o->path != CCC_PATH_TC) return CCC_EINVAL;
-  if (o->norm != CCC_NORM_PERSNP && o->norm != CCC_NORM_JOINT) return CCC_EINVAL;
-  if (!(o->gamma >= 0.0 && o->gamma <= 1.0)) return CCC_EINVAL;
-  if (p->n_f > CCC_MAX_NF) return CCC_ERANGE;
 
   // Scratch layout: [status 256 B][factors n_v x 2 floats][e4m3 operands].
   const int64_t kpad = (p->n_f + 127) / 128 * 128;
@@ -91,8 +91,7 @@ extern "C" int ccc2_tally_metric_noalloc(const ccc_panel *p, int32_t *tally, flo
   if (cudaMemsetAsync(st, 0, sizeof(int32_t), s) != cudaSuccess) return CCC_ECUDA;
   if (p->n_v < 2) return CCC_OK;
 
-  int rc;
-  if (o->norm == CCC_NORM_PERSNP) {
+  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP) {
     rc = launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s);
     if (rc != CCC_OK) return rc;
   }
@@ -105,8 +104,10 @@ extern "C" int ccc2_tally_metric_noalloc(const ccc_panel *p, int32_t *tally, flo
   a.status = st;
   a.gamma = static_cast<float>(o->gamma);
   a.norm = o->norm;
+  a.group = o->group;
   a.out_len = pairs_in_rows(p->n_v, 0, p->n_v);
   rc = launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s);
   if (rc != CCC_OK) return rc;
-  return launch_tally2_tc(a, op, rows_pad, kpad, sms, s);
+  return o->tile == 1 ? launch_tally2_tc(a, op, rows_pad, kpad, sms, s)
+                      : launch_tally2_tc_pair(a, op, rows_pad, kpad, sms, s);
 }

@@ -70,10 +70,11 @@ struct EpiMulti {
   static constexpr int PW = snps_per_quarter(S);
   static constexpr int STAGE_BYTES_PER_WARP = 0;
 
-  template <int NC>
+  template <int NC, bool PRELOAD = false>
   __device__ static void tile(const Params &args, const TriSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *) {
+    static_assert(!PRELOAD, "s-state tiles run on the two-accumulator pipeline");
     const int u = lane / S;
     const int a = lane - u * S;
     const int64_t n_v = args.n_v;
@@ -158,10 +159,11 @@ struct EpiMultiSplit {
   static constexpr int PW = snps_per_quarter(S);
   static constexpr int STAGE_BYTES_PER_WARP = 0;
 
-  template <int NC>
+  template <int NC, bool PRELOAD = false>
   __device__ static void tile(const Params &args, const SplitSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *) {
+    static_assert(!PRELOAD, "s-state tiles run on the two-accumulator pipeline");
     const int u = lane / S;
     const int a = lane - u * S;
     const int64_t n_v = args.n_v;
@@ -234,7 +236,10 @@ int multi_max_clusters(K kernel, int num_sms) {
 template <int S>
 int launch_tally2_multi_split_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB, int group,
                                 int nkb, int split, int num_sms, cudaStream_t s) {
-  static int max_clusters = 0;
+  static int max_clusters_dev[kMaxDevices] = {};
+  const int dev_c = current_device();
+  if (dev_c < 0) return CCC_ECUDA;
+  int &max_clusters = max_clusters_dev[dev_c];
   if (max_clusters == 0) max_clusters = multi_max_clusters(k_tally2_multi_split<S>, num_sms);
   if (max_clusters == 0) return CCC_ECUDA;
   if (split < 1 || split > nkb) return CCC_EINVAL;
@@ -274,7 +279,10 @@ int launch_tally2_multi_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB,
   const int64_t rows = sp.I1 > sp.I0 ? sp.I1 - sp.I0 : 0;
   const int64_t tiles = rows * nB - (static_cast<int64_t>(sp.I0) + sp.I1 - 1) * rows / 2;
   if (tiles <= 0) return CCC_OK;
-  static int max_clusters = 0;
+  static int max_clusters_dev[kMaxDevices] = {};
+  const int dev_c = current_device();
+  if (dev_c < 0) return CCC_ECUDA;
+  int &max_clusters = max_clusters_dev[dev_c];
   if (max_clusters == 0) {
     if (cudaFuncSetAttribute(k_tally2_multi<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)

@@ -154,6 +154,63 @@ __global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, in
   *reinterpret_cast<uint4 *>(d1) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
 }
 
+// Spread the sixteen 2-bit fields of x into the low two bits of sixteen 4-bit
+// fields (field q of x -> bits 4q, 4q + 1 of the result).
+__device__ __forceinline__ uint64_t spread_2to4(uint32_t x32) {
+  uint64_t x = x32;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  return x;
+}
+
+// FP4 (e2m1) operand rows: as k_unpack_e4m3, with each count 0, 1, 2 stored as
+// the e2m1 nibble 0x0, 0x2, 0x4 (2^(e-1) (1 + m/2) with e, m = 1, 0 and 2, 0),
+// two entries per byte, entry q in the low nibble of byte q / 2 for even q.
+// A row holds kpad / 2 bytes (kpad a multiple of 256: one 128-byte K stage is
+// 256 entries).  One thread per packed word: 32 entries -> 16 bytes in each of
+// the two rows, so that each warp store covers 512 contiguous bytes of a row.
+// Per 2-bit field with l = low and h = high code bit: rho(1) = l + (l & h) and,
+// for a present entry (not h & ~l), rho(0) = 2 - l; both are 0 when missing.
+__global__ void k_unpack_e2m1(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
+                              int64_t ld, uint8_t *__restrict__ op, int64_t kpad,
+                              int64_t snps_pad, int64_t blocked_rows) {
+  const int64_t wpr = kpad / 32;  // packed words (32 entries) per operand row
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= wpr * snps_pad) return;
+  const int64_t i = t / wpr;
+  const int64_t k = t - i * wpr;
+  uint64_t v = 0xAAAAAAAAAAAAAAAAull;  // all entries "missing" -> zero operands
+  if (i < n_v && k * 32 < n_f) {
+    const uint64_t valid = valid_even_mask(k, n_f);
+    const uint64_t vm = valid | (valid << 1);
+    v = (__ldg(geno + i * ld + k) & vm) | (0xAAAAAAAAAAAAAAAAull & ~vm);
+  }
+  uint64_t n0[2], n1[2];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const uint32_t x = static_cast<uint32_t>(v >> (32 * half));
+    const uint32_t l = x & 0x55555555u;
+    const uint32_t h = (x >> 1) & 0x55555555u;
+    const uint32_t nh = ~h & 0x55555555u;
+    const uint32_t rho1 = l + (l & h);         // 2-bit fields 0, 1, 2
+    const uint32_t rho0 = (nh << 1) - (l & nh);  // no borrow between fields
+    n0[half] = spread_2to4(rho0) << 1;
+    n1[half] = spread_2to4(rho1) << 1;
+  }
+  // Row-major [row][kpad / 2], or K-block-major [kpad / 256][blocked_rows][128].
+  uint8_t *d0 = blocked_rows > 0 ? op + ((k >> 3) * blocked_rows + 2 * i) * 128 + (k & 7) * 16
+                                 : op + (2 * i) * (kpad / 2) + k * 16;
+  uint8_t *d1 = blocked_rows > 0 ? d0 + 128 : d0 + kpad / 2;
+  *reinterpret_cast<uint4 *>(d0) =
+      make_uint4(static_cast<uint32_t>(n0[0]), static_cast<uint32_t>(n0[0] >> 32),
+                 static_cast<uint32_t>(n0[1]), static_cast<uint32_t>(n0[1] >> 32));
+  *reinterpret_cast<uint4 *>(d1) =
+      make_uint4(static_cast<uint32_t>(n1[0]), static_cast<uint32_t>(n1[0] >> 32),
+                 static_cast<uint32_t>(n1[1]), static_cast<uint32_t>(n1[1] >> 32));
+}
+
 // Gather the 32 even-position bits of x into the low 32 bits.
 __device__ __forceinline__ uint64_t compact_even(uint64_t x) {
   x &= kEven;
@@ -239,6 +296,18 @@ int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
   const int64_t total = (kpad / 16) * snps_pad;
   const int64_t blocks = (total + threads - 1) / threads;
   k_unpack_e4m3<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
+                                                                   snps_pad, blocked_rows);
+  return note_launch();
+}
+
+int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows) {
+  if (kpad % 256 != 0) return CCC_EINVAL;
+  if (blocked_rows != 0 && blocked_rows < 2 * snps_pad) return CCC_EINVAL;
+  const int threads = 256;
+  const int64_t total = (kpad / 32) * snps_pad;
+  const int64_t blocks = (total + threads - 1) / threads;
+  k_unpack_e2m1<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
                                                                    snps_pad, blocked_rows);
   return note_launch();
 }

@@ -47,8 +47,9 @@ struct Epi2 {
 
   // Accumulator lane = A row (2i + a) of the tile, column = 2j + b.  The
   // release arrive goes to a CTA-local barrier, or (CLUSTER) to a barrier given
-  // by its cluster address.
-  template <int NC, bool CLUSTER>
+  // by its cluster address.  PRELOAD (cluster only): all NC chunks are loaded,
+  // and the accumulator released, before the first is processed.
+  template <int NC, bool CLUSTER, bool PRELOAD = false>
   __device__ static void body(const Params &args, Tile2 sc, int quarter, int lane,
                               uint32_t t_base, uint32_t release_bar, int c0) {
     const int row = quarter * 32 + lane;
@@ -64,66 +65,87 @@ struct Epi2 {
       wi1 = __ldg(args.w + 2 * i + 1);
     }
     const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1;  // pair index = row_base + j
-    for (int c = c0; c < c0 + NC; ++c) {
-      uint32_t v[32];
-      tmem_ld_32x32b_x32(t_base + c * 32, v);
-      tmem_ld_wait();
-      if (c == c0 + NC - 1) {
-        tc_fence_before();
-        if (CLUSTER)
-          mbar_arrive_cluster(release_bar);
-        else
-          mbar_arrive(release_bar);
-      }
+    if constexpr (PRELOAD) {
+      static_assert(CLUSTER, "the preloading epilogue releases at cluster scope");
+      uint32_t pre[NC][32];
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        // columns 4p, 4p+1: j even (b = 0, 1); columns 4p+2, 4p+3: j odd.
-        const float e0 = __uint_as_float(v[4 * p + 0]);
-        const float e1 = __uint_as_float(v[4 * p + 1]);
-        const float o0 = __uint_as_float(v[4 * p + 2]);
-        const float o1 = __uint_as_float(v[4 * p + 3]);
-        // Allele-0 rows keep the even j and take the partner's (r10, r11);
-        // allele-1 rows keep the odd j and take the partner's (r00, r01).
-        const float g0 = __shfl_xor_sync(0xffffffffu, a ? e0 : o0, 1);
-        const float g1 = __shfl_xor_sync(0xffffffffu, a ? e1 : o1, 1);
-        int32_t r00, r01, r10, r11;
-        if (a == 0) {
-          r00 = __float2int_rn(e0);
-          r01 = __float2int_rn(e1);
-          r10 = __float2int_rn(g0);
-          r11 = __float2int_rn(g1);
-        } else {
-          r00 = __float2int_rn(g0);
-          r01 = __float2int_rn(g1);
-          r10 = __float2int_rn(o0);
-          r11 = __float2int_rn(o1);
+      for (int cc = 0; cc < NC; ++cc) tmem_ld_32x32b_x32(t_base + (c0 + cc) * 32, pre[cc]);
+      tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive_cluster(release_bar);
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc)
+        chunk(args, sc, a, i, row_base, wi0, wi1, filter, want_ccc, c0 + cc, pre[cc]);
+    } else {
+      for (int c = c0; c < c0 + NC; ++c) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(t_base + c * 32, v);
+        tmem_ld_wait();
+        if (c == c0 + NC - 1) {
+          tc_fence_before();
+          if (CLUSTER)
+            mbar_arrive_cluster(release_bar);
+          else
+            mbar_arrive(release_bar);
         }
-        const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + 2 * p + a;
-        if (i < j && j < n_v && i >= args.i_begin && i < args.i_end) {
-          const int64_t pidx = row_base + j - args.pair0;
-          if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
-          // Streaming stores: the output passes through L2 once and should not
-          // evict the operand blocks that other tiles still read.
-          if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
-          if (want_ccc) {
-            float wj0 = 1.f, wj1 = 1.f;
-            if (args.norm == CCC_NORM_PERSNP) {
-              const float2 wj = __ldg(reinterpret_cast<const float2 *>(args.w) + j);
-              wj0 = wj.x;
-              wj1 = wj.y;
-            }
-            // Thresholded output: most pairs are ruled out without a division.
-            const bool skip = filter && args.norm == CCC_NORM_PERSNP &&
-                              !may_exceed(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.threshold);
-            if (!skip) {
-              const float4 cv =
-                  ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
-              if (filter)
-                filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10,
-                            r11, cv);
-              else
-                __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
-            }
+        chunk(args, sc, a, i, row_base, wi0, wi1, filter, want_ccc, c, v);
+      }
+    }
+  }
+
+  // The 32 columns of chunk c of lane (i, a): 16 SNPs j, tallies and CCC values.
+  __device__ __forceinline__ static void chunk(const Params &args, Tile2 sc, int a, int64_t i,
+                                               int64_t row_base, float wi0, float wi1, bool filter,
+                                               bool want_ccc, int c, const uint32_t (&v)[32]) {
+    const int64_t n_v = args.n_v;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      // columns 4p, 4p+1: j even (b = 0, 1); columns 4p+2, 4p+3: j odd.
+      const float e0 = __uint_as_float(v[4 * p + 0]);
+      const float e1 = __uint_as_float(v[4 * p + 1]);
+      const float o0 = __uint_as_float(v[4 * p + 2]);
+      const float o1 = __uint_as_float(v[4 * p + 3]);
+      // Allele-0 rows keep the even j and take the partner's (r10, r11);
+      // allele-1 rows keep the odd j and take the partner's (r00, r01).
+      const float g0 = __shfl_xor_sync(0xffffffffu, a ? e0 : o0, 1);
+      const float g1 = __shfl_xor_sync(0xffffffffu, a ? e1 : o1, 1);
+      int32_t r00, r01, r10, r11;
+      if (a == 0) {
+        r00 = __float2int_rn(e0);
+        r01 = __float2int_rn(e1);
+        r10 = __float2int_rn(g0);
+        r11 = __float2int_rn(g1);
+      } else {
+        r00 = __float2int_rn(g0);
+        r01 = __float2int_rn(g1);
+        r10 = __float2int_rn(o0);
+        r11 = __float2int_rn(o1);
+      }
+      const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + 2 * p + a;
+      if (i < j && j < n_v && i >= args.i_begin && i < args.i_end) {
+        const int64_t pidx = row_base + j - args.pair0;
+        if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
+        // Streaming stores: the output passes through L2 once and should not
+        // evict the operand blocks that other tiles still read.
+        if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
+        if (want_ccc) {
+          float wj0 = 1.f, wj1 = 1.f;
+          if (args.norm == CCC_NORM_PERSNP) {
+            const float2 wj = __ldg(reinterpret_cast<const float2 *>(args.w) + j);
+            wj0 = wj.x;
+            wj1 = wj.y;
+          }
+          // Thresholded output: most pairs are ruled out without a division.
+          const bool skip = filter && args.norm == CCC_NORM_PERSNP &&
+                            !may_exceed(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.threshold);
+          if (!skip) {
+            const float4 cv =
+                ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
+            if (filter)
+              filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10,
+                          r11, cv);
+            else
+              __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
           }
         }
       }
@@ -143,65 +165,84 @@ struct Epi2Staged {
   static constexpr int STRIDE = 33;
   static constexpr int STAGE_BYTES_PER_WARP = 32 * STRIDE * 4;
 
-  template <int NC>
+  // PRELOAD: all NC chunks are loaded, and the accumulator released, before
+  // the first is processed.
+  template <int NC, bool PRELOAD = false>
   __device__ static void body(const Tally2Args &args, Tile2 sc, int quarter, int lane,
                               uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *stage) {
+    if constexpr (PRELOAD) {
+      uint32_t pre[NC][32];
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) tmem_ld_32x32b_x32(t_base + (c0 + cc) * 32, pre[cc]);
+      tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive_cluster(release_cluster_bar);
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) chunk(args, sc, quarter, lane, c0 + cc, pre[cc], stage);
+    } else {
+      for (int c = c0; c < c0 + NC; ++c) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(t_base + c * 32, v);
+        tmem_ld_wait();
+        if (c == c0 + NC - 1) {
+          tc_fence_before();
+          mbar_arrive_cluster(release_cluster_bar);
+        }
+        chunk(args, sc, quarter, lane, c, v, stage);
+      }
+    }
+  }
+
+  __device__ __forceinline__ static void chunk(const Tally2Args &args, Tile2 sc, int quarter,
+                                               int lane, int c, const uint32_t (&v)[32],
+                                               float *stage) {
     const int64_t n_v = args.n_v;
     const bool filter = args.hits != nullptr;
     const bool want_ccc = filter || args.ccc != nullptr;
     const bool persnp = args.norm == CCC_NORM_PERSNP;
     const int jl = lane & 15;
     const int64_t i0 = static_cast<int64_t>(sc.I) * SNP_I + quarter * 16 + (lane >> 4);
-    for (int c = c0; c < c0 + NC; ++c) {
-      uint32_t v[32];
-      tmem_ld_32x32b_x32(t_base + c * 32, v);
-      tmem_ld_wait();
-      if (c == c0 + NC - 1) {
-        tc_fence_before();
-        mbar_arrive_cluster(release_cluster_bar);
-      }
-      __syncwarp();  // the previous chunk's reads are done
+    __syncwarp();  // the previous chunk's reads are done
 #pragma unroll
-      for (int k = 0; k < 32; ++k) stage[lane * STRIDE + k] = __uint_as_float(v[k]);
-      __syncwarp();
-      const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + jl;
-      float wj0 = 1.f, wj1 = 1.f;
-      if (want_ccc && persnp && j < n_v) {
-        const float2 wj = __ldg(reinterpret_cast<const float2 *>(args.w) + j);
-        wj0 = wj.x;
-        wj1 = wj.y;
-      }
+    for (int k = 0; k < 32; ++k) stage[lane * STRIDE + k] = __uint_as_float(v[k]);
+    __syncwarp();
+    const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + jl;
+    float wj0 = 1.f, wj1 = 1.f;
+    if (want_ccc && persnp && j < n_v) {
+      const float2 wj = __ldg(reinterpret_cast<const float2 *>(args.w) + j);
+      wj0 = wj.x;
+      wj1 = wj.y;
+    }
 #pragma unroll 2
-      for (int t = 0; t < 8; ++t) {
-        const int il = 2 * t + (lane >> 4);  // SNP i of this store within the chunk's 16
-        const int64_t i = i0 + 2 * t;
-        const float *r0 = stage + (2 * il) * STRIDE + 2 * jl;  // row (i, 0)
-        const float *r1 = r0 + STRIDE;                          // row (i, 1)
-        const int32_t r00 = __float2int_rn(r0[0]);
-        const int32_t r01 = __float2int_rn(r0[1]);
-        const int32_t r10 = __float2int_rn(r1[0]);
-        const int32_t r11 = __float2int_rn(r1[1]);
-        if (!(i < j && j < n_v && i >= args.i_begin && i < args.i_end)) continue;
-        const int64_t pidx = i * (2 * n_v - i - 1) / 2 - i - 1 + j - args.pair0;
-        if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
-        if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
-        if (!want_ccc) continue;
-        float wi0 = 1.f, wi1 = 1.f;
-        if (persnp) {
-          const float2 wi = __ldg(reinterpret_cast<const float2 *>(args.w) + i);
-          wi0 = wi.x;
-          wi1 = wi.y;
-        }
-        const bool skip = filter && persnp &&
-                          !may_exceed(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.threshold);
-        if (skip) continue;
-        const float4 cv = ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
-        if (filter)
-          filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10, r11, cv);
-        else
-          __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
+    for (int t = 0; t < 8; ++t) {
+      const int il = 2 * t + (lane >> 4);  // SNP i of this store within the chunk's 16
+      const int64_t i = i0 + 2 * t;
+      const float *r0 = stage + (2 * il) * STRIDE + 2 * jl;  // row (i, 0)
+      const float *r1 = r0 + STRIDE;                          // row (i, 1)
+      const int32_t r00 = __float2int_rn(r0[0]);
+      const int32_t r01 = __float2int_rn(r0[1]);
+      const int32_t r10 = __float2int_rn(r1[0]);
+      const int32_t r11 = __float2int_rn(r1[1]);
+      if (!(i < j && j < n_v && i >= args.i_begin && i < args.i_end)) continue;
+      const int64_t pidx = i * (2 * n_v - i - 1) / 2 - i - 1 + j - args.pair0;
+      if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
+      if (!filter) __stcs(reinterpret_cast<int4 *>(args.tally) + pidx, make_int4(r00, r01, r10, r11));
+      if (!want_ccc) continue;
+      float wi0 = 1.f, wi1 = 1.f;
+      if (persnp) {
+        const float2 wi = __ldg(reinterpret_cast<const float2 *>(args.w) + i);
+        wi0 = wi.x;
+        wi1 = wi.y;
       }
+      const bool skip = filter && persnp &&
+                        !may_exceed(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.threshold);
+      if (skip) continue;
+      const float4 cv = ccc2_values(r00, r01, r10, r11, wi0, wi1, wj0, wj1, args.norm, args.gamma);
+      if (filter)
+        filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, j, r00, r01, r10, r11, cv);
+      else
+        __stcs(reinterpret_cast<float4 *>(args.ccc) + pidx, cv);
     }
   }
 };
@@ -221,16 +262,16 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1)
 struct Epi2Pair {
   using Params = Tally2Args;
   static constexpr int STAGE_BYTES_PER_WARP = Epi2Staged::STAGE_BYTES_PER_WARP;
-  template <int NC>
+  template <int NC, bool PRELOAD = false>
   __device__ static void tile(const Params &args, const TriSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *stage) {
     if (args.hits != nullptr)  // thresholded output stores little: no staging
-      Epi2::body<NC, true>(args, Tile2{2 * sc.I + rank, sc.J}, quarter, lane, t_base,
-                           release_cluster_bar, c0);
+      Epi2::body<NC, true, PRELOAD>(args, Tile2{2 * sc.I + rank, sc.J}, quarter, lane, t_base,
+                                    release_cluster_bar, c0);
     else
-      Epi2Staged::body<NC>(args, Tile2{2 * sc.I + rank, sc.J}, quarter, lane, t_base,
-                           release_cluster_bar, c0, stage);
+      Epi2Staged::body<NC, PRELOAD>(args, Tile2{2 * sc.I + rank, sc.J}, quarter, lane, t_base,
+                                    release_cluster_bar, c0, stage);
   }
 };
 
@@ -241,6 +282,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
   tcp::persistent_gemm_pair<TriSchedPair, Epi2Pair, EW>(&tm, sp, args, nkb, args.status);
 }
 
+// FP4 (e2m1) operands: one accumulator, 8 epilogue warps that load their whole
+// quarter-half before releasing it (tcp::persistent_gemm_pair, FP4).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_EW, 1)
+    k_tally2_tc_pair_fp4(const __grid_constant__ CUtensorMap tm, const Tally2Args args,
+                         TriSched::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<TriSchedPair, Epi2Pair, tcp::FP4_EW, false, true>(&tm, sp, args, nkb,
+                                                                              args.status);
+}
+
 // ---------------------------------------------------------------- split K
 
 // Partial tallies of one K part, added into the zeroed tally array with
@@ -249,32 +299,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
 struct Epi2Split {
   using Params = Tally2Args;
   static constexpr int STAGE_BYTES_PER_WARP = 0;
-  template <int NC>
+  template <int NC, bool PRELOAD = false>
   __device__ static void tile(const Params &args, const SplitSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *) {
     const int row = quarter * 32 + lane;
     const int a = row & 1;
-    const int64_t n_v = args.n_v;
     const int64_t i = static_cast<int64_t>(2 * sc.I + rank) * SNP_I + (row >> 1);
-    const bool row_ok = i < n_v && i >= args.i_begin && i < args.i_end;
-    const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1 - args.pair0;
-    for (int c = c0; c < c0 + NC; ++c) {
-      uint32_t v[32];
-      tmem_ld_32x32b_x32(t_base + c * 32, v);
-      tmem_ld_wait();
-      if (c == c0 + NC - 1) {
-        tc_fence_before();
-        mbar_arrive_cluster(release_cluster_bar);
-      }
+    const bool row_ok = i < args.n_v && i >= args.i_begin && i < args.i_end;
+    const int64_t row_base = i * (2 * args.n_v - i - 1) / 2 - i - 1 - args.pair0;
+    if constexpr (PRELOAD) {
+      uint32_t pre[NC][32];
 #pragma unroll
-      for (int col = 0; col < 32; ++col) {
-        const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + (col >> 1);
-        const int32_t r = __float2int_rn(__uint_as_float(v[col]));
-        if (row_ok && i < j && j < n_v && r != 0 &&
-            CCC_IN_BOUNDS(row_base + j, args.out_len, args.status))
-          atomicAdd(args.tally + (row_base + j) * 4 + 2 * a + (col & 1), r);
+      for (int cc = 0; cc < NC; ++cc) tmem_ld_32x32b_x32(t_base + (c0 + cc) * 32, pre[cc]);
+      tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive_cluster(release_cluster_bar);
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) chunk(args, sc, a, i, row_ok, row_base, c0 + cc, pre[cc]);
+    } else {
+      for (int c = c0; c < c0 + NC; ++c) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(t_base + c * 32, v);
+        tmem_ld_wait();
+        if (c == c0 + NC - 1) {
+          tc_fence_before();
+          mbar_arrive_cluster(release_cluster_bar);
+        }
+        chunk(args, sc, a, i, row_ok, row_base, c, v);
       }
+    }
+  }
+
+  __device__ __forceinline__ static void chunk(const Params &args, const SplitSchedPair &sc, int a,
+                                               int64_t i, bool row_ok, int64_t row_base, int c,
+                                               const uint32_t (&v)[32]) {
+#pragma unroll
+    for (int col = 0; col < 32; ++col) {
+      const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + (col >> 1);
+      const int32_t r = __float2int_rn(__uint_as_float(v[col]));
+      if (row_ok && i < j && j < args.n_v && r != 0 &&
+          CCC_IN_BOUNDS(row_base + j, args.out_len, args.status))
+        atomicAdd(args.tally + (row_base + j) * 4 + 2 * a + (col & 1), r);
     }
   }
 };
@@ -284,6 +350,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
     k_tally2_tc_pair_split(const __grid_constant__ CUtensorMap tm, const Tally2Args args,
                            SplitSchedPair::Params sp, int nkb) {
   tcp::persistent_gemm_pair<SplitSchedPair, Epi2Split, EW, true>(&tm, sp, args, nkb, args.status);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_EW, 1)
+    k_tally2_tc_pair_split_fp4(const __grid_constant__ CUtensorMap tm, const Tally2Args args,
+                               SplitSchedPair::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<SplitSchedPair, Epi2Split, tcp::FP4_EW, true, true>(&tm, sp, args, nkb,
+                                                                                args.status);
 }
 
 // ---------------------------------------------------------------- packed operands
@@ -381,12 +454,12 @@ struct BatchSchedPair : BatchSchedT<TriSchedPair> {};
 struct EpiBatchPair {
   using Params = BatchParams;
   static constexpr int STAGE_BYTES_PER_WARP = Epi2Staged::STAGE_BYTES_PER_WARP;
-  template <int NC>
+  template <int NC, bool PRELOAD = false>
   __device__ static void tile(const Params &bp, const BatchSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *stage) {
-    Epi2Staged::body<NC>(bp.p[sc.p].args, Tile2{2 * sc.t.I + rank, sc.t.J}, quarter, lane, t_base,
-                         release_cluster_bar, c0, stage);
+    Epi2Staged::body<NC, PRELOAD>(bp.p[sc.p].args, Tile2{2 * sc.t.I + rank, sc.t.J}, quarter, lane,
+                                  t_base, release_cluster_bar, c0, stage);
   }
 };
 
@@ -479,9 +552,11 @@ int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1) {
 int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *ops,
                                   const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                                   int num_sms, cudaStream_t s) {
-  static bool attr_set = false;
+  static bool attr_set[kMaxDevices] = {};
   if (n < 1 || n > kMaxBatchPanels) return CCC_EINVAL;
-  if (!attr_set) {
+  const int dev = current_device();
+  if (dev < 0) return CCC_ECUDA;
+  if (!attr_set[dev]) {
     if (cudaFuncSetAttribute(k_tally2_tc_pair_batched<4>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(pair_smem(4))) != cudaSuccess ||
@@ -489,7 +564,7 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(pair_smem(8))) != cudaSuccess)
       return CCC_ECUDA;
-    attr_set = true;
+    attr_set[dev] = true;
   }
   thread_local BatchMaps maps;
   thread_local BatchParams bp;
@@ -514,8 +589,8 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
   }
   if (tiles == 0) return CCC_OK;
   const int ew = epilogue_warps(static_cast<int>(kw / static_cast<double>(tiles)));
-  static int max_clusters[2] = {0, 0};
-  int &mc = max_clusters[ew == 4 ? 0 : 1];
+  static int max_clusters[kMaxDevices][2] = {};
+  int &mc = max_clusters[dev][ew == 4 ? 0 : 1];
   if (mc == 0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
@@ -547,15 +622,17 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
 int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
                              const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                              int num_sms, cudaStream_t s) {
-  static bool attr_set = false;
+  static bool attr_set[kMaxDevices] = {};
   if (n < 1 || n > kMaxBatchPanels) return CCC_EINVAL;
-  if (!attr_set) {
+  const int dev = current_device();
+  if (dev < 0) return CCC_ECUDA;
+  if (!attr_set[dev]) {
     if (cudaFuncSetAttribute(k_tally2_tc_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES)) != cudaSuccess ||
         cudaFuncSetAttribute(k_tally2_tc_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES)) != cudaSuccess)
       return CCC_ECUDA;
-    attr_set = true;
+    attr_set[dev] = true;
   }
   thread_local BatchMaps maps;
   thread_local BatchParams bp;
@@ -592,18 +669,26 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
 }
 
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
-                          int num_sms, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
+                          int num_sms, cudaStream_t s, bool fp4) {
+  static bool attr_set[kMaxDevices] = {};
+  const int dev = current_device();
+  if (dev < 0) return CCC_ECUDA;
+  if (!attr_set[dev]) {
     if (cudaFuncSetAttribute(k_tally2_tc_pair<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(pair_smem(4))) != cudaSuccess ||
         cudaFuncSetAttribute(k_tally2_tc_pair<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(pair_smem(8))) != cudaSuccess)
+                             static_cast<int>(pair_smem(8))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_pair_fp4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(pair_smem(tcp::FP4_EW))) != cudaSuccess)
       return CCC_ECUDA;
-    attr_set = true;
+    attr_set[dev] = true;
   }
+  // e2m1 rows hold two entries per byte: kpad entries in kpad / 2 bytes, and
+  // each 128-byte K stage covers 256 entries.
+  if (fp4 && kpad % 256 != 0) return CCC_EINVAL;
+  const int64_t row_bytes = fp4 ? kpad / 2 : kpad;
   CUtensorMap tm;
-  if (!make_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
+  if (!make_operand_map(&tm, op, rows_pad, row_bytes, tcp::BMH)) return CCC_ECUDA;
   TriSched::Params sp;
   sp.nI = static_cast<int>((a.n_v + 127) / 128);
   sp.nJ = sp.nI;
@@ -611,13 +696,13 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
   sp.shift = 0;
   sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / 128);
   sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.nI);
-  const int nkb = static_cast<int>(kpad / BK);
+  const int nkb = static_cast<int>(row_bytes / BK);
   const int64_t tiles = tc2_pair_tiles(a.n_v, sp.I0, sp.I1);
   if (tiles == 0) return CCC_OK;
-  const int ew = epilogue_warps(nkb);
+  const int ew = fp4 ? tcp::FP4_EW : epilogue_warps(nkb);
   // Persistent grid: as many SM pairs as can be resident at once.
-  static int max_clusters[2] = {0, 0};
-  int &mc = max_clusters[ew == 4 ? 0 : 1];
+  static int max_clusters[kMaxDevices][3] = {};
+  int &mc = max_clusters[dev][fp4 ? 2 : ew == 4 ? 0 : 1];
   if (mc == 0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
@@ -632,14 +717,17 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
     cfg.numAttrs = 1;
     int n = 0;
     const cudaError_t e =
-        ew == 4 ? cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair<4>, &cfg)
-                : cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair<8>, &cfg);
+        fp4 ? cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair_fp4, &cfg)
+        : ew == 4 ? cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair<4>, &cfg)
+                  : cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair<8>, &cfg);
     if (e != cudaSuccess || n < 1) return CCC_ECUDA;
     mc = n < num_sms / 2 ? n : num_sms / 2;
   }
   const int64_t clusters = tiles < mc ? tiles : mc;
   const int grid = static_cast<int>(2 * clusters);
-  if (ew == 4)
+  if (fp4)
+    k_tally2_tc_pair_fp4<<<grid, 64 + 32 * tcp::FP4_EW, pair_smem(tcp::FP4_EW), s>>>(tm, a, sp, nkb);
+  else if (ew == 4)
     k_tally2_tc_pair<4><<<grid, 64 + 32 * 4, pair_smem(4), s>>>(tm, a, sp, nkb);
   else
     k_tally2_tc_pair<8><<<grid, 64 + 32 * 8, pair_smem(8), s>>>(tm, a, sp, nkb);
@@ -647,11 +735,19 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
 }
 
 int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t rows_pad,
-                                int64_t kpad, int split, int num_sms, cudaStream_t s) {
-  static int max_clusters = 0;
+                                int64_t kpad, int split, int num_sms, cudaStream_t s, bool fp4) {
+  static int max_clusters_dev[kMaxDevices][2] = {};
+  const int dev = current_device();
+  if (dev < 0) return CCC_ECUDA;
+  int &max_clusters = max_clusters_dev[dev][fp4 ? 1 : 0];
+  const int threads = 64 + 32 * (fp4 ? tcp::FP4_EW : 4);
+  const size_t smem = tcp::SMEM_BYTES;
   if (max_clusters == 0) {
     if (cudaFuncSetAttribute(k_tally2_tc_pair_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+                             static_cast<int>(smem)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_pair_split_fp4,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
       return CCC_ECUDA;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
@@ -660,19 +756,22 @@ int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t 
     attr.val.clusterDim.y = 1;
     attr.val.clusterDim.z = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
-    cfg.blockDim = dim3(64 + 32 * 4, 1, 1);
-    cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+    cfg.blockDim = dim3(static_cast<unsigned>(threads), 1, 1);
+    cfg.dynamicSmemBytes = smem;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair_split<4>, &cfg) != cudaSuccess || n < 1)
-      return CCC_ECUDA;
+    const cudaError_t e = fp4 ? cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair_split_fp4, &cfg)
+                              : cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair_split<4>, &cfg);
+    if (e != cudaSuccess || n < 1) return CCC_ECUDA;
     max_clusters = n < num_sms / 2 ? n : num_sms / 2;
   }
-  const int nkb = static_cast<int>(kpad / BK);
+  if (fp4 && kpad % 256 != 0) return CCC_EINVAL;
+  const int64_t row_bytes = fp4 ? kpad / 2 : kpad;
+  const int nkb = static_cast<int>(row_bytes / BK);
   if (split < 1 || split > nkb) return CCC_EINVAL;
   CUtensorMap tm;
-  if (!make_blocked_operand_map(&tm, op, rows_pad, kpad, tcp::BMH)) return CCC_ECUDA;
+  if (!make_blocked_operand_map(&tm, op, rows_pad, row_bytes, tcp::BMH)) return CCC_ECUDA;
   SplitSchedPair::Params sp;
   sp.tri.nI = static_cast<int>((a.n_v + 127) / 128);
   sp.tri.nJ = sp.tri.nI;
@@ -686,8 +785,12 @@ int launch_tally2_tc_pair_split(const Tally2Args &a, const uint8_t *op, int64_t 
   const int64_t units = sp.tiles * split;
   if (units == 0) return CCC_OK;
   const int64_t clusters = units < max_clusters ? units : max_clusters;
-  k_tally2_tc_pair_split<4><<<static_cast<unsigned>(2 * clusters), 64 + 32 * 4, tcp::SMEM_BYTES, s>>>(
-      tm, a, sp, nkb);
+  if (fp4)
+    k_tally2_tc_pair_split_fp4<<<static_cast<unsigned>(2 * clusters), threads, smem, s>>>(tm, a, sp,
+                                                                                         nkb);
+  else
+    k_tally2_tc_pair_split<4><<<static_cast<unsigned>(2 * clusters), threads, smem, s>>>(tm, a, sp,
+                                                                                        nkb);
   return note_launch();
 }
 
@@ -711,7 +814,11 @@ static bool make_packed_map(CUtensorMap *map, const uint64_t *geno, int64_t n_f,
 }
 
 template <class K>
-static int pair_clusters(K kernel, int threads, size_t smem, int num_sms, int *cache) {
+static int pair_clusters(K kernel, int threads, size_t smem, int num_sms,
+                         int (&cache_dev)[kMaxDevices]) {
+  const int dev = current_device();
+  if (dev < 0) return -1;
+  int *cache = &cache_dev[dev];
   if (*cache == 0) {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
@@ -755,11 +862,11 @@ int launch_tally2_tc_pair_packed(const Tally2Args &a, const uint64_t *geno, int6
   const int64_t tiles = tc2_pair_tiles(a.n_v, sp.I0, sp.I1);
   if (tiles == 0) return CCC_OK;
   const int ew = epilogue_warps(nkb);
-  static int cache[2] = {0, 0};
+  static int cache4[kMaxDevices] = {}, cache8[kMaxDevices] = {};
   const int mc = ew == 4 ? pair_clusters(k_tally2_tc_pair_packed<4>, 64 + 32 * 4 + CT,
-                                         packed_smem(4), num_sms, &cache[0])
+                                         packed_smem(4), num_sms, cache4)
                          : pair_clusters(k_tally2_tc_pair_packed<8>, 64 + 32 * 8 + CT,
-                                         packed_smem(8), num_sms, &cache[1]);
+                                         packed_smem(8), num_sms, cache8);
   if (mc < 1) return CCC_ECUDA;
   const int grid = static_cast<int>(2 * (tiles < mc ? tiles : mc));
   if (ew == 4)
@@ -783,9 +890,9 @@ int launch_tally2_tc_pair_split_packed(const Tally2Args &a, const uint64_t *geno
   sp.tiles = tc2_pair_tiles(a.n_v, sp.tri.I0, sp.tri.I1);
   const int64_t units = sp.tiles * split;
   if (units == 0) return CCC_OK;
-  static int cache = 0;
+  static int cache[kMaxDevices] = {};
   const int mc = pair_clusters(k_tally2_tc_pair_split_packed<4>, 64 + 32 * 4 + CT,
-                               tcp::pk::SMEM_BYTES, num_sms, &cache);
+                               tcp::pk::SMEM_BYTES, num_sms, cache);
   if (mc < 1) return CCC_ECUDA;
   const int64_t clusters = units < mc ? units : mc;
   k_tally2_tc_pair_split_packed<4><<<static_cast<unsigned>(2 * clusters), 64 + 32 * 4 + CT,
@@ -795,14 +902,16 @@ int launch_tally2_tc_pair_split_packed(const Tally2Args &a, const uint64_t *geno
 
 int launch_tally2_tc(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      int num_sms, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[kMaxDevices] = {};
+  const int dev = current_device();
+  if (dev < 0) return CCC_ECUDA;
+  if (!attr_set[dev]) {
     if (cudaFuncSetAttribute(k_tally2_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES)) != cudaSuccess ||
         cudaFuncSetAttribute(k_tally2_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES)) != cudaSuccess)
       return CCC_ECUDA;
-    attr_set = true;
+    attr_set[dev] = true;
   }
   CUtensorMap tmA, tmB;
   if (!make_operand_map(&tmA, op, rows_pad, kpad, BM) ||

@@ -545,7 +545,10 @@ static bool make_code_map(CUtensorMap *map, const uint64_t *geno, int64_t n_v, i
 
 int launch_tally3_fused(const Tally3Args &a, const uint64_t *geno, int64_t ld, const uint8_t *op,
                         int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t s) {
-  static bool attr_set = false;
+  static bool attr_set_dev[kMaxDevices] = {};
+  const int dev_a = current_device();
+  if (dev_a < 0) return CCC_ECUDA;
+  bool &attr_set = attr_set_dev[dev_a];
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_tally3_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(F_SMEM_BYTES)) != cudaSuccess ||
@@ -579,7 +582,10 @@ int launch_tally3_fused(const Tally3Args &a, const uint64_t *geno, int64_t ld, c
 int launch_tally3_tc(const Tally3Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                      uint8_t *lop, int64_t lop_rows, int64_t j0, int64_t j1, int num_sms,
                      cudaStream_t s) {
-  static bool attr_set = false;
+  static bool attr_set_dev[kMaxDevices] = {};
+  const int dev_a = current_device();
+  if (dev_a < 0) return CCC_ECUDA;
+  bool &attr_set = attr_set_dev[dev_a];
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_tally3_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES)) != cudaSuccess ||

@@ -1220,7 +1220,10 @@ template <int MODE>
 static int launch_wide_mode(const CUtensorMap &tmOp, const CUtensorMap &tmC, const ClassArgs &ca,
                             const wide::Sched::Params &sp, int64_t tiles, int num_sms,
                             cudaStream_t s) {
-  static int max_clusters = 0;
+  static int max_clusters_dev[kMaxDevices] = {};
+  const int dev_c = current_device();
+  if (dev_c < 0) return CCC_ECUDA;
+  int &max_clusters = max_clusters_dev[dev_c];
   if (max_clusters == 0) {
     if (cudaFuncSetAttribute(k_tally3_class_w<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(wide::kSmem)) != cudaSuccess)
@@ -1289,7 +1292,10 @@ int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows,
   if (a.n_f <= kWideMaxNf && dscratch != nullptr)
     return launch_tally3_class_w(a, op, op_rows, mrow0, kpad, rtab, cbuf, missing, dscratch, j0, j1,
                                  num_sms, s);
-  static bool attr_set = false;
+  static bool attr_set_dev[kMaxDevices] = {};
+  const int dev_a = current_device();
+  if (dev_a < 0) return CCC_ECUDA;
+  bool &attr_set = attr_set_dev[dev_a];
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_tally3_class, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kSmemBytes)) != cudaSuccess)
@@ -1306,7 +1312,10 @@ int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows,
       !tc::make_operand_map(&tmCA, cbuf, crows, kCap, 128) ||
       !tc::make_operand_map(&tmCB, cbuf, crows, kCap, kBRows))
     return CCC_ECUDA;
-  static int max_clusters = 0;
+  static int max_clusters_dev[kMaxDevices] = {};
+  const int dev_c = current_device();
+  if (dev_c < 0) return CCC_ECUDA;
+  int &max_clusters = max_clusters_dev[dev_c];
   if (max_clusters == 0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;

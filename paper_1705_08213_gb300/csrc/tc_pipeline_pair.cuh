@@ -38,6 +38,18 @@ constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int NUM_BARS = 2 * STAGES + 5;
 constexpr uint32_t IDESC = idesc_e4m3_f32(256, 256);
+// FP4 (e2m1) operands, kind::mxf4 with UE8M0 scale factors per 32 elements,
+// all 1.0: a 128-byte K stage holds 256 entries and one MMA takes K = 64.  The
+// block-scaled MMA reads its scale factors from TMEM, and two 256-column
+// accumulators already fill the 512 columns, so the FP4 pipeline keeps ONE
+// accumulator (columns 0-255) and the scale factors of A and B in columns
+// 256-271 and 272-287, written once per launch.  Its epilogue loads the whole
+// accumulator into registers before releasing it (8 warps, 128 values each),
+// so the next tile's MMAs wait only for that read, not for the stores.
+constexpr uint32_t IDESC_FP4 = idesc_e2m1_f32(256, 256, true);
+constexpr uint32_t SF_COL = 256;
+constexpr uint32_t SF_ONE_UE8M0 = 0x7F7F7F7Fu;
+constexpr int FP4_EW = 8;
 constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE_BYTES + NUM_BARS * 8 + 64;
 // Dynamic shared memory of a kernel whose epilogue warps each stage
 // `stage_bytes` (Epi::STAGE_BYTES_PER_WARP) after the barriers.
@@ -111,6 +123,35 @@ __device__ __forceinline__ void mma_f8f6f4_pair(uint32_t d_tmem, uint64_t a_desc
       : "memory");
 }
 
+// Block-scaled FP4: D[tmem] (+)= (A * SA) (B * SB)^T with E2M1 operands, K = 64
+// per instruction.  kind::mxf4 takes one UE8M0 scale factor per 32 elements
+// along K (scale_vec::2X: two per row and instruction), kind::mxf4nvf4 with
+// scale_vec::4X one UE4M3 factor per 16 elements; the factors are read from
+// TMEM at sfa (rows of A along lanes) and sfb (rows of B).
+__device__ __forceinline__ void mma_mxf4_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                              uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %6, 0;\n"
+      "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], "
+      "p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_mxf4nvf4_pair(uint32_t d_tmem, uint64_t a_desc,
+                                                  uint64_t b_desc, uint32_t idesc, uint32_t sfa,
+                                                  uint32_t sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %6, 0;\n"
+      "tcgen05.mma.cta_group::2.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, [%4], "
+      "[%5], p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive once on the barrier at this CTA-relative address in every CTA of mask
 // when all prior tcgen05 operations of this thread complete.
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
@@ -134,7 +175,10 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
 // KBLK: the operand is stored K-block-major, [nkb][rows][128 bytes], behind a
 // 3-D tensor map (x = byte, y = row, z = K block), so that each 128-row box is
 // one contiguous 16 KB run.
-template <class Sched, class Epi, int EW, bool KBLK = false>
+// FP4: e2m1 operands (kind::mxf4, unit scale factors), one accumulator, the
+// epilogue's Epi::tile loading all of its chunks before its release arrive
+// (EW must be FP4_EW).
+template <class Sched, class Epi, int EW, bool KBLK = false, bool FP4 = false>
 __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
                                                      const typename Sched::Params &sp,
                                                      const typename Epi::Params &ep, int nkb,
@@ -151,6 +195,8 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       (reinterpret_cast<uintptr_t>(tmem_slot) + 64 + 15) & ~static_cast<uintptr_t>(15));
 
   constexpr int EPI_THREADS = tc::Epilogue<EW>::THREADS;
+  constexpr int NACC = FP4 ? 1 : 2;  // accumulator buffers
+  static_assert(!FP4 || EW == FP4_EW, "the FP4 epilogue holds 4 chunks per thread");
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -187,6 +233,22 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
   const uint32_t tmem_base = *tmem_slot;
   const int64_t cstart = blockIdx.x >> 1;
   const int64_t cstep = gridDim.x >> 1;
+  if (FP4) {
+    // Scale factors 1.0 in both CTAs' columns SF_COL .. SF_COL + 31 (every
+    // byte), written by the first four epilogue warps, one lane quarter each,
+    // before the leader's first MMA reads them.
+    if (warp >= 2 && warp < 6) {
+      uint32_t v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = SF_ONE_UE8M0;
+      tmem_st_32x32b_x32(tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16) + SF_COL, v);
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+  }
 
   if (warp == 0) {
     if (lane == 0) {
@@ -248,8 +310,8 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       bool ok = true;
       Sched sc;
       for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep), ++lt) {
-        const int acc = lt & 1;
-        const uint32_t acc_phase = (lt >> 1) & 1;
+        const int acc = NACC == 1 ? 0 : (lt & 1);
+        const uint32_t acc_phase = NACC == 1 ? (lt & 1) : ((lt >> 1) & 1);
         if (!mbar_wait_bounded(tempty_bar(acc), acc_phase ^ 1u, status, abort_flag)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
@@ -263,9 +325,15 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
           const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
           const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
 #pragma unroll
-          for (int k = 0; k < BK / UK; ++k)
-            mma_f8f6f4_pair(d_tmem, smem_desc_sw128(a0 + k * UK), smem_desc_sw128(b0 + k * UK),
-                            IDESC, (kb | k) != 0 ? 1u : 0u);
+          for (int k = 0; k < BK / UK; ++k) {
+            if (FP4)
+              mma_mxf4_pair(d_tmem, smem_desc_sw128(a0 + k * UK), smem_desc_sw128(b0 + k * UK),
+                            IDESC_FP4, tmem_base + SF_COL, tmem_base + SF_COL + 16,
+                            (kb | k) != 0 ? 1u : 0u);
+            else
+              mma_f8f6f4_pair(d_tmem, smem_desc_sw128(a0 + k * UK), smem_desc_sw128(b0 + k * UK),
+                              IDESC, (kb | k) != 0 ? 1u : 0u);
+          }
           mma_commit_pair(empty_bar(stage), 0x3);
           if (++stage == STAGES) {
             stage = 0;
@@ -286,16 +354,16 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
     int lt = 0;
     Sched sc;
     for (sc.init(sp, cstart); sc.valid; sc.advance(cstep), ++lt) {
-      const int acc = lt & 1;
-      const uint32_t acc_phase = (lt >> 1) & 1;
+      const int acc = NACC == 1 ? 0 : (lt & 1);
+      const uint32_t acc_phase = NACC == 1 ? (lt & 1) : ((lt >> 1) & 1);
       const bool ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, status, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const uint32_t t_base =
           tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * ACC_COLS;
-      Epi::template tile<NC>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
-                             map_to_rank(tempty_bar(acc), 0), c0,
-                             stage_base + (warp - 2) * (Epi::STAGE_BYTES_PER_WARP / 4));
+      Epi::template tile<NC, FP4>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
+                                  map_to_rank(tempty_bar(acc), 0), c0,
+                                  stage_base + (warp - 2) * (Epi::STAGE_BYTES_PER_WARP / 4));
     }
   }
 

@@ -22,16 +22,23 @@ def workspace(nbytes):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
 
 
-def run_2way(geno_np, n_f, path, norm=0, gamma=2.0 / 3.0, fused=True, tile=0):
-    """Tallies (int32 [npairs, 4]) and CCC (float32 [npairs, 4]) through the C ABI."""
+def run_2way(geno_np, n_f, path, norm=0, gamma=2.0 / 3.0, fused=True, tile=0, split=0, operand=0):
+    """Tallies (int32 [npairs, 4]) and CCC (float32 [npairs, 4]) through the C ABI.
+
+    split: ccc_opts.split (0 automatic, 1 off); operand: ccc_opts.operand (0 e4m3, 1 e2m1)."""
     import paper_1705_08213_gb300 as ccc
     torch = torch_mod()
     g = to_device(geno_np)
     n_v = geno_np.shape[0]
     npairs = ccc.ccc2_count(n_v)
     opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, tile=tile)
+    if operand:
+        opts.operand = operand
     ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
     opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, workspace=ws, tile=tile)
+    opts.split = split
+    if operand:
+        opts.operand = operand
     tally = torch.full((max(npairs, 1), 4), -7, dtype=torch.int32, device="cuda")
     out = torch.full((max(npairs, 1), 4), -7.0, dtype=torch.float32, device="cuda")
     if fused:

@@ -86,10 +86,19 @@ def test_opts_default_and_strerror(lib):
 
 
 def test_workspace_size(lib):
-    o = ccc.ccc_opts_default()
+    o = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3)
     tc = ccc.ccc_workspace_size((1000, 32), 2000, o, ccc.CCC_OP_2WAY)
     # e4m3 operand matrix: (round_up(2000, 256) + 256) rows x round_up(2000, 128) bytes dominates
     assert tc >= (2048 + 256) * 2048
+    # e2m1 (the automatic choice for SM-pair tiles): rows of round_up(2000, 256) / 2 bytes
+    fp4 = ccc.ccc_workspace_size((1000, 32), 2000, ccc.ccc_opts_default(), ccc.CCC_OP_2WAY)
+    assert (2048 + 256) * 1024 <= fp4 < tc
+    assert fp4 == ccc.ccc_workspace_size((1000, 32), 2000,
+                                         ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E2M1),
+                                         ccc.CCC_OP_2WAY)
+    # one-SM tiles have no FP4 variant: automatic = e4m3
+    assert tc == ccc.ccc_workspace_size((1000, 32), 2000, ccc.ccc_opts_default(tile=1),
+                                        ccc.CCC_OP_2WAY)
     o.path = ccc.CCC_PATH_POPC
     pc = ccc.ccc_workspace_size((1000, 32), 2000, o, ccc.CCC_OP_2WAY)
     assert pc >= 1000 * 32 * 32
@@ -120,12 +129,20 @@ def test_workspace_size_3way_variants(lib):
     assert sizes[3] >= 16 * n_v * (n_v - 1) // 2 + n_v * 2 * n_v * 256
     assert sizes[2] < sizes[1] and sizes[2] < sizes[3]
     w3 = ccc.ccc_workspace_size((n_v, ld), n_f, ccc.ccc_opts_default(tile=3), ccc.CCC_OP_2WAY)
-    w2 = ccc.ccc_workspace_size((n_v, ld), n_f, ccc.ccc_opts_default(tile=2), ccc.CCC_OP_2WAY)
+    w2 = ccc.ccc_workspace_size((n_v, ld), n_f,
+                                ccc.ccc_opts_default(tile=2, operand=ccc.CCC_OPERAND_E4M3),
+                                ccc.CCC_OP_2WAY)
     assert w2 - w3 >= 2 * n_v * n_f  # (2 n_v rows) x (n_f bytes) of e4m3 counts
+    w2f = ccc.ccc_workspace_size((n_v, ld), n_f, ccc.ccc_opts_default(tile=2), ccc.CCC_OP_2WAY)
+    assert w2f - w3 >= n_v * n_f  # (2 n_v rows) x (n_f / 2 bytes) of e2m1 counts
     o = ccc.ccc_opts_default(tile=3)
     o.tile = 4
     with pytest.raises(ccc.CCCError) as e:
         ccc.ccc_workspace_size((n_v, ld), n_f, o, ccc.CCC_OP_3WAY)
+    assert e.value.status == ccc.CCC_EINVAL
+    o = ccc.ccc_opts_default(operand=3)
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc_workspace_size((n_v, ld), n_f, o, ccc.CCC_OP_2WAY)
     assert e.value.status == ccc.CCC_EINVAL
 
 

@@ -109,9 +109,9 @@ def test_allele_counts():
 
 def test_at_scale_tc_equals_popc_and_oracle_rows():
     """20,000 SNPs x 16,384 individuals (Hardy-Weinberg, Beta(1/2,1/2) MAF, 1% missing):
-    the tensor-core tallies equal the popcount tallies on every pair (tallies reach
-    4 n_f = 65,536, far past the exact range of narrower accumulators), and sampled
-    rows equal the oracle."""
+    the tensor-core tallies, with FP4 (the automatic operands) and with e4m3 operands,
+    equal the popcount tallies on every pair (tallies reach 4 n_f = 65,536, far past the
+    exact range of narrower accumulators), and sampled rows equal the oracle."""
     import torch
 
     import paper_1705_08213_gb300 as ccc
@@ -121,10 +121,12 @@ def test_at_scale_tc_equals_popc_and_oracle_rows():
     g = to_device(geno)
     npairs = ccc.ccc2_count(n_v)
     outs = {}
-    for path in PATHS:
-        opts = ccc.ccc_opts_default(path=path)
+    for path in PATHS + ["e4m3"]:
+        operand = ccc.CCC_OPERAND_E4M3 if path == "e4m3" else ccc.CCC_OPERAND_AUTO
+        path_id = 0 if path == "e4m3" else path
+        opts = ccc.ccc_opts_default(path=path_id, operand=operand)
         ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
-        opts = ccc.ccc_opts_default(path=path, workspace=ws)
+        opts = ccc.ccc_opts_default(path=path_id, workspace=ws, operand=operand)
         tally = torch.empty((npairs, 4), dtype=torch.int32, device="cuda")
         out = torch.empty((npairs, 4), dtype=torch.float32, device="cuda")
         ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
@@ -134,6 +136,8 @@ def test_at_scale_tc_equals_popc_and_oracle_rows():
         del ws
     assert torch.equal(outs[0][0], outs[1][0])
     assert torch.equal(outs[0][1], outs[1][1])
+    assert torch.equal(outs[0][0], outs["e4m3"][0])
+    assert torch.equal(outs[0][1], outs["e4m3"][1])
     # row sums of each table are 4 n_ij <= 4 n_f
     s = outs[0][0].sum(dim=1, dtype=torch.int64)
     assert int(s.max()) <= 4 * n_f and int(s.min()) >= 0

@@ -49,6 +49,21 @@ def test_2way_at_the_length_limit(path):
     assert_ccc_close(c, ec, what="n_f limit")
 
 
+@pytest.mark.parametrize("tile", [1, 2])
+def test_2way_unsplit_accumulator_at_the_length_limit(tile):
+    # With the K split off, one FP32 accumulator per tally sums all n_f individuals:
+    # r^{00} of an all-(0,0) pair reaches 4 n_f = 8,388,604 in a single accumulator.
+    n_f = _max_nf()
+    t, c = run_2way(_all_hom0(4, n_f), n_f, 0, tile=tile, split=1)
+    assert np.all(t[:, 0] == 4 * n_f) and np.all(t[:, 1:] == 0)
+    np.testing.assert_allclose(c[:, 0], 1.0 / 9.0, rtol=1e-6)
+    geno = synth.panel_hwe(5, n_f, seed=63, p_missing=0.01)
+    t, c = run_2way(geno, n_f, 0, tile=tile, split=1)
+    et, ec = oracle.ccc2_all(geno, n_f)
+    assert_tally_equal(t, et, "unsplit at the n_f limit")
+    assert_ccc_close(c, ec, what="unsplit at the n_f limit")
+
+
 @pytest.mark.parametrize("path,tile", [(0, 0), (0, 1), (1, 0)])
 def test_3way_at_the_length_limit(path, tile):
     n_f = _max_nf()

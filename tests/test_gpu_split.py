@@ -89,36 +89,6 @@ def test_tally_only_and_host_outputs():
     assert_ccc_close(c, ec, what="host outputs")
 
 
-def test_split_is_faster_on_few_tiles():
-    """512 SNPs (10 SM-pair tiles) x 600,000 individuals: the automatic split fills the SM
-    pairs that the unsplit call leaves idle."""
-    import torch
-
-    import paper_1705_08213_gb300 as ccc
-    n_v, n_f = 512, 600000
-    geno = synth.panel_hwe(n_v, n_f, seed=74, p_missing=0.01)
-    g = to_device(geno)
-    npairs = ccc.ccc2_count(n_v)
-    tally = torch.empty((npairs, 4), dtype=torch.int32, device="cuda")
-    out = torch.empty((npairs, 4), dtype=torch.float32, device="cuda")
-    times = {}
-    for split in (1, 0):
-        opts = ccc.ccc_opts_default()
-        ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
-        opts = ccc.ccc_opts_default(workspace=ws)
-        opts.split = split
-        ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(3):
-            ccc.ccc2_tally_metric(g, n_f, tally, out, opts)
-        e1.record()
-        torch.cuda.synchronize()
-        times[split] = e0.elapsed_time(e1) / 3
-    assert times[0] < 0.5 * times[1], times
-
-
 @pytest.mark.parametrize("s", [3, 4, 11])
 def test_multi_split_equals_unsplit_and_oracle(s):
     import torch

@@ -194,3 +194,93 @@ def test_two_gloo_ranks_sum_field_slices(tmp_path):
     res = np.load(tmp_path / "field.npy", allow_pickle=True)[0]
     np.testing.assert_array_equal(res["t2"], res["full2"])
     np.testing.assert_array_equal(res["t3"], res["full3"])
+
+
+# ---------------------------------------------------------------- block-circulant (n_pv axis)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 5, 8])
+def test_circulant_blocks_cover_every_pair_once(world):
+    """Sec. 4's block-circulant subset: every unordered pair of vector blocks (and every
+    diagonal block) lies in exactly one rank's block row, every pair i < j of the triangle
+    is computed once, and a rank holds only the blocks of its row (about half the panel)."""
+    from paper_1705_08213_gb300 import shard
+    blocks_seen = {}
+    for r in range(world):
+        for q in shard.circulant_plan(1000, world, r)["blocks"]:
+            key = (min(r, q), max(r, q))
+            blocks_seen[key] = blocks_seen.get(key, 0) + 1
+    assert sorted(blocks_seen) == [(p, q) for p in range(world) for q in range(p, world)]
+    assert all(v == 1 for v in blocks_seen.values())
+    for n_v in (1, 2, 129, 700, 4096):
+        b = shard.vector_blocks(n_v, world)
+        counts = np.zeros(n_v * (n_v - 1) // 2, np.int64)
+        held = []
+        work = []
+        for r in range(world):
+            plan = shard.circulant_plan(n_v, world, r)
+            lo, hi, swap = shard.circulant_pairs(plan)
+            assert np.all(lo < hi)
+            np.add.at(counts, lo * (2 * n_v - lo - 1) // 2 + (hi - lo - 1), 1)
+            held.append(plan["snps"].size)
+            work.append(lo.size)
+            assert len(plan["blocks"]) <= world // 2 + 1
+            assert np.array_equal(plan["snps"][:plan["rows"][1]], np.arange(b[r], b[r + 1]))
+        assert np.all(counts == 1)
+        if n_v >= 4096 and world > 2:
+            assert max(held) <= (world // 2 + 1) * (n_v / world + 128)
+            assert max(work) <= 1.6 * sum(work) / world
+
+
+def _circulant_worker(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_1705_08213_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n_v, n_f = 300, 500
+        geno = synth.panel_hwe(n_v, n_f, seed=9, p_missing=0.03)
+        plan = shard.circulant_plan(n_v, world, rank)
+        local = shard.circulant_local_panel(geno, plan)  # the only vectors this rank holds
+        t, c = oracle.ccc2_rows(np.ascontiguousarray(local), n_f, np.arange(*plan["rows"]))
+        idx, t, c = shard.circulant_scatter(plan, t, c)
+        mine = {"idx": idx, "t": t, "c": c, "held": local.shape[0]}
+        gathered = [None] * world
+        dist.all_gather_object(gathered, mine)
+        tm = torch.tensor([float(rank)])
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            et, ec = oracle.ccc2_all(geno, n_f)
+            np.save(os.path.join(out_dir, "circ.npy"),
+                    np.array([{"parts": gathered, "et": et, "ec": ec, "n_v": n_v,
+                               "tmax": float(tm.item())}], dtype=object), allow_pickle=True)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_block_circulant(tmp_path):
+    """Two ranks, each holding only its block row's vectors: the union of their result
+    blocks is the full triangle, each pair once, equal to the oracle on the full panel."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    mp.start_processes(_circulant_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    res = np.load(tmp_path / "circ.npy", allow_pickle=True)[0]
+    n_v = res["n_v"]
+    idx = np.concatenate([p["idx"] for p in res["parts"]])
+    assert idx.size == n_v * (n_v - 1) // 2 and np.unique(idx).size == idx.size
+    t = np.concatenate([p["t"] for p in res["parts"]])
+    c = np.concatenate([p["c"] for p in res["parts"]])
+    np.testing.assert_array_equal(t, res["et"][idx])
+    np.testing.assert_allclose(c, res["ec"][idx], rtol=1e-12, atol=0)
+    assert all(p["held"] < n_v for p in res["parts"][1:]) or len(res["parts"]) == 1
+    assert res["tmax"] == 1.0
