@@ -130,6 +130,8 @@ def parse():
                     help="e2e leg: ccc2_stream phases (stream), results stored by the kernels "
                          "straight into pinned host memory (direct), or one copy per output "
                          "after the call (copy); auto = stream for 2-way, copy otherwise")
+    ap.add_argument("--panels", type=int, default=None,
+                    help="batched workload: only the first N of its 64 panels (a reduced case)")
     ap.add_argument("--no-sub", action="store_true",
                     help="default 2-way line only: no 3way / batched / filter sub-records")
     ap.add_argument("--source-hash", action="store_true",
@@ -140,6 +142,11 @@ def parse():
             print(k, source_hash(k))
         raise SystemExit(0)
     w = workload_dict(a.workload, a.n_v, a.n_f)
+    if a.panels is not None and a.workload == "batched":
+        w["shapes"] = w["shapes"][:max(1, a.panels)]
+        w["text"] = (f"reduced case of the batched workload: its first {len(w['shapes'])} panels "
+                     "(not the bench line's configuration)")
+        w["reduced"] = True
     if a.steps is None:
         a.steps = DEFAULT_STEPS[a.workload]
     return a, w
@@ -206,6 +213,9 @@ KERNEL_SOURCES = {
                              "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_split_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
                                    "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_batched_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
+                                     "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh",
+                                     "ccc_launch.h"],
     "k_tally2_tc_pair_split": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
                                "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_packed": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
@@ -685,22 +695,33 @@ def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
     bf16_peak, _, peak_src = measured_peaks()
     kstep = kernel_ms / args.steps
     achieved = 8.0 * cmp_per_step / (kstep * 1e-3) / 1e12
-    peak = 2.0 * bf16_peak
+    # The tuned schedule: SM-pair tiles run e2m1 operands (automatic), one-SM tiles e4m3.
+    fp4 = opts.tile != 1
+    ratio = 6.0 if fp4 else 2.0
+    peak = ratio * bf16_peak
+    kind = "e2m1" if fp4 else "e4m3"
     result = {
         "metric": w["metric"], "value": cmp_per_step / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "e4m3 operands, fp32 accumulate", "data": "synthetic",
+        "dtype": ("e2m1 operands (kind::mxf4, unit scale factors), fp32 accumulate" if fp4 else
+                  "e4m3 operands, fp32 accumulate"), "data": "synthetic",
         "config": {"workload": w["text"], "panels": len(shapes), "comparisons": cmp_per_step,
-                   "schedule": {"group": group, "order": order, "tuned_by": "ccc2_batched_tune"},
+                   "schedule": {"group": group, "order": order, "tile": int(opts.tile),
+                                "split": int(opts.split), "solo": int(opts.solo),
+                                "tuned_by": "ccc2_batched_tune"},
                    "l2": "inputs larger than L2"},
         "gpu_launches": int(direct_launches // args.steps),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_tally2_tc_batched",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_tally2_tc_pair_batched_fp4" if fp4 else "k_tally2_tc_batched",
                      "kernel_ms_per_step": kstep, "kernel_launches": kernel_n,
-                     "note": "kernel time from the library's events over the same number of direct "
-                             "(not graph) steps right after the graph replays",
-                     "peak_note": f"e4m3 dense = 2 x {peak_src} bf16 burst {bf16_peak:.0f}"},
+                     "note": "kernel time: summed duration of the tally launches (the shared "
+                             "persistent launch and any solo launches), from the library's events "
+                             "over the same number of direct (not graph) steps right after the "
+                             "graph replays",
+                     "peak_note": f"{kind} dense = {ratio:.0f} x {peak_src} bf16 burst "
+                                  f"{bf16_peak:.0f} (nominal dense ratio)"},
         "clocks": clocks,
         "direct_calls": {"ms_per_step": ms_direct, "value": cmp_per_step / (ms_direct * 1e-3)},
         "sequential_64_calls": {"ms_per_step": ms_seq, "value": cmp_per_step / (ms_seq * 1e-3),
@@ -708,8 +729,8 @@ def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
     }
     rates = probe_rates(ccc, torch, dev)
     result["roofline"]["clock_normalised"] = clock_normalised(
-        achieved, rates["e4m3"]["flops_per_sm_per_clock"], clocks, rates["sms"],
-        "e4m3 flops per SM per clock of the ccc_mma_rate probe")
+        achieved, rates[kind]["flops_per_sm_per_clock"], clocks, rates["sms"],
+        f"{kind} flops per SM per clock of the ccc_mma_rate probe")
     if e2e is not None:
         result["e2e"] = e2e
     if not args.skip_cpu:
@@ -802,9 +823,11 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
     geno_np = make_panel(w, 0 if strong else rank)
     operand = {"auto": ccc.CCC_OPERAND_AUTO, "e4m3": ccc.CCC_OPERAND_E4M3,
                "e2m1": ccc.CCC_OPERAND_E2M1}[args.operand]
-    # The library's automatic choice: e2m1 on the 2-way SM-pair tiles (not s states).
-    fp4 = (path == ccc.CCC_PATH_TC and w["kind"] == 2 and not w.get("states")
-           and args.tile in (0, 2) and operand != ccc.CCC_OPERAND_E4M3)
+    # The library's automatic choice: e2m1 on the 2-way SM-pair tiles (not s states) and on
+    # the 3-way genotype-class route's wide tiles (n_f <= 16,383).
+    fp4 = (path == ccc.CCC_PATH_TC and operand != ccc.CCC_OPERAND_E4M3 and
+           ((w["kind"] == 2 and not w.get("states") and args.tile in (0, 2)) or
+            (w["kind"] == 3 and args.tile in (0, 3) and w["n_f"] <= 16383)))
     run = Runner(ccc, torch, dev, w, path, geno_np, tile=args.tile,
                  shard=shard_range if strong else None, operand=operand)
     stream = torch.cuda.current_stream(dev)
@@ -856,6 +879,8 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
     bf16_peak, hbm_peak, peak_src = measured_peaks()
     kernel_step_ms = kernel_ms / args.steps
     packed = "_packed" if args.tile == 3 else "_fp4" if fp4 else ""
+    if w["kind"] == 3:
+        packed = ""
     kname = {(2, True): ("k_tally2_multi" if w.get("states") else
                          "k_tally2_tc_pair_split" + packed if w.get("split_compare") else
                          "k_tally2_tc_pair" + packed if args.tile != 1 else "k_tally2_tc"),
@@ -980,16 +1005,20 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
             if hasattr(run, name):
                 delattr(run, name)
         if not run.filter and not hasattr(run, "tally"):
-            rows = ccc.ccc2_count(w["n_v"])
-            run.tally = torch.empty((rows, 4), dtype=torch.int32, device=dev)
-            run.out = torch.empty((rows, 4), dtype=torch.float32, device=dev)
+            lo, hi = run.shard if run.shard is not None else (0, w["n_v"])
+            rows = (ccc.ccc2_rows_count(w["n_v"], lo, hi) if w["kind"] == 2 else
+                    ccc.ccc3_count(w["n_v"], lo, hi))
+            width = 4 if w["kind"] == 2 else 8
+            run.tally = torch.empty((rows, width), dtype=torch.int32, device=dev)
+            run.out = torch.empty((rows, width), dtype=torch.float32, device=dev)
         o8 = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3)
-        ws8 = torch.empty(ccc.ccc_workspace_size(run.geno, w["n_f"], o8, ccc.CCC_OP_2WAY),
+        op8 = ccc.CCC_OP_2WAY if w["kind"] == 2 else ccc.CCC_OP_3WAY
+        ws8 = torch.empty(ccc.ccc_workspace_size(run.geno, w["n_f"], o8, op8),
                           dtype=torch.uint8, device=dev)
         run.opts = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3, workspace=ws8)
         run.step(stream)
         torch.cuda.synchronize(dev)
-        n8 = max(1, min(args.steps, 10))
+        n8 = max(1, min(args.steps, 10 if w["kind"] == 2 else 4))
         ccc.ccc_timing_enable(True)
         ccc.ccc_timing_read()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

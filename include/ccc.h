@@ -147,9 +147,13 @@ typedef struct ccc_opts {
                              exact in both and the FP32 accumulation is exact below 2^24, so
                              both give the same tallies and CCC values bit for bit.  E2M1 is
                              built for the 2-way SM-pair tiles (opts->tile 0 or 2, with K split,
-                             row ranges, ccc2_stream and ccc2_filter); elsewhere an explicit
-                             E2M1 returns CCC_EUNSUPPORTED.  AUTO (0) = E2M1 where it is built,
+                             row ranges, ccc2_stream, ccc2_filter and ccc2_batched) and for the
+                             3-way genotype-class route (opts->tile 0 or 3, n_f <= 16,383);
+                             elsewhere an explicit E2M1 returns CCC_EUNSUPPORTED.  AUTO (0) = E2M1 where it is built,
                              else E4M3.  The workspace size depends on it. */
+  int32_t solo;           /* ccc2_batched on SM pairs: a panel with at least this many 256 x 256
+                             tiles runs as its own launch, the others share one persistent
+                             launch; 0 = 1024, < 0 = none (every panel in the shared launch). */
 } ccc_opts;
 
 /* Operand encodings (ccc_opts.operand). */
@@ -294,14 +298,21 @@ int ccc3_stream(const ccc_panel *panel, int n_phases, int32_t *host_tally, float
  * Batched 2-way over independent panels (many SNP panels of uneven n_v and n_f,
  * as in a multi-study run): for every panel k, the tallies and CCC values that
  * ccc2_tally_metric would write to tally[k] and ccc[k].  On the tensor-core
- * path a panel with at least 1024 SM-pair tiles (n_v >= 5,633) runs as its
- * own launch, and all tiles of up to 64 smaller panels run in one persistent
- * launch, so small panels fill the SMs that large ones leave idle;
- * opts->order and opts->group choose the schedule (see ccc2_batched_tune).  panels: host array of
- * n_panels panels; tally, ccc: host arrays of n_panels device pointers (ccc
- * may be NULL for tallies only).  Workspace: ccc2_batched_workspace_size().
- * The call queues only stream work (memsets and kernels), so it can be
- * captured into a CUDA graph once a first call has run outside capture.
+ * path with SM-pair tiles a panel with at least opts->solo tiles (default
+ * 1024, n_v >= 5,633) runs as its own launch, and all tiles of up to 64
+ * smaller panels run in one persistent launch, so small panels fill the SMs
+ * that large ones leave idle.  When that shared launch has fewer tiles than
+ * two per SM pair and opts->split is 0, its panels' tiles run as K parts
+ * (the n_pf axis of Sec. 4 within one launch) whose partial tallies are
+ * summed, with the CCC values formed from the sums; opts->split = 1 keeps
+ * every tile whole, n >= 2 splits every shared panel into up to n parts.
+ * opts->order and opts->group choose the tile order (see ccc2_batched_tune).
+ * panels: host array of n_panels panels; tally, ccc: host arrays of n_panels
+ * device pointers (ccc may be NULL for tallies only).  Workspace:
+ * ccc2_batched_workspace_size(); with opts->tile = 0 it has room for every
+ * tile variant that ccc2_batched_tune tries.  The call queues only stream work (memsets
+ * and kernels), so it can be captured into a CUDA graph once a first call has
+ * run outside capture.
  */
 int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc_opts *opts,
                                 size_t *bytes);
@@ -309,18 +320,21 @@ int ccc2_batched(const ccc_panel *panels, int n_panels, int32_t *const *tally,
                  float *const *ccc, const ccc_opts *opts, void *stream);
 
 /*
- * Schedule autotuner for ccc2_batched: runs the batch once for each candidate
- * (group 4, 8, 16 x order 0, 1), timing each with CUDA events on the stream
- * (synchronising it), and stores the fastest group and order in *opts.  The
- * outputs hold a correct result afterwards.
+ * Schedule autotuner for ccc2_batched: runs the batch once per candidate,
+ * timing each with CUDA events on the stream (synchronising it), one choice
+ * after another: the tile variant (SM pairs or one SM, when opts->tile is 0),
+ * the K-split policy (automatic or off), the solo-launch threshold (1024,
+ * none, 512, 2048 tiles), then group 4, 8, 16 x order 0, 1; each choice keeps
+ * the fastest candidate.  The choices are stored in opts->tile, split, solo,
+ * group and order; the outputs hold a correct result afterwards.
  * The choice is cached under the batch's shape: the multiset of its panels'
  * (n_v, n_f) power-of-two buckets (bucket(x) = bit length of x - 1), with
- * opts->path, opts->tile and the device's SM count.  A later call whose batch
- * has the same key takes the cached choice and runs the batch once, without
- * the timing runs.  The cache lives in the process; when the environment
- * variable CCC_TUNE_CACHE names a file, choices are also appended to it (one
- * text line each) and read back by later processes.  CCC_EINVAL for a null
- * opts or panels or n_panels outside 1 .. 1024.
+ * opts->path, opts->tile, opts->operand and the device's SM count.  A later
+ * call whose batch has the same key takes the cached choice and runs the
+ * batch once, without the timing runs.  The cache lives in the process; when
+ * the environment variable CCC_TUNE_CACHE names a file, choices are also
+ * appended to it (one text line each) and read back by later processes.
+ * CCC_EINVAL for a null opts or panels or n_panels outside 1 .. 1024.
  */
 int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tally,
                       float *const *ccc, ccc_opts *opts, void *stream);
@@ -561,6 +575,11 @@ int64_t ccc3_count(int64_t n_v, int64_t j_begin, int64_t j_end); /* S(j_end) - S
 
 /* Text for a status code. */
 const char *ccc_strerror(int status);
+
+/* The CUDA error code (cudaError_t) behind the last CCC_ECUDA of the calling
+ * thread: the error a kernel launch reported, else the runtime's pending error
+ * (cudaPeekAtLastError); 0 when there is none.  Host only. */
+int ccc_last_cuda_error(void);
 
 /* Number of kernels this library has launched in this process (all entry points). */
 uint64_t ccc_launch_count(void);

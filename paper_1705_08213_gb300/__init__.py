@@ -38,7 +38,7 @@ __all__ = [
     "ccc_checked_shrink_outputs",
     "ccc_tune_cache_clear",
     "CCC_MMA_E4M3", "CCC_MMA_E2M1", "CCC_MMA_E2M1_NVF4", "ccc_mma_rate", "ccc_popc_rate",
-    "CCC_OPERAND_AUTO", "CCC_OPERAND_E4M3", "CCC_OPERAND_E2M1",
+    "CCC_OPERAND_AUTO", "CCC_OPERAND_E4M3", "CCC_OPERAND_E2M1", "ccc_last_cuda_error",
 ]
 
 CCC_OK = 0
@@ -75,6 +75,8 @@ class CCCError(RuntimeError):
     def __init__(self, name, status):
         self.status = status
         msg = _lib_strerror(status) if isinstance(status, int) else str(status)
+        if status == CCC_ECUDA:
+            msg += f"; CUDA error {ccc_last_cuda_error()}"
         super().__init__(f"{name}: {msg} ({status})")
 
 
@@ -97,7 +99,7 @@ class ccc_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("norm", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("group", ctypes.c_int32), ("order", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("operand", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("operand", ctypes.c_int32), ("solo", ctypes.c_int32)]
 
 
 _lib = None
@@ -424,6 +426,16 @@ def ccc3_count(n_v, j_begin, j_end):
 
 def ccc_strerror(status):
     return load().ccc_strerror(int(status)).decode()
+
+
+def ccc_last_cuda_error():
+    """The cudaError_t value behind the last CCC_ECUDA of this thread (0 if none)."""
+    try:
+        lib = load()
+    except CCCError:
+        return 0
+    lib.ccc_last_cuda_error.restype = ctypes.c_int
+    return int(lib.ccc_last_cuda_error())
 
 
 def ccc_launch_count():

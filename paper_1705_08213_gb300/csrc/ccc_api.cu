@@ -103,6 +103,14 @@ bool fp4_2way(const ccc_opts *o) {
   return o->tile == 0 || o->tile == 2;
 }
 
+// FP4 (e2m1) operands for a 3-way tensor-core call: built for the
+// genotype-class route's wide tiles (tile 0 or 3, n_f <= 16,383, where the D
+// counts fit 16 bits); automatic = FP4 there.
+bool fp4_3way(const ccc_opts *o, int64_t n_f) {
+  if (o->path != CCC_PATH_TC || o->operand == CCC_OPERAND_E4M3) return false;
+  return (o->tile == 0 || o->tile == 3) && n_f <= 16383;
+}
+
 // Options of a 2-way call: tile 3 names a 3-way variant only.
 int check_opts2(const ccc_opts *o) {
   CCC_TRY_INNER(check_opts(o));
@@ -161,7 +169,7 @@ Layout make_layout(int64_t n_f, int64_t n_v, int path, int op, int tile = 0, boo
         // largest slab) right after R, so that one tensor map covers both.
         const int64_t all_rows = tc3_class_mask_rows(0, n_v, n_v);
         const int64_t max_slab = tc3_class_mask_rows((n_v - 1) / 2, (n_v - 1) / 2 + 1, n_v);
-        int64_t cap = static_cast<int64_t>(kLopBytes / static_cast<size_t>(L.kpad));
+        int64_t cap = static_cast<int64_t>(kLopBytes / static_cast<size_t>(fp4 ? L.kpad / 2 : L.kpad));
         if (cap < max_slab) cap = max_slab;
         L.mask_rows = all_rows < cap ? all_rows : cap;
         if (L.mask_rows < 1) L.mask_rows = 1;
@@ -263,9 +271,15 @@ void timing_end(int slot, cudaStream_t s) {
 
 }  // namespace
 
+// The CUDA error behind the last CCC_ECUDA that a launch of this thread saw.
+thread_local int g_cuda_error = 0;
+
 int note_launch() {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError() == cudaSuccess ? CCC_OK : CCC_ECUDA;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return CCC_OK;
+  g_cuda_error = static_cast<int>(e);
+  return CCC_ECUDA;
 }
 
 int64_t pair_index(int64_t i, int64_t j, int64_t n_v) {
@@ -538,18 +552,20 @@ struct Run3 {
   Layout L;
   DeviceInfo dev;
   Tally3Args a;
+  bool fp4 = false;  // e2m1 operands (fp4_3way)
 };
 
 static int begin_3way(Run3 &R, const ccc_panel *p, const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_panel(p));
   CCC_TRY(check_opts(o));
-  if (o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;
+  R.fp4 = fp4_3way(o, p->n_f);
+  if (o->operand == CCC_OPERAND_E2M1 && !R.fp4) return CCC_EUNSUPPORTED;
   if (p->n_v > 65535) return CCC_ERANGE;
   CCC_TRY(query_device(&R.dev));
   R.p = p;
   R.o = o;
   R.s = s;
-  R.L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY, o->tile);
+  R.L = make_layout(p->n_f, p->n_v, o->path, CCC_OP_3WAY, o->tile, R.fp4);
   CCC_TRY(check_workspace(o, R.L));
   CCC_TRY(clear_status(o, R.L, s));
   R.a.n_v = p->n_v;
@@ -578,7 +594,10 @@ static int prep_3way(Run3 &R, bool want_ccc, int64_t j_last) {
   if (o->path != CCC_PATH_TC)
     return launch_planes(p->geno, p->n_f, p->n_v, p->ld, at<uint64_t>(o, R.L.planes), R.L.w64, s);
   uint8_t *op = at<uint8_t>(o, R.L.op);
-  CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s));
+  if (R.fp4)
+    CCC_TRY(launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s));
+  else
+    CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s));
   if (!class_route(o)) return CCC_OK;
   const int64_t je = j_last < p->n_v - 1 ? j_last : p->n_v - 1;
   if (je < 2) return CCC_OK;
@@ -595,7 +614,7 @@ static int prep_3way(Run3 &R, bool want_ccc, int64_t j_last) {
   a2.i_end = je - 1;
   a2.pair0 = 0;
   a2.out_len = pairs_in_rows(p->n_v, 0, p->n_v);  // the table holds every pair
-  return launch_tally2_tc_pair(a2, op, R.L.rows_pad, R.L.kpad, R.dev.sms, s);
+  return launch_tally2_tc_pair(a2, op, R.L.rows_pad, R.L.kpad, R.dev.sms, s, R.fp4);
 }
 
 // Tallies (and CCC values) of the slabs [R.a.j_begin, R.a.j_end) into
@@ -645,14 +664,15 @@ static int slabs_3way(Run3 &R) {
       const int64_t mrow0 = L.rows_pad + h * L.mask_rows;
       if (P != nullptr && b >= 2 && cudaStreamWaitEvent(ps, P->consumed[h], 0) != cudaSuccess)
         return CCC_ECUDA;
-      CCC_TRY(launch_compact3(p->geno, p->n_f, p->n_v, p->ld, cb, ms, j0, j1, ps));
-      CCC_TRY(launch_mask3c(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, mrow0, ms, j0, j1, ps));
+      CCC_TRY(launch_compact3(p->geno, p->n_f, p->n_v, p->ld, cb, ms, j0, j1, ps, R.fp4));
+      CCC_TRY(launch_mask3c(p->geno, p->n_f, p->n_v, p->ld, op, L.kpad, mrow0, ms, j0, j1, ps,
+                            R.fp4));
       if (P != nullptr && (cudaEventRecord(P->prepared[h], ps) != cudaSuccess ||
                            cudaStreamWaitEvent(s, P->prepared[h], 0) != cudaSuccess))
         return CCC_ECUDA;
       const int slot = timing_begin(s);
       const int rc = launch_tally3_class(a, op, op_rows, mrow0, L.kpad, rtab, cb, ms,
-                                         at<uint32_t>(o, L.dscratch), j0, j1, R.dev.sms, s);
+                                         at<uint32_t>(o, L.dscratch), j0, j1, R.dev.sms, s, R.fp4);
       timing_end(slot, s);
       if (rc != CCC_OK) return rc;
       if (P != nullptr && cudaEventRecord(P->consumed[h], s) != cudaSuccess) return CCC_ECUDA;
@@ -719,18 +739,21 @@ struct BatchLayout {
   int64_t kpad[kMaxPanelsPerCall] = {}, rows_pad[kMaxPanelsPerCall] = {}, w64[kMaxPanelsPerCall] = {};
 };
 
-static int batch_layout(const ccc_panel *panels, int n, int path, BatchLayout *B) {
+// fp4: e2m1 operand rows (K padded to 256 entries, kpad / 2 bytes per row).
+static int batch_layout(const ccc_panel *panels, int n, int path, bool fp4, BatchLayout *B) {
   size_t off = kAlign;
   for (int k = 0; k < n; ++k) {
     const ccc_panel &p = panels[k];
     B->w[k] = off;
     off = align_up(off + sizeof(float) * 2 * static_cast<size_t>(p.n_v), kAlign);
     if (path == CCC_PATH_TC) {
-      B->kpad[k] = round_up(p.n_f, 128);
+      B->kpad[k] = round_up(p.n_f, fp4 ? 256 : 128);
       B->rows_pad[k] = tc_rows_pad(p.n_v);
       off = align_up(off, 1024);
       B->op[k] = off;
-      off = align_up(off + static_cast<size_t>(B->rows_pad[k]) * static_cast<size_t>(B->kpad[k]), 1024);
+      off = align_up(off + static_cast<size_t>(B->rows_pad[k]) *
+                               static_cast<size_t>(fp4 ? B->kpad[k] / 2 : B->kpad[k]),
+                     1024);
     } else {
       B->w64[k] = (p.n_f + 63) / 64;
       B->op[k] = off;
@@ -741,11 +764,37 @@ static int batch_layout(const ccc_panel *panels, int n, int path, BatchLayout *B
   return CCC_OK;
 }
 
+// Default solo-launch threshold of ccc2_batched, in SM-pair tiles.  On GB300
+// (e4m3 operands) the 64-panel workload ran at 4.53e14 comparisons/s with
+// 1024 (4.47e14 with 512, 4.1e14 with every panel in the persistent launch);
+// ccc2_batched_tune measures the alternatives per batch shape.
+constexpr int64_t kSoloTiles = 1024;
+
+// K parts of the shared launch's panels (opts->split 0: automatic): when the
+// launch holds fewer tiles than two per SM pair, every panel's tiles are split
+// by the factor that brings the units to about two per SM pair, each part
+// keeping at least 16 K stages; n >= 2: every panel into min(n, stages) parts.
+static void batch_splits(const int64_t *tiles, const int64_t *stages, int m, int requested,
+                         int sms, int *split) {
+  int64_t total = 0;
+  for (int x = 0; x < m; ++x) total += tiles[x];
+  const int64_t clusters = sms / 2;
+  int64_t f = 1;
+  if (requested >= 2) f = requested;
+  else if (requested == 0 && total > 0 && total < 2 * clusters)
+    f = (2 * clusters + total - 1) / total;
+  for (int x = 0; x < m; ++x) {
+    int64_t p = f;
+    const int64_t cap = requested >= 2 ? stages[x] : stages[x] / 16;
+    if (p > cap) p = cap;
+    split[x] = p > 1 ? static_cast<int>(p) : 1;
+  }
+}
+
 static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, float *const *out_ccc,
                        const ccc_opts *o, cudaStream_t s) {
   CCC_TRY(check_opts2(o));
   if (o->tile == 3) return CCC_EINVAL;  // batched panels use the operand matrices
-  if (o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;  // e4m3 operands only
   if (panels == nullptr || tally == nullptr || n < 1 || n > kMaxPanelsPerCall) return CCC_EINVAL;
   for (int k = 0; k < n; ++k) {
     CCC_TRY(check_panel(&panels[k]));
@@ -754,8 +803,9 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
   }
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
+  const bool fp4 = fp4_2way(o);
   static thread_local BatchLayout B;
-  batch_layout(panels, n, o->path, &B);
+  batch_layout(panels, n, o->path, fp4, &B);
   if (o->workspace == nullptr || !aligned(o->workspace, kAlign)) return CCC_EINVAL;
   if (o->workspace_bytes < B.total) return CCC_ENOSPACE;
   int32_t *status = at<int32_t>(o, 0);
@@ -782,8 +832,7 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
     args[k] = a;
     if (p.n_v < 2) continue;
     if (o->path == CCC_PATH_TC) {
-      CCC_TRY(launch_unpack_e4m3(p.geno, p.n_f, p.n_v, p.ld, at<uint8_t>(o, B.op[k]), B.kpad[k],
-                                 B.rows_pad[k] / 2, s));
+      CCC_TRY(unpack_2way(&p, o, at<uint8_t>(o, B.op[k]), B.kpad[k], B.rows_pad[k], s));
     } else {
       uint64_t *planes = at<uint64_t>(o, B.op[k]);
       CCC_TRY(launch_planes(p.geno, p.n_f, p.n_v, p.ld, planes, B.w64[k], s));
@@ -809,21 +858,20 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
         order[y - 1] = t;
       }
   }
-  // SM-pair tiles: a panel with at least kSoloTiles tiles keeps every SM busy on
-  // its own, and runs as its own launch (its operand blocks then have L2 to
-  // themselves); the smaller panels share persistent launches.  On GB300 the
-  // 64-panel workload ran at 4.53e14 comparisons/s with 1024 (4.47e14 with 512,
-  // 4.1e14 with every panel in the persistent launches).
-  constexpr int64_t kSoloTiles = 1024;
+  // SM-pair tiles: a panel with at least `solo` tiles keeps every SM busy on its
+  // own, and runs as its own launch (its operand blocks then have L2 to
+  // themselves); the smaller panels share persistent launches.
+  const int64_t solo = o->solo == 0 ? kSoloTiles : o->solo < 0 ? (int64_t(1) << 62) : o->solo;
+  const int64_t stage_bytes = fp4 ? 256 : 128;  // entries per 128-byte K stage
   int nb = 0;
   if (o->tile != 1) {
     for (int x = 0; x < n; ++x) {
       const int k = order[x];
       const int64_t nB = (panels[k].n_v + 127) / 128;
-      if (panels[k].n_v >= 2 && tc2_pair_tiles(panels[k].n_v, 0, nB) >= kSoloTiles) {
+      if (panels[k].n_v >= 2 && tc2_pair_tiles(panels[k].n_v, 0, nB) >= solo) {
         const int slot = timing_begin(s);
         const int rc = launch_tally2_tc_pair(args[k], at<uint8_t>(o, B.op[k]), B.rows_pad[k],
-                                             B.kpad[k], dev.sms, s);
+                                             B.kpad[k], dev.sms, s, fp4);
         timing_end(slot, s);
         if (rc != CCC_OK) return rc;
       } else {
@@ -835,6 +883,8 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
   }
   static thread_local Tally2Args oargs[kMaxBatchPanels];
   static thread_local int64_t orows[kMaxBatchPanels], okpad[kMaxBatchPanels];
+  static thread_local int64_t otiles[kMaxBatchPanels], ostages[kMaxBatchPanels];
+  static thread_local int osplit[kMaxBatchPanels];
   for (int c0 = 0; c0 < nb; c0 += kMaxBatchPanels) {
     const int m = nb - c0 < kMaxBatchPanels ? nb - c0 : kMaxBatchPanels;
     for (int x = 0; x < m; ++x) {
@@ -843,14 +893,34 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
       ops[x] = at<uint8_t>(o, B.op[k]);
       orows[x] = B.rows_pad[k];
       okpad[x] = B.kpad[k];
+      otiles[x] = panels[k].n_v >= 2 ? tc2_pair_tiles(panels[k].n_v, 0, (panels[k].n_v + 127) / 128)
+                                     : 0;
+      ostages[x] = B.kpad[k] / stage_bytes;
     }
+    if (o->tile != 1) {
+      batch_splits(otiles, ostages, m, o->split, dev.sms, osplit);
+    } else {
+      for (int x = 0; x < m; ++x) osplit[x] = 1;
+    }
+    // Split panels add their partial tallies into zeroed outputs.
+    for (int x = 0; x < m; ++x)
+      if (osplit[x] > 1 && oargs[x].n_v >= 2 &&
+          cudaMemsetAsync(oargs[x].tally, 0,
+                          16 * static_cast<size_t>(oargs[x].n_v) * static_cast<size_t>(oargs[x].n_v - 1) / 2,
+                          s) != cudaSuccess)
+        return CCC_ECUDA;
     const int slot = timing_begin(s);
     const int rc = o->tile == 1
                        ? launch_tally2_tc_batched(oargs, ops, orows, okpad, m, o->group, dev.sms, s)
-                       : launch_tally2_tc_pair_batched(oargs, ops, orows, okpad, m, o->group,
-                                                       dev.sms, s);
+                       : launch_tally2_tc_pair_batched(oargs, ops, orows, okpad, osplit, m,
+                                                       o->group, dev.sms, s, fp4);
     timing_end(slot, s);
     if (rc != CCC_OK) return rc;
+    // CCC values of the split panels from their summed tallies.
+    for (int x = 0; x < m; ++x)
+      if (osplit[x] > 1 && oargs[x].ccc != nullptr && oargs[x].n_v >= 2)
+        CCC_TRY(launch_metric2(oargs[x].tally, oargs[x].w, oargs[x].n_v, oargs[x].gamma,
+                               oargs[x].norm, oargs[x].ccc, s));
   }
   return CCC_OK;
 }
@@ -992,9 +1062,9 @@ int ccc_workspace_size(const ccc_panel *panel, const ccc_opts *opts, int op, siz
   if (panel == nullptr || panel->n_f < 1 || panel->n_v < 1) return CCC_EINVAL;
   if (panel->n_f > CCC_MAX_NF || panel->n_v > kMaxNV) return CCC_ERANGE;
   if (op != CCC_OP_2WAY && op != CCC_OP_3WAY && op != CCC_OP_METRIC) return CCC_EINVAL;
-  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile,
-                       op == CCC_OP_2WAY && fp4_2way(opts))
-               .total;
+  const bool fp4 = (op == CCC_OP_2WAY && fp4_2way(opts)) ||
+                   (op == CCC_OP_3WAY && fp4_3way(opts, panel->n_f));
+  *bytes = make_layout(panel->n_f, panel->n_v, opts->path, op, opts->tile, fp4).total;
   return CCC_OK;
 }
 
@@ -1313,8 +1383,15 @@ int ccc2_batched_workspace_size(const ccc_panel *panels, int n_panels, const ccc
     if (panels[k].n_f > CCC_MAX_NF || panels[k].n_v > kMaxNV) return CCC_ERANGE;
   }
   static thread_local BatchLayout B;
-  batch_layout(panels, n_panels, opts->path, &B);
-  *bytes = B.total;
+  batch_layout(panels, n_panels, opts->path, fp4_2way(opts), &B);
+  size_t total = B.total;
+  if (opts->path == CCC_PATH_TC && opts->tile == 0 && fp4_2way(opts)) {
+    // Automatic tiles: room for the e4m3 operands of the one-SM variant too,
+    // which ccc2_batched_tune may try and choose.
+    batch_layout(panels, n_panels, opts->path, false, &B);
+    if (B.total > total) total = B.total;
+  }
+  *bytes = total;
   return CCC_OK;
 }
 
@@ -1334,46 +1411,91 @@ int ccc2_batched_tune(const ccc_panel *panels, int n_panels, int32_t *const *tal
   CCC_TRY(query_device(&dev));
   // A batch whose panel sizes fall in already-tuned buckets takes the cached
   // schedule without the timing runs.
-  const uint64_t key = tune_key(panels, n_panels, opts->path, opts->tile, dev.sms);
+  const uint64_t key =
+      tune_key(panels, n_panels, opts->path, opts->tile, opts->operand, dev.sms);
+  auto apply = [](ccc_opts *o, const TuneChoice &c) {
+    o->group = c.group;
+    o->order = c.order;
+    o->tile = c.tile;
+    o->split = c.split;
+    o->solo = c.solo;
+  };
   TuneChoice cached;
   if (tune_lookup(key, &cached)) {
-    opts->group = cached.group;
-    opts->order = cached.order;
+    apply(opts, cached);
     return run_batched(panels, n_panels, tally, ccc, opts, s);
   }
-  const int groups[3] = {4, 8, 16};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return CCC_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return CCC_ECUDA;
   }
-  ccc_opts o = *opts;
-  float best = -1.f;
-  int best_g = 8, best_o = 0, rc = CCC_OK;
-  for (int ord = 0; ord < 2 && rc == CCC_OK; ++ord)
-    for (int gi = 0; gi < 3 && rc == CCC_OK; ++gi) {
-      o.group = groups[gi];
-      o.order = ord;
-      cudaEventRecord(e0, s);
-      rc = run_batched(panels, n_panels, tally, ccc, &o, s);
-      cudaEventRecord(e1, s);
-      float ms = 0.f;
-      if (rc == CCC_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
-                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        rc = CCC_ECUDA;
-      if (rc == CCC_OK && (best < 0.f || ms < best)) {
-        best = ms;
-        best_g = groups[gi];
-        best_o = ord;
-      }
+  int rc = CCC_OK;
+  // Whether a candidate's operands fit the caller's workspace.
+  auto fits = [&](const TuneChoice &c) -> bool {
+    ccc_opts o = *opts;
+    apply(&o, c);
+    static thread_local BatchLayout BL;
+    batch_layout(panels, n_panels, o.path, fp4_2way(&o), &BL);
+    return BL.total <= opts->workspace_bytes;
+  };
+  // One timed run of a candidate; -1 on an error (rc set).
+  auto time_run = [&](const TuneChoice &c) -> float {
+    ccc_opts o = *opts;
+    apply(&o, c);
+    cudaEventRecord(e0, s);
+    rc = run_batched(panels, n_panels, tally, ccc, &o, s);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (rc == CCC_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = CCC_ECUDA;
+    return rc == CCC_OK ? ms : -1.f;
+  };
+  // Each choice in turn keeps the fastest candidate, the others fixed.
+  TuneChoice best{8, 0, opts->tile == 1 ? 1 : 2, 0, static_cast<int>(kSoloTiles)};
+  float best_ms = time_run(best);
+  auto consider = [&](TuneChoice c) {
+    if (rc != CCC_OK || !fits(c)) return;
+    const float ms = time_run(c);
+    if (rc == CCC_OK && ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  };
+  if (opts->tile == 0) {
+    TuneChoice c = best;
+    c.tile = 1;
+    consider(c);
+  }
+  if (best.tile == 2) {
+    TuneChoice c = best;
+    c.split = 1;
+    consider(c);
+    const int solos[3] = {-1, 512, 2048};
+    const TuneChoice base = best;
+    for (int k = 0; k < 3; ++k) {
+      c = base;
+      c.solo = solos[k];
+      consider(c);
+    }
+  }
+  const int groups[3] = {4, 8, 16};
+  const TuneChoice base = best;
+  for (int ord = 0; ord < 2; ++ord)
+    for (int gi = 0; gi < 3; ++gi) {
+      if (groups[gi] == base.group && ord == base.order) continue;
+      TuneChoice c = base;
+      c.group = groups[gi];
+      c.order = ord;
+      consider(c);
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != CCC_OK) return rc;
-  opts->group = best_g;
-  opts->order = best_o;
-  tune_store(key, TuneChoice{best_g, best_o}, best);
+  apply(opts, best);
+  tune_store(key, best, best_ms);
   // Leave the outputs as the chosen schedule writes them (all schedules agree).
   return run_batched(panels, n_panels, tally, ccc, opts, s);
 }
@@ -1454,6 +1576,11 @@ int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream) {
   CCC_TRY(query_device(&dev));
   return launch_wait_selftest(status, static_cast<uint64_t>(limit_ns),
                               static_cast<cudaStream_t>(stream));
+}
+
+int ccc_last_cuda_error(void) {
+  if (g_cuda_error != 0) return g_cuda_error;
+  return static_cast<int>(cudaPeekAtLastError());
 }
 
 int ccc_mma_rate(int kind, int n_cols, int n_mma, int clusters, int64_t *cycles, int32_t *bad,

@@ -114,10 +114,14 @@ constexpr int kMaxBatchPanels = 64;
 int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
                              const int64_t *rows_pad, const int64_t *kpad, int n, int group,
                              int num_sms, cudaStream_t s);
-// The same on SM pairs (256 x 256 tiles, cta_group::2).
+// The same on SM pairs (256 x 256 tiles, cta_group::2).  split[k] > 1 (or
+// null: all 1): panel k's tiles run as that many K parts whose partial tallies
+// are added into args[k].tally, which must then be zero and gets no CCC values
+// (the caller forms them from the summed tallies).  fp4: e2m1 operand rows of
+// kpad[k] / 2 bytes (kpad[k] a multiple of 256).
 int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *ops,
-                                  const int64_t *rows_pad, const int64_t *kpad, int n, int group,
-                                  int num_sms, cudaStream_t s);
+                                  const int64_t *rows_pad, const int64_t *kpad, const int *split,
+                                  int n, int group, int num_sms, cudaStream_t s, bool fp4 = false);
 
 // Square 128-SNP tiles of the triangle (J >= I) in row blocks [I0, I1).
 int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1);
@@ -197,18 +201,22 @@ int launch_tally3_fused(const Tally3Args &a, const uint64_t *geno, int64_t ld, c
 int64_t tc3_class_cap();
 int64_t tc3_class_cbuf_rows(int64_t n_slabs, int64_t n_v);
 int64_t tc3_class_mask_rows(int64_t j0, int64_t j1, int64_t n_v);
+// fp4: e2m1 nibbles; compacted rows of tc3_class_cap() / 2 bytes, masked rows
+// (and R) of kpad / 2 bytes.
 int launch_compact3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *cbuf,
-                    int32_t *missing, int64_t j0, int64_t j1, cudaStream_t s);
+                    int32_t *missing, int64_t j0, int64_t j1, cudaStream_t s, bool fp4 = false);
 int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                   int64_t kpad, int64_t mrow0, const int32_t *missing, int64_t j0, int64_t j1,
-                  cudaStream_t s);
+                  cudaStream_t s, bool fp4 = false);
 //                    dscratch (tc3_class_dscratch_bytes()) holds the D counts
 //                    of the tiles in flight when n_f <= 16383.
 int64_t tc3_class_dscratch_bytes();
+//                    fp4: e2m1 operands (the wide tiles only, n_f <= 16383;
+//                    else CCC_EUNSUPPORTED).
 int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows, int64_t mrow0,
                         int64_t kpad, const int32_t *rtab, const uint8_t *cbuf,
                         const int32_t *missing, uint32_t *dscratch, int64_t j0, int64_t j1,
-                        int num_sms, cudaStream_t s);
+                        int num_sms, cudaStream_t s, bool fp4 = false);
 int launch_tally3_popc(const Tally3Args &a, const uint64_t *planes, int64_t w64, cudaStream_t s);
 int launch_metric3(const int32_t *tally, const float *w, int64_t n_v, int64_t j_begin,
                    int64_t j_end, float gamma, int32_t norm, float *ccc, cudaStream_t s);

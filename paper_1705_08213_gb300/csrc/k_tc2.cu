@@ -283,7 +283,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
 }
 
 // FP4 (e2m1) operands: one accumulator, 8 epilogue warps that load their whole
-// quarter-half before releasing it (tcp::persistent_gemm_pair, FP4).
+// quarter-half before releasing it (tcp::persistent_gemm_pair, FP4).  Each
+// epilogue thread holds 128 accumulator values.  The 10 warps of a CTA put 3
+// warps on two of the SM's four sub-partitions, whose register files hold 16K
+// registers each, so a thread may use at most 168 (3 x 32 x 168 <= 16,384):
+// that is what __launch_bounds__(320, 1) gives, with a few dozen bytes spilled.
+// A higher cap (183 registers, no spills) left no CTA resident.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_EW, 1)
     k_tally2_tc_pair_fp4(const __grid_constant__ CUtensorMap tm, const Tally2Args args,
                          TriSched::Params sp, int nkb) {
@@ -303,9 +308,17 @@ struct Epi2Split {
   __device__ static void tile(const Params &args, const SplitSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *) {
+    body<NC, PRELOAD>(args, Tile2{2 * sc.I + rank, sc.J}, quarter, lane, t_base,
+                      release_cluster_bar, c0);
+  }
+
+  // sc: the CTA's 64-SNP row block I and the tile's 128-SNP column block J.
+  template <int NC, bool PRELOAD = false>
+  __device__ static void body(const Params &args, Tile2 sc, int quarter, int lane, uint32_t t_base,
+                              uint32_t release_cluster_bar, int c0) {
     const int row = quarter * 32 + lane;
     const int a = row & 1;
-    const int64_t i = static_cast<int64_t>(2 * sc.I + rank) * SNP_I + (row >> 1);
+    const int64_t i = static_cast<int64_t>(sc.I) * SNP_I + (row >> 1);
     const bool row_ok = i < args.n_v && i >= args.i_begin && i < args.i_end;
     const int64_t row_base = i * (2 * args.n_v - i - 1) / 2 - i - 1 - args.pair0;
     if constexpr (PRELOAD) {
@@ -331,7 +344,7 @@ struct Epi2Split {
     }
   }
 
-  __device__ __forceinline__ static void chunk(const Params &args, const SplitSchedPair &sc, int a,
+  __device__ __forceinline__ static void chunk(const Params &args, Tile2 sc, int a,
                                                int64_t i, bool row_ok, int64_t row_base, int c,
                                                const uint32_t (&v)[32]) {
 #pragma unroll
@@ -390,7 +403,8 @@ struct BatchPanel {
   Tally2Args args;
   TriSched::Params tri;
   int nkb;
-  int64_t tiles;
+  int split;      // K parts per tile (SM-pair launches; 1 = unsplit)
+  int64_t tiles;  // tiles of the panel's triangle
 };
 
 struct BatchParams {
@@ -405,19 +419,22 @@ struct BatchMaps {
 
 static_assert(sizeof(BatchParams) + sizeof(BatchMaps) < 32000, "kernel parameter space");
 
-// All tiles of panel 0, then of panel 1, ...: the CTAs of one persistent launch
-// share every panel's triangle, so small panels fill the SMs big ones leave idle.
+// All units of panel 0, then of panel 1, ...: the CTAs of one persistent
+// launch share every panel's triangle, so small panels fill the SMs big ones
+// leave idle.  A panel with split > 1 has tiles x split units, part-major as in
+// SplitSchedPair (unit u = tile u % tiles, K part u / tiles).
 template <class Inner>
 struct BatchSchedT {
   using Params = BatchParams;
   const BatchParams *bp;
   int p;
-  int64_t pos;  // tile position inside panel p
+  int64_t pos;  // unit position inside panel p
   Inner t;
   bool valid;
 
+  __device__ int64_t units(int q) const { return bp->p[q].tiles * bp->p[q].split; }
   __device__ void start_panel() {
-    while (p < bp->n && bp->p[p].tiles == 0) ++p;
+    while (p < bp->n && units(p) == 0) ++p;
     valid = p < bp->n;
     pos = 0;
     if (valid) t.init(bp->p[p].tri, 0);
@@ -430,10 +447,13 @@ struct BatchSchedT {
   }
   __device__ void advance(int64_t step) {
     while (valid && step > 0) {
-      const int64_t rem = bp->p[p].tiles - 1 - pos;
+      const int64_t rem = units(p) - 1 - pos;
       if (step <= rem) {
-        t.advance(step);
         pos += step;
+        if (bp->p[p].split == 1)
+          t.advance(step);
+        else
+          t.init(bp->p[p].tri, pos % bp->p[p].tiles);
         return;
       }
       step -= rem + 1;
@@ -441,9 +461,15 @@ struct BatchSchedT {
       start_panel();
     }
   }
+  __device__ int part() const { return static_cast<int>(pos / bp->p[p].tiles); }
   __device__ int map_index() const { return p; }
-  __device__ int k_blocks(int) const { return bp->p[p].nkb; }
-  __device__ int k_begin() const { return 0; }
+  __device__ int k_begin() const {
+    return static_cast<int>(static_cast<int64_t>(part()) * bp->p[p].nkb / bp->p[p].split);
+  }
+  __device__ int k_blocks(int) const {
+    return static_cast<int>(static_cast<int64_t>(part() + 1) * bp->p[p].nkb / bp->p[p].split) -
+           k_begin();
+  }
   __device__ int a_row() const { return t.a_row(); }
   __device__ int b_row() const { return t.b_row(); }
 };
@@ -458,8 +484,13 @@ struct EpiBatchPair {
   __device__ static void tile(const Params &bp, const BatchSchedPair &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *stage) {
-    Epi2Staged::body<NC, PRELOAD>(bp.p[sc.p].args, Tile2{2 * sc.t.I + rank, sc.t.J}, quarter, lane,
-                                  t_base, release_cluster_bar, c0, stage);
+    const BatchPanel &q = bp.p[sc.p];
+    if (q.split > 1)  // a K part: partial tallies added into the zeroed output
+      Epi2Split::body<NC, PRELOAD>(q.args, Tile2{2 * sc.t.I + rank, sc.t.J}, quarter, lane, t_base,
+                                   release_cluster_bar, c0);
+    else
+      Epi2Staged::body<NC, PRELOAD>(q.args, Tile2{2 * sc.t.I + rank, sc.t.J}, quarter, lane,
+                                    t_base, release_cluster_bar, c0, stage);
   }
 };
 
@@ -469,6 +500,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EW, 1)
                              const __grid_constant__ BatchParams bp) {
   tcp::persistent_gemm_pair<BatchSchedPair, EpiBatchPair, EW>(maps.a, bp, bp, 0,
                                                              bp.p[0].args.status);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_EW, 1)
+    k_tally2_tc_pair_batched_fp4(const __grid_constant__ BatchMaps maps,
+                                 const __grid_constant__ BatchParams bp) {
+  tcp::persistent_gemm_pair<BatchSchedPair, EpiBatchPair, tcp::FP4_EW, false, true>(
+      maps.a, bp, bp, 0, bp.p[0].args.status);
 }
 
 struct EpiBatch {
@@ -550,8 +588,8 @@ int64_t tc2_pair_tiles(int64_t n_v, int64_t I0, int64_t I1) {
 }
 
 int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *ops,
-                                  const int64_t *rows_pad, const int64_t *kpad, int n, int group,
-                                  int num_sms, cudaStream_t s) {
+                                  const int64_t *rows_pad, const int64_t *kpad, const int *split,
+                                  int n, int group, int num_sms, cudaStream_t s, bool fp4) {
   static bool attr_set[kMaxDevices] = {};
   if (n < 1 || n > kMaxBatchPanels) return CCC_EINVAL;
   const int dev = current_device();
@@ -562,7 +600,10 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
                              static_cast<int>(pair_smem(4))) != cudaSuccess ||
         cudaFuncSetAttribute(k_tally2_tc_pair_batched<8>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(pair_smem(8))) != cudaSuccess)
+                             static_cast<int>(pair_smem(8))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_pair_batched_fp4,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(pair_smem(tcp::FP4_EW))) != cudaSuccess)
       return CCC_ECUDA;
     attr_set[dev] = true;
   }
@@ -570,10 +611,13 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
   thread_local BatchParams bp;
   memset(&bp, 0, sizeof(bp));
   bp.n = n;
-  int64_t tiles = 0;
+  int64_t units = 0;
   double kw = 0.0;
   for (int k = 0; k < n; ++k) {
     BatchPanel &q = bp.p[k];
+    // e2m1 rows hold kpad entries in kpad / 2 bytes; a K stage is 128 bytes.
+    if (fp4 && kpad[k] % 256 != 0) return CCC_EINVAL;
+    const int64_t row_bytes = fp4 ? kpad[k] / 2 : kpad[k];
     q.args = args[k];
     q.tri.nI = static_cast<int>((args[k].n_v + 127) / 128);
     q.tri.nJ = q.tri.nI;
@@ -581,16 +625,17 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
     q.tri.shift = 0;
     q.tri.I0 = 0;
     q.tri.I1 = q.tri.nI;
-    q.nkb = static_cast<int>(kpad[k] / BK);
+    q.nkb = static_cast<int>(row_bytes / BK);
+    q.split = split != nullptr && split[k] > 1 ? (split[k] < q.nkb ? split[k] : q.nkb) : 1;
     q.tiles = args[k].n_v >= 2 ? tc2_pair_tiles(args[k].n_v, 0, q.tri.nI) : 0;
-    tiles += q.tiles;
+    units += q.tiles * q.split;
     kw += static_cast<double>(q.tiles) * q.nkb;
-    if (!make_operand_map(&maps.a[k], ops[k], rows_pad[k], kpad[k], tcp::BMH)) return CCC_ECUDA;
+    if (!make_operand_map(&maps.a[k], ops[k], rows_pad[k], row_bytes, tcp::BMH)) return CCC_ECUDA;
   }
-  if (tiles == 0) return CCC_OK;
-  const int ew = epilogue_warps(static_cast<int>(kw / static_cast<double>(tiles)));
-  static int max_clusters[kMaxDevices][2] = {};
-  int &mc = max_clusters[dev][ew == 4 ? 0 : 1];
+  if (units == 0) return CCC_OK;
+  const int ew = fp4 ? tcp::FP4_EW : epilogue_warps(static_cast<int>(kw / static_cast<double>(units)));
+  static int max_clusters[kMaxDevices][3] = {};
+  int &mc = max_clusters[dev][fp4 ? 2 : ew == 4 ? 0 : 1];
   if (mc == 0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
@@ -605,14 +650,18 @@ int launch_tally2_tc_pair_batched(const Tally2Args *args, const uint8_t *const *
     cfg.numAttrs = 1;
     int m = 0;
     const cudaError_t e =
-        ew == 4 ? cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched<4>, &cfg)
-                : cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched<8>, &cfg);
+        fp4 ? cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched_fp4, &cfg)
+        : ew == 4 ? cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched<4>, &cfg)
+                  : cudaOccupancyMaxActiveClusters(&m, k_tally2_tc_pair_batched<8>, &cfg);
     if (e != cudaSuccess || m < 1) return CCC_ECUDA;
     mc = m < num_sms / 2 ? m : num_sms / 2;
   }
-  const int64_t clusters = tiles < mc ? tiles : mc;
+  const int64_t clusters = units < mc ? units : mc;
   const int grid = static_cast<int>(2 * clusters);
-  if (ew == 4)
+  if (fp4)
+    k_tally2_tc_pair_batched_fp4<<<grid, 64 + 32 * tcp::FP4_EW, pair_smem(tcp::FP4_EW), s>>>(maps,
+                                                                                           bp);
+  else if (ew == 4)
     k_tally2_tc_pair_batched<4><<<grid, 64 + 32 * 4, pair_smem(4), s>>>(maps, bp);
   else
     k_tally2_tc_pair_batched<8><<<grid, 64 + 32 * 8, pair_smem(8), s>>>(maps, bp);
@@ -649,6 +698,7 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
     q.tri.I0 = 0;
     q.tri.I1 = q.tri.nI;
     q.nkb = static_cast<int>(kpad[k] / BK);
+    q.split = 1;
     q.tiles = args[k].n_v >= 2 ? tc2_num_tiles(args[k].n_v) : 0;
     tiles += q.tiles;
     if (!make_operand_map(&maps.a[k], ops[k], rows_pad[k], kpad[k], BM) ||

@@ -125,8 +125,9 @@ __host__ __device__ inline int64_t mask_prefix(int64_t x, int64_t n_v) {
 }
 
 // Tiles of the slabs [j0, j1): slab j has ceil(j / 128) i-blocks times
-// ceil((n_v - 1 - j) / SNPK) k-blocks, i-block-major.
-template <int SNPK>
+// ceil((n_v - 1 - j) / SNPK) k-blocks, i-block-major.  KBI: individuals per
+// 128-byte K stage (128 for e4m3 operands, 256 for e2m1).
+template <int SNPK, int KBI = kBK>
 struct ClassSchedT {
   struct Params {
     int j0, j1, n_v, nkb;
@@ -196,7 +197,7 @@ struct ClassSchedT {
   __device__ int d_blocks(bool *full) const {
     const int c = missing();
     *full = c > kCap;
-    return *full ? nkb : static_cast<int>(cdiv(c, kBK));
+    return *full ? nkb : static_cast<int>(cdiv(c, KBI));
   }
 };
 using ClassSched = ClassSchedT<kSnpK>;
@@ -579,8 +580,20 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
 // a small global scratch (two tiles per CTA, 128 KB, L2-resident) before the
 // T phase of tile u overwrites the accumulator.
 namespace wide {
-constexpr int kSnpK = 128;
-constexpr int kN = 256;
+// Tile shape by operand type.  e4m3: 128 SNPs k (N = 256), two 256-column T
+// accumulators.  e2m1 (FP4, block-scaled kind::mxf4): the scale factors need
+// 32 TMEM columns of their own, so the T accumulators are 240 columns wide
+// (120 SNPs k, N = 240), at 0 and 240, and the factors sit at 480-511; a
+// 128-byte K stage then holds 256 individuals.
+template <bool FP4>
+struct Cfg {
+  static constexpr int kSnpK = FP4 ? 120 : 128;
+  static constexpr int kN = 2 * kSnpK;
+  static constexpr int kKBI = FP4 ? 256 : kBK;  // individuals per K stage
+  static constexpr int kChunks = kSnpK / 8;     // 8-SNP epilogue chunks
+  using Sched = ClassSchedT<kSnpK, kKBI>;
+};
+constexpr uint32_t kSfCol = 480;
 constexpr int kStages = 6;
 constexpr int kTile = 128 * kBK;                  // 128 rows x 128 bytes
 constexpr int kStageBytes = 2 * kTile;            // A + B per CTA
@@ -593,28 +606,30 @@ constexpr size_t kSmem = 1024 + static_cast<size_t>(kStages) * kStageBytes + kNu
 // their register cap of 146 cost more than the added overlap gave).
 constexpr int kEpiWarps = 8;
 constexpr int kGroups = kEpiWarps / 4;
-constexpr int kChunks = kSnpK / 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 static_assert(kSmem <= 232448, "dynamic shared memory limit");
-using Sched = ClassSchedT<kSnpK>;
+static_assert(2 * Cfg<true>::kN + 32 <= 512 && kSfCol == 2 * Cfg<true>::kN, "FP4 TMEM layout");
+static_assert(Cfg<true>::kN % 16 == 0 && Cfg<true>::kN / 2 <= 128, "FP4 tile: N per CTA in the B box");
 }  // namespace wide
 
 constexpr int64_t kWideMaxNf = 16383;  // 4 n_f < 2^16
 
 // MODE 0: tallies only; 1: tallies and CCC, PERSNP; 2: tallies and CCC, JOINT.
-template <int MODE>
+// FP4: e2m1 operands (see wide::Cfg).
+template <int MODE, bool FP4>
 __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
     k_tally3_class_w(const __grid_constant__ CUtensorMap tmOp,
                      const __grid_constant__ CUtensorMap tmC, const ClassArgs args,
-                     wide::Sched::Params sp) {
+                     typename wide::Cfg<FP4>::Sched::Params sp) {
   constexpr int kStages = wide::kStages;
   constexpr int kTile = wide::kTile;
   constexpr int kStageBytes = wide::kStageBytes;
   constexpr int kDWords = wide::kDWords;
   constexpr int kNumBars = wide::kNumBars;
-  constexpr int kN = wide::kN;
+  constexpr int kN = wide::Cfg<FP4>::kN;
+  constexpr int kChunks = wide::Cfg<FP4>::kChunks;
   constexpr int kEpiWarps = wide::kEpiWarps;
-  using Sched = wide::Sched;
+  using Sched = typename wide::Cfg<FP4>::Sched;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -671,6 +686,22 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
   const uint32_t tmem_base = *tmem_slot;
   const int64_t cstart = blockIdx.x >> 1;
   const int64_t cstep = gridDim.x >> 1;
+  if (FP4) {
+    // Scale factors 1.0 (UE8M0) in columns kSfCol .. kSfCol + 31 of both CTAs,
+    // one lane quarter per epilogue warp, before the leader's first MMA.
+    if (warp >= 2 && warp < 6) {
+      uint32_t v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = tcp::SF_ONE_UE8M0;
+      tmem_st_32x32b_x32(tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16) + wide::kSfCol,
+                         v);
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+  }
   const int64_t n_v = args.t.n_v;
   const int nkb = sp.nkb;
   // T k-blocks of a tile before the next tile's D phase is issued: late enough
@@ -701,7 +732,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
       // Rows of a tile: i side of this CTA, k side of this CTA.
       auto rows_t = [&](const Sched &t, int *ya, int *yb) {
         const int ia = 2 * (t.i0() + 64 * static_cast<int>(rank));
-        const int kr = 2 * t.k0() + 128 * static_cast<int>(rank);
+        const int kr = 2 * t.k0() + (kN / 2) * static_cast<int>(rank);
         const int mrow = t.mrow();
         if (t.i_masked()) {
           *ya = mrow + ia;
@@ -725,7 +756,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
         } else {
           const int cb = t.slab() * static_cast<int>(2 * n_v);
           const int ia = cb + 2 * (t.i0() + 64 * static_cast<int>(rank));
-          const int kr = cb + 2 * t.k0() + 128 * static_cast<int>(rank);
+          const int kr = cb + 2 * t.k0() + (kN / 2) * static_cast<int>(rank);
           for (int kb = 0; kb < nd; ++kb)
             if (!step(&tmC, ia, kr, kb * kBK)) return false;
         }
@@ -762,7 +793,15 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
       // ---------------- MMA issuer (leader CTA)
       const uint64_t dA0 = smem_desc_sw128(smem_u32(sA));
       const uint64_t dB0 = smem_desc_sw128(smem_u32(sB));
-      constexpr uint32_t idesc = idesc_e4m3_f32(256, kN);
+      constexpr uint32_t idesc = FP4 ? idesc_e2m1_f32(256, kN, true) : idesc_e4m3_f32(256, kN);
+      const uint32_t sfa = tmem_base + wide::kSfCol, sfb = tmem_base + wide::kSfCol + 16;
+      // One MMA of the kind: K = 32 e4m3 or 64 e2m1 entries = 32 bytes of the stage.
+      auto mma = [&](uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t acc) {
+        if (FP4)
+          tcp::mma_mxf4_pair(d_tmem, da, db, idesc, sfa, sfb, acc);
+        else
+          tcp::mma_f8f6f4_pair(d_tmem, da, db, idesc, acc);
+      };
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -773,10 +812,9 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
           tc_fence_after();
           const uint64_t da = dA0 + static_cast<uint64_t>(stage * (kTile >> 4));
           const uint64_t db = dB0 + static_cast<uint64_t>(stage * (kTile >> 4));
-          tcp::mma_f8f6f4_pair(d_tmem, da, db, idesc, kb != 0 ? 1u : 0u);
+          mma(d_tmem, da, db, kb != 0 ? 1u : 0u);
 #pragma unroll
-          for (int k = 1; k < kBK / kUK; ++k)
-            tcp::mma_f8f6f4_pair(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), idesc, 1u);
+          for (int k = 1; k < kBK / kUK; ++k) mma(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), 1u);
           tcp::mma_commit_pair(empty_bar(stage), 0x3);
           if (++stage == kStages) {
             stage = 0;
@@ -792,10 +830,9 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
           tc_fence_after();
           const uint64_t da = dA0 + static_cast<uint64_t>(stage * (kTile >> 4));
           const uint64_t db = dB0 + static_cast<uint64_t>(stage * (kTile >> 4));
-          tcp::mma_f8f6f4_pair(d_tmem, da, db, idesc, kb != 0 ? 1u : 0u);
+          mma(d_tmem, da, db, kb != 0 ? 1u : 0u);
 #pragma unroll
-          for (int k = 1; k < kBK / kUK; ++k)
-            tcp::mma_f8f6f4_pair(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), idesc, 1u);
+          for (int k = 1; k < kBK / kUK; ++k) mma(d_tmem, da + (k * kUK >> 4), db + (k * kUK >> 4), 1u);
           tcp::mma_commit_pair(empty_bar(stage), 0x3);
           if (++stage == kStages) {
             stage = 0;
@@ -910,7 +947,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
           tc_fence_after();
           uint32_t *slot = dsc + (u & 1) * kDWords;
 #pragma unroll 1
-          for (int c = group; c < wide::kChunks; c += wide::kGroups) {
+          for (int c = group; c < kChunks; c += wide::kGroups) {
             uint32_t v[16];
             tmem_ld_32x32b_x16(lane_base + (u & 1) * kN + 16 * c, v);
             tmem_ld_wait();
@@ -950,8 +987,8 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
           wj1 = __ldg(wv + 2 * j + 1);
         }
         constexpr int KC = 8;  // SNPs k per chunk (16 accumulator columns)
-        const int c_last = group + wide::kGroups * ((wide::kChunks - 1 - group) / wide::kGroups);
-        for (int c = group; c < wide::kChunks; c += wide::kGroups) {
+        const int c_last = group + wide::kGroups * ((kChunks - 1 - group) / wide::kGroups);
+        for (int c = group; c < kChunks; c += wide::kGroups) {
           const int kl = KC * c;  // first local SNP k of the chunk
           const int64_t kc = k_first + kl;
           uint32_t x[2 * KC];
@@ -1057,6 +1094,8 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
 // next batch's preparation overlaps the current batch's tallies.
 constexpr int kPrepThreads = 128;
 
+// FP4: the compacted rows in e2m1 nibbles, 256 individuals in 128 bytes per row.
+template <bool FP4>
 __global__ void __launch_bounds__(kPrepThreads, 9) k_compact3(const uint64_t *__restrict__ geno, int64_t n_f,
                                                   int64_t n_v, int64_t ld, int64_t j0,
                                                   uint8_t *__restrict__ cbuf,
@@ -1104,23 +1143,85 @@ __global__ void __launch_bounds__(kPrepThreads, 9) k_compact3(const uint64_t *__
   }
   if (blockIdx.y == 0 && tid == 0) missing[blockIdx.x] = running;
   if (running == 0 || running > kCap) return;
-  const int ncols = (running + kBK - 1) / kBK * kBK;
   const int64_t s_lo = static_cast<int64_t>(blockIdx.y) * snps_per_cta;
   const int64_t s_hi = s_lo + snps_per_cta < n_v ? s_lo + snps_per_cta : n_v;
-  for (int64_t s = s_lo + warp; s < s_hi; s += kWarps) {
-    uint8_t *row0 = cbuf + (static_cast<int64_t>(blockIdx.x) * 2 * n_v + 2 * s) * kCap;
-    for (int idx = lane; idx < ncols; idx += 32) {
-      uint32_t code = 2u;  // missing: both counts 0
-      if (idx < running) {
-        const int q = pos[idx];
-        code = static_cast<uint32_t>(__ldg(geno + s * ld + (q >> 5)) >> (2 * (q & 31))) & 3u;
+  // Code of compacted column idx of SNP s (missing past the count: both counts 0).
+  auto code_at = [&](int64_t s, int idx) -> uint32_t {
+    if (idx >= running) return 2u;
+    const int q = pos[idx];
+    return static_cast<uint32_t>(__ldg(geno + s * ld + (q >> 5)) >> (2 * (q & 31))) & 3u;
+  };
+  if constexpr (FP4) {
+    // e2m1 nibbles: 0 -> 0x0, 1 -> 0x2, 2 -> 0x4; column idx in the low nibble of
+    // byte idx / 2 for even idx.  One K stage of 256 individuals = 128 bytes.
+    constexpr int kRow = kCap / 2;
+    const int nbytes = (running + 255) / 256 * 128;
+    for (int64_t s = s_lo + warp; s < s_hi; s += kWarps) {
+      uint8_t *row0 = cbuf + (static_cast<int64_t>(blockIdx.x) * 2 * n_v + 2 * s) * kRow;
+      for (int b = lane; b < nbytes; b += 32) {
+        uint32_t n0 = 0u, n1 = 0u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t code = code_at(s, 2 * b + h);
+          const uint32_t r0 = code == 0u ? 4u : (code == 1u ? 2u : 0u);
+          const uint32_t r1 = code == 3u ? 4u : (code == 1u ? 2u : 0u);
+          n0 |= r0 << (4 * h);
+          n1 |= r1 << (4 * h);
+        }
+        row0[b] = static_cast<uint8_t>(n0);
+        row0[kRow + b] = static_cast<uint8_t>(n1);
       }
-      // e4m3: 0 -> 0x00, 1 -> 0x38, 2 -> 0x40
-      const uint8_t e0 = code == 0u ? 0x40 : (code == 1u ? 0x38 : 0x00);
-      const uint8_t e1 = code == 3u ? 0x40 : (code == 1u ? 0x38 : 0x00);
-      row0[idx] = e0;
-      row0[kCap + idx] = e1;
     }
+  } else {
+    const int ncols = (running + kBK - 1) / kBK * kBK;
+    for (int64_t s = s_lo + warp; s < s_hi; s += kWarps) {
+      uint8_t *row0 = cbuf + (static_cast<int64_t>(blockIdx.x) * 2 * n_v + 2 * s) * kCap;
+      for (int idx = lane; idx < ncols; idx += 32) {
+        const uint32_t code = code_at(s, idx);
+        // e4m3: 0 -> 0x00, 1 -> 0x38, 2 -> 0x40
+        const uint8_t e0 = code == 0u ? 0x40 : (code == 1u ? 0x38 : 0x00);
+        const uint8_t e1 = code == 3u ? 0x40 : (code == 1u ? 0x38 : 0x00);
+        row0[idx] = e0;
+        row0[kCap + idx] = e1;
+      }
+    }
+  }
+}
+
+// Per-nibble masks of the 32 individuals of one packed code word w: keep
+// nibble q = 0xF where the selected class holds for individual q (low nibble
+// of byte q / 2 for even q, as the e2m1 operand rows store them), neg nibble q
+// = 0x8 (the e2m1 sign bit) where the sign flips.
+__device__ __forceinline__ uint64_t spread_2to4_64(uint32_t x32) {
+  uint64_t x = x32;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  return x;
+}
+
+__device__ __forceinline__ void class_masks_e2m1(uint64_t w, bool missing_mode, uint32_t (&keep)[4],
+                                                 uint32_t (&neg)[4]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t x = static_cast<uint32_t>(w >> (32 * h));
+    uint32_t kb, nb;
+    if (!missing_mode) {
+      kb = ~(x ^ (x >> 1)) & 0x55555555u;  // codes 00 and 11 (homozygous)
+      nb = x & (x >> 1) & 0x55555555u;     // code 11: s_j = -1
+    } else {
+      kb = (x >> 1) & ~x & 0x55555555u;  // code 10: missing
+      nb = 0u;
+    }
+    const uint64_t yk = spread_2to4_64(kb);  // 1 in the low bit of each kept nibble
+    const uint64_t yn = spread_2to4_64(nb);
+    const uint64_t km = (yk << 4) - yk;     // 0xF per kept nibble
+    const uint64_t nm = yn << 3;            // 0x8 per negated nibble
+    keep[2 * h] = static_cast<uint32_t>(km);
+    keep[2 * h + 1] = static_cast<uint32_t>(km >> 32);
+    neg[2 * h] = static_cast<uint32_t>(nm);
+    neg[2 * h + 1] = static_cast<uint32_t>(nm >> 32);
   }
 }
 
@@ -1131,6 +1232,9 @@ __global__ void __launch_bounds__(kPrepThreads, 9) k_compact3(const uint64_t *__
 //                                                          more than kCap missing)
 // in the operand buffer op (rows of kpad bytes; R occupies the first rows).
 // A CTA takes every gridDim.x-th row of its slab; a thread 16 bytes at a time.
+// FP4: e2m1 rows of kpad / 2 bytes, 16 bytes = the 32 individuals of one packed
+// word; the sign of a nibble is its bit 3.
+template <bool FP4>
 __global__ void __launch_bounds__(kPrepThreads, 9) k_mask3c(const uint64_t *__restrict__ geno, int64_t n_f,
                                                 int64_t n_v, int64_t ld, uint8_t *__restrict__ op,
                                                 int64_t kpad, int64_t mrow0, int64_t j0,
@@ -1140,7 +1244,8 @@ __global__ void __launch_bounds__(kPrepThreads, 9) k_mask3c(const uint64_t *__re
   const bool im = 2 * j <= n_v - 1;
   const bool dfull = __ldg(missing + blockIdx.y) > kCap;
   const int64_t rows = (dfull ? 4 : 2) * side;
-  const int chunks = static_cast<int>(kpad / 16);
+  const int64_t row_bytes = FP4 ? kpad / 2 : kpad;
+  const int chunks = static_cast<int>(row_bytes / 16);
   const int64_t mrow = mrow0 + 4 * (mask_prefix(j, n_v) - mask_prefix(j0, n_v));
   const int64_t words = (n_f + 31) / 32;
   const uint64_t *__restrict__ gj = geno + j * ld;
@@ -1158,19 +1263,25 @@ __global__ void __launch_bounds__(kPrepThreads, 9) k_mask3c(const uint64_t *__re
       dm[u] = r >= 2 * side;
       const int64_t rt = dm[u] ? r - 2 * side : r;
       const int64_t sn = im ? (rt >> 1) : j + 1 + (rt >> 1);
-      src[u] = reinterpret_cast<const uint4 *>(op + (2 * sn + (rt & 1)) * kpad);
-      dst[u] = reinterpret_cast<uint4 *>(op + (mrow + r) * kpad);
+      src[u] = reinterpret_cast<const uint4 *>(op + (2 * sn + (rt & 1)) * row_bytes);
+      dst[u] = reinterpret_cast<uint4 *>(op + (mrow + r) * row_bytes);
     }
     for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-      const int wi = c >> 1;
-      uint32_t w = 0u;
-      if (wi < words) w = static_cast<uint32_t>(__ldg(gj + wi) >> (32 * (c & 1)));
+      uint32_t ks[4], ns[4], km[4], nm[4];
+      if (FP4) {
+        const uint64_t w = c < words ? __ldg(gj + c) : 0ull;
+        class_masks_e2m1(w, false, ks, ns);
+        class_masks_e2m1(w, true, km, nm);
+      } else {
+        const int wi = c >> 1;
+        uint32_t w = 0u;
+        if (wi < words) w = static_cast<uint32_t>(__ldg(gj + wi) >> (32 * (c & 1)));
+        class_masks(w, false, ks, ns);
+        class_masks(w, true, km, nm);
+      }
       uint4 v[kRows];
 #pragma unroll
       for (int u = 0; u < kRows; ++u) v[u] = live[u] ? __ldg(src[u] + c) : make_uint4(0u, 0u, 0u, 0u);
-      uint32_t ks[4], ns[4], km[4], nm[4];
-      class_masks(w, false, ks, ns);
-      class_masks(w, true, km, nm);
 #pragma unroll
       for (int u = 0; u < kRows; ++u) {
         if (!live[u]) continue;
@@ -1194,38 +1305,48 @@ int64_t tc3_class_mask_rows(int64_t j0, int64_t j1, int64_t n_v) {
 }
 
 int launch_compact3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *cbuf,
-                    int32_t *missing, int64_t j0, int64_t j1, cudaStream_t s) {
+                    int32_t *missing, int64_t j0, int64_t j1, cudaStream_t s, bool fp4) {
   if (j1 <= j0) return CCC_OK;
   const int snps_per_cta = 64;
   const dim3 grid(static_cast<unsigned>(j1 - j0), static_cast<unsigned>(cdiv(n_v, snps_per_cta)), 1);
-  k_compact3<<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, j0, cbuf, missing, snps_per_cta);
+  if (fp4)
+    k_compact3<true><<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, j0, cbuf, missing,
+                                                   snps_per_cta);
+  else
+    k_compact3<false><<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, j0, cbuf, missing,
+                                                    snps_per_cta);
   return note_launch();
 }
 
 int launch_mask3c(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                   int64_t kpad, int64_t mrow0, const int32_t *missing, int64_t j0, int64_t j1,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool fp4) {
   if (j1 <= j0) return CCC_OK;
   // About 8 CTAs per SM in total; each slab's rows are spread over bx CTAs.
   int64_t bx = cdiv(8 * 160, j1 - j0);
   if (bx < 2) bx = 2;
   if (bx > 256) bx = 256;
   const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(j1 - j0), 1);
-  k_mask3c<<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, op, kpad, mrow0, j0, missing);
+  if (fp4 && kpad % 256 != 0) return CCC_EINVAL;
+  if (fp4)
+    k_mask3c<true><<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, op, kpad, mrow0, j0, missing);
+  else
+    k_mask3c<false><<<grid, kPrepThreads, 0, s>>>(geno, n_f, n_v, ld, op, kpad, mrow0, j0, missing);
   return note_launch();
 }
 
 // Wide tiles (k_tally3_class_w) when 4 n_f fits in 16 bits, else N = 160 tiles.
-template <int MODE>
+template <int MODE, bool FP4>
 static int launch_wide_mode(const CUtensorMap &tmOp, const CUtensorMap &tmC, const ClassArgs &ca,
-                            const wide::Sched::Params &sp, int64_t tiles, int num_sms,
-                            cudaStream_t s) {
+                            const typename wide::Cfg<FP4>::Sched::Params &sp, int64_t tiles,
+                            int num_sms, cudaStream_t s) {
   static int max_clusters_dev[kMaxDevices] = {};
   const int dev_c = current_device();
   if (dev_c < 0) return CCC_ECUDA;
   int &max_clusters = max_clusters_dev[dev_c];
   if (max_clusters == 0) {
-    if (cudaFuncSetAttribute(k_tally3_class_w<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tally3_class_w<MODE, FP4>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(wide::kSmem)) != cudaSuccess)
       return CCC_ECUDA;
     cudaLaunchConfig_t cfg = {};
@@ -1240,44 +1361,52 @@ static int launch_wide_mode(const CUtensorMap &tmOp, const CUtensorMap &tmC, con
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_tally3_class_w<MODE>, &cfg) != cudaSuccess || n < 1)
+    if (cudaOccupancyMaxActiveClusters(&n, k_tally3_class_w<MODE, FP4>, &cfg) != cudaSuccess ||
+        n < 1)
       return CCC_ECUDA;
     max_clusters = n < num_sms / 2 ? n : num_sms / 2;
     if (max_clusters > wide::kMaxCtas / 2) max_clusters = wide::kMaxCtas / 2;
   }
   const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
-  k_tally3_class_w<MODE><<<static_cast<unsigned>(2 * clusters), wide::kThreads, wide::kSmem, s>>>(
-      tmOp, tmC, ca, sp);
+  k_tally3_class_w<MODE, FP4><<<static_cast<unsigned>(2 * clusters), wide::kThreads, wide::kSmem,
+                                s>>>(tmOp, tmC, ca, sp);
   return note_launch();
 }
 
 // Wide tiles (k_tally3_class_w) when 4 n_f fits in 16 bits, else N = 160 tiles.
+// fp4: op rows (R and the masked rows) of kpad / 2 bytes, compacted rows of
+// kCap / 2 bytes, all e2m1.
+template <bool FP4>
 static int launch_tally3_class_w(const Tally3Args &a, const uint8_t *op, int64_t op_rows,
                                  int64_t mrow0, int64_t kpad, const int32_t *rtab,
                                  const uint8_t *cbuf, const int32_t *missing, uint32_t *dscratch,
                                  int64_t j0, int64_t j1, int num_sms, cudaStream_t s) {
+  using C = wide::Cfg<FP4>;
   int64_t tiles = 0;
-  for (int64_t j = j0; j < j1; ++j) tiles += cdiv(j, kSnpI) * cdiv(a.n_v - 1 - j, wide::kSnpK);
+  for (int64_t j = j0; j < j1; ++j) tiles += cdiv(j, kSnpI) * cdiv(a.n_v - 1 - j, C::kSnpK);
   if (tiles == 0) return CCC_OK;
+  if (FP4 && kpad % 256 != 0) return CCC_EINVAL;
+  const int64_t row_bytes = FP4 ? kpad / 2 : kpad;
   CUtensorMap tmOp, tmC;
   const int64_t crows = tc3_class_cbuf_rows(j1 - j0, a.n_v);
-  if (!tc::make_operand_map(&tmOp, op, op_rows, kpad, 128) ||
-      !tc::make_operand_map(&tmC, cbuf, crows, kCap, 128))
+  if (!tc::make_operand_map(&tmOp, op, op_rows, row_bytes, 128) ||
+      !tc::make_operand_map(&tmC, cbuf, crows, FP4 ? kCap / 2 : kCap, 128))
     return CCC_ECUDA;
   ClassArgs ca;
   ca.t = a;
   ca.rtab = rtab;
   ca.dscratch = dscratch;
-  wide::Sched::Params sp;
+  typename C::Sched::Params sp;
   sp.j0 = static_cast<int>(j0);
   sp.j1 = static_cast<int>(j1);
   sp.n_v = static_cast<int>(a.n_v);
-  sp.nkb = static_cast<int>(kpad / kBK);
+  sp.nkb = static_cast<int>(row_bytes / kBK);
   sp.mrow0 = static_cast<int>(mrow0);
   sp.missing = missing;
-  if (a.ccc == nullptr) return launch_wide_mode<0>(tmOp, tmC, ca, sp, tiles, num_sms, s);
-  if (a.norm == CCC_NORM_PERSNP) return launch_wide_mode<1>(tmOp, tmC, ca, sp, tiles, num_sms, s);
-  return launch_wide_mode<2>(tmOp, tmC, ca, sp, tiles, num_sms, s);
+  if (a.ccc == nullptr) return launch_wide_mode<0, FP4>(tmOp, tmC, ca, sp, tiles, num_sms, s);
+  if (a.norm == CCC_NORM_PERSNP)
+    return launch_wide_mode<1, FP4>(tmOp, tmC, ca, sp, tiles, num_sms, s);
+  return launch_wide_mode<2, FP4>(tmOp, tmC, ca, sp, tiles, num_sms, s);
 }
 
 int64_t tc3_class_dscratch_bytes() {
@@ -1287,11 +1416,14 @@ int64_t tc3_class_dscratch_bytes() {
 int launch_tally3_class(const Tally3Args &a, const uint8_t *op, int64_t op_rows, int64_t mrow0,
                         int64_t kpad, const int32_t *rtab, const uint8_t *cbuf,
                         const int32_t *missing, uint32_t *dscratch, int64_t j0, int64_t j1,
-                        int num_sms, cudaStream_t s) {
+                        int num_sms, cudaStream_t s, bool fp4) {
   if (j1 <= j0) return CCC_OK;
+  if (fp4 && !(a.n_f <= kWideMaxNf && dscratch != nullptr)) return CCC_EUNSUPPORTED;
   if (a.n_f <= kWideMaxNf && dscratch != nullptr)
-    return launch_tally3_class_w(a, op, op_rows, mrow0, kpad, rtab, cbuf, missing, dscratch, j0, j1,
-                                 num_sms, s);
+    return fp4 ? launch_tally3_class_w<true>(a, op, op_rows, mrow0, kpad, rtab, cbuf, missing,
+                                             dscratch, j0, j1, num_sms, s)
+               : launch_tally3_class_w<false>(a, op, op_rows, mrow0, kpad, rtab, cbuf, missing,
+                                              dscratch, j0, j1, num_sms, s);
   static bool attr_set_dev[kMaxDevices] = {};
   const int dev_a = current_device();
   if (dev_a < 0) return CCC_ECUDA;

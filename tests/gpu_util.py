@@ -56,16 +56,17 @@ def run_2way(geno_np, n_f, path, norm=0, gamma=2.0 / 3.0, fused=True, tile=0, sp
 
 
 def run_3way(geno_np, n_f, path, j_begin=0, j_end=None, norm=0, gamma=2.0 / 3.0, fused=True,
-             tile=0):
+             tile=0, operand=0):
     import paper_1705_08213_gb300 as ccc
     torch = torch_mod()
     g = to_device(geno_np)
     n_v = geno_np.shape[0]
     j_end = n_v if j_end is None else j_end
     nt = ccc.ccc3_count(n_v, j_begin, j_end)
-    opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, tile=tile)
+    opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, tile=tile, operand=operand)
     ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_3WAY))
-    opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, workspace=ws, tile=tile)
+    opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, workspace=ws, tile=tile,
+                                operand=operand)
     tally = torch.full((max(nt, 1), 8), -7, dtype=torch.int32, device="cuda")
     out = torch.full((max(nt, 1), 8), -7.0, dtype=torch.float32, device="cuda")
     if fused:

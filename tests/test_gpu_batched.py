@@ -24,7 +24,8 @@ def _batch(shapes, seed):
             for k, (n_v, n_f) in enumerate(shapes)]
 
 
-def _run_batched(genos_np, shapes, path=0, tune=False, group=0, order=0):
+def _run_batched(genos_np, shapes, path=0, tune=False, group=0, order=0, split=0, solo=0,
+                 operand=0, tile=0, opts_out=None):
     import torch
 
     import paper_1705_08213_gb300 as ccc
@@ -34,8 +35,8 @@ def _run_batched(genos_np, shapes, path=0, tune=False, group=0, order=0):
                for n_v, _ in shapes]
     cccs = [torch.full((max(ccc.ccc2_count(n_v), 1), 4), -7.0, dtype=torch.float32, device="cuda")
             for n_v, _ in shapes]
-    opts = ccc.ccc_opts_default(path=path)
-    opts.group, opts.order = group, order
+    opts = ccc.ccc_opts_default(path=path, operand=operand, tile=tile)
+    opts.group, opts.order, opts.split, opts.solo = group, order, split, solo
     ws = torch.empty(ccc.ccc2_batched_workspace_size(genos, n_fs, opts), dtype=torch.uint8,
                      device="cuda")
     opts.workspace = ws.data_ptr()
@@ -47,6 +48,8 @@ def _run_batched(genos_np, shapes, path=0, tune=False, group=0, order=0):
         ccc.ccc2_batched(genos, n_fs, tallies, cccs, opts)
     torch.cuda.synchronize()
     assert ccc.ccc_status(opts) == ccc.CCC_OK
+    if opts_out is not None:
+        opts_out.append(opts)
     return ([t[:ccc.ccc2_count(n_v)].cpu().numpy() for t, (n_v, _) in zip(tallies, shapes)],
             [c[:ccc.ccc2_count(n_v)].cpu().numpy() for c, (n_v, _) in zip(cccs, shapes)])
 
@@ -177,11 +180,10 @@ def _tune_launches(genos_np, shapes):
 
 
 def test_tune_cache_by_shape_buckets_and_file(tmp_path, monkeypatch):
-    """ccc2_batched_tune times six schedules and runs the chosen one: seven identical runs
-    of the batch.  A batch whose panel sizes fall in the same (n_v, n_f) power-of-two
-    buckets then takes the cached choice and runs once; with CCC_TUNE_CACHE set the choice
-    goes to a file that a cleared cache reads back.  Results stay those of the plain
-    call."""
+    """ccc2_batched_tune times a dozen schedules and runs the chosen one.  A batch whose
+    panel sizes fall in the same (n_v, n_f) power-of-two buckets then takes the cached
+    choice and runs once; with CCC_TUNE_CACHE set the choice goes to a file that a cleared
+    cache reads back.  Results stay those of the plain call."""
     import paper_1705_08213_gb300 as ccc
     shapes = [(300, 1000), (700, 2100), (1500, 600)]
     same_buckets = [(400, 1020), (600, 2050), (1100, 700)]
@@ -193,19 +195,91 @@ def test_tune_cache_by_shape_buckets_and_file(tmp_path, monkeypatch):
     for a, b in zip(t + c, ref_t + ref_c):
         np.testing.assert_array_equal(a, b)
     hit, _, _ = _tune_launches(genos, shapes)
-    assert first == 7 * hit and hit > 0, (first, hit)
+    assert first > 5 * hit and hit > 0, (first, hit)
     hit_b, t_b, _ = _tune_launches(genos_b, same_buckets)
     assert hit_b < first / 2, (first, hit_b)
     et, _ = oracle.ccc2_all(genos_b[0], same_buckets[0][1])
     assert_tally_equal(t_b[0], et, "cached schedule")
-    # the same through a file
+    # the same through a file (the candidates a tuning run times depend on which one wins
+    # each choice, so only "several runs" versus "one run" is compared)
     path = tmp_path / "tune.txt"
     monkeypatch.setenv("CCC_TUNE_CACHE", str(path))
     ccc.ccc_tune_cache_clear()
-    assert _tune_launches(genos, shapes)[0] == first
+    tuned = _tune_launches(genos, shapes)[0]
+    assert tuned > 3 * hit, (tuned, hit)
     lines = path.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("ccc-tune-v1 ")
+    assert len(lines) == 1 and lines[0].startswith("ccc-tune-v2 ")
+    f = lines[0].split()
+    assert int(f[2]) in (4, 8, 16) and int(f[3]) in (0, 1) and int(f[4]) in (1, 2)
+    assert int(f[5]) in (0, 1) and int(f[6]) in (-1, 512, 1024, 2048)
     ccc.ccc_tune_cache_clear()  # forget the process's copy: the file answers
-    assert _tune_launches(genos, shapes)[0] == hit
+    from_file, t_f, c_f = _tune_launches(genos, shapes)
+    assert from_file < tuned / 3, (tuned, from_file)
+    for a, b in zip(t_f + c_f, ref_t + ref_c):
+        np.testing.assert_array_equal(a, b)
+    assert len(path.read_text().splitlines()) == 1  # a cache hit appends nothing
     monkeypatch.delenv("CCC_TUNE_CACHE")
     ccc.ccc_tune_cache_clear()
+
+
+def test_tune_stores_the_whole_schedule_in_opts():
+    shapes = [(500, 2000), (260, 9000), (40, 100)]
+    genos = _batch(shapes, seed=55)
+    got = []
+    ts, cs = _run_batched(genos, shapes, tune=True, opts_out=got)
+    o = got[0]
+    assert o.tile in (1, 2) and o.split in (0, 1) and o.solo in (-1, 512, 1024, 2048)
+    assert o.group in (4, 8, 16) and o.order in (0, 1)
+    for g, (n_v, n_f), t, c in zip(genos, shapes, ts, cs):
+        et, ec = oracle.ccc2_all(g, n_f)
+        assert_tally_equal(t, et, f"tuned n_v={n_v}")
+        assert_ccc_close(c, ec, what=f"tuned n_v={n_v}")
+
+
+def test_batched_fp4_equals_e4m3():
+    import paper_1705_08213_gb300 as ccc
+    rng = np.random.default_rng(5)
+    shapes = [(int(rng.integers(2, 900)), int(rng.integers(1, 6000))) for _ in range(20)]
+    genos = _batch(shapes, seed=56)
+    t4, c4 = _run_batched(genos, shapes, operand=ccc.CCC_OPERAND_E2M1)
+    t8, c8 = _run_batched(genos, shapes, operand=ccc.CCC_OPERAND_E4M3)
+    for a, b in zip(t4 + c4, t8 + c8):
+        np.testing.assert_array_equal(a, b)
+    for g, (n_v, n_f), t in zip(genos[:5], shapes[:5], t4[:5]):
+        assert_tally_equal(t, oracle.ccc2_all(g, n_f)[0], f"fp4 batched n_v={n_v}")
+
+
+@pytest.mark.parametrize("operand", [0, 1])
+def test_batched_k_split_in_the_shared_launch(operand):
+    """Few small panels with long vectors: the shared launch has 8 SM-pair tiles for 76 SM
+    pairs, so its tiles run as K parts (automatic), whose summed tallies and CCC values equal
+    the oracle; every split setting gives the same results."""
+    shapes = [(300, 40000), (200, 30000), (130, 50000)]
+    genos = _batch(shapes, seed=57)
+    ref = [oracle.ccc2_all(g, f) for g, (_, f) in zip(genos, shapes)]
+    outs = {}
+    for split in (0, 1, 5):
+        outs[split] = _run_batched(genos, shapes, split=split, operand=operand)
+    for k, (et, ec) in enumerate(ref):
+        assert_tally_equal(outs[0][0][k], et, f"auto split panel {k}")
+        assert_ccc_close(outs[0][1][k], ec, what=f"auto split panel {k}")
+        for split in (1, 5):
+            np.testing.assert_array_equal(outs[split][0][k], outs[0][0][k])
+            np.testing.assert_array_equal(outs[split][1][k], outs[0][1][k])
+
+
+def test_batched_solo_thresholds_agree():
+    # One panel of 300 SM-pair tiles beside small ones: solo 100 runs it alone, the default
+    # (1024) and -1 put it in the shared launch.
+    shapes = [(3000, 1500), (200, 800), (90, 300), (500, 2100)]
+    genos = _batch(shapes, seed=58)
+    outs = [_run_batched(genos, shapes, solo=solo) for solo in (0, 100, -1)]
+    for k, (g, (n_v, n_f)) in enumerate(zip(genos, shapes)):
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o[0][k], outs[0][0][k])
+            np.testing.assert_array_equal(o[1][k], outs[0][1][k])
+    rows = np.array([0, 1500, 2998])
+    et, ec = oracle.ccc2_rows(genos[0], 1500, rows)
+    idx = np.concatenate([oracle.pair_index(i, np.arange(i + 1, 3000), 3000) for i in rows])
+    assert_tally_equal(outs[1][0][0][idx], et, "solo panel rows")
+    assert_ccc_close(outs[1][1][0][idx], ec, what="solo panel rows")

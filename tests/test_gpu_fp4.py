@@ -1,4 +1,4 @@
-"""FP4 (e2m1) count operands on the 2-way tensor-core path against the oracle.
+"""FP4 (e2m1) count operands on the 2-way and 3-way tensor-core paths against the oracle.
 
 Counts 0, 1, 2 are exact in e2m1 (nibbles 0x0, 0x2, 0x4) and every partial sum
 is an integer below 2^24, so the block-scaled MMA with unit scale factors must
@@ -12,7 +12,8 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import assert_ccc_close, assert_tally_equal, run_2way, to_device, workspace
+from tests.gpu_util import (assert_ccc_close, assert_tally_equal, run_2way, run_3way, to_device,
+                            workspace)
 
 pytestmark = pytest.mark.gpu
 
@@ -173,4 +174,78 @@ def test_fp4_where_not_built_is_refused():
         opts = ccc.ccc_opts_default(tile=tile, operand=E2M1, workspace=ws)
         with pytest.raises(ccc.CCCError) as e:
             ccc.ccc2_tally(geno, 100, t, opts)
+        assert e.value.status == ccc.CCC_EUNSUPPORTED
+
+
+# ---------------------------------------------------------------- 3-way (genotype classes)
+#
+# The sign-masked rows rho(x) s_j take the values 0, +-1, +-2 (e2m1 nibbles 0x0, 0x2, 0xA,
+# 0x4, 0xC; a masked-out count is +-0), the compacted rows of the individuals with v_j missing
+# 0, 1, 2; the wide class tiles are 128 SNPs i x 120 SNPs k here.
+
+
+@pytest.mark.parametrize("n_f", [1, 255, 256, 257, 700])
+@pytest.mark.parametrize("n_v", [3, 34, 130, 260])
+def test_fp4_3way_edges_against_oracle(n_v, n_f):
+    geno = synth.panel_uniform(n_v, n_f, seed=700 + n_v + n_f, p_missing=0.05, pad_seed=n_f + 3)
+    t, c = run_3way(geno, n_f, 0, operand=E2M1)
+    et, ec = oracle.ccc3_slabs(geno, n_f)
+    assert_tally_equal(t, et, f"fp4 3-way tally n_v={n_v} n_f={n_f}")
+    assert_ccc_close(c, ec, what=f"fp4 3-way ccc n_v={n_v} n_f={n_f}")
+
+
+@pytest.mark.parametrize("norm", [0, 1])
+def test_fp4_3way_equals_e4m3_bit_for_bit(norm):
+    n_v, n_f = 300, 3000
+    geno = synth.panel_hwe(n_v, n_f, seed=701, p_missing=0.02, pad_seed=13)
+    t4, c4 = run_3way(geno, n_f, 0, norm=norm, operand=E2M1)
+    t8, c8 = run_3way(geno, n_f, 0, norm=norm, operand=E4M3)
+    np.testing.assert_array_equal(t4, t8)
+    assert np.array_equal(c4.view(np.int32), c8.view(np.int32)), "CCC bits differ"
+    # slab ranges, and the largest n_f of the wide tiles (D counts up to 4 n_f in 16 bits)
+    for jb, je in ((0, 1), (117, 123), (150, 151), (240, 300)):
+        t, c = run_3way(geno, n_f, 0, jb, je, norm=norm, operand=E2M1)
+        et, ec = oracle.ccc3_slabs(geno, n_f, jb, je, norm=norm)
+        assert_tally_equal(t, et, f"fp4 3-way slabs [{jb},{je})")
+        assert_ccc_close(c, ec, what=f"fp4 3-way slabs [{jb},{je})")
+
+
+def test_fp4_3way_missing_counts_and_the_width_limit():
+    # SNPs with 0 .. 600 missing entries around the 256-individual compaction capacity,
+    # and n_f = 16,383, the longest vectors of the wide tiles.
+    n_f = 600
+    counts = [0, 1, 127, 128, 255, 256, 257, 400, 600]
+    g = synth.genotypes_uniform(8, 0, np.arange(3 * len(counts)), n_f, 0.0)
+    rng = np.random.default_rng(14)
+    for s_, m in enumerate(counts):
+        g[3 * s_, rng.choice(n_f, size=m, replace=False)] = -1
+    geno = synth.pack(synth.codes_from_genotypes(g), pad_seed=4)
+    t, c = run_3way(geno, n_f, 0, operand=E2M1)
+    et, ec = oracle.ccc3_slabs(geno, n_f)
+    assert_tally_equal(t, et, "fp4 3-way missing counts")
+    assert_ccc_close(c, ec, what="fp4 3-way missing counts")
+    n_f = 16383
+    geno = synth.pack(np.zeros((5, n_f), np.uint8))  # all (0,0): r^{000} = 8 n_f, D = 0
+    t, _ = run_3way(geno, n_f, 0, operand=E2M1)
+    assert np.all(t[:, 0] == 8 * n_f) and np.all(t[:, 1:] == 0)
+    geno = synth.panel_hwe(40, n_f, seed=702, p_missing=0.02)
+    t, c = run_3way(geno, n_f, 0, operand=E2M1)
+    et, ec = oracle.ccc3_slabs(geno, n_f)
+    assert_tally_equal(t, et, "fp4 3-way n_f = 16,383")
+    assert_ccc_close(c, ec, what="fp4 3-way n_f = 16,383")
+
+
+def test_fp4_3way_where_not_built_is_refused():
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    for n_f, tile in ((16384, 0), (300, 1), (300, 2)):
+        geno = to_device(synth.panel_uniform(10, n_f, seed=703))
+        nt = ccc.ccc3_count(10, 0, 10)
+        t = torch.empty((nt, 8), dtype=torch.int32, device="cuda")
+        opts = ccc.ccc_opts_default(tile=tile, operand=E2M1)
+        ws = workspace(ccc.ccc_workspace_size(geno, n_f, opts, ccc.CCC_OP_3WAY))
+        opts = ccc.ccc_opts_default(tile=tile, operand=E2M1, workspace=ws)
+        with pytest.raises(ccc.CCCError) as e:
+            ccc.ccc3_tally(geno, n_f, 0, 10, t, opts)
         assert e.value.status == ccc.CCC_EUNSUPPORTED
