@@ -112,6 +112,26 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)
       : "memory");
 }
 
+// D-slot accesses with an L2 evict-last policy: each slot is written and read
+// back by the same thread one tile later, while the tiles' outputs stream
+// through L2 (evict-first stores); without the hint the slots were evicted and
+// written back to DRAM between the two.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void st_l2_keep(uint32_t *p, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_l2_keep(const uint32_t *p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+
 // P(x) = sum_{j < x} min(j, n_v - 1 - j): SNPs on the masked side of the
 // slabs before x.  Slab j owns 4 min(j, n_v - 1 - j) masked rows (2 per SNP
 // for s_j, 2 for the missing mask).
@@ -929,6 +949,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
     const float gamma = args.t.gamma;
     const int64_t s_begin = slab_offset_dev(args.t.j_begin, n_v);
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16);
+    const uint64_t keep_pol = l2_evict_last_policy();
     int dcount = 0;
     bool ok_all = true;
     Sched sc, pv;
@@ -955,7 +976,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
             for (int e = 0; e < 8; ++e) {
               const uint32_t d0 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[2 * e])));
               const uint32_t d1 = static_cast<uint32_t>(__float2int_rn(__uint_as_float(v[2 * e + 1])));
-              __stcg(slot + (8 * c + e) * 128 + L, (d0 & 0xFFFFu) | (d1 << 16));
+              st_l2_keep(slot + (8 * c + e) * 128 + L, (d0 & 0xFFFFu) | (d1 << 16), keep_pol);
             }
           }
           tc_fence_before();
@@ -1005,7 +1026,7 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
                        : make_int2(0, 0);
             wk[kk] = (ok && want_ccc && persnp) ? __ldg(reinterpret_cast<const float2 *>(wv) + k)
                                                 : make_float2(1.f, 1.f);
-            dd[kk] = pv_has_d ? __ldcg(slot + (kl + kk) * 128 + L) : 0u;
+            dd[kk] = pv_has_d ? ld_l2_keep(slot + (kl + kk) * 128 + L, keep_pol) : 0u;
           }
           tmem_ld_wait();
           if (c == c_last) {
