@@ -538,7 +538,7 @@ int ccc_check_bounded_wait(int32_t *status, int64_t limit_ns, void *stream);
  * ccc_mma_rate: `clusters` clusters of two CTAs (one per SM pair, each CTA
  * alone on its SM; 1 <= clusters <= SMs / 2) each issue n_mma
  * (1 <= n_mma <= 65536) dense cta_group::2 MMAs of M = 256, N = n_cols
- * (128 or 256) back to back from shared-memory operands into one TMEM
+ * (a multiple of 16 from 64 to 256) back to back from shared-memory operands into one TMEM
  * accumulator, with operands of the given kind:
  *   CCC_MMA_E4M3       kind::f8f6f4, e4m3 operands, K = 32 per MMA;
  *   CCC_MMA_E2M1       kind::mxf4, e2m1 operands with UE8M0 scale factors per

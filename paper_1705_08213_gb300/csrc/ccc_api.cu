@@ -1586,7 +1586,7 @@ int ccc_last_cuda_error(void) {
 int ccc_mma_rate(int kind, int n_cols, int n_mma, int clusters, int64_t *cycles, int32_t *bad,
                  void *stream) {
   if (kind < CCC_MMA_E4M3 || kind > CCC_MMA_E2M1_NVF4) return CCC_EINVAL;
-  if (n_cols != 128 && n_cols != 256) return CCC_EINVAL;
+  if (n_cols < 64 || n_cols > 256 || n_cols % 16 != 0) return CCC_EINVAL;
   if (n_mma < 1 || n_mma > 65536) return CCC_EINVAL;
   if (cycles == nullptr || !aligned(cycles, 8) || bad == nullptr || !aligned(bad, 4))
     return CCC_EINVAL;

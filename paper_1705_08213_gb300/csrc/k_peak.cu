@@ -5,7 +5,7 @@
 //
 // MMA probe: one cluster of two CTAs per SM pair, each CTA alone on its SM
 // (its shared-memory request exceeds half of an SM's).  Both CTAs fill one
-// 128-byte K stage of A (128 rows) and of B (n_cols / 2 rows) with the value
+// 128-byte K stage of A (128 rows) and of B (n_cols / 2 <= 128 rows) with the value
 // 1.0 of the kind, and for the block-scaled kinds 32 TMEM columns with the
 // scale factor 1.0; the leader's thread issues n_mma MMAs (M = 256,
 // N = n_cols) back to back into one accumulator, cycling through the four K
@@ -101,12 +101,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
   tc_fence_after();
   const float expect = static_cast<float>(n_mma) * (kind == CCC_MMA_E4M3 ? 32.f : 64.f);
   int wrong = 0;
+  // 32 columns per load (inside the 512 allocated); only the n_cols written count.
   for (int c = 0; c < n_cols; c += 32) {
     uint32_t v[32];
     tmem_ld_32x32b_x32(tmem + lane_off + static_cast<uint32_t>(c), v);
     tmem_ld_wait();
 #pragma unroll
-    for (int k = 0; k < 32; ++k) wrong += __uint_as_float(v[k]) != expect ? 1 : 0;
+    for (int k = 0; k < 32; ++k) wrong += (c + k < n_cols && __uint_as_float(v[k]) != expect) ? 1 : 0;
   }
   if (wrong) atomicAdd(bad, wrong);
   tc_fence_before();

@@ -20,7 +20,7 @@ def _build():
     build.build()
 
 
-@pytest.mark.parametrize("n_cols", [128, 256])
+@pytest.mark.parametrize("n_cols", [128, 224, 240, 256])
 @pytest.mark.parametrize("kind", [0, 1, 2])
 def test_mma_probe_accumulators_exact(kind, n_cols):
     import paper_1705_08213_gb300 as ccc
@@ -34,7 +34,7 @@ def test_mma_probe_rejects_bad_arguments():
 
     import paper_1705_08213_gb300 as ccc
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    for args in ((3, 256, 10, 1), (0, 192, 10, 1), (0, 256, 0, 1), (0, 256, 65537, 1),
+    for args in ((3, 256, 10, 1), (0, 200, 10, 1), (0, 272, 10, 1), (0, 48, 10, 1), (0, 256, 0, 1), (0, 256, 65537, 1),
                  (0, 256, 10, sms // 2 + 1)):
         with pytest.raises(ccc.CCCError) as e:
             ccc.ccc_mma_rate(*args)
