@@ -211,6 +211,8 @@ KERNEL_SOURCES = {
                          "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
                              "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_tc_pair_fp4w": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh", "tc_sched.cuh",
+                              "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_split_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
                                    "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_batched_fp4": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
@@ -883,7 +885,9 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
         packed = ""
     kname = {(2, True): ("k_tally2_multi" if w.get("states") else
                          "k_tally2_tc_pair_split" + packed if w.get("split_compare") else
-                         "k_tally2_tc_pair" + packed if args.tile != 1 else "k_tally2_tc"),
+                         "k_tally2_tc_pair" + packed + ("w" if fp4 and w.get("threshold") is not None
+                                                        else "")
+                         if args.tile != 1 else "k_tally2_tc"),
              (3, True): {1: "k_tally3_tc", 2: "k_tally3_fused"}.get(
                  args.tile, "k_tally3_class_w" if w["n_f"] <= 16383 else "k_tally3_class"),
              (2, False): "k_tally2_popc", (3, False): "k_tally3_popc"}[(w["kind"],

@@ -97,9 +97,19 @@ struct Epi2 {
   __device__ __forceinline__ static void chunk(const Params &args, Tile2 sc, int a, int64_t i,
                                                int64_t row_base, float wi0, float wi1, bool filter,
                                                bool want_ccc, int c, const uint32_t (&v)[32]) {
+    cols<32>(args, static_cast<int64_t>(sc.J) * SNP_J + c * 16, a, i, row_base, wi0, wi1, filter,
+             want_ccc, v);
+  }
+
+  // W accumulator columns of lane (i, a) whose first column is (SNP jb, b = 0):
+  // W / 2 SNPs j, tallies and CCC values.
+  template <int W>
+  __device__ __forceinline__ static void cols(const Params &args, int64_t jb, int a, int64_t i,
+                                              int64_t row_base, float wi0, float wi1, bool filter,
+                                              bool want_ccc, const uint32_t (&v)[W]) {
     const int64_t n_v = args.n_v;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
+    for (int p = 0; p < W / 4; ++p) {
       // columns 4p, 4p+1: j even (b = 0, 1); columns 4p+2, 4p+3: j odd.
       const float e0 = __uint_as_float(v[4 * p + 0]);
       const float e1 = __uint_as_float(v[4 * p + 1]);
@@ -121,7 +131,7 @@ struct Epi2 {
         r10 = __float2int_rn(o0);
         r11 = __float2int_rn(o1);
       }
-      const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + 2 * p + a;
+      const int64_t j = jb + 2 * p + a;
       if (i < j && j < n_v && i >= args.i_begin && i < args.i_end) {
         const int64_t pidx = row_base + j - args.pair0;
         if (!filter && !CCC_IN_BOUNDS(pidx, args.out_len, args.status)) continue;
@@ -197,17 +207,24 @@ struct Epi2Staged {
   __device__ __forceinline__ static void chunk(const Tally2Args &args, Tile2 sc, int quarter,
                                                int lane, int c, const uint32_t (&v)[32],
                                                float *stage) {
+    at(args, static_cast<int64_t>(sc.I) * SNP_I + quarter * 16,
+       static_cast<int64_t>(sc.J) * SNP_J + c * 16, lane, v, stage);
+  }
+
+  // The 32 x 32 chunk of SNPs i ib .. ib + 15 (lanes) and j jb .. jb + 15 (columns).
+  __device__ __forceinline__ static void at(const Tally2Args &args, int64_t ib, int64_t jb,
+                                            int lane, const uint32_t (&v)[32], float *stage) {
     const int64_t n_v = args.n_v;
     const bool filter = args.hits != nullptr;
     const bool want_ccc = filter || args.ccc != nullptr;
     const bool persnp = args.norm == CCC_NORM_PERSNP;
     const int jl = lane & 15;
-    const int64_t i0 = static_cast<int64_t>(sc.I) * SNP_I + quarter * 16 + (lane >> 4);
+    const int64_t i0 = ib + (lane >> 4);
     __syncwarp();  // the previous chunk's reads are done
 #pragma unroll
     for (int k = 0; k < 32; ++k) stage[lane * STRIDE + k] = __uint_as_float(v[k]);
     __syncwarp();
-    const int64_t j = static_cast<int64_t>(sc.J) * SNP_J + c * 16 + jl;
+    const int64_t j = jb + jl;
     float wj0 = 1.f, wj1 = 1.f;
     if (want_ccc && persnp && j < n_v) {
       const float2 wj = __ldg(reinterpret_cast<const float2 *>(args.w) + j);
@@ -299,6 +316,201 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_E
   tcp::persistent_gemm_pair<TriSchedPair, Epi2Pair, tcp::FP4_EW, false, true>(&tm, sp, args, nkb,
                                                                               args.status);
 }
+
+// Thresholded FP4 output with two accumulators: tiles of 128 SNPs i by
+// kRectJ = 120 SNPs j (N = 240 columns, B rows 120 per CTA), so that two
+// accumulators and the scale factors fill the 512 TMEM columns and the MMAs of
+// a tile run while the epilogue tests the previous one.  Tiles over
+// RectSchedT<120>; A through maps.m[0] (box 128 rows), B through maps.m[1]
+// (box 120 rows).  Per column the MMA is 1.4% slower at N = 240 (153.8 cycles
+// per instruction against 161.8 at N = 256), and the tiles are 6.6% more per
+// triangle, but at short K the single-accumulator kernel above waits for its
+// epilogue's read-out on every tile: GB300, 200,000 x 4,096 thresholded,
+// 109.3 ms against 119.9.  Full output stays on the single-accumulator kernel,
+// whose epilogue stores interleave with the next tile's MMAs there as well
+// (20,000 x 16,384: 3.64 ms against 3.81 with these tiles; x 32,768: 6.67
+// against 7.15).
+constexpr int kRectJ = 120;
+constexpr int kRectNB = 2 * kRectJ;
+
+struct PairMaps {
+  CUtensorMap m[2];
+};
+
+// Epilogue of a rect tile (thresholded output only): 7 chunks of 32 columns
+// (16 SNPs j) and a 16-column tail (8 SNPs j) at column 224; the warps of
+// column half 0 take chunks 0-3, those of half 1 chunks 4-6 and the tail, with
+// two TMEM loads per wait, releasing the accumulator after their last load.
+// The epilogue is what bounds this kernel at short K (about 10,000 cycles of
+// MMAs per tile at K = 4,096), so each pair is tested with the accumulator's
+// float values and factors staged in shared memory before any integer or
+// division work.
+struct Epi2Rect {
+  using Params = Tally2Args;
+  using Sched = RectSchedT<kRectJ>;
+  static constexpr int STAGE_BYTES_PER_WARP = kRectJ * 8;  // float2 factors of the tile's j
+  static constexpr int CHUNKS = kRectJ / 16;  // whole 32-column chunks
+  static constexpr int TAIL = kRectNB - 32 * CHUNKS;
+  static_assert(TAIL == 16 && CHUNKS == 7, "chunks 0-3, 4-6 and a 16-column tail");
+  static_assert(STAGE_BYTES_PER_WARP % 16 == 0, "16-byte staged rows");
+
+  template <int NC, bool PRELOAD>
+  __device__ static void tile(const Params &args, const Sched &sc, int rank, int quarter, int lane,
+                              uint32_t t_base, uint32_t release_cluster_bar, int c0,
+                              float *stage) {
+    static_assert(!PRELOAD, "two accumulators: each warp releases after its last load");
+    const int half = c0 / NC;
+    const int64_t ib = static_cast<int64_t>(2 * sc.I + rank) * SNP_I;  // the CTA's first SNP i
+    const int64_t j0 = static_cast<int64_t>(sc.J) * kRectJ;
+    if (args.hits == nullptr) {  // launched for thresholded output only
+      record_error(args.status, CCC_EINVAL);
+      release(release_cluster_bar);
+      return;
+    }
+    filter_tile(args, ib, j0, quarter, lane, t_base, release_cluster_bar, half, stage);
+  }
+
+  __device__ __forceinline__ static void release(uint32_t bar) {
+    tc_fence_before();
+    mbar_arrive_cluster(bar);
+  }
+
+  // Thresholded output: lane = row (i, a).  For each pair of the lane's row, its
+  // own row's largest weighted entry and sum are exchanged with the partner row
+  // (lane ^ 1); only pairs that may exceed the threshold (PERSNP, see
+  // may_exceed; every pair for JOINT) go through the integer tallies, the CCC
+  // values and filter_pair, so the hit list is what Epi2 produces.
+  __device__ static void filter_tile(const Params &args, int64_t ib, int64_t j0, int quarter,
+                                     int lane, uint32_t t_base, uint32_t rel, int half,
+                                     float *stage) {
+    const int64_t n_v = args.n_v;
+    const int row = quarter * 32 + lane;
+    const int a = row & 1;
+    const int64_t i = ib + (row >> 1);
+    const bool persnp = args.norm == CCC_NORM_PERSNP;
+    float wi0 = 1.f, wi1 = 1.f;
+    if (persnp && i < n_v) {
+      wi0 = __ldg(args.w + 2 * i);
+      wi1 = __ldg(args.w + 2 * i + 1);
+    }
+    const bool rowok = i < n_v && i >= args.i_begin && i < args.i_end;
+    // The factors of the tile's kRectJ SNPs j, in the warp's staging buffer
+    // (read by every lane with the same address: broadcasts).
+    float2 *wjs = reinterpret_cast<float2 *>(stage);
+    const float2 *w2 = reinterpret_cast<const float2 *>(args.w);
+    __syncwarp();  // the previous tile's reads are done
+    for (int k = lane; k < kRectJ; k += 32) {
+      const int64_t j = j0 + k;
+      wjs[k] = persnp ? __ldg(w2 + (j < n_v ? j : n_v - 1)) : make_float2(1.f, 1.f);
+    }
+    __syncwarp();
+    // Two TMEM loads per wait: the four pieces of a warp expose two load
+    // latencies instead of four.
+    const int cb = half ? 4 : 0;
+    {
+      uint32_t va[32], vb[32];
+      tmem_ld_32x32b_x32(t_base + cb * 32, va);
+      tmem_ld_32x32b_x32(t_base + (cb + 1) * 32, vb);
+      tmem_ld_wait();
+      filter_cols<32>(args, j0, 16 * cb, a, i, rowok, persnp, wi0, wi1, va, wjs);
+      filter_cols<32>(args, j0, 16 * (cb + 1), a, i, rowok, persnp, wi0, wi1, vb, wjs);
+    }
+    if (half == 0) {
+      uint32_t va[32], vb[32];
+      tmem_ld_32x32b_x32(t_base + 2 * 32, va);
+      tmem_ld_32x32b_x32(t_base + 3 * 32, vb);
+      tmem_ld_wait();
+      release(rel);
+      filter_cols<32>(args, j0, 32, a, i, rowok, persnp, wi0, wi1, va, wjs);
+      filter_cols<32>(args, j0, 48, a, i, rowok, persnp, wi0, wi1, vb, wjs);
+    } else {
+      uint32_t va[32], vt[TAIL];
+      tmem_ld_32x32b_x32(t_base + 6 * 32, va);
+      tmem_ld_32x32b_x16(t_base + 32 * CHUNKS, vt);
+      tmem_ld_wait();
+      release(rel);
+      filter_cols<32>(args, j0, 96, a, i, rowok, persnp, wi0, wi1, va, wjs);
+      filter_cols<TAIL>(args, j0, 16 * CHUNKS, a, i, rowok, persnp, wi0, wi1, vt, wjs);
+    }
+  }
+
+  // W columns from SNP jb = j0 + jo on: columns 4p, 4p + 1 are (j = jb + 2p,
+  // b = 0, 1), 4p + 2, 4p + 3 are (j = jb + 2p + 1, b = 0, 1); allele-0 rows take
+  // the even j, allele-1 rows the odd j.  wjs[k]: factors of SNP j0 + k.
+  template <int W>
+  __device__ __forceinline__ static void filter_cols(const Params &args, int64_t j0, int jo, int a,
+                                                     int64_t i, bool rowok, bool persnp, float wi0,
+                                                     float wi1, const uint32_t (&v)[W],
+                                                     const float2 *wjs) {
+    constexpr int P = W / 4;
+    const int64_t n_v = args.n_v;
+    const int64_t jb = j0 + jo;
+    const float wia = a ? wi1 : wi0;
+    const float thr = args.threshold;
+    float2 wje[P], wjo[P];  // factors of j = jb + 2p and jb + 2p + 1 (the same in every lane)
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float4 q = *reinterpret_cast<const float4 *>(wjs + jo + 2 * p);
+      wje[p] = make_float2(q.x, q.y);
+      wjo[p] = make_float2(q.z, q.w);
+    }
+    uint32_t cand = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float e0 = __uint_as_float(v[4 * p + 0]), e1 = __uint_as_float(v[4 * p + 1]);
+      const float o0 = __uint_as_float(v[4 * p + 2]), o1 = __uint_as_float(v[4 * p + 3]);
+      // this row's part of the pairs (i, j even) and (i, j odd): largest weighted entry, sum
+      const float me = fmaxf(e0 * (wia * wje[p].x), e1 * (wia * wje[p].y));
+      const float mo = fmaxf(o0 * (wia * wjo[p].x), o1 * (wia * wjo[p].y));
+      const float se = e0 + e1, so = o0 + o1;
+      const float pm = __shfl_xor_sync(0xffffffffu, a ? me : mo, 1);
+      const float ps = __shfl_xor_sync(0xffffffffu, a ? se : so, 1);
+      const int64_t j = jb + 2 * p + a;
+      const float m = fmaxf(a ? mo : me, pm);
+      const float n4 = (a ? so : se) + ps;  // 4 n_ij, an exact integer below 2^24
+      const bool may = !persnp || m * (1.f + 0x1p-18f) >= thr * n4;
+      cand |= (rowok && i < j && j < n_v && may ? 1u : 0u) << p;
+    }
+    if (!__any_sync(0xffffffffu, cand != 0)) return;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const float e0 = __uint_as_float(v[4 * p + 0]), e1 = __uint_as_float(v[4 * p + 1]);
+      const float o0 = __uint_as_float(v[4 * p + 2]), o1 = __uint_as_float(v[4 * p + 3]);
+      const float g0 = __shfl_xor_sync(0xffffffffu, a ? e0 : o0, 1);
+      const float g1 = __shfl_xor_sync(0xffffffffu, a ? e1 : o1, 1);
+      if (!((cand >> p) & 1u)) continue;
+      int32_t r00, r01, r10, r11;
+      if (a == 0) {
+        r00 = __float2int_rn(e0);
+        r01 = __float2int_rn(e1);
+        r10 = __float2int_rn(g0);
+        r11 = __float2int_rn(g1);
+      } else {
+        r00 = __float2int_rn(g0);
+        r01 = __float2int_rn(g1);
+        r10 = __float2int_rn(o0);
+        r11 = __float2int_rn(o1);
+      }
+      const float2 wj = a ? wjo[p] : wje[p];
+      if (persnp && !may_exceed(r00, r01, r10, r11, wi0, wi1, wj.x, wj.y, args.threshold)) continue;
+      const float4 cv = ccc2_values(r00, r01, r10, r11, wi0, wi1, wj.x, wj.y, args.norm, args.gamma);
+      filter_pair(args.hits, args.n_hits, args.cap, args.threshold, i, jb + 2 * p + a, r00, r01,
+                  r10, r11, cv);
+    }
+  }
+};
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_EW, 1)
+    k_tally2_tc_pair_fp4w(const __grid_constant__ PairMaps maps, const Tally2Args args,
+                          TriSched::Params sp, int nkb) {
+  tcp::persistent_gemm_pair<Epi2Rect::Sched, Epi2Rect, tcp::FP4_EW, false, true, kRectNB>(
+      maps.m, sp, args, nkb, args.status);
+}
+
+constexpr size_t rect_smem() {
+  return tcp::smem_bytes_nb(kRectNB, tcp::FP4_EW, Epi2Rect::STAGE_BYTES_PER_WARP);
+}
+static_assert(rect_smem() <= 232448, "dynamic shared memory limit");
 
 // ---------------------------------------------------------------- split K
 
@@ -722,6 +934,19 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
   return note_launch();
 }
 
+// Rect tiles (128-SNP row blocks I by kRectJ-SNP column blocks J) holding a
+// pair i < j, in row blocks [I0, I1).
+int64_t tc2_rect_tiles(int64_t n_v, int64_t I0, int64_t I1) {
+  const int64_t nI = (n_v + 127) / 128;
+  const int64_t nJ = (n_v + kRectJ - 1) / kRectJ;
+  int64_t t = 0;
+  for (int64_t I = I0; I < nI && I < I1; ++I) {
+    const int64_t jm = Epi2Rect::Sched::jmin(static_cast<int>(I));
+    if (jm < nJ) t += nJ - jm;
+  }
+  return t;
+}
+
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                           int num_sms, cudaStream_t s, bool fp4) {
   static bool attr_set[kMaxDevices] = {};
@@ -733,7 +958,9 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
         cudaFuncSetAttribute(k_tally2_tc_pair<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(pair_smem(8))) != cudaSuccess ||
         cudaFuncSetAttribute(k_tally2_tc_pair_fp4, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(pair_smem(tcp::FP4_EW))) != cudaSuccess)
+                             static_cast<int>(pair_smem(tcp::FP4_EW))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tally2_tc_pair_fp4w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(rect_smem())) != cudaSuccess)
       return CCC_ECUDA;
     attr_set[dev] = true;
   }
@@ -741,6 +968,45 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
   // each 128-byte K stage covers 256 entries.
   if (fp4 && kpad % 256 != 0) return CCC_EINVAL;
   const int64_t row_bytes = fp4 ? kpad / 2 : kpad;
+  static int max_clusters[kMaxDevices][4] = {};
+  if (fp4 && a.hits != nullptr) {  // thresholded output: the two-accumulator rect tiles
+    PairMaps maps;
+    if (!make_operand_map(&maps.m[0], op, rows_pad, row_bytes, tcp::BMH) ||
+        !make_operand_map(&maps.m[1], op, rows_pad, row_bytes, kRectJ))
+      return CCC_ECUDA;
+    TriSched::Params sp;
+    sp.nI = static_cast<int>((a.n_v + 127) / 128);
+    sp.nJ = static_cast<int>((a.n_v + kRectJ - 1) / kRectJ);
+    sp.group = a.group > 0 ? a.group : kFp4Group;
+    sp.shift = 0;
+    sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / 128);
+    sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.nI);
+    const int nkb = static_cast<int>(row_bytes / BK);
+    const int64_t tiles = tc2_rect_tiles(a.n_v, sp.I0, sp.I1);
+    if (tiles == 0) return CCC_OK;
+    int &mc = max_clusters[dev][3];
+    if (mc == 0) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = 2;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+      cfg.blockDim = dim3(static_cast<unsigned>(64 + 32 * tcp::FP4_EW), 1, 1);
+      cfg.dynamicSmemBytes = rect_smem();
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_tally2_tc_pair_fp4w, &cfg) != cudaSuccess || n < 1)
+        return CCC_ECUDA;
+      mc = n < num_sms / 2 ? n : num_sms / 2;
+    }
+    const int64_t clusters = tiles < mc ? tiles : mc;
+    k_tally2_tc_pair_fp4w<<<static_cast<int>(2 * clusters), 64 + 32 * tcp::FP4_EW, rect_smem(),
+                            s>>>(maps, a, sp, nkb);
+    return note_launch();
+  }
   CUtensorMap tm;
   if (!make_operand_map(&tm, op, rows_pad, row_bytes, tcp::BMH)) return CCC_ECUDA;
   TriSched::Params sp;
@@ -755,7 +1021,6 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
   if (tiles == 0) return CCC_OK;
   const int ew = fp4 ? tcp::FP4_EW : epilogue_warps(nkb);
   // Persistent grid: as many SM pairs as can be resident at once.
-  static int max_clusters[kMaxDevices][3] = {};
   int &mc = max_clusters[dev][fp4 ? 2 : ew == 4 ? 0 : 1];
   if (mc == 0) {
     cudaLaunchConfig_t cfg = {};

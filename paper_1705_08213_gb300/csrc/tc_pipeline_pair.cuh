@@ -56,6 +56,10 @@ constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE_BYTES +
 constexpr size_t smem_bytes(int epi_warps, int stage_bytes) {
   return SMEM_BYTES + (stage_bytes > 0 ? 16 + static_cast<size_t>(epi_warps) * stage_bytes : 0);
 }
+// The same for tiles of NB < 256 columns (B rows NB / 2 per CTA).
+constexpr size_t smem_bytes_nb(int nb, int epi_warps, int stage_bytes) {
+  return smem_bytes(epi_warps, stage_bytes) - static_cast<size_t>(STAGES) * (BNH - nb / 2) * BK;
+}
 
 static_assert(SMEM_BYTES <= 232448, "dynamic shared memory limit");
 
@@ -178,7 +182,13 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
 // FP4: e2m1 operands (kind::mxf4, unit scale factors), one accumulator, the
 // epilogue's Epi::tile loading all of its chunks before its release arrive
 // (EW must be FP4_EW).
-template <class Sched, class Epi, int EW, bool KBLK = false, bool FP4 = false>
+// NB: accumulator columns of a tile (N of the MMA; B rows NB / 2 per CTA).
+// Below 256 (FP4 only) two accumulators of NB columns and the scale factors
+// fit in the 512 TMEM columns (at 0, NB and 2 NB), so the MMAs of a tile run
+// while the epilogue reads the previous one, as for e4m3; B is then loaded
+// through tm[1] (box NB / 2 rows) and A through tm[0], and Epi::tile is called
+// with PRELOAD false and c0 = (warp's column half) x NC.
+template <class Sched, class Epi, int EW, bool KBLK = false, bool FP4 = false, int NB = 256>
 __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
                                                      const typename Sched::Params &sp,
                                                      const typename Epi::Params &ep, int nkb,
@@ -186,16 +196,25 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  constexpr int NBH = NB / 2;             // B rows per CTA
+  constexpr int B_BYTES_T = NBH * BK;     // B bytes per CTA and K stage
+  constexpr int STAGE_BYTES_T = A_BYTES + B_BYTES_T;
+  constexpr int NACC = FP4 && NB == 256 ? 1 : 2;  // accumulator buffers
+  constexpr uint32_t SF_T = NACC == 1 ? SF_COL : 2u * NB;  // FP4 scale-factor columns
+  static_assert(NB == 256 || (FP4 && !KBLK && NB % 16 == 0 && NB >= 128 &&
+                              SF_T + 32 <= static_cast<uint32_t>(TMEM_COLS)),
+                "narrow tiles: FP4, two accumulators and the scale factors in TMEM");
+  static_assert(B_BYTES_T % 1024 == 0, "B stages on 1024-byte boundaries (128-byte swizzle)");
+  constexpr uint32_t IDESC_T = FP4 ? idesc_e2m1_f32(256, NB, true) : IDESC;
   uint8_t *sA = smem;
   uint8_t *sB = smem + STAGES * A_BYTES;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES_T);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NUM_BARS);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   float *const stage_base = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(tmem_slot) + 64 + 15) & ~static_cast<uintptr_t>(15));
 
   constexpr int EPI_THREADS = tc::Epilogue<EW>::THREADS;
-  constexpr int NACC = FP4 ? 1 : 2;  // accumulator buffers
   static_assert(!FP4 || EW == FP4_EW, "the FP4 epilogue holds 4 chunks per thread");
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -234,14 +253,14 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
   const int64_t cstart = blockIdx.x >> 1;
   const int64_t cstep = gridDim.x >> 1;
   if (FP4) {
-    // Scale factors 1.0 in both CTAs' columns SF_COL .. SF_COL + 31 (every
+    // Scale factors 1.0 in both CTAs' columns SF_T .. SF_T + 31 (every
     // byte), written by the first four epilogue warps, one lane quarter each,
     // before the leader's first MMA reads them.
     if (warp >= 2 && warp < 6) {
       uint32_t v[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = SF_ONE_UE8M0;
-      tmem_st_32x32b_x32(tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16) + SF_COL, v);
+      tmem_st_32x32b_x32(tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16) + SF_T, v);
       tmem_st_wait();
     }
     tc_fence_before();
@@ -261,8 +280,9 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       Sched sc;
       for (sc.init(sp, cstart); sc.valid && ok; sc.advance(cstep)) {
         const int ya = sc.a_row() + BMH * static_cast<int>(rank);
-        const int yb = sc.b_row() + BNH * static_cast<int>(rank);
+        const int yb = sc.b_row() + NBH * static_cast<int>(rank);
         const CUtensorMap *m = tm + sc.map_index();
+        const CUtensorMap *mb = NB == 256 ? m : tm + 1;
         const int kbs = sc.k_blocks(nkb);
         const int kb0 = sc.k_begin();
         for (int kb = 0; kb < kbs; ++kb) {
@@ -270,14 +290,14 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
             ok = false;
             break;
           }
-          if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * STAGE_BYTES);
+          if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * STAGE_BYTES_T);
           const uint32_t fb = map_to_rank(full_bar(stage), 0);
           if (KBLK) {
             tma_load_3d_pair(smem_u32(sA + stage * A_BYTES), m, 0, ya, kb0 + kb, fb);
-            tma_load_3d_pair(smem_u32(sB + stage * B_BYTES), m, 0, yb, kb0 + kb, fb);
+            tma_load_3d_pair(smem_u32(sB + stage * B_BYTES_T), m, 0, yb, kb0 + kb, fb);
           } else {
             tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), m, (kb0 + kb) * BK, ya, fb);
-            tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), m, (kb0 + kb) * BK, yb, fb);
+            tma_load_2d_pair(smem_u32(sB + stage * B_BYTES_T), mb, (kb0 + kb) * BK, yb, fb);
           }
           last_parity[stage] = static_cast<int>(phase);
           if (++stage == STAGES) {
@@ -314,7 +334,7 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
         const uint32_t acc_phase = NACC == 1 ? (lt & 1) : ((lt >> 1) & 1);
         if (!mbar_wait_bounded(tempty_bar(acc), acc_phase ^ 1u, status, abort_flag)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
+        const uint32_t d_tmem = tmem_base + acc * NB;
         const int kbs = sc.k_blocks(nkb);
         for (int kb = 0; kb < kbs; ++kb) {
           if (!mbar_wait_bounded(full_bar(stage), phase, status, abort_flag)) {
@@ -323,12 +343,12 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
           }
           tc_fence_after();
           const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
-          const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
+          const uint32_t b0 = smem_u32(sB + stage * B_BYTES_T);
 #pragma unroll
           for (int k = 0; k < BK / UK; ++k) {
             if (FP4)
               mma_mxf4_pair(d_tmem, smem_desc_sw128(a0 + k * UK), smem_desc_sw128(b0 + k * UK),
-                            IDESC_FP4, tmem_base + SF_COL, tmem_base + SF_COL + 16,
+                            IDESC_T, tmem_base + SF_T, tmem_base + SF_T + 16,
                             (kb | k) != 0 ? 1u : 0u);
             else
               mma_f8f6f4_pair(d_tmem, smem_desc_sw128(a0 + k * UK), smem_desc_sw128(b0 + k * UK),
@@ -359,11 +379,10 @@ __device__ __forceinline__ void persistent_gemm_pair(const CUtensorMap *tm,
       const bool ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, status, abort_flag);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const uint32_t t_base =
-          tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * ACC_COLS;
-      Epi::template tile<NC, FP4>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
-                                  map_to_rank(tempty_bar(acc), 0), c0,
-                                  stage_base + (warp - 2) * (Epi::STAGE_BYTES_PER_WARP / 4));
+      const uint32_t t_base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * NB;
+      Epi::template tile<NC, NACC == 1>(ep, sc, static_cast<int>(rank), quarter, lane, t_base,
+                                        map_to_rank(tempty_bar(acc), 0), c0,
+                                        stage_base + (warp - 2) * (Epi::STAGE_BYTES_PER_WARP / 4));
     }
   }
 

@@ -1,5 +1,7 @@
 // Tile order over the upper triangle of a Gram product, shared by the 2-way
-// tally kernels (biallelic and multi-allelic), and its K-split form.
+// tally kernels (biallelic and multi-allelic), and its K-split form.  The
+// triangle orders are host-callable too, so that their coverage can be
+// checked without a GPU.
 #pragma once
 
 #include "tc_pipeline.cuh"
@@ -20,12 +22,12 @@ struct TriSched {
   int g, I, J, col_end, row_end;
   bool valid;
 
-  __device__ void set_group() {
+  __host__ __device__ void set_group() {
     col_end = min((g + 1) * G, nJ);
     row_end = min(nI, col_end << sh);
   }
   // From group g on, the first group holding a row >= I0; rows start at I0.
-  __device__ void enter_group() {
+  __host__ __device__ void enter_group() {
     while (g < nG) {
       set_group();
       if (I0 < row_end) {
@@ -37,7 +39,7 @@ struct TriSched {
     }
     valid = false;
   }
-  __device__ void init(const Params &p, int64_t start) {
+  __host__ __device__ void init(const Params &p, int64_t start) {
     nI = min(p.nI, p.I1);
     nJ = p.nJ;
     G = p.group;
@@ -49,7 +51,7 @@ struct TriSched {
     if (valid) enter_group();
     advance(start);
   }
-  __device__ void advance(int64_t step) {
+  __host__ __device__ void advance(int64_t step) {
     while (valid && step > 0) {
       const int64_t rem = col_end - 1 - J;
       if (step <= rem) {
@@ -65,17 +67,88 @@ struct TriSched {
       }
     }
   }
-  __device__ int map_index() const { return 0; }
-  __device__ int k_blocks(int nkb) const { return nkb; }
-  __device__ int k_begin() const { return 0; }
-  __device__ int a_row() const { return I * tc::BM; }
-  __device__ int b_row() const { return J * tc::BN; }
+  __host__ __device__ int map_index() const { return 0; }
+  __host__ __device__ int k_blocks(int nkb) const { return nkb; }
+  __host__ __device__ int k_begin() const { return 0; }
+  __host__ __device__ int a_row() const { return I * tc::BM; }
+  __host__ __device__ int b_row() const { return J * tc::BN; }
 };
 
 // 256 x 256 tiles on pairs of SMs: I, J count 256-row blocks.
 struct TriSchedPair : TriSched {
-  __device__ int a_row() const { return I * 256; }
-  __device__ int b_row() const { return J * 256; }
+  __host__ __device__ int a_row() const { return I * 256; }
+  __host__ __device__ int b_row() const { return J * 256; }
+};
+
+// Upper-triangle tiles of 128-SNP row blocks I by SNPJ-SNP column blocks J (the
+// FP4 double-buffered SM-pair kernel: SNPJ = 112).  A tile holds a pair i < j
+// iff its last j exceeds its first i: SNPJ J + SNPJ - 1 > 128 I, i.e.
+// J >= jmin(I) = ceil((128 I - SNPJ + 2) / SNPJ).  Order as TriSched: groups of
+// `group` column blocks, rows inside a group in increasing order, row blocks
+// [I0, I1) only.
+template <int SNPJ>
+struct RectSchedT {
+  using Params = TriSched::Params;  // nI, nJ, group, I0, I1 (shift unused)
+  int nI, nJ, nG, G, I0;
+  int g, I, J, col_end, row_end;
+  bool valid;
+
+  __host__ __device__ static int jmin(int I) {
+    const int x = 128 * I - SNPJ + 2;
+    return x <= 0 ? 0 : (x + SNPJ - 1) / SNPJ;
+  }
+  // One past the last row block with a column block below col_end.
+  __host__ __device__ static int rows_below(int col_end) {
+    return (SNPJ * (col_end - 1) + SNPJ - 2) / 128 + 1;
+  }
+  __host__ __device__ void set_group() {
+    col_end = min((g + 1) * G, nJ);
+    row_end = min(nI, rows_below(col_end));
+  }
+  __host__ __device__ void enter_group() {
+    while (g < nG) {
+      set_group();
+      if (I0 < row_end) {
+        I = I0;
+        J = max(g * G, jmin(I));
+        return;
+      }
+      ++g;
+    }
+    valid = false;
+  }
+  __host__ __device__ void init(const Params &p, int64_t start) {
+    nI = min(p.nI, p.I1);
+    nJ = p.nJ;
+    G = p.group;
+    I0 = p.I0;
+    nG = (nJ + G - 1) / G;
+    valid = nI > I0 && nJ > 0;
+    g = jmin(I0) / G;
+    if (valid) enter_group();
+    advance(start);
+  }
+  __host__ __device__ void advance(int64_t step) {
+    while (valid && step > 0) {
+      const int64_t rem = col_end - 1 - J;
+      if (step <= rem) {
+        J += static_cast<int>(step);
+        return;
+      }
+      step -= rem + 1;
+      if (++I >= row_end) {
+        ++g;
+        enter_group();
+      } else {
+        J = max(g * G, jmin(I));
+      }
+    }
+  }
+  __host__ __device__ int map_index() const { return 0; }
+  __host__ __device__ int k_blocks(int nkb) const { return nkb; }
+  __host__ __device__ int k_begin() const { return 0; }
+  __host__ __device__ int a_row() const { return I * 256; }
+  __host__ __device__ int b_row() const { return J * 2 * SNPJ; }
 };
 
 // Units of a K-split launch, part-major: unit u = (tile u % tiles, part

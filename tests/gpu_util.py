@@ -22,10 +22,12 @@ def workspace(nbytes):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
 
 
-def run_2way(geno_np, n_f, path, norm=0, gamma=2.0 / 3.0, fused=True, tile=0, split=0, operand=0):
+def run_2way(geno_np, n_f, path, norm=0, gamma=2.0 / 3.0, fused=True, tile=0, split=0, operand=0,
+             group=0):
     """Tallies (int32 [npairs, 4]) and CCC (float32 [npairs, 4]) through the C ABI.
 
-    split: ccc_opts.split (0 automatic, 1 off); operand: ccc_opts.operand (0 e4m3, 1 e2m1)."""
+    split: ccc_opts.split (0 automatic, 1 off); operand: ccc_opts.operand (0 automatic,
+    1 e4m3, 2 e2m1); group: ccc_opts.group (0 the kernel's default tile order)."""
     import paper_1705_08213_gb300 as ccc
     torch = torch_mod()
     g = to_device(geno_np)
@@ -37,6 +39,7 @@ def run_2way(geno_np, n_f, path, norm=0, gamma=2.0 / 3.0, fused=True, tile=0, sp
     ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
     opts = ccc.ccc_opts_default(path=path, norm=norm, gamma=gamma, workspace=ws, tile=tile)
     opts.split = split
+    opts.group = group
     if operand:
         opts.operand = operand
     tally = torch.full((max(npairs, 1), 4), -7, dtype=torch.int32, device="cuda")

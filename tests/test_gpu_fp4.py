@@ -39,6 +39,52 @@ def test_fp4_edges_against_oracle(n_v, n_f):
     assert_ccc_close(c, ec, what=f"fp4 ccc n_v={n_v} n_f={n_f}")
 
 
+HIT_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("tally", np.int32, 4),
+                      ("ccc", np.float32, 4)])
+
+
+# Thresholded FP4 output tiles the triangle by 128 SNPs i x 120 SNPs j (two accumulators of 240
+# columns): SNP counts around multiples of 120 and of 128, tile orders of 1 to 64 column blocks,
+# both normalisations; a low threshold keeps most pairs, so nearly every tile entry is checked.
+@pytest.mark.parametrize("n_v,group,norm", [(119, 0, 0), (120, 0, 1), (121, 0, 0), (240, 0, 0),
+                                            (241, 0, 1), (257, 0, 0), (361, 0, 0), (385, 0, 1),
+                                            (961, 0, 0), (961, 1, 0), (1500, 3, 1),
+                                            (1500, 64, 0)])
+def test_fp4_rect_tile_edges(n_v, group, norm):
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    from tests.gpu_util import CCC_RTOL
+    n_f, thr = 513, 0.05
+    geno = synth.panel_uniform(n_v, n_f, seed=520 + n_v, p_missing=0.05, pad_seed=n_v + 3)
+    et, ec = oracle.ccc2_all(geno, n_f, norm=norm)
+    g = to_device(geno)
+    opts = ccc.ccc_opts_default(norm=norm, operand=E2M1)
+    ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
+    opts = ccc.ccc_opts_default(norm=norm, workspace=ws, operand=E2M1)
+    opts.group = group
+    cap = ccc.ccc2_count(n_v)
+    hits = torch.zeros(cap * HIT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    n_hits = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ccc.ccc2_filter(g, n_f, thr, hits, cap, n_hits, opts)
+    torch.cuda.synchronize()
+    assert ccc.ccc_status(opts) == ccc.CCC_OK
+    n = int(n_hits.item())
+    rec = np.frombuffer(hits[:n * HIT_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=HIT_DTYPE)
+    ii, jj = np.triu_indices(n_v, 1)
+    mx = ec.max(axis=1)
+    tie = np.abs(mx - thr) <= CCC_RTOL * thr
+    keep = (mx > thr) & ~tie
+    assert keep.sum() > 0.5 * keep.size
+    got = {(int(h["i"]), int(h["j"])) for h in rec}
+    assert len(got) == n
+    want = set(zip(ii[keep].tolist(), jj[keep].tolist()))
+    assert want <= got <= want | set(zip(ii[tie].tolist(), jj[tie].tolist()))
+    idx = oracle.pair_index(rec["i"].astype(np.int64), rec["j"].astype(np.int64), n_v)
+    assert_tally_equal(rec["tally"], et[idx], f"fp4 rect tiles n_v={n_v} group={group}")
+    assert_ccc_close(rec["ccc"], ec[idx], what=f"fp4 rect tiles n_v={n_v} group={group}")
+
+
 @pytest.mark.parametrize("norm", [0, 1])
 def test_fp4_equals_e4m3_bit_for_bit(norm):
     n_v, n_f = 1100, 5000
