@@ -603,17 +603,29 @@ struct Cfg {
   using Sched = ClassSchedT<kSnpK, kKBI>;
 };
 constexpr uint32_t kSfCol = 480;
-constexpr int kStages = 6;
+constexpr int kStages = 5;
 constexpr int kTile = 128 * kBK;                  // 128 rows x 128 bytes
 constexpr int kStageBytes = 2 * kTile;            // A + B per CTA
 constexpr int kDWords = 128 * 128;                // per tile: [k (0..127)][lane] x (u16 c = 0, u16 c = 1)
 constexpr int kMaxCtas = 256;                     // CTAs the D scratch is sized for
-constexpr int kNumBars = 2 * kStages + 2 + 2 + 3;  // full, empty, tfull, tempty, dready, ddone, drain
-constexpr size_t kSmem = 1024 + static_cast<size_t>(kStages) * kStageBytes + kNumBars * 8 + 64;
 // Epilogue: 2 warps per TMEM lane quarter; warp g of a quarter takes the
 // 8-SNP chunks c = g, g + 2, ... of the tile's 16 (12 warps measured slower:
 // their register cap of 146 cost more than the added overlap gave).
 constexpr int kEpiWarps = 8;
+// The 2-way tallies r_ik of an epilogue warp's next chunk (its 16 SNPs i x 8
+// SNPs k, 128 bytes per i) are copied into shared memory with asynchronous
+// 16-byte copies (cp.async, each warp instruction 4 whole rows) while it works
+// on the current chunk: rows 144 bytes apart, so that the lanes' 8-byte reads
+// of one k are free of bank conflicts.  GB300, 1,536 x 8,192: class kernels
+// 14.24 -> 13.7 ms against one 8-byte load per lane and k from the 2-way table
+// (16 rows per warp load); a second buffer (prefetching two chunks ahead)
+// measured the same.  Five operand stages measured as fast as six here and
+// leave shared memory for the preparation kernels of the next batch.
+constexpr int kRowStride = 144;
+constexpr int kRbufBytes = 16 * kRowStride;
+constexpr int kNumBars = 2 * kStages + 2 + 2 + 3;  // full, empty, tfull, tempty, dready, ddone, drain
+constexpr size_t kSmem = 1024 + static_cast<size_t>(kStages) * kStageBytes + kNumBars * 8 + 64 +
+                         16 + static_cast<size_t>(kEpiWarps) * kRbufBytes;
 constexpr int kGroups = kEpiWarps / 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 static_assert(kSmem <= 232448, "dynamic shared memory limit");
@@ -939,12 +951,39 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
     const int64_t s_begin = slab_offset_dev(args.t.j_begin, n_v);
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16);
     const uint64_t keep_pol = l2_evict_last_policy();
+    // r_ik staging of this warp: row il (SNP i = the warp's first + il) at
+    // rbuf + il kRowStride, pair (i, kc + kk) at + 16 kk.
+    const uint32_t rbuf =
+        static_cast<uint32_t>(((smem_u32(tmem_slot) + 64 + 15) & ~15u) +
+                              static_cast<uint32_t>(warp - 2) * wide::kRbufBytes);
+    // Asynchronous copies of the r_ik of chunk c of tile t for this warp's rows:
+    // lane copies pair lane % 8 of rows lane / 8 + 4 m, m = 0..3, 16 bytes each;
+    // none for rows i >= j or pairs past n_v.
+    auto issue_rows = [&](const Sched &t, int c) {
+      const int64_t kk = t.k0() + 8 * c + (lane & 7);  // this lane's pair column, in every piece
+      int64_t ii = t.i0() + 64 * static_cast<int64_t>(rank) + 16 * quarter + (lane >> 3);
+      int64_t pb = ii * (2 * n_v - ii - 1) / 2 - ii - 1;  // pair (ii, k) at pb + k
+      uint32_t dst = rbuf + static_cast<uint32_t>(lane >> 3) * wide::kRowStride +
+                     16u * static_cast<uint32_t>(lane & 7);
+#pragma unroll 1
+      for (int m = 0; m < 4; ++m) {  // rows lane / 8 + 4 m
+        if (ii < t.j && kk < n_v)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                       "l"(rtab + 4 * (pb + kk))
+                       : "memory");
+        pb += 4 * n_v - 4 * ii - 14;  // pb(ii + 4) = pb(ii) + sum of n_v - i - 2 over 4 rows
+        ii += 4;
+        dst += 4 * wide::kRowStride;
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     int dcount = 0;
     bool ok_all = true;
     Sched sc, pv;
     bool pv_has_d = false;
     sc.init(sp, cstart);
     for (int u = 0; ok_all; ++u) {
+      if (u >= 1) issue_rows(pv, group);  // the first chunk of tile u - 1, processed in (2)
       // (1) move the D accumulator of tile u to this thread's shared-memory slot
       bool cur_has_d = false;
       if (sc.valid) {
@@ -1009,14 +1048,29 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
 #pragma unroll
           for (int kk = 0; kk < KC; ++kk) {
             const int64_t k = kc + kk;
-            const bool ok = row_ok && k < n_v &&
-                            CCC_IN_BOUNDS(pbase + k, n_v * (n_v - 1) / 2, args.t.status);
-            r[kk] = ok ? __ldg(reinterpret_cast<const int2 *>(rtab + 4 * (pbase + k)) + a)
-                       : make_int2(0, 0);
+            const bool ok = row_ok && k < n_v;
             wk[kk] = (ok && want_ccc && persnp) ? __ldg(reinterpret_cast<const float2 *>(wv) + k)
                                                 : make_float2(1.f, 1.f);
             dd[kk] = pv_has_d ? ld_l2_keep(slot + (kl + kk) * 128 + L, keep_pol) : 0u;
           }
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+          __syncwarp();  // every lane's copies of the chunk have landed
+          const uint32_t rrow = rbuf + static_cast<uint32_t>((L >> 1) & 15) * wide::kRowStride +
+                                8u * static_cast<uint32_t>(a);
+#pragma unroll
+          for (int kk = 0; kk < KC; ++kk) {
+            const bool ok = row_ok && kc + kk < n_v &&
+                            CCC_IN_BOUNDS(pbase + kc + kk, n_v * (n_v - 1) / 2, args.t.status);
+            int2 v;
+            asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];"
+                         : "=r"(v.x), "=r"(v.y)
+                         : "r"(rrow + 16u * kk)
+                         : "memory");
+            r[kk] = ok ? v : make_int2(0, 0);
+          }
+          // The buffer takes the next chunk's rows once every lane has read it.
+          __syncwarp();
+          if (c + wide::kGroups < kChunks) issue_rows(pv, c + wide::kGroups);
           tmem_ld_wait();
           if (c == c_last) {
             tc_fence_before();
@@ -1085,6 +1139,8 @@ __global__ void __launch_bounds__(wide::kThreads, 1) __cluster_dims__(2, 1, 1)
       pv_has_d = cur_has_d;
       sc.advance(cstep);
     }
+    // Copies still in flight (after a wait that gave up) land before the CTA exits.
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
 
   tc_fence_before();
