@@ -367,13 +367,18 @@ static int launch_tally2_tc_auto(const Tally2Args &a, const ccc_opts *o, const u
 
 // Count operands of a 2-way tensor-core call: e2m1 or e4m3 rows, row-major or
 // (blocked_rows > 0) K-block-major.
+// The operand rows of a 2-way tensor-core call and, when w is set, the
+// per-SNP factors (for e2m1 rows from the same read of the codes).
 static int unpack_2way(const ccc_panel *p, const ccc_opts *o, uint8_t *op, int64_t kpad,
-                       int64_t rows_pad, cudaStream_t s, int64_t blocked_rows = 0) {
-  return fp4_2way(o)
-             ? launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
-                                  blocked_rows)
-             : launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
-                                  blocked_rows);
+                       int64_t rows_pad, cudaStream_t s, int64_t blocked_rows = 0,
+                       float *w = nullptr) {
+  if (fp4_2way(o))
+    return launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
+                              blocked_rows, w, o->gamma);
+  if (w != nullptr)
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
+  return launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
+                            blocked_rows);
 }
 
 static bool on_device(const void *p) {
@@ -471,7 +476,10 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
     return CCC_ECUDA;
   if (p->n_v < 2) return CCC_OK;
   float *w = at<float>(o, L.w);
-  if ((out_ccc != nullptr || filter != nullptr) && o->norm == CCC_NORM_PERSNP)
+  const bool want_w = (out_ccc != nullptr || filter != nullptr) && o->norm == CCC_NORM_PERSNP;
+  // With tensor-core operand rows the factors come with the unpack.
+  const bool w_in_unpack = o->path == CCC_PATH_TC && o->tile != 3;
+  if (want_w && !w_in_unpack)
     CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   Tally2Args a;
   a.group = o->group;
@@ -508,7 +516,9 @@ static int run_2way(const ccc_panel *p, int32_t *tally, float *out_ccc, const cc
                           ? k_split(o->split, p->n_v, fp4 ? L.kpad / 2 : L.kpad, dev.sms)
                           : 1;
     // The K-split kernel reads its operand K-block-major.
-    if (!packed) CCC_TRY(unpack_2way(p, o, op, L.kpad, L.rows_pad, s, split > 1 ? L.rows_pad : 0));
+    if (!packed)
+      CCC_TRY(unpack_2way(p, o, op, L.kpad, L.rows_pad, s, split > 1 ? L.rows_pad : 0,
+                          want_w ? w : nullptr));
     if (split > 1) {
       // Partial tallies of the K parts are summed into the zeroed output; the
       // CCC values follow from the complete tallies.
@@ -588,14 +598,17 @@ static int prep_3way(Run3 &R, bool want_ccc, int64_t j_last) {
   const ccc_panel *p = R.p;
   const ccc_opts *o = R.o;
   cudaStream_t s = R.s;
-  if (want_ccc && o->norm == CCC_NORM_PERSNP)
-    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, at<float>(o, R.L.w),
-                                 o->gamma, s));
+  const bool want_w = want_ccc && o->norm == CCC_NORM_PERSNP;
+  float *w = at<float>(o, R.L.w);
+  // e2m1 operand rows come with the factors from the same read of the codes.
+  if (want_w && !(o->path == CCC_PATH_TC && R.fp4))
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   if (o->path != CCC_PATH_TC)
     return launch_planes(p->geno, p->n_f, p->n_v, p->ld, at<uint64_t>(o, R.L.planes), R.L.w64, s);
   uint8_t *op = at<uint8_t>(o, R.L.op);
   if (R.fp4)
-    CCC_TRY(launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s));
+    CCC_TRY(launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s,
+                               0, want_w ? w : nullptr, o->gamma));
   else
     CCC_TRY(launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, R.L.kpad, R.L.rows_pad / 2, s));
   if (!class_route(o)) return CCC_OK;
@@ -816,7 +829,8 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
   for (int k = 0; k < n; ++k) {
     const ccc_panel &p = panels[k];
     float *w = at<float>(o, B.w[k]);
-    if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP && p.n_v >= 2)
+    const bool want_w = out_ccc != nullptr && o->norm == CCC_NORM_PERSNP && p.n_v >= 2;
+    if (want_w && o->path != CCC_PATH_TC)  // tensor cores: the factors come with the unpack
       CCC_TRY(launch_allele_counts(p.geno, p.n_f, p.n_v, p.ld, nullptr, w, o->gamma, s));
     Tally2Args a;
     a.n_v = p.n_v;
@@ -832,7 +846,8 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
     args[k] = a;
     if (p.n_v < 2) continue;
     if (o->path == CCC_PATH_TC) {
-      CCC_TRY(unpack_2way(&p, o, at<uint8_t>(o, B.op[k]), B.kpad[k], B.rows_pad[k], s));
+      CCC_TRY(unpack_2way(&p, o, at<uint8_t>(o, B.op[k]), B.kpad[k], B.rows_pad[k], s, 0,
+                          want_w ? w : nullptr));
     } else {
       uint64_t *planes = at<uint64_t>(o, B.op[k]);
       CCC_TRY(launch_planes(p.geno, p.n_f, p.n_v, p.ld, planes, B.w64[k], s));
@@ -1192,14 +1207,15 @@ int ccc2_stream(const ccc_panel *p, int n_phases, int32_t *host_tally, float *ho
   const size_t slot0 = align_up(L.total, 1024);
   // Preparation once for all phases.
   float *w = at<float>(o, L.w);
-  if (want_ccc && o->norm == CCC_NORM_PERSNP)
-    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
+  const bool want_w = want_ccc && o->norm == CCC_NORM_PERSNP;
   uint8_t *op = nullptr;
   uint64_t *planes = nullptr;
   const bool packed = o->path == CCC_PATH_TC && o->tile == 3;
+  if (want_w && (o->path != CCC_PATH_TC || packed))  // else the factors come with the unpack
+    CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   if (o->path == CCC_PATH_TC && !packed) {
     op = at<uint8_t>(o, L.op);
-    CCC_TRY(unpack_2way(p, o, op, L.kpad, L.rows_pad, s));
+    CCC_TRY(unpack_2way(p, o, op, L.kpad, L.rows_pad, s, 0, want_w ? w : nullptr));
   } else if (o->path != CCC_PATH_TC) {
     planes = at<uint64_t>(o, L.planes);
     CCC_TRY(launch_planes(p->geno, p->n_f, p->n_v, p->ld, planes, L.w64, s));

@@ -60,8 +60,11 @@ int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
                        int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0);
 // The same with e2m1 (FP4) counts, two entries per byte: rows of kpad / 2
 // bytes (kpad a multiple of 256); blocked: [kpad / 256][blocked_rows][128].
+// w != null: also the per-SNP factors of launch_allele_counts (w[n_v][2],
+// 1 - gamma f_i(a)) from the same read of the codes.
 int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
-                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0);
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0,
+                       float *w = nullptr, double gamma = 0.0);
 int launch_planes(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint64_t *planes,
                   int64_t w64, cudaStream_t s);
 

@@ -211,6 +211,79 @@ __global__ void k_unpack_e2m1(const uint64_t *__restrict__ geno, int64_t n_f, in
                  static_cast<uint32_t>(n1[1]), static_cast<uint32_t>(n1[1] >> 32));
 }
 
+// k_unpack_e2m1 with the per-SNP factors w = 1 - gamma f_i(a) of
+// k_allele_counts formed in the same pass over the codes: one 128-thread block
+// per SNP row pair (SNPs >= n_v write zero rows), each thread one packed word
+// at a time (a warp stores 512 contiguous bytes of a row), the counts n_i and
+// s_i^1 summed over the block.
+__global__ void __launch_bounds__(128) k_unpack_e2m1_w(const uint64_t *__restrict__ geno,
+                                                      int64_t n_f, int64_t n_v, int64_t ld,
+                                                      uint8_t *__restrict__ op, int64_t kpad,
+                                                      int64_t blocked_rows, float *__restrict__ w,
+                                                      double gamma) {
+  __shared__ long long part[4][2];
+  const int64_t i = blockIdx.x;
+  const int64_t wpr = kpad / 32;
+  const bool snp = i < n_v;
+  int64_t n = 0, s1 = 0;
+  for (int64_t k = threadIdx.x; k < wpr; k += 128) {
+    uint64_t v = 0xAAAAAAAAAAAAAAAAull;  // all entries "missing" -> zero operands
+    if (snp && k * 32 < n_f) {
+      const uint64_t raw = __ldg(geno + i * ld + k);
+      const uint64_t valid = valid_even_mask(k, n_f);
+      const uint64_t l = raw & valid;
+      const uint64_t h = (raw >> 1) & valid;
+      n += __popcll(valid & ~(h & ~l));
+      s1 += __popcll(l) + __popcll(h & l);
+      const uint64_t vm = valid | (valid << 1);
+      v = (raw & vm) | (0xAAAAAAAAAAAAAAAAull & ~vm);
+    }
+    uint64_t n0[2], n1[2];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const uint32_t x = static_cast<uint32_t>(v >> (32 * half));
+      const uint32_t l = x & 0x55555555u;
+      const uint32_t h = (x >> 1) & 0x55555555u;
+      const uint32_t nh = ~h & 0x55555555u;
+      const uint32_t rho1 = l + (l & h);
+      const uint32_t rho0 = (nh << 1) - (l & nh);
+      n0[half] = spread_2to4(rho0) << 1;
+      n1[half] = spread_2to4(rho1) << 1;
+    }
+    uint8_t *d0 = blocked_rows > 0 ? op + ((k >> 3) * blocked_rows + 2 * i) * 128 + (k & 7) * 16
+                                   : op + (2 * i) * (kpad / 2) + k * 16;
+    uint8_t *d1 = blocked_rows > 0 ? d0 + 128 : d0 + kpad / 2;
+    *reinterpret_cast<uint4 *>(d0) =
+        make_uint4(static_cast<uint32_t>(n0[0]), static_cast<uint32_t>(n0[0] >> 32),
+                   static_cast<uint32_t>(n0[1]), static_cast<uint32_t>(n0[1] >> 32));
+    *reinterpret_cast<uint4 *>(d1) =
+        make_uint4(static_cast<uint32_t>(n1[0]), static_cast<uint32_t>(n1[0] >> 32),
+                   static_cast<uint32_t>(n1[1]), static_cast<uint32_t>(n1[1] >> 32));
+  }
+  if (!snp) return;  // the whole block: i is uniform
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    part[warp][0] = n;
+    part[warp][1] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    n = part[0][0] + part[1][0] + part[2][0] + part[3][0];
+    s1 = part[0][1] + part[1][1] + part[2][1] + part[3][1];
+    const int64_t s0 = 2 * n - s1;
+    // 1 - gamma f_i(a), f_i(a) = s_i^a / (2 n_i), rounded once to fp32 (as k_allele_counts).
+    const double f0 = n > 0 ? static_cast<double>(s0) / (2.0 * static_cast<double>(n)) : 0.0;
+    const double f1 = n > 0 ? static_cast<double>(s1) / (2.0 * static_cast<double>(n)) : 0.0;
+    w[2 * i + 0] = static_cast<float>(1.0 - gamma * f0);
+    w[2 * i + 1] = static_cast<float>(1.0 - gamma * f1);
+  }
+}
+
 // Gather the 32 even-position bits of x into the low 32 bits.
 __device__ __forceinline__ uint64_t compact_even(uint64_t x) {
   x &= kEven;
@@ -301,9 +374,16 @@ int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
 }
 
 int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
-                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows) {
+                       int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows,
+                       float *w, double gamma) {
   if (kpad % 256 != 0) return CCC_EINVAL;
   if (blocked_rows != 0 && blocked_rows < 2 * snps_pad) return CCC_EINVAL;
+  if (w != nullptr) {
+    if (snps_pad < n_v) return CCC_EINVAL;
+    k_unpack_e2m1_w<<<static_cast<unsigned>(snps_pad), 128, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
+                                                                     blocked_rows, w, gamma);
+    return note_launch();
+  }
   const int threads = 256;
   const int64_t total = (kpad / 32) * snps_pad;
   const int64_t blocks = (total + threads - 1) / threads;
