@@ -926,6 +926,12 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
                                             "over individuals with v_j missing not counted)",
                                 "achieved": ex, "frac": ex / peak,
                                 "frac_clock_normalised": ex / roof["clock_normalised"]["peak"]}
+            if fp4:
+                # The same executed rate against the e4m3 operand peak (2 x the bf16
+                # burst), the denominator the class route was first read against.
+                e4m3_peak = 2.0 * bf16_peak
+                roof["executed"]["frac_of_e4m3_peak"] = ex / e4m3_peak
+                roof["executed"]["e4m3_peak"] = e4m3_peak
     else:
         per = 8.0 / 64.0 if w["kind"] == 2 else 24.0 / 64.0
         achieved = per * cmp_rank / (kernel_step_ms * 1e-3) / 1e12

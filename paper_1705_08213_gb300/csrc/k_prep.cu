@@ -378,11 +378,18 @@ int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
                        float *w, double gamma) {
   if (kpad % 256 != 0) return CCC_EINVAL;
   if (blocked_rows != 0 && blocked_rows < 2 * snps_pad) return CCC_EINVAL;
-  if (w != nullptr) {
+  // Fused with the factors while one 128-thread block per SNP still gives the
+  // GPU enough loads in flight (152 SMs x 8 blocks); a few long rows take the
+  // flat unpack (a thread per word) and the multi-warp count kernel instead.
+  if (w != nullptr && snps_pad >= 152 * 8) {
     if (snps_pad < n_v) return CCC_EINVAL;
     k_unpack_e2m1_w<<<static_cast<unsigned>(snps_pad), 128, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
                                                                      blocked_rows, w, gamma);
     return note_launch();
+  }
+  if (w != nullptr) {
+    const int rc = launch_allele_counts(geno, n_f, n_v, ld, nullptr, w, gamma, s);
+    if (rc != CCC_OK) return rc;
   }
   const int threads = 256;
   const int64_t total = (kpad / 32) * snps_pad;
