@@ -855,8 +855,7 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
     args[k] = a;
     if (p.n_v < 2) continue;
     if (o->path == CCC_PATH_TC) {
-      CCC_TRY(unpack_2way(&p, o, at<uint8_t>(o, B.op[k]), B.kpad[k], B.rows_pad[k], s, 0,
-                          want_w ? w : nullptr));
+      // the operand rows (and factors) are unpacked below, in launch order
     } else {
       uint64_t *planes = at<uint64_t>(o, B.op[k]);
       CCC_TRY(launch_planes(p.geno, p.n_f, p.n_v, p.ld, planes, B.w64[k], s));
@@ -882,6 +881,23 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
         order[y - 1] = t;
       }
   }
+  // Operand rows of every panel, in launch order, on the side stream: each
+  // tally launch waits only for its own panel's rows (the event's latest
+  // record), so the unpacks of later panels run in the SMs that the earlier
+  // tally launches leave idle in their last waves.
+  PrepRes *P = nullptr;
+  CCC_TRY(prep_res(dev.device, &P));
+  cudaStream_t ps = P->side;
+  if (cudaEventRecord(P->fork, s) != cudaSuccess || cudaStreamWaitEvent(ps, P->fork, 0) != cudaSuccess)
+    return CCC_ECUDA;
+  auto unpack_panel = [&](int k) -> int {
+    const ccc_panel &p = panels[k];
+    if (p.n_v < 2) return CCC_OK;
+    const bool want_w = out_ccc != nullptr && o->norm == CCC_NORM_PERSNP;
+    CCC_TRY(unpack_2way(&p, o, at<uint8_t>(o, B.op[k]), B.kpad[k], B.rows_pad[k], ps, 0,
+                        want_w ? at<float>(o, B.w[k]) : nullptr));
+    return cudaEventRecord(P->prepared[0], ps) == cudaSuccess ? CCC_OK : CCC_ECUDA;
+  };
   // SM-pair tiles: a panel with at least `solo` tiles keeps every SM busy on its
   // own, and runs as its own launch (its operand blocks then have L2 to
   // themselves); the smaller panels share persistent launches.
@@ -893,6 +909,8 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
       const int k = order[x];
       const int64_t nB = (panels[k].n_v + 127) / 128;
       if (panels[k].n_v >= 2 && tc2_pair_tiles(panels[k].n_v, 0, nB) >= solo) {
+        CCC_TRY(unpack_panel(k));
+        if (cudaStreamWaitEvent(s, P->prepared[0], 0) != cudaSuccess) return CCC_ECUDA;
         const int slot = timing_begin(s);
         const int rc = launch_tally2_tc_pair(args[k], at<uint8_t>(o, B.op[k]), B.rows_pad[k],
                                              B.kpad[k], dev.sms, s, fp4);
@@ -905,6 +923,11 @@ static int run_batched(const ccc_panel *panels, int n, int32_t *const *tally, fl
   } else {
     nb = n;
   }
+  for (int x = 0; x < nb; ++x) CCC_TRY(unpack_panel(order[x]));
+  // Every unpack has been issued: the main stream joins the side stream here.
+  if (cudaEventRecord(P->prepared[0], ps) != cudaSuccess ||
+      cudaStreamWaitEvent(s, P->prepared[0], 0) != cudaSuccess)
+    return CCC_ECUDA;
   static thread_local Tally2Args oargs[kMaxBatchPanels];
   static thread_local int64_t orows[kMaxBatchPanels], okpad[kMaxBatchPanels];
   static thread_local int64_t otiles[kMaxBatchPanels], ostages[kMaxBatchPanels];
