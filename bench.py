@@ -224,6 +224,8 @@ KERNEL_SOURCES = {
                                 "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc_pair_split_packed": ["k_tc2.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
                                       "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
+    "k_tally2_multi_fp4": ["k_multi.cuh", "k_multi.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
+                           "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_multi": ["k_multi.cuh", "k_multi.cu", "tc_pipeline_pair.cuh", "tc_pipeline.cuh",
                        "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh", "ccc_launch.h"],
     "k_tally2_tc": ["k_tc2.cu", "tc_pipeline.cuh", "tc_sched.cuh", "ccc_dev.cuh", "ccc_metric.cuh",
@@ -825,10 +827,12 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
     geno_np = make_panel(w, 0 if strong else rank)
     operand = {"auto": ccc.CCC_OPERAND_AUTO, "e4m3": ccc.CCC_OPERAND_E4M3,
                "e2m1": ccc.CCC_OPERAND_E2M1}[args.operand]
-    # The library's automatic choice: e2m1 on the 2-way SM-pair tiles (not s states) and on
-    # the 3-way genotype-class route's wide tiles (n_f <= 16,383).
+    # The library's automatic choice: e2m1 on the 2-way SM-pair tiles, for markers with at
+    # most 8 states (no K split at these sizes), and on the 3-way genotype-class route's wide
+    # tiles (n_f <= 16,383).
     fp4 = (path == ccc.CCC_PATH_TC and operand != ccc.CCC_OPERAND_E4M3 and
            ((w["kind"] == 2 and not w.get("states") and args.tile in (0, 2)) or
+            (w["kind"] == 2 and w.get("states") and w["states"] <= 8 and args.tile in (0, 2)) or
             (w["kind"] == 3 and args.tile in (0, 3) and w["n_f"] <= 16383)))
     run = Runner(ccc, torch, dev, w, path, geno_np, tile=args.tile,
                  shard=shard_range if strong else None, operand=operand)
@@ -883,7 +887,7 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
     packed = "_packed" if args.tile == 3 else "_fp4" if fp4 else ""
     if w["kind"] == 3:
         packed = ""
-    kname = {(2, True): ("k_tally2_multi" if w.get("states") else
+    kname = {(2, True): ("k_tally2_multi" + ("_fp4" if fp4 else "") if w.get("states") else
                          "k_tally2_tc_pair_split" + packed if w.get("split_compare") else
                          "k_tally2_tc_pair" + packed + ("w" if fp4 and w.get("threshold") is not None
                                                         else "")
@@ -1023,8 +1027,9 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
             run.out = torch.empty((rows, width), dtype=torch.float32, device=dev)
         o8 = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3)
         op8 = ccc.CCC_OP_2WAY if w["kind"] == 2 else ccc.CCC_OP_3WAY
-        ws8 = torch.empty(ccc.ccc_workspace_size(run.geno, w["n_f"], o8, op8),
-                          dtype=torch.uint8, device=dev)
+        size8 = (ccc.ccc_multi_workspace_size(run.geno, w["n_f"], w["states"], o8)
+                 if w.get("states") else ccc.ccc_workspace_size(run.geno, w["n_f"], o8, op8))
+        ws8 = torch.empty(size8, dtype=torch.uint8, device=dev)
         run.opts = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3, workspace=ws8)
         run.step(stream)
         torch.cuda.synchronize(dev)

@@ -148,9 +148,11 @@ typedef struct ccc_opts {
                              both give the same tallies and CCC values bit for bit.  E2M1 is
                              built for the 2-way SM-pair tiles (opts->tile 0 or 2, with K split,
                              row ranges, ccc2_stream, ccc2_filter and ccc2_batched) and for the
-                             3-way genotype-class route (opts->tile 0 or 3, n_f <= 16,383);
-                             elsewhere an explicit E2M1 returns CCC_EUNSUPPORTED.  AUTO (0) = E2M1 where it is built,
-                             else E4M3.  The workspace size depends on it. */
+                             3-way genotype-class route (opts->tile 0 or 3, n_f <= 16,383) and
+                             for markers with s <= 8 states (ccc2_multi_*, without K split);
+                             elsewhere an explicit E2M1 returns CCC_EUNSUPPORTED.  AUTO (0) =
+                             E2M1 where it is built, else E4M3.  The workspace size depends on
+                             it (for markers it is that of E4M3 rows, which are never smaller). */
   int32_t solo;           /* ccc2_batched on SM pairs: a panel with at least this many 256 x 256
                              tiles runs as its own launch, the others share one persistent
                              launch; 0 = 1024, < 0 = none (every panel in the shared launch). */

@@ -984,8 +984,18 @@ static int check_panel_multi(const ccc_panel_multi *p) {
 
 static int check_opts_multi(const ccc_opts *o) {
   CCC_TRY(check_opts(o));
-  if (o->path != CCC_PATH_TC || o->operand == CCC_OPERAND_E2M1) return CCC_EUNSUPPORTED;
+  if (o->path != CCC_PATH_TC) return CCC_EUNSUPPORTED;
   return (o->tile == 0 || o->tile == 2) ? CCC_OK : CCC_EINVAL;
+}
+
+// e2m1 operands for markers with s states: automatic (or asked for) with at
+// most 8 states and no K split; asked for with more states: refused.
+static int multi_fp4(const ccc_opts *o, int s, int split, bool *fp4) {
+  *fp4 = false;
+  if (o->operand == CCC_OPERAND_E4M3) return CCC_OK;
+  if (s > 8 || split > 1) return o->operand == CCC_OPERAND_E2M1 ? CCC_EUNSUPPORTED : CCC_OK;
+  *fp4 = true;
+  return CCC_OK;
 }
 
 // Workspace of the multi-allelic calls: [status][factors w[n_v][s]][operand rows].
@@ -994,17 +1004,21 @@ struct MultiLayout {
   int64_t kpad = 0, rows_pad = 0;
 };
 
-static MultiLayout make_multi_layout(int64_t n_f, int64_t n_v, int s, bool with_op) {
+// fp4: e2m1 rows (kpad a multiple of 256, kpad / 2 bytes per row), never
+// larger than the e4m3 rows the workspace size is given for.
+static MultiLayout make_multi_layout(int64_t n_f, int64_t n_v, int s, bool with_op,
+                                     bool fp4 = false) {
   MultiLayout L;
   size_t off = kAlign;
   L.w = off;
   off = align_up(off + sizeof(float) * static_cast<size_t>(n_v) * static_cast<size_t>(s), kAlign);
   if (with_op) {
-    L.kpad = round_up(n_f, 128);
+    L.kpad = round_up(n_f, fp4 ? 256 : 128);
     L.rows_pad = multi_rows_pad(n_v, s);
     off = align_up(off, 1024);
     L.op = off;
-    off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(L.kpad), 1024);
+    off = align_up(off + static_cast<size_t>(L.rows_pad) * static_cast<size_t>(fp4 ? L.kpad / 2 : L.kpad),
+                   1024);
   }
   L.total = off;
   return L;
@@ -1032,23 +1046,29 @@ static int run_multi(const ccc_panel_multi *p, int32_t *tally, float *out_ccc, c
   DeviceInfo dev;
   CCC_TRY(query_device(&dev));
   const int ns = p->n_states;
-  const MultiLayout L = make_multi_layout(p->n_f, p->n_v, ns, true);
-  CCC_TRY(check_multi_workspace(o, L, s));
-  if (p->n_v < 2) return CCC_OK;
-  float *w = at<float>(o, L.w);
-  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
-    CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
-  uint8_t *op = at<uint8_t>(o, L.op);
-  CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s));
+  const MultiLayout L8 = make_multi_layout(p->n_f, p->n_v, ns, true);
+  CCC_TRY(check_multi_workspace(o, L8, s));
   const bool whole = i_end < 0;
   if (whole) {
     i_begin = 0;
     i_end = p->n_v;
   }
-  const int split = whole && on_device(tally)
-                        ? k_split_tiles(o->split, (L.rows_pad / 256) * (L.rows_pad / 256 + 1) / 2,
-                                        L.kpad, dev.sms)
+  // An explicit E2M1 keeps the automatic K split off (it runs on e4m3 rows);
+  // AUTO splits where that pays and takes e4m3 rows for it.
+  const bool auto_split_off = o->operand == CCC_OPERAND_E2M1 && o->split == 0;
+  const int split = whole && on_device(tally) && !auto_split_off
+                        ? k_split_tiles(o->split, (L8.rows_pad / 256) * (L8.rows_pad / 256 + 1) / 2,
+                                        L8.kpad, dev.sms)
                         : 1;
+  bool fp4 = false;
+  CCC_TRY(multi_fp4(o, ns, split, &fp4));
+  const MultiLayout L = fp4 ? make_multi_layout(p->n_f, p->n_v, ns, true, true) : L8;
+  if (p->n_v < 2) return CCC_OK;
+  float *w = at<float>(o, L.w);
+  if (out_ccc != nullptr && o->norm == CCC_NORM_PERSNP)
+    CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
+  uint8_t *op = at<uint8_t>(o, L.op);
+  CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s, fp4));
   if (split > 1) {
     // Partial tallies of the K parts summed into the zeroed output; CCC values
     // from the complete tallies.
@@ -1068,7 +1088,7 @@ static int run_multi(const ccc_panel_multi *p, int32_t *tally, float *out_ccc, c
   const int rc = launch_tally2_multi(ns, p->n_v, w, tally, out_ccc, at<int32_t>(o, L.status),
                                      static_cast<float>(o->gamma), o->norm, o->group, op,
                                      L.rows_pad, L.kpad, dev.sms, s, i_begin, i_end,
-                                     pair_index(i_begin, i_begin + 1, p->n_v));
+                                     pair_index(i_begin, i_begin + 1, p->n_v), 1, fp4);
   timing_end(slot, s);
   return rc;
 }
@@ -1842,20 +1862,23 @@ int ccc2_multi_stream(const ccc_panel_multi *p, int n_phases, int32_t *host_tall
   CCC_TRY(stream_res(d, &R));
   const int ns = p->n_states;
   const int64_t ss = static_cast<int64_t>(ns) * ns;
-  const MultiLayout L = make_multi_layout(p->n_f, p->n_v, ns, true);
+  const MultiLayout L8 = make_multi_layout(p->n_f, p->n_v, ns, true);
+  bool fp4 = false;
+  CCC_TRY(multi_fp4(o, ns, 1, &fp4));
+  const MultiLayout L = fp4 ? make_multi_layout(p->n_f, p->n_v, ns, true, true) : L8;
   if (cudaMemsetAsync(at<int32_t>(o, L.status), 0, sizeof(int32_t), s) != cudaSuccess)
     return CCC_ECUDA;
   if (p->n_v < 2) return CCC_OK;
   const bool want_ccc = host_ccc != nullptr;
   const int64_t slot_pairs = max_phase_pairs_multi(p->n_v, ns, n_phases);
   const size_t slot_bytes = align_up(static_cast<size_t>(slot_pairs * ss) * 8, 1024);
-  const size_t slot0 = align_up(L.total, 1024);
+  const size_t slot0 = align_up(L8.total, 1024);  // as ccc2_multi_stream_workspace_size
   // Preparation once for all phases.
   float *w = at<float>(o, L.w);
   if (want_ccc && o->norm == CCC_NORM_PERSNP)
     CCC_TRY(launch_multi_counts(p->geno, p->n_f, p->n_v, p->ld, ns, nullptr, w, o->gamma, s));
   uint8_t *op = at<uint8_t>(o, L.op);
-  CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s));
+  CCC_TRY(launch_multi_unpack(p->geno, p->n_f, p->n_v, p->ld, ns, op, L.kpad, L.rows_pad, s, fp4));
   int64_t bounds[1025];
   phase_bounds(p->n_v, n_phases, bounds, multi_block_rows(ns));
   for (int ph = 0; ph < n_phases; ++ph) {
@@ -1875,7 +1898,7 @@ int ccc2_multi_stream(const ccc_panel_multi *p, int n_phases, int32_t *host_tall
     const int rc = launch_tally2_multi(ns, p->n_v, w, st, want_ccc ? sc : nullptr,
                                        at<int32_t>(o, L.status), static_cast<float>(o->gamma),
                                        o->norm, o->group, op, L.rows_pad, L.kpad, dev.sms, s, i0, i1,
-                                       pair0);
+                                       pair0, 1, fp4);
     timing_end(slot, s);
     if (rc != CCC_OK) return rc;
     if (cudaEventRecord(R->computed[k], s) != cudaSuccess) return CCC_ECUDA;

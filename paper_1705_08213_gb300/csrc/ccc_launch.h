@@ -232,16 +232,21 @@ int launch_multi_counts(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t l
                         int32_t *counts, float *w, double gamma, cudaStream_t st);
 int launch_multi_factors(const int32_t *counts, int64_t n_v, int s, float *w, double gamma,
                          cudaStream_t st);
+// fp4: e2m1 rows of kpad / 2 bytes (kpad a multiple of 256).
 int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t ld, int s,
-                        uint8_t *op, int64_t kpad, int64_t rows_pad, cudaStream_t st);
+                        uint8_t *op, int64_t kpad, int64_t rows_pad, cudaStream_t st,
+                        bool fp4 = false);
 // Tallies and, when out_ccc is set, CCC values of the pairs with
 // i_begin <= i < i_end (s*s each), pair (i, j) at pair_index(i, j) - pair0.
 // split > 1 (whole triangle only): the K stages in `split` parts whose partial
 // tallies are added into the zeroed tally array, no CCC values.
+// fp4 (s <= 8, split 1): op holds e2m1 rows (launch_multi_unpack with fp4) and
+// the tiles are 256 x 192 on the block-scaled FP4 MMA.
 int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                         int32_t *status, float gamma, int32_t norm, int32_t group, const uint8_t *op,
                         int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st,
-                        int64_t i_begin, int64_t i_end, int64_t pair0, int split = 1);
+                        int64_t i_begin, int64_t i_end, int64_t pair0, int split = 1,
+                        bool fp4 = false);
 int launch_tally2_multi_wide(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                              int32_t *status, float gamma, int32_t norm, int32_t group,
                              const uint8_t *op, int64_t rows_pad, int64_t kpad, int num_sms,

@@ -163,6 +163,77 @@ __global__ void __launch_bounds__(256) k_multi_unpack(const uint8_t *__restrict_
   }
 }
 
+// FP4 (e2m1) operand rows: as k_multi_unpack with each count 0, 1, 2 stored
+// as the nibble 0x0, 0x2, 0x4, two entries per byte (entry q in the low nibble
+// of byte q / 2 for even q), rows of kpad / 2 bytes (kpad a multiple of 256).
+// One thread per (32-row quarter, 32 individuals): 16 bytes per row.
+__global__ void __launch_bounds__(256) k_multi_unpack_e2m1(const uint8_t *__restrict__ geno,
+                                                           int64_t n_f, int64_t n_v, int64_t ld,
+                                                           int s, uint8_t *__restrict__ op,
+                                                           int64_t kpad, int64_t n_quarters) {
+  const int64_t chunks = kpad / 32;
+  const int64_t row_bytes = kpad / 2;
+  const int64_t total = n_quarters * chunks;
+  const int pw = snps_per_quarter(s);
+  const uint32_t us = static_cast<uint32_t>(s);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t g = t / chunks;
+    const int64_t c = t - g * chunks;
+    const int64_t q0 = 32 * c;
+    uint8_t *dst = op + (32 * g) * row_bytes + 16 * c;
+    int r = 0;
+    for (int u = 0; u < pw; ++u) {
+      const int64_t i = g * pw + u;
+      uint32_t words[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      if (i < n_v && q0 < n_f) {
+        const uint4 v0 = *reinterpret_cast<const uint4 *>(geno + i * ld + q0);
+        words[0] = v0.x;
+        words[1] = v0.y;
+        words[2] = v0.z;
+        words[3] = v0.w;
+        if (q0 + 16 < n_f) {  // the row holds ld >= n_f bytes, ld a multiple of 16
+          const uint4 v1 = *reinterpret_cast<const uint4 *>(geno + i * ld + q0 + 16);
+          words[4] = v1.x;
+          words[5] = v1.y;
+          words[6] = v1.z;
+          words[7] = v1.w;
+        }
+      }
+      uint32_t lo[8], hi[8], present[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        lo[k] = words[k] & 0x0F0F0F0Fu;
+        hi[k] = (words[k] >> 4) & 0x0F0F0F0Fu;
+        present[k] = (i < n_v ? valid_bytes(q0 + 4 * k, n_f) : 0u) &
+                     ~(nibble_ge(lo[k], us) | nibble_ge(hi[k], us));
+      }
+      for (int a = 0; a < s; ++a, ++r) {
+        uint32_t e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint32_t x[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int kk = 2 * k + h;
+            const uint32_t fx = nibble_eq(lo[kk], a) & present[kk];
+            const uint32_t fy = nibble_eq(hi[kk], a) & present[kk];
+            // count 1 -> 0x2, 2 -> 0x4 in each byte; then the 4 bytes -> 4 nibbles
+            uint32_t b = ((fx ^ fy) << 1) | ((fx & fy) << 2);
+            b = (b | (b >> 4)) & 0x00FF00FFu;
+            b = (b | (b >> 8)) & 0x0000FFFFu;
+            x[h] = b;
+          }
+          e[k] = x[0] | (x[1] << 16);
+        }
+        *reinterpret_cast<uint4 *>(dst + r * row_bytes) = make_uint4(e[0], e[1], e[2], e[3]);
+      }
+    }
+    for (; r < 32; ++r)
+      *reinterpret_cast<uint4 *>(dst + r * row_bytes) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
 // ---------------------------------------------------------------- CCC from stored tallies
 
 // One thread per pair: Eq. 3 over the pair's s x s table, the same operations
@@ -250,8 +321,17 @@ int launch_multi_factors(const int32_t *counts, int64_t n_v, int s, float *w, do
 }
 
 int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t ld, int s,
-                        uint8_t *op, int64_t kpad, int64_t rows_pad, cudaStream_t st) {
+                        uint8_t *op, int64_t kpad, int64_t rows_pad, cudaStream_t st, bool fp4) {
   const int64_t quarters = rows_pad / 32;
+  if (fp4) {
+    if (kpad % 256 != 0) return CCC_EINVAL;
+    const int64_t total4 = quarters * (kpad / 32);
+    if (total4 < 1) return CCC_OK;
+    const int64_t blocks4 = (total4 + 255) / 256 < 152 * 16 ? (total4 + 255) / 256 : 152 * 16;
+    k_multi_unpack_e2m1<<<static_cast<unsigned>(blocks4), 256, 0, st>>>(geno, n_f, n_v, ld, s, op,
+                                                                         kpad, quarters);
+    return note_launch();
+  }
   const int64_t total = quarters * (kpad / 16);
   if (total < 1) return CCC_OK;
   const int64_t blocks = (total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16;
@@ -263,8 +343,29 @@ int launch_multi_unpack(const uint8_t *geno, int64_t n_f, int64_t n_v, int64_t l
 int launch_tally2_multi(int s, int64_t n_v, const float *w, int32_t *tally, float *out_ccc,
                         int32_t *status, float gamma, int32_t norm, int32_t group, const uint8_t *op,
                         int64_t rows_pad, int64_t kpad, int num_sms, cudaStream_t st,
-                        int64_t i_begin, int64_t i_end, int64_t pair0, int split) {
+                        int64_t i_begin, int64_t i_end, int64_t pair0, int split, bool fp4) {
   if (n_v < 2) return CCC_OK;
+  if (fp4) {
+    // e2m1 rows of kpad / 2 bytes; 256 x 192 tiles, no K split; s <= 8.
+    if (split > 1 || s > 8 || kpad % 256 != 0) return CCC_EINVAL;
+    MultiMaps maps;
+    if (!tc::make_operand_map(&maps.m[0], op, rows_pad, kpad / 2, tcp::BMH) ||
+        !tc::make_operand_map(&maps.m[1], op, rows_pad, kpad / 2, kMultiRectNB / 2))
+      return CCC_ECUDA;
+    MultiArgs a4{n_v, w, tally, out_ccc, status, gamma, norm, i_begin, i_end, pair0};
+    a4.out_len = checked_out_len(pairs_in_rows(n_v, i_begin, i_end));
+    const int nkb4 = static_cast<int>((kpad / 2) / tcp::BK);
+    switch (s) {
+      case 2: return launch_tally2_multi_fp4_s<2>(maps, a4, group, nkb4, num_sms, st);
+      case 3: return launch_tally2_multi_fp4_s<3>(maps, a4, group, nkb4, num_sms, st);
+      case 4: return launch_tally2_multi_fp4_s<4>(maps, a4, group, nkb4, num_sms, st);
+      case 5: return launch_tally2_multi_fp4_s<5>(maps, a4, group, nkb4, num_sms, st);
+      case 6: return launch_tally2_multi_fp4_s<6>(maps, a4, group, nkb4, num_sms, st);
+      case 7: return launch_tally2_multi_fp4_s<7>(maps, a4, group, nkb4, num_sms, st);
+      case 8: return launch_tally2_multi_fp4_s<8>(maps, a4, group, nkb4, num_sms, st);
+      default: return CCC_EINVAL;
+    }
+  }
   if (s > 8) return launch_tally2_multi_wide(s, n_v, w, tally, out_ccc, status, gamma, norm, group,
                                              op, rows_pad, kpad, num_sms, st, i_begin, i_end, pair0,
                                              split);

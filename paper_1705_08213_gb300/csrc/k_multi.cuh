@@ -9,6 +9,8 @@
 #include "tc_pipeline_pair.cuh"
 #include "tc_sched.cuh"
 
+#include <type_traits>
+
 namespace ccc {
 namespace {
 
@@ -64,17 +66,30 @@ __device__ __forceinline__ void store_row(float *dst, const float (&v)[S]) {
   }
 }
 
-template <int S>
-struct EpiMulti {
+// B blocks of NBQ quarters (32 operand rows each): 8 for the 256 x 256 e4m3
+// tiles (TriSchedPair), 6 for the 256 x 192 FP4 tiles (RectSchedT; two
+// 192-column accumulators and the scale factors fit the 512 TMEM columns).
+constexpr int kMultiRectQ = 6;
+constexpr int kMultiRectNB = 32 * kMultiRectQ;
+
+template <int S, int NBQ = 8>
+struct EpiMultiT {
   using Params = MultiArgs;
   static constexpr int PW = snps_per_quarter(S);
   static constexpr int STAGE_BYTES_PER_WARP = 0;
+  using Sched = std::conditional_t<NBQ == 8, TriSchedPair,
+                                   RectSchedT<8 * PW, NBQ * PW, 32 * NBQ>>;
 
+  // The warps of column half h (c0 = h NC) take the chunks of 32 columns
+  // [h NBQ / 2, (h + 1) NBQ / 2); chunk c is B quarter NBQ J + c.
   template <int NC, bool PRELOAD = false>
-  __device__ static void tile(const Params &args, const TriSchedPair &sc, int rank, int quarter,
+  __device__ static void tile(const Params &args, const Sched &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
                               float *) {
     static_assert(!PRELOAD, "s-state tiles run on the two-accumulator pipeline");
+    static_assert(NBQ % 2 == 0, "two column halves");
+    const int cb = (c0 / NC) * (NBQ / 2);
+    const int ce = cb + NBQ / 2;
     const int u = lane / S;
     const int a = lane - u * S;
     const int64_t n_v = args.n_v;
@@ -87,16 +102,16 @@ struct EpiMulti {
     if (want_ccc && persnp && row_ok) wi = __ldg(args.w + i * S + a);
     const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1;  // pair index = row_base + j
     const int src0 = (u < PW ? u : 0) * S;                        // first lane of SNP i
-    for (int c = c0; c < c0 + NC; ++c) {
+    for (int c = cb; c < ce; ++c) {
       uint32_t v[32];
       tmem_ld_32x32b_x32(t_base + c * 32, v);
       tmem_ld_wait();
-      if (c == c0 + NC - 1) {
+      if (c == ce - 1) {
         tc_fence_before();
         mbar_arrive_cluster(release_cluster_bar);
       }
-      // Column chunk c = 32 rows of the B block: quarter (c & 3) of half c >> 2.
-      const int64_t j0 = ((2 * static_cast<int64_t>(sc.J) + (c >> 2)) * 4 + (c & 3)) * PW;
+      // Column chunk c = 32 rows of the B block: its quarter c.
+      const int64_t j0 = (NBQ * static_cast<int64_t>(sc.J) + c) * PW;
 #pragma unroll
       for (int jl = 0; jl < PW; ++jl) {
         const int64_t j = j0 + jl;
@@ -204,11 +219,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
 }
 
 template <int S>
+using EpiMulti = EpiMultiT<S, 8>;
+
+template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
     k_tally2_multi(const __grid_constant__ CUtensorMap tm, const MultiArgs args,
                    TriSched::Params sp, int nkb) {
   tcp::persistent_gemm_pair<TriSchedPair, EpiMulti<S>, kMultiEpiWarps>(&tm, sp, args, nkb, args.status);
 }
+
+// FP4 (e2m1) operands: 256 x 192 tiles on SM pairs, two accumulators
+// (tcp::persistent_gemm_pair with NB = 192); A through maps.m[0] (box 128 rows),
+// B through maps.m[1] (box 96 rows).
+struct MultiMaps {
+  CUtensorMap m[2];
+};
+
+template <int S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
+    k_tally2_multi_fp4(const __grid_constant__ MultiMaps maps, const MultiArgs args,
+                       TriSched::Params sp, int nkb) {
+  using Epi = EpiMultiT<S, kMultiRectQ>;
+  tcp::persistent_gemm_pair<typename Epi::Sched, Epi, kMultiEpiWarps, false, true, kMultiRectNB>(
+      maps.m, sp, args, nkb, args.status);
+}
+
+constexpr size_t multi_fp4_smem() { return tcp::smem_bytes_nb(kMultiRectNB, kMultiEpiWarps, 0); }
 
 // Persistent grid size for a pair kernel of kMultiThreads threads.
 template <typename K>
@@ -258,6 +294,54 @@ int launch_tally2_multi_split_s(const CUtensorMap &tm, const MultiArgs &a, int64
   const int64_t clusters = units < max_clusters ? units : max_clusters;
   k_tally2_multi_split<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, tcp::SMEM_BYTES,
                             s>>>(tm, a, sp, nkb);
+  return note_launch();
+}
+
+// FP4 launch over the rows [i_begin, i_end) (nI row blocks of 8 PW markers,
+// nJ column blocks of 6 PW).
+template <int S>
+int launch_tally2_multi_fp4_s(const MultiMaps &maps, const MultiArgs &a, int group, int nkb,
+                              int num_sms, cudaStream_t s) {
+  using Epi = EpiMultiT<S, kMultiRectQ>;
+  constexpr int64_t pi = 8 * static_cast<int64_t>(snps_per_quarter(S));
+  constexpr int64_t pj = kMultiRectQ * static_cast<int64_t>(snps_per_quarter(S));
+  TriSched::Params sp;
+  sp.nI = static_cast<int>((a.n_v + pi - 1) / pi);
+  sp.nJ = static_cast<int>((a.n_v + pj - 1) / pj);
+  sp.group = group > 0 ? group : 16;
+  sp.shift = 0;
+  sp.I0 = static_cast<int>(a.i_begin / pi);
+  const int64_t iend = a.i_end < a.n_v ? a.i_end : a.n_v;
+  sp.I1 = static_cast<int>((iend + pi - 1) / pi < sp.nI ? (iend + pi - 1) / pi : sp.nI);
+  const int64_t tiles = rect_tiles<typename Epi::Sched>(sp.nI, sp.nJ, sp.I0, sp.I1);
+  if (tiles <= 0) return CCC_OK;
+  static int max_clusters_dev[kMaxDevices] = {};
+  const int dev_c = current_device();
+  if (dev_c < 0) return CCC_ECUDA;
+  int &max_clusters = max_clusters_dev[dev_c];
+  if (max_clusters == 0) {
+    if (cudaFuncSetAttribute(k_tally2_multi_fp4<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(multi_fp4_smem())) != cudaSuccess)
+      return CCC_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
+    cfg.blockDim = dim3(kMultiThreads, 1, 1);
+    cfg.dynamicSmemBytes = multi_fp4_smem();
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tally2_multi_fp4<S>, &cfg) != cudaSuccess || n < 1)
+      return CCC_ECUDA;
+    max_clusters = n < num_sms / 2 ? n : num_sms / 2;
+  }
+  const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
+  k_tally2_multi_fp4<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, multi_fp4_smem(),
+                          s>>>(maps, a, sp, nkb);
   return note_launch();
 }
 

@@ -353,7 +353,7 @@ struct PairMaps {
 // division work.
 struct Epi2Rect {
   using Params = Tally2Args;
-  using Sched = RectSchedT<kRectJ>;
+  using Sched = RectSchedT<128, kRectJ, kRectNB>;
   static constexpr int STAGE_BYTES_PER_WARP = kRectJ * 8;  // float2 factors of the tile's j
   static constexpr int CHUNKS = kRectJ / 16;  // whole 32-column chunks
   static constexpr int TAIL = kRectNB - 32 * CHUNKS;
@@ -940,19 +940,6 @@ int launch_tally2_tc_batched(const Tally2Args *args, const uint8_t *const *ops,
   return note_launch();
 }
 
-// Rect tiles (128-SNP row blocks I by kRectJ-SNP column blocks J) holding a
-// pair i < j, in row blocks [I0, I1).
-int64_t tc2_rect_tiles(int64_t n_v, int64_t I0, int64_t I1) {
-  const int64_t nI = (n_v + 127) / 128;
-  const int64_t nJ = (n_v + kRectJ - 1) / kRectJ;
-  int64_t t = 0;
-  for (int64_t I = I0; I < nI && I < I1; ++I) {
-    const int64_t jm = Epi2Rect::Sched::jmin(static_cast<int>(I));
-    if (jm < nJ) t += nJ - jm;
-  }
-  return t;
-}
-
 int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_pad, int64_t kpad,
                           int num_sms, cudaStream_t s, bool fp4) {
   static bool attr_set[kMaxDevices] = {};
@@ -988,7 +975,7 @@ int launch_tally2_tc_pair(const Tally2Args &a, const uint8_t *op, int64_t rows_p
     sp.I0 = static_cast<int>((a.i_begin > 0 ? a.i_begin : 0) / 128);
     sp.I1 = static_cast<int>(a.i_end < a.n_v ? (a.i_end + 127) / 128 : sp.nI);
     const int nkb = static_cast<int>(row_bytes / BK);
-    const int64_t tiles = tc2_rect_tiles(a.n_v, sp.I0, sp.I1);
+    const int64_t tiles = rect_tiles<Epi2Rect::Sched>(sp.nI, sp.nJ, sp.I0, sp.I1);
     if (tiles == 0) return CCC_OK;
     int &mc = max_clusters[dev][3];
     if (mc == 0) {

@@ -80,13 +80,15 @@ struct TriSchedPair : TriSched {
   __host__ __device__ int b_row() const { return J * 256; }
 };
 
-// Upper-triangle tiles of 128-SNP row blocks I by SNPJ-SNP column blocks J (the
-// FP4 double-buffered SM-pair kernel: SNPJ = 112).  A tile holds a pair i < j
-// iff its last j exceeds its first i: SNPJ J + SNPJ - 1 > 128 I, i.e.
-// J >= jmin(I) = ceil((128 I - SNPJ + 2) / SNPJ).  Order as TriSched: groups of
-// `group` column blocks, rows inside a group in increasing order, row blocks
-// [I0, I1) only.
-template <int SNPJ>
+// Upper-triangle tiles of SNPI-SNP row blocks I (256 operand rows, A rows
+// 256 I ..) by SNPJ-SNP column blocks J (NB operand rows, B rows NB J ..): the
+// narrow-tile FP4 SM-pair kernels (biallelic thresholded: 128 x 120 SNPs,
+// NB = 240; s-state markers: 8 PW x 6 PW markers, NB = 192).  A tile holds a
+// pair i < j iff its last j exceeds its first i: SNPJ J + SNPJ - 1 > SNPI I,
+// i.e. J >= jmin(I) = ceil((SNPI I - SNPJ + 2) / SNPJ).  Order as TriSched:
+// groups of `group` column blocks, rows inside a group in increasing order, row
+// blocks [I0, I1) only.
+template <int SNPI, int SNPJ, int NB>
 struct RectSchedT {
   using Params = TriSched::Params;  // nI, nJ, group, I0, I1 (shift unused)
   int nI, nJ, nG, G, I0;
@@ -94,12 +96,12 @@ struct RectSchedT {
   bool valid;
 
   __host__ __device__ static int jmin(int I) {
-    const int x = 128 * I - SNPJ + 2;
+    const int x = SNPI * I - SNPJ + 2;
     return x <= 0 ? 0 : (x + SNPJ - 1) / SNPJ;
   }
   // One past the last row block with a column block below col_end.
   __host__ __device__ static int rows_below(int col_end) {
-    return (SNPJ * (col_end - 1) + SNPJ - 2) / 128 + 1;
+    return (SNPJ * (col_end - 1) + SNPJ - 2) / SNPI + 1;
   }
   __host__ __device__ void set_group() {
     col_end = min((g + 1) * G, nJ);
@@ -148,8 +150,20 @@ struct RectSchedT {
   __host__ __device__ int k_blocks(int nkb) const { return nkb; }
   __host__ __device__ int k_begin() const { return 0; }
   __host__ __device__ int a_row() const { return I * 256; }
-  __host__ __device__ int b_row() const { return J * 2 * SNPJ; }
+  __host__ __device__ int b_row() const { return J * NB; }
 };
+
+// Tiles of RectSchedT<SNPI, SNPJ, NB> over nI row and nJ column blocks, row
+// blocks [I0, I1) (the host's grid size; the same count the schedule visits).
+template <class Rect>
+inline int64_t rect_tiles(int nI, int nJ, int I0, int I1) {
+  int64_t t = 0;
+  for (int I = I0; I < nI && I < I1; ++I) {
+    const int jm = Rect::jmin(I);
+    if (jm < nJ) t += nJ - jm;
+  }
+  return t;
+}
 
 // Units of a K-split launch, part-major: unit u = (tile u % tiles, part
 // u / tiles); part p takes the K stages [p nkb / split, (p + 1) nkb / split)

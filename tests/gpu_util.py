@@ -113,8 +113,11 @@ def to_device_bytes(geno_np):
     return torch.from_numpy(np.ascontiguousarray(geno_np, dtype=np.uint8)).cuda()
 
 
-def run_multi(geno_np, n_f, s, norm=0, gamma=2.0 / 3.0, fused=True, group=0):
-    """Multi-allelic tallies (int32 [npairs, s*s]) and CCC (float32 [npairs, s*s]) via the C ABI."""
+def run_multi(geno_np, n_f, s, norm=0, gamma=2.0 / 3.0, fused=True, group=0, operand=0, split=0):
+    """Multi-allelic tallies (int32 [npairs, s*s]) and CCC (float32 [npairs, s*s]) via the C ABI.
+
+    operand: ccc_opts.operand (0 automatic: e2m1 for s <= 8 without K split); split:
+    ccc_opts.split (0 automatic, 1 off)."""
     import paper_1705_08213_gb300 as ccc
     torch = torch_mod()
     g = to_device_bytes(geno_np)
@@ -124,6 +127,8 @@ def run_multi(geno_np, n_f, s, norm=0, gamma=2.0 / 3.0, fused=True, group=0):
     ws = workspace(ccc.ccc_multi_workspace_size(g, n_f, s, opts))
     opts = ccc.ccc_opts_default(norm=norm, gamma=gamma, workspace=ws)
     opts.group = group
+    opts.operand = operand
+    opts.split = split
     tally = torch.full((max(npairs, 1), s * s), -7, dtype=torch.int32, device="cuda")
     out = torch.full((max(npairs, 1), s * s), -7.0, dtype=torch.float32, device="cuda")
     if fused:

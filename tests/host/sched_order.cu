@@ -1,10 +1,11 @@
 // Host enumeration of the 2-way tile orders, for checks without a GPU.
 //
 // usage: sched_order KIND n_v I0 I1 group clusters
-//   KIND 0: square 128-SNP tiles (TriSchedPair, shift 0), 1: 128 x 120-SNP
-//   tiles (RectSchedT<120>).  Cluster c of `clusters` visits the tiles
-//   start = c, c + clusters, ... as the persistent kernels do; one line
-//   "c I J" per visit, clusters in turn.
+//   KIND 0: square 128-SNP tiles (TriSchedPair, shift 0); 1: 128 x 120-SNP
+//   tiles (RectSchedT<128, 120, 240>); 2, 3: the s-state tiles of 8 PW x 6 PW
+//   markers for s = 4 (PW = 8) and s = 3 (PW = 10) (RectSchedT<8 PW, 6 PW, 192>).
+//   Cluster c of `clusters` visits the tiles start = c, c + clusters, ... as
+//   the persistent kernels do; one line "c I J" per visit, clusters in turn.
 #include <cstdio>
 #include <cstdlib>
 
@@ -25,8 +26,9 @@ int main(int argc, char **argv) {
   const int kind = std::atoi(argv[1]);
   const long long n_v = std::atoll(argv[2]);
   TriSched::Params p;
-  const int snpj = kind == 0 ? 128 : 120;
-  p.nI = static_cast<int>((n_v + 127) / 128);
+  const int snpi = kind <= 1 ? 128 : kind == 2 ? 64 : 80;
+  const int snpj = kind == 0 ? 128 : kind == 1 ? 120 : kind == 2 ? 48 : 60;
+  p.nI = static_cast<int>((n_v + snpi - 1) / snpi);
   p.nJ = static_cast<int>((n_v + snpj - 1) / snpj);
   p.I0 = std::atoi(argv[3]);
   p.I1 = std::atoi(argv[4]);
@@ -35,7 +37,11 @@ int main(int argc, char **argv) {
   const int clusters = std::atoi(argv[6]);
   if (kind == 0)
     run<TriSchedPair>(p, clusters);
+  else if (kind == 1)
+    run<RectSchedT<128, 120, 240>>(p, clusters);
+  else if (kind == 2)
+    run<RectSchedT<64, 48, 192>>(p, clusters);
   else
-    run<RectSchedT<120>>(p, clusters);
+    run<RectSchedT<80, 60, 192>>(p, clusters);
   return 0;
 }

@@ -4,6 +4,8 @@ Tallies must equal the oracle's exactly and CCC values agree within 1e-6
 relative, for every state count 2..15, both normalisations, ragged sizes that
 span several 256-row blocks and K stages, the degenerate cases, and sampled
 rows of the full-size workload.  s = 2 must reproduce the biallelic kernel bit
+for bit.  With s <= 8 the automatic operands are e2m1 (256 x 192 tiles of
+8 PW x 6 PW markers, PW = floor(32 / s)); they must equal the e4m3 operands bit
 for bit.
 """
 
@@ -253,3 +255,79 @@ def test_stream_to_pinned_host(n_phases):
     ccc.ccc2_multi_stream(g, n_f, s, n_phases, ht2, None, opts)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(ht2.numpy(), t_full)
+
+
+E4M3, E2M1 = 1, 2
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("norm", [0, 1])
+def test_fp4_equals_e4m3_bit_for_bit(s, norm):
+    pw = 32 // s
+    n_v, n_f = 6 * pw * 3 + 8 * pw + 5, 700
+    g = synth.panel_multi(n_v, n_f, s, seed=140 + s, p_missing=0.04, pad_seed=9)
+    t4, c4 = run_multi(g, n_f, s, norm=norm, operand=E2M1, split=1)
+    t8, c8 = run_multi(g, n_f, s, norm=norm, operand=E4M3, split=1)
+    np.testing.assert_array_equal(t4, t8)
+    assert np.array_equal(c4.view(np.int32), c8.view(np.int32)), "CCC bits differ"
+
+
+# e2m1 tiles: marker counts around multiples of the 6 PW column block and the 8 PW row block,
+# individual counts around the 256-entry K stage
+FP4_EDGES = [(4, 47, 255), (4, 48, 256), (4, 49, 257), (4, 64, 513), (4, 97, 300),
+             (3, 59, 256), (3, 60, 511), (3, 81, 700), (7, 23, 129), (7, 25, 1000),
+             (8, 24, 257), (2, 95, 600), (2, 130, 1)]
+
+
+@pytest.mark.parametrize("s,n_v,n_f", FP4_EDGES, ids=[f"s{s}-{v}x{f}" for s, v, f in FP4_EDGES])
+def test_fp4_tile_edges_against_oracle(s, n_v, n_f):
+    g = synth.panel_multi(n_v, n_f, s, seed=160 + n_v, p_missing=0.05, pad_seed=n_f)
+    t, c = run_multi(g, n_f, s, operand=E2M1)
+    et, ec = oracle.ccc2_multi_all(g, n_f, s)
+    assert_tally_equal(t, et, f"fp4 s={s} {n_v}x{n_f}")
+    assert_ccc_close(c, ec, what=f"fp4 s={s} {n_v}x{n_f}")
+
+
+def test_fp4_long_vectors_unsplit():
+    """One e2m1 accumulator per entry summing all n_f: tallies up to 4 n_f."""
+    s, n_v, n_f = 3, 20, 300000
+    g = np.zeros((n_v, synth.multi_default_ld(n_f)), np.uint8)
+    g[:, :n_f] = 0x22
+    g[5, :n_f:2] = 0x10
+    t, c = run_multi(g, n_f, s, operand=E2M1, split=1)
+    et, ec = oracle.ccc2_multi_all(g, n_f, s)
+    assert_tally_equal(t, et, "fp4 long")
+    assert_ccc_close(c, ec, what="fp4 long")
+    assert t.max() == 4 * n_f
+
+
+def test_fp4_refused_where_not_built():
+    import torch
+
+    import paper_1705_08213_gb300 as ccc
+    s, n_v, n_f = 9, 20, 300
+    g = synth.panel_multi(n_v, n_f, s, seed=170)
+    dg = to_device_bytes(g)
+    opts = ccc.ccc_opts_default()
+    ws = workspace(ccc.ccc_multi_workspace_size(dg, n_f, s, opts))
+    npairs = ccc.ccc2_count(n_v)
+    tally = torch.zeros((npairs, s * s), dtype=torch.int32, device="cuda")
+    out = torch.zeros((npairs, s * s), dtype=torch.float32, device="cuda")
+    for kw in (dict(operand=E2M1), dict(operand=E2M1, split=4)):
+        opts = ccc.ccc_opts_default(workspace=ws)
+        opts.operand = kw["operand"]
+        opts.split = kw.get("split", 0)
+        with pytest.raises(ccc.CCCError) as e:
+            ccc.ccc2_multi_tally_metric(dg, n_f, s, tally, out, opts)
+        assert e.value.status == ccc.CCC_EUNSUPPORTED
+    # s <= 8 with an explicit K split: e2m1 is not built there either
+    g4 = synth.panel_multi(n_v, n_f, 4, seed=171)
+    dg4 = to_device_bytes(g4)
+    ws4 = workspace(ccc.ccc_multi_workspace_size(dg4, n_f, 4, ccc.ccc_opts_default()))
+    opts = ccc.ccc_opts_default(workspace=ws4)
+    opts.operand = E2M1
+    opts.split = 2
+    t4 = torch.zeros((npairs, 16), dtype=torch.int32, device="cuda")
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc2_multi_tally(dg4, n_f, 4, t4, opts)
+    assert e.value.status == ccc.CCC_EUNSUPPORTED

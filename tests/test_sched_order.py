@@ -42,10 +42,14 @@ CASES = [(2, 0, 1, 8, 1), (129, 0, 2, 8, 3), (1000, 0, 8, 4, 3), (1000, 2, 5, 16
          (3840, 0, 30, 16, 11)]
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+# (SNPs per row block, per column block) of each tile kind of sched_order.cu
+SHAPES = {0: (128, 128), 1: (128, 120), 2: (64, 48), 3: (80, 60)}
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 @pytest.mark.parametrize("n_v,I0,I1,group,clusters", CASES)
 def test_tile_order_covers_triangle_once(sched_bin, kind, n_v, I0, I1, group, clusters):
-    snpj = 128 if kind == 0 else 120
+    snpi, snpj = SHAPES[kind]
     v = visits(sched_bin, kind, n_v, I0, I1, group, clusters)
     tiles = [tuple(t) for t in v[:, 1:]]
     assert len(set(tiles)) == len(tiles), "a tile visited twice"
@@ -54,9 +58,9 @@ def test_tile_order_covers_triangle_once(sched_bin, kind, n_v, I0, I1, group, cl
     assert counts.max() - counts.min() <= 1
     cover = np.zeros((n_v, n_v), dtype=np.int32)
     for I, J in tiles:
-        i0, i1 = 128 * I, min(128 * I + 128, n_v)
+        i0, i1 = snpi * I, min(snpi * I + snpi, n_v)
         j0, j1 = snpj * J, min(snpj * J + snpj, n_v)
-        assert 0 <= I < (n_v + 127) // 128 and 0 <= J < (n_v + snpj - 1) // snpj
+        assert 0 <= I < (n_v + snpi - 1) // snpi and 0 <= J < (n_v + snpj - 1) // snpj
         ii, jj = np.meshgrid(np.arange(i0, i1), np.arange(j0, j1), indexing="ij")
         m = ii < jj
         if i1 - i0 > 1 or j1 - j0 > 1:
@@ -64,6 +68,6 @@ def test_tile_order_covers_triangle_once(sched_bin, kind, n_v, I0, I1, group, cl
             assert m.any() or i1 == n_v or j1 == n_v
         cover[ii[m], jj[m]] += 1
     rows = np.zeros(n_v, dtype=bool)
-    rows[128 * I0:min(128 * I1, n_v)] = True
+    rows[snpi * I0:min(snpi * I1, n_v)] = True
     want = np.triu(np.ones((n_v, n_v), dtype=np.int32), 1) * rows[:, None]
     np.testing.assert_array_equal(cover, want)
