@@ -308,7 +308,9 @@ int launch_tally2_multi_fp4_s(const MultiMaps &maps, const MultiArgs &a, int gro
   TriSched::Params sp;
   sp.nI = static_cast<int>((a.n_v + pi - 1) / pi);
   sp.nJ = static_cast<int>((a.n_v + pj - 1) / pj);
-  sp.group = group > 0 ? group : 16;
+  // Default tile order: groups of 32 column blocks (GB300, s = 4, 10,000 x
+  // 16,384, per call: 4.81 ms against 4.86 with 16, 4.95 with 8, 4.84 with 64).
+  sp.group = group > 0 ? group : 32;
   sp.shift = 0;
   sp.I0 = static_cast<int>(a.i_begin / pi);
   const int64_t iend = a.i_end < a.n_v ? a.i_end : a.n_v;
