@@ -1022,7 +1022,7 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
             lo, hi = run.shard if run.shard is not None else (0, w["n_v"])
             rows = (ccc.ccc2_rows_count(w["n_v"], lo, hi) if w["kind"] == 2 else
                     ccc.ccc3_count(w["n_v"], lo, hi))
-            width = 4 if w["kind"] == 2 else 8
+            width = ((w["states"] ** 2 if w.get("states") else 4) if w["kind"] == 2 else 8)
             run.tally = torch.empty((rows, width), dtype=torch.int32, device=dev)
             run.out = torch.empty((rows, width), dtype=torch.float32, device=dev)
         o8 = ccc.ccc_opts_default(operand=ccc.CCC_OPERAND_E4M3)

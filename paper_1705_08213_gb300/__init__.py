@@ -208,6 +208,16 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _out(name, t, count, width, elem_size=4):
+    """Pointer of an output array that must hold count x width elements of elem_size bytes
+    (the library writes that many through the raw pointer; a smaller tensor is refused here)."""
+    if t is None:
+        return None
+    if t.numel() * t.element_size() < int(count) * int(width) * elem_size:
+        raise CCCError(name, CCC_EINVAL)
+    return _ptr(t)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -260,8 +270,9 @@ def ccc_allele_counts(geno, n_f, counts, stream=None):
 
 def ccc2_tally(geno, n_f, tally, opts, stream=None):
     p = _panel(geno, n_f)
-    _check("ccc2_tally", load().ccc2_tally(ctypes.byref(p), _ptr(tally), ctypes.byref(opts),
-                                           _stream(stream)))
+    n = ccc2_count(p.n_v)
+    _check("ccc2_tally", load().ccc2_tally(ctypes.byref(p), _out("ccc2_tally", tally, n, 4),
+                                           ctypes.byref(opts), _stream(stream)))
 
 
 def ccc2_metric(tally, counts, n_v, opts, ccc, stream=None):
@@ -307,9 +318,11 @@ def ccc2_batched_tune(genos, n_fs, tallies, cccs, opts, stream=None):
 def ccc2_tally_metric_rows(geno, n_f, i_begin, i_end, tally, ccc, opts, stream=None):
     """2-way over the rows [i_begin, i_end) (one phase)."""
     p = _panel(geno, n_f)
-    _check("ccc2_tally_metric_rows",
-           load().ccc2_tally_metric_rows(ctypes.byref(p), int(i_begin), int(i_end), _ptr(tally),
-                                         _ptr(ccc), ctypes.byref(opts), _stream(stream)))
+    name = "ccc2_tally_metric_rows"
+    n = ccc2_rows_count(p.n_v, max(0, min(int(i_begin), p.n_v)), max(0, min(int(i_end), p.n_v)))
+    _check(name, load().ccc2_tally_metric_rows(ctypes.byref(p), int(i_begin), int(i_end),
+                                               _out(name, tally, n, 4), _out(name, ccc, n, 4),
+                                               ctypes.byref(opts), _stream(stream)))
 
 
 def ccc2_rows_count(n_v, i_begin, i_end):
@@ -372,20 +385,29 @@ def ccc2_filter(geno, n_f, threshold, hits, cap, n_hits, opts, stream=None):
     """Thresholded 2-way output: hits is a device buffer of cap ccc_hit records (40 bytes
     each; may be None when cap is 0); n_hits a device int64 tensor receiving the total."""
     p = _panel(geno, n_f)
-    _check("ccc2_filter", load().ccc2_filter(ctypes.byref(p), float(threshold), _ptr(hits), int(cap),
-                                             _ptr(n_hits), ctypes.byref(opts), _stream(stream)))
+    _check("ccc2_filter", load().ccc2_filter(ctypes.byref(p), float(threshold),
+                                             _out("ccc2_filter", hits, int(cap), 40, 1), int(cap),
+                                             _out("ccc2_filter", n_hits, 1, 8, 1),
+                                             ctypes.byref(opts), _stream(stream)))
 
 
 def ccc2_tally_metric(geno, n_f, tally, ccc, opts, stream=None):
     p = _panel(geno, n_f)
-    _check("ccc2_tally_metric", load().ccc2_tally_metric(ctypes.byref(p), _ptr(tally), _ptr(ccc),
-                                                         ctypes.byref(opts), _stream(stream)))
+    n, name = ccc2_count(p.n_v), "ccc2_tally_metric"
+    _check(name, load().ccc2_tally_metric(ctypes.byref(p), _out(name, tally, n, 4),
+                                          _out(name, ccc, n, 4), ctypes.byref(opts), _stream(stream)))
+
+
+def _slab_count(n_v, j_begin, j_end):
+    return ccc3_count(n_v, max(0, min(int(j_begin), n_v)), max(0, min(int(j_end), n_v)))
 
 
 def ccc3_tally(geno, n_f, j_begin, j_end, tally, opts, stream=None):
     p = _panel(geno, n_f)
-    _check("ccc3_tally", load().ccc3_tally(ctypes.byref(p), int(j_begin), int(j_end), _ptr(tally),
-                                           ctypes.byref(opts), _stream(stream)))
+    n = _slab_count(p.n_v, j_begin, j_end)
+    _check("ccc3_tally", load().ccc3_tally(ctypes.byref(p), int(j_begin), int(j_end),
+                                           _out("ccc3_tally", tally, n, 8), ctypes.byref(opts),
+                                           _stream(stream)))
 
 
 def ccc3_metric(tally, counts, n_v, j_begin, j_end, opts, ccc, stream=None):
@@ -396,9 +418,10 @@ def ccc3_metric(tally, counts, n_v, j_begin, j_end, opts, ccc, stream=None):
 
 def ccc3_tally_metric(geno, n_f, j_begin, j_end, tally, ccc, opts, stream=None):
     p = _panel(geno, n_f)
-    _check("ccc3_tally_metric", load().ccc3_tally_metric(ctypes.byref(p), int(j_begin), int(j_end),
-                                                         _ptr(tally), _ptr(ccc), ctypes.byref(opts),
-                                                         _stream(stream)))
+    n, name = _slab_count(p.n_v, j_begin, j_end), "ccc3_tally_metric"
+    _check(name, load().ccc3_tally_metric(ctypes.byref(p), int(j_begin), int(j_end),
+                                          _out(name, tally, n, 8), _out(name, ccc, n, 8),
+                                          ctypes.byref(opts), _stream(stream)))
 
 
 def ccc_status(opts, stream=None):
@@ -499,15 +522,18 @@ def ccc_multi_counts(geno, n_f, s, counts, stream=None):
 
 def ccc2_multi_tally(geno, n_f, s, tally, opts, stream=None):
     p = _panel_multi(geno, n_f, s)
-    _check("ccc2_multi_tally", load().ccc2_multi_tally(ctypes.byref(p), _ptr(tally),
+    n = ccc2_count(p.n_v)
+    _check("ccc2_multi_tally", load().ccc2_multi_tally(ctypes.byref(p),
+                                                       _out("ccc2_multi_tally", tally, n, s * s),
                                                        ctypes.byref(opts), _stream(stream)))
 
 
 def ccc2_multi_tally_metric(geno, n_f, s, tally, ccc, opts, stream=None):
     p = _panel_multi(geno, n_f, s)
-    _check("ccc2_multi_tally_metric",
-           load().ccc2_multi_tally_metric(ctypes.byref(p), _ptr(tally), _ptr(ccc), ctypes.byref(opts),
-                                          _stream(stream)))
+    n, name = ccc2_count(p.n_v), "ccc2_multi_tally_metric"
+    _check(name, load().ccc2_multi_tally_metric(ctypes.byref(p), _out(name, tally, n, s * s),
+                                                _out(name, ccc, n, s * s), ctypes.byref(opts),
+                                                _stream(stream)))
 
 
 def ccc2_multi_metric(tally, counts, n_v, s, opts, ccc, stream=None):
@@ -518,9 +544,12 @@ def ccc2_multi_metric(tally, counts, n_v, s, opts, ccc, stream=None):
 
 def ccc2_multi_tally_metric_rows(geno, n_f, s, i_begin, i_end, tally, ccc, opts, stream=None):
     p = _panel_multi(geno, n_f, s)
-    _check("ccc2_multi_tally_metric_rows",
-           load().ccc2_multi_tally_metric_rows(ctypes.byref(p), int(i_begin), int(i_end), _ptr(tally),
-                                               _ptr(ccc), ctypes.byref(opts), _stream(stream)))
+    name = "ccc2_multi_tally_metric_rows"
+    n = ccc2_rows_count(p.n_v, max(0, min(int(i_begin), p.n_v)), max(0, min(int(i_end), p.n_v)))
+    _check(name, load().ccc2_multi_tally_metric_rows(ctypes.byref(p), int(i_begin), int(i_end),
+                                                     _out(name, tally, n, s * s),
+                                                     _out(name, ccc, n, s * s), ctypes.byref(opts),
+                                                     _stream(stream)))
 
 
 def ccc2_multi_phase_bounds(n_v, s, n_phases):

@@ -308,3 +308,30 @@ def test_checked_build_exports_the_same_entry_points_and_its_hook(lib):
     with pytest.raises(ccc.CCCError) as e:
         ccc.ccc_checked_shrink_outputs(3)  # this process loaded the normal build
     assert e.value.status == ccc.CCC_EUNSUPPORTED
+
+
+def test_binding_refuses_outputs_smaller_than_the_call_writes():
+    """The Python binding checks every output tensor's size before the library writes
+    through the raw pointer (a (pairs, 4) array for an s-state call would be overrun)."""
+    import torch
+    n_v = 10
+    npairs = ccc.ccc2_count(n_v)
+    geno = torch.zeros((n_v, 32), dtype=torch.int64)
+    o = ccc.ccc_opts_default()
+    small = torch.zeros((npairs - 1, 4), dtype=torch.int32)
+    for call in (lambda: ccc.ccc2_tally(geno, 1000, small, o),
+                 lambda: ccc.ccc2_tally_metric(geno, 1000, small, None, o),
+                 lambda: ccc.ccc2_tally_metric_rows(geno, 1000, 0, n_v, small, None, o),
+                 lambda: ccc.ccc3_tally(geno, 1000, 0, n_v, small, o)):
+        with pytest.raises(ccc.CCCError) as e:
+            call()
+        assert e.value.status == ccc.CCC_EINVAL
+    mgeno = torch.zeros((n_v, 1024), dtype=torch.uint8)
+    t4 = torch.zeros((npairs, 4), dtype=torch.int32)  # an s = 4 table needs 16 per pair
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc2_multi_tally_metric(mgeno, 1000, 4, t4, None, o)
+    assert e.value.status == ccc.CCC_EINVAL
+    with pytest.raises(ccc.CCCError) as e:
+        ccc.ccc2_filter(geno, 1000, 0.5, torch.zeros(39, dtype=torch.uint8), 1,
+                        torch.zeros(1, dtype=torch.int64), o)
+    assert e.value.status == ccc.CCC_EINVAL
