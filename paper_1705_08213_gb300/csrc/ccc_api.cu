@@ -632,11 +632,6 @@ static int prep_3way(Run3 &R, bool want_ccc, int64_t j_last) {
 
 // Tallies (and CCC values) of the slabs [R.a.j_begin, R.a.j_end) into
 // R.a.tally / R.a.ccc (first triple = slab j_begin's first).
-// First 3-way class batch: this fraction of the masked-row buffer (GB300,
-// 1,536 x 8,192 per step: 14.04 ms with 1/4, 14.08 with 1/8, 14.13 with the
-// whole buffer, the class kernels taking 13.80 / 13.80 / 13.59 ms of it).
-constexpr int64_t kFirstBatchDiv = 4;
-
 static int slabs_3way(Run3 &R) {
   const ccc_panel *p = R.p;
   const ccc_opts *o = R.o;
@@ -671,13 +666,13 @@ static int slabs_3way(Run3 &R) {
     const int64_t op_rows = L.rows_pad + L.halves * L.mask_rows;
     int64_t j0 = jb;
     for (int b = 0; j0 < je; ++b) {
-      // The first batch's preparation cannot overlap a tally kernel: with two
-      // buffers it takes a quarter of the masked rows, so that its class kernel
-      // starts sooner while the next batch is prepared beside it.
-      const int64_t cap_rows = L.halves == 2 && b == 0 ? L.mask_rows / kFirstBatchDiv : L.mask_rows;
+      // (A first batch of a quarter of the masked rows, so that less preparation
+      // precedes the first class kernel, measured 14.04 against 14.13 ms per step
+      // at 1,536 x 8,192 but 13.80 against 13.59 ms of class kernels: the extra
+      // launch's last wave.  Not kept.)
       int64_t j1 = j0 + 1;
       while (j1 < je && j1 - j0 < L.cbuf_slabs &&
-             tc3_class_mask_rows(j0, j1 + 1, p->n_v) <= cap_rows)
+             tc3_class_mask_rows(j0, j1 + 1, p->n_v) <= L.mask_rows)
         ++j1;
       if (tc3_class_mask_rows(j0, j1, p->n_v) > L.mask_rows) return CCC_ERANGE;
       const int h = L.halves == 2 ? (b & 1) : 0;
