@@ -76,7 +76,8 @@ template <int S, int NBQ = 8>
 struct EpiMultiT {
   using Params = MultiArgs;
   static constexpr int PW = snps_per_quarter(S);
-  static constexpr int STAGE_BYTES_PER_WARP = 0;
+  // The PERSNP factors w_j of the warp's NBQ / 2 quarters of markers.
+  static constexpr int STAGE_BYTES_PER_WARP = (NBQ / 2) * 32 * 4;
   using Sched = std::conditional_t<NBQ == 8, TriSchedPair,
                                    RectSchedT<8 * PW, NBQ * PW, 32 * NBQ>>;
 
@@ -85,7 +86,7 @@ struct EpiMultiT {
   template <int NC, bool PRELOAD = false>
   __device__ static void tile(const Params &args, const Sched &sc, int rank, int quarter,
                               int lane, uint32_t t_base, uint32_t release_cluster_bar, int c0,
-                              float *) {
+                              float *stage) {
     static_assert(!PRELOAD, "s-state tiles run on the two-accumulator pipeline");
     static_assert(NBQ % 2 == 0, "two column halves");
     const int cb = (c0 / NC) * (NBQ / 2);
@@ -102,6 +103,17 @@ struct EpiMultiT {
     if (want_ccc && persnp && row_ok) wi = __ldg(args.w + i * S + a);
     const int64_t row_base = i * (2 * n_v - i - 1) / 2 - i - 1;  // pair index = row_base + j
     const int src0 = (u < PW ? u : 0) * S;                        // first lane of SNP i
+    // w_j of the warp's markers jw0 .. (NBQ / 2 quarters), staged once per tile; every lane
+    // then reads the same address (a broadcast) instead of its own global load per pair.
+    const int64_t jw0 = (NBQ * static_cast<int64_t>(sc.J) + cb) * PW;
+    if (want_ccc && persnp) {
+      __syncwarp();  // the previous tile's reads are done
+      for (int k = lane; k < (NBQ / 2) * PW * S; k += 32) {
+        const int64_t e = jw0 * S + k;
+        stage[k] = e < n_v * S ? __ldg(args.w + e) : 1.f;
+      }
+      __syncwarp();
+    }
     for (int c = cb; c < ce; ++c) {
       uint32_t v[32];
       tmem_ld_32x32b_x32(t_base + c * 32, v);
@@ -146,11 +158,10 @@ struct EpiMultiT {
           for (int b = 0; b < S; ++b) cv[b] = 0.f;
         } else if (persnp) {
           const float inv = __frcp_rn(static_cast<float>(n4));
+          const float *wjs = stage + ((c - cb) * PW + jl) * S;
 #pragma unroll
-          for (int b = 0; b < S; ++b) {
-            const float wj = __ldg(args.w + j * S + b);
-            cv[b] = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r[b]), inv), wi), wj);
-          }
+          for (int b = 0; b < S; ++b)
+            cv[b] = __fmul_rn(__fmul_rn(__fmul_rn(static_cast<float>(r[b]), inv), wi), wjs[b]);
         } else {
           const float d = static_cast<float>(n4);
           const float wia = joint_factor(rs, d, args.gamma);
@@ -244,7 +255,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMultiThreads, 1)
       maps.m, sp, args, nkb, args.status);
 }
 
-constexpr size_t multi_fp4_smem() { return tcp::smem_bytes_nb(kMultiRectNB, kMultiEpiWarps, 0); }
+constexpr size_t multi_fp4_smem() {
+  return tcp::smem_bytes_nb(kMultiRectNB, kMultiEpiWarps, EpiMultiT<2, kMultiRectQ>::STAGE_BYTES_PER_WARP);
+}
+constexpr size_t multi_smem() {
+  return tcp::smem_bytes(kMultiEpiWarps, EpiMultiT<2, 8>::STAGE_BYTES_PER_WARP);
+}
 
 // Persistent grid size for a pair kernel of kMultiThreads threads.
 template <typename K>
@@ -371,7 +387,7 @@ int launch_tally2_multi_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB,
   int &max_clusters = max_clusters_dev[dev_c];
   if (max_clusters == 0) {
     if (cudaFuncSetAttribute(k_tally2_multi<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(tcp::SMEM_BYTES)) != cudaSuccess)
+                             static_cast<int>(multi_smem())) != cudaSuccess)
       return CCC_ECUDA;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
@@ -381,7 +397,7 @@ int launch_tally2_multi_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB,
     attr.val.clusterDim.z = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(num_sms), 1, 1);
     cfg.blockDim = dim3(kMultiThreads, 1, 1);
-    cfg.dynamicSmemBytes = tcp::SMEM_BYTES;
+    cfg.dynamicSmemBytes = multi_smem();
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
@@ -390,7 +406,7 @@ int launch_tally2_multi_s(const CUtensorMap &tm, const MultiArgs &a, int64_t nB,
     max_clusters = n < num_sms / 2 ? n : num_sms / 2;
   }
   const int64_t clusters = tiles < max_clusters ? tiles : max_clusters;
-  k_tally2_multi<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, tcp::SMEM_BYTES, s>>>(tm, a, sp,
+  k_tally2_multi<S><<<static_cast<unsigned>(2 * clusters), kMultiThreads, multi_smem(), s>>>(tm, a, sp,
                                                                                           nkb);
   return note_launch();
 }
