@@ -65,8 +65,7 @@ __global__ void __launch_bounds__(256) k_multi_counts(const uint8_t *__restrict_
   for (int a = 0; a < S; ++a) c[a] = 0;
   uint32_t n = 0;
   const uint32_t us = static_cast<uint32_t>(s);
-  for (int64_t q0 = 16 * static_cast<int64_t>(lane); q0 < n_f; q0 += 16 * 32) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(row + q0);
+  auto count16 = [&](int64_t q0, const uint4 &v) {
     const uint32_t words[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -78,7 +77,17 @@ __global__ void __launch_bounds__(256) k_multi_counts(const uint8_t *__restrict_
       for (int a = 0; a < S; ++a)
         c[a] += __popc(nibble_eq(lo, a) & present) + __popc(nibble_eq(hi, a) & present);
     }
+  };
+  // Four 16-byte loads in flight per lane, then the remainder one at a time.
+  int64_t q0 = 16 * static_cast<int64_t>(lane);
+  for (; q0 + 3 * 16 * 32 < n_f; q0 += 4 * 16 * 32) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const uint4 *>(row + q0 + u * 16 * 32);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) count16(q0 + u * 16 * 32, v[u]);
   }
+  for (; q0 < n_f; q0 += 16 * 32) count16(q0, *reinterpret_cast<const uint4 *>(row + q0));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     n += __shfl_xor_sync(0xffffffffu, n, o);
