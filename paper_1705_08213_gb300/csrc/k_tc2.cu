@@ -321,12 +321,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * tcp::FP4_E
 // kRectJ = 120 SNPs j (N = 240 columns, B rows 120 per CTA), so that two
 // accumulators and the scale factors fill the 512 TMEM columns and the MMAs of
 // a tile run while the epilogue tests the previous one.  Tiles over
-// RectSchedT<120>; A through maps.m[0] (box 128 rows), B through maps.m[1]
+// RectSchedT<128, 120, 240>; A through maps.m[0] (box 128 rows), B through maps.m[1]
 // (box 120 rows).  Per column the MMA is 1.4% slower at N = 240 (153.8 cycles
 // per instruction against 161.8 at N = 256), and the tiles are 6.6% more per
 // triangle, but at short K the single-accumulator kernel above waits for its
 // epilogue's read-out on every tile: GB300, 200,000 x 4,096 thresholded,
-// 109.3 ms against 119.9.  Full output stays on the single-accumulator kernel,
+// 104.2 ms (109.3 with the tile order of the full-output kernel) against 119.9.  Full output stays on the single-accumulator kernel,
 // whose epilogue stores interleave with the next tile's MMAs there as well
 // (20,000 x 16,384: 3.64 ms against 3.81 with these tiles; x 32,768: 6.67
 // against 7.15).
