@@ -240,8 +240,8 @@ int ccc2_filter(const ccc_panel *panel, float threshold, ccc_hit *hits, int64_t 
  * stored at index ccc2_index(i, j, n_v) - ccc2_index(i_begin, i_begin + 1, n_v)
  * (these rows are contiguous in the upper-triangle order).  tally, ccc:
  * device [ccc2_rows_count(n_v, i_begin, i_end)][4].  Workspace: CCC_OP_2WAY.
- * 0 <= i_begin <= i_end <= n_v.  Row ranges that start on a multiple of 64
- * waste no tensor-core work.
+ * 0 <= i_begin <= i_end <= n_v.  Row ranges that start on a multiple of 128
+ * (64 with opts->tile = 1) waste no tensor-core work.
  */
 int ccc2_tally_metric_rows(const ccc_panel *panel, int64_t i_begin, int64_t i_end,
                            int32_t *tally, float *ccc, const ccc_opts *opts, void *stream);
