@@ -365,16 +365,18 @@ static int launch_tally2_tc_auto(const Tally2Args &a, const ccc_opts *o, const u
               : launch_tally2_tc(a, op, rows_pad, kpad, sms, s);
 }
 
-// Count operands of a 2-way tensor-core call: e2m1 or e4m3 rows, row-major or
-// (blocked_rows > 0) K-block-major.
-// The operand rows of a 2-way tensor-core call and, when w is set, the
-// per-SNP factors (for e2m1 rows from the same read of the codes).
+// The count operand rows of a 2-way tensor-core call, e2m1 or e4m3, row-major
+// or (blocked_rows > 0) K-block-major, and, when w is set, the per-SNP factors
+// (from the same read of the codes for e2m1 rows and for K-block-major rows).
 static int unpack_2way(const ccc_panel *p, const ccc_opts *o, uint8_t *op, int64_t kpad,
                        int64_t rows_pad, cudaStream_t s, int64_t blocked_rows = 0,
                        float *w = nullptr) {
   if (fp4_2way(o))
     return launch_unpack_e2m1(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,
                               blocked_rows, w, o->gamma);
+  if (blocked_rows > 0)
+    return launch_unpack_blocked(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2,
+                                 blocked_rows, false, w, o->gamma, s);
   if (w != nullptr)
     CCC_TRY(launch_allele_counts(p->geno, p->n_f, p->n_v, p->ld, nullptr, w, o->gamma, s));
   return launch_unpack_e4m3(p->geno, p->n_f, p->n_v, p->ld, op, kpad, rows_pad / 2, s,

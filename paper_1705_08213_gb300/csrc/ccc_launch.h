@@ -53,9 +53,15 @@ int launch_allele_counts(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t
                          int32_t *counts, float *w, double gamma, cudaStream_t s);
 int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, double gamma,
                                cudaStream_t s);
-// blocked_rows > 0: K-block-major layout [kpad / 128][blocked_rows][128], the
-// operand buffer holding blocked_rows >= 2 snps_pad rows (the K-split kernel
-// reads it so); 0: row-major [2 snps_pad][kpad].
+// K-block-major operand rows, [K block][blocked_rows][128 bytes] (the K-split
+// kernel reads them so; blocked_rows >= 2 snps_pad, snps_pad a multiple of 32):
+// e4m3 (fp4 false, K blocks of 128 entries) or e2m1 (256 entries).  w != null:
+// also the per-SNP factors of launch_allele_counts (w[n_v][2]), counted in the
+// same pass over the codes.
+int launch_unpack_blocked(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                          int64_t kpad, int64_t snps_pad, int64_t blocked_rows, bool fp4, float *w,
+                          double gamma, cudaStream_t s);
+// blocked_rows > 0: launch_unpack_blocked (e4m3); 0: row-major [2 snps_pad][kpad].
 int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                        int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows = 0);
 // The same with e2m1 (FP4) counts, two entries per byte: rows of kpad / 2

@@ -125,7 +125,7 @@ constexpr uint32_t kRho1E4M3 = 0x40003800u;
 // that each warp store covers 512 contiguous bytes of a row.
 __global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
                               int64_t ld, uint8_t *__restrict__ op, int64_t kpad,
-                              int64_t snps_pad, int64_t blocked_rows) {
+                              int64_t snps_pad) {
   const int64_t hpr = kpad / 16;  // 16-entry chunks per operand row
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= hpr * snps_pad) return;
@@ -146,10 +146,8 @@ __global__ void k_unpack_e4m3(const uint64_t *__restrict__ geno, int64_t n_f, in
     r0[b] = __byte_perm(kRho0E4M3, 0u, sel);
     r1[b] = __byte_perm(kRho1E4M3, 0u, sel);
   }
-  // Row-major [row][kpad], or K-block-major [kpad / 128][blocked_rows][128].
-  uint8_t *d0 = blocked_rows > 0 ? op + ((c >> 3) * blocked_rows + 2 * i) * 128 + (c & 7) * 16
-                                 : op + (2 * i) * kpad + c * 16;
-  uint8_t *d1 = blocked_rows > 0 ? d0 + 128 : d0 + kpad;
+  uint8_t *d0 = op + (2 * i) * kpad + c * 16;  // row-major [row][kpad]
+  uint8_t *d1 = d0 + kpad;
   *reinterpret_cast<uint4 *>(d0) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
   *reinterpret_cast<uint4 *>(d1) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
 }
@@ -175,7 +173,7 @@ __device__ __forceinline__ uint64_t spread_2to4(uint32_t x32) {
 // for a present entry (not h & ~l), rho(0) = 2 - l; both are 0 when missing.
 __global__ void k_unpack_e2m1(const uint64_t *__restrict__ geno, int64_t n_f, int64_t n_v,
                               int64_t ld, uint8_t *__restrict__ op, int64_t kpad,
-                              int64_t snps_pad, int64_t blocked_rows) {
+                              int64_t snps_pad) {
   const int64_t wpr = kpad / 32;  // packed words (32 entries) per operand row
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= wpr * snps_pad) return;
@@ -199,10 +197,8 @@ __global__ void k_unpack_e2m1(const uint64_t *__restrict__ geno, int64_t n_f, in
     n0[half] = spread_2to4(rho0) << 1;
     n1[half] = spread_2to4(rho1) << 1;
   }
-  // Row-major [row][kpad / 2], or K-block-major [kpad / 256][blocked_rows][128].
-  uint8_t *d0 = blocked_rows > 0 ? op + ((k >> 3) * blocked_rows + 2 * i) * 128 + (k & 7) * 16
-                                 : op + (2 * i) * (kpad / 2) + k * 16;
-  uint8_t *d1 = blocked_rows > 0 ? d0 + 128 : d0 + kpad / 2;
+  uint8_t *d0 = op + (2 * i) * (kpad / 2) + k * 16;  // row-major [row][kpad / 2]
+  uint8_t *d1 = d0 + kpad / 2;
   *reinterpret_cast<uint4 *>(d0) =
       make_uint4(static_cast<uint32_t>(n0[0]), static_cast<uint32_t>(n0[0] >> 32),
                  static_cast<uint32_t>(n0[1]), static_cast<uint32_t>(n0[1] >> 32));
@@ -219,8 +215,7 @@ __global__ void k_unpack_e2m1(const uint64_t *__restrict__ geno, int64_t n_f, in
 __global__ void __launch_bounds__(128) k_unpack_e2m1_w(const uint64_t *__restrict__ geno,
                                                       int64_t n_f, int64_t n_v, int64_t ld,
                                                       uint8_t *__restrict__ op, int64_t kpad,
-                                                      int64_t blocked_rows, float *__restrict__ w,
-                                                      double gamma) {
+                                                      float *__restrict__ w, double gamma) {
   __shared__ long long part[4][2];
   const int64_t i = blockIdx.x;
   const int64_t wpr = kpad / 32;
@@ -250,9 +245,8 @@ __global__ void __launch_bounds__(128) k_unpack_e2m1_w(const uint64_t *__restric
       n0[half] = spread_2to4(rho0) << 1;
       n1[half] = spread_2to4(rho1) << 1;
     }
-    uint8_t *d0 = blocked_rows > 0 ? op + ((k >> 3) * blocked_rows + 2 * i) * 128 + (k & 7) * 16
-                                   : op + (2 * i) * (kpad / 2) + k * 16;
-    uint8_t *d1 = blocked_rows > 0 ? d0 + 128 : d0 + kpad / 2;
+    uint8_t *d0 = op + (2 * i) * (kpad / 2) + k * 16;
+    uint8_t *d1 = d0 + kpad / 2;
     *reinterpret_cast<uint4 *>(d0) =
         make_uint4(static_cast<uint32_t>(n0[0]), static_cast<uint32_t>(n0[0] >> 32),
                    static_cast<uint32_t>(n0[1]), static_cast<uint32_t>(n0[1] >> 32));
@@ -282,6 +276,111 @@ __global__ void __launch_bounds__(128) k_unpack_e2m1_w(const uint64_t *__restric
     w[2 * i + 0] = static_cast<float>(1.0 - gamma * f0);
     w[2 * i + 1] = static_cast<float>(1.0 - gamma * f1);
   }
+}
+
+// K-block-major operand rows, [K block][row][128 bytes], for the K-split
+// tally kernel: a 256-thread block takes 32 SNPs (8 threads per SNP, each 16
+// bytes of both of its rows per K block) over a range of K blocks, so that a
+// warp store covers 1 KB of one K block (4 SNPs x 2 rows x 128 bytes) and a
+// block's stores 8 KB; each thread's loads walk along its SNP's packed row.
+// FP4: a K block is 256 entries (8 packed words, one per thread); e4m3: 128
+// entries (4 words, a half word per thread).  SNPs in [n_v, snps_pad) get zero
+// rows, as do entries past n_f.  COUNT: each SNP's n_i and s_i^1 (Eq. 1) over
+// the block's entries are added into cnt[2 i], cnt[2 i + 1] (zeroed before).
+template <bool FP4, bool COUNT>
+__global__ void __launch_bounds__(256) k_unpack_blocked(const uint64_t *__restrict__ geno,
+                                                       int64_t n_f, int64_t n_v, int64_t ld,
+                                                       uint8_t *__restrict__ op, int64_t snps_pad,
+                                                       int64_t nkb, int64_t blocked_rows,
+                                                       int64_t kb_per, int32_t *__restrict__ cnt) {
+  const int sub = threadIdx.x & 7;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * 32 + (threadIdx.x >> 3);
+  if (i >= snps_pad) return;
+  const int64_t kb0 = static_cast<int64_t>(blockIdx.y) * kb_per;
+  const int64_t kb1 = kb0 + kb_per < nkb ? kb0 + kb_per : nkb;
+  const bool snp = i < n_v;
+  const uint64_t *row = geno + i * ld;
+  uint8_t *base = op + 2 * i * 128 + sub * 16;
+  const int64_t kb_stride = blocked_rows * 128;
+  int32_t n = 0, s1 = 0;
+#pragma unroll 4
+  for (int64_t kb = kb0; kb < kb1; ++kb) {
+    const int64_t c = kb * 8 + sub;      // 16-byte piece of the row pair
+    const int64_t k = FP4 ? c : c >> 1;  // packed word
+    uint64_t v = 0xAAAAAAAAAAAAAAAAull;  // all entries "missing" -> zero operands
+    if (snp && k * 32 < n_f) {
+      const uint64_t valid = valid_even_mask(k, n_f);
+      const uint64_t vm = valid | (valid << 1);
+      v = (__ldg(row + k) & vm) | (0xAAAAAAAAAAAAAAAAull & ~vm);
+    }
+    if constexpr (COUNT) {
+      // Present entries (not h & ~l) and rho(1) = l + (l & h) of this thread's
+      // entries: the whole word (e2m1) or its half (e4m3); padding reads as missing.
+      const uint64_t x = FP4 ? v : (v >> (32 * (sub & 1))) & 0xFFFFFFFFull;
+      const uint64_t even = FP4 ? kEven : 0x55555555ull;
+      const uint64_t l = x & even, h = (x >> 1) & even;
+      n += __popcll(even & ~(h & ~l));
+      s1 += __popcll(l) + __popcll(h & l);
+    }
+    uint4 q0, q1;
+    if constexpr (FP4) {
+      uint64_t n0[2], n1[2];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const uint32_t x = static_cast<uint32_t>(v >> (32 * half));
+        const uint32_t l = x & 0x55555555u;
+        const uint32_t h = (x >> 1) & 0x55555555u;
+        const uint32_t nh = ~h & 0x55555555u;
+        n0[half] = spread_2to4((nh << 1) - (l & nh)) << 1;
+        n1[half] = spread_2to4(l + (l & h)) << 1;
+      }
+      q0 = make_uint4(static_cast<uint32_t>(n0[0]), static_cast<uint32_t>(n0[0] >> 32),
+                      static_cast<uint32_t>(n0[1]), static_cast<uint32_t>(n0[1] >> 32));
+      q1 = make_uint4(static_cast<uint32_t>(n1[0]), static_cast<uint32_t>(n1[0] >> 32),
+                      static_cast<uint32_t>(n1[1]), static_cast<uint32_t>(n1[1] >> 32));
+    } else {
+      const uint32_t h = static_cast<uint32_t>(v >> (32 * (sub & 1)));
+      uint32_t r0[4], r1[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t sel = code_nibbles((h >> (8 * b)) & 0xFFu);
+        r0[b] = __byte_perm(kRho0E4M3, 0u, sel);
+        r1[b] = __byte_perm(kRho1E4M3, 0u, sel);
+      }
+      q0 = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+      q1 = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+    }
+    uint8_t *d0 = base + kb * kb_stride;
+    *reinterpret_cast<uint4 *>(d0) = q0;
+    *reinterpret_cast<uint4 *>(d0 + 128) = q1;
+  }
+  if constexpr (COUNT) {
+    // The 8 threads of a SNP are 8 aligned lanes of one warp.
+    const unsigned group = 0xFFu << (threadIdx.x & 24);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      n += __shfl_xor_sync(group, n, o);
+      s1 += __shfl_xor_sync(group, s1, o);
+    }
+    if (sub == 0 && snp && kb0 < kb1) {
+      atomicAdd(cnt + 2 * i, n);
+      atomicAdd(cnt + 2 * i + 1, s1);
+    }
+  }
+}
+
+// The per-SNP factors 1 - gamma f_i(a) in place of the counts n_i, s_i^1 that
+// k_unpack_blocked summed into the same 8 bytes per SNP (the same arithmetic
+// as k_allele_counts).
+__global__ void k_factors_in_place(float *__restrict__ w, int64_t n_v, double gamma) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_v) return;
+  const int2 c = reinterpret_cast<const int2 *>(w)[i];
+  const int64_t n = c.x, s1 = c.y, s0 = 2 * n - s1;
+  const double f0 = n > 0 ? static_cast<double>(s0) / (2.0 * static_cast<double>(n)) : 0.0;
+  const double f1 = n > 0 ? static_cast<double>(s1) / (2.0 * static_cast<double>(n)) : 0.0;
+  reinterpret_cast<float2 *>(w)[i] = make_float2(static_cast<float>(1.0 - gamma * f0),
+                                                 static_cast<float>(1.0 - gamma * f1));
 }
 
 // Gather the 32 even-position bits of x into the low 32 bits.
@@ -362,14 +461,55 @@ int launch_factors_from_counts(const int32_t *counts, int64_t n_v, float *w, dou
   return note_launch();
 }
 
+int launch_unpack_blocked(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
+                          int64_t kpad, int64_t snps_pad, int64_t blocked_rows, bool fp4, float *w,
+                          double gamma, cudaStream_t s) {
+  const int64_t kblock = fp4 ? 256 : 128;  // entries per 128-byte K block
+  if (kpad % kblock != 0 || snps_pad % 32 != 0 || snps_pad < n_v || blocked_rows < 2 * snps_pad)
+    return CCC_EINVAL;
+  const int64_t nkb = kpad / kblock;
+  if (snps_pad < 1 || nkb < 1) return CCC_OK;
+  // 32-SNP blocks times K ranges, about 16 blocks per SM in all.
+  const int64_t gx = snps_pad / 32;
+  if (gx > 0x7FFFFFFF) return CCC_EINVAL;
+  int64_t gy = (152 * 16 + gx - 1) / gx;
+  if (gy > nkb) gy = nkb;
+  if (gy > 65535) gy = 65535;
+  const int64_t kb_per = (nkb + gy - 1) / gy;
+  gy = (nkb + kb_per - 1) / kb_per;
+  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
+  int32_t *cnt = reinterpret_cast<int32_t *>(w);
+  if (w != nullptr && cudaMemsetAsync(w, 0, 8 * static_cast<size_t>(n_v), s) != cudaSuccess)
+    return CCC_ECUDA;
+  if (fp4 && w != nullptr)
+    k_unpack_blocked<true, true><<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, op, snps_pad, nkb,
+                                                      blocked_rows, kb_per, cnt);
+  else if (fp4)
+    k_unpack_blocked<true, false><<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, op, snps_pad, nkb,
+                                                       blocked_rows, kb_per, nullptr);
+  else if (w != nullptr)
+    k_unpack_blocked<false, true><<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, op, snps_pad, nkb,
+                                                       blocked_rows, kb_per, cnt);
+  else
+    k_unpack_blocked<false, false><<<grid, 256, 0, s>>>(geno, n_f, n_v, ld, op, snps_pad, nkb,
+                                                        blocked_rows, kb_per, nullptr);
+  const int rc = note_launch();
+  if (rc != CCC_OK || w == nullptr) return rc;
+  const unsigned fb = static_cast<unsigned>((n_v + 255) / 256);
+  k_factors_in_place<<<fb, 256, 0, s>>>(w, n_v, gamma);
+  return note_launch();
+}
+
 int launch_unpack_e4m3(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t ld, uint8_t *op,
                        int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows) {
-  if (blocked_rows != 0 && blocked_rows < 2 * snps_pad) return CCC_EINVAL;
+  if (blocked_rows != 0)
+    return launch_unpack_blocked(geno, n_f, n_v, ld, op, kpad, snps_pad, blocked_rows, false,
+                                 nullptr, 0.0, s);
   const int threads = 256;
   const int64_t total = (kpad / 16) * snps_pad;
   const int64_t blocks = (total + threads - 1) / threads;
   k_unpack_e4m3<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
-                                                                   snps_pad, blocked_rows);
+                                                                   snps_pad);
   return note_launch();
 }
 
@@ -377,14 +517,16 @@ int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
                        int64_t kpad, int64_t snps_pad, cudaStream_t s, int64_t blocked_rows,
                        float *w, double gamma) {
   if (kpad % 256 != 0) return CCC_EINVAL;
-  if (blocked_rows != 0 && blocked_rows < 2 * snps_pad) return CCC_EINVAL;
+  if (blocked_rows != 0)
+    return launch_unpack_blocked(geno, n_f, n_v, ld, op, kpad, snps_pad, blocked_rows, true, w,
+                                 gamma, s);
   // Fused with the factors while one 128-thread block per SNP still gives the
   // GPU enough loads in flight (152 SMs x 8 blocks); a few long rows take the
   // flat unpack (a thread per word) and the multi-warp count kernel instead.
   if (w != nullptr && snps_pad >= 152 * 8) {
     if (snps_pad < n_v) return CCC_EINVAL;
     k_unpack_e2m1_w<<<static_cast<unsigned>(snps_pad), 128, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
-                                                                     blocked_rows, w, gamma);
+                                                                     w, gamma);
     return note_launch();
   }
   if (w != nullptr) {
@@ -395,7 +537,7 @@ int launch_unpack_e2m1(const uint64_t *geno, int64_t n_f, int64_t n_v, int64_t l
   const int64_t total = (kpad / 32) * snps_pad;
   const int64_t blocks = (total + threads - 1) / threads;
   k_unpack_e2m1<<<static_cast<unsigned>(blocks), threads, 0, s>>>(geno, n_f, n_v, ld, op, kpad,
-                                                                   snps_pad, blocked_rows);
+                                                                   snps_pad);
   return note_launch();
 }
 

@@ -28,16 +28,18 @@ def _build():
     build.build()
 
 
-def _run(geno, n_f, split, norm=0, tally_only=False, host=False):
+def _run(geno, n_f, split, norm=0, tally_only=False, host=False, operand=0):
     import torch
 
     import paper_1705_08213_gb300 as ccc
     g = to_device(geno)
     n_v = geno.shape[0]
     opts = ccc.ccc_opts_default(norm=norm)
+    opts.operand = operand
     ws = workspace(ccc.ccc_workspace_size(g, n_f, opts, ccc.CCC_OP_2WAY))
     opts = ccc.ccc_opts_default(norm=norm, workspace=ws)
     opts.split = split
+    opts.operand = operand
     npairs = ccc.ccc2_count(n_v)
     kw = dict(dtype=torch.int32, pin_memory=True) if host else dict(dtype=torch.int32, device="cuda")
     tally = torch.full((npairs, 4), -7, **kw)
@@ -52,16 +54,19 @@ def _run(geno, n_f, split, norm=0, tally_only=False, host=False):
     return tally.cpu().numpy(), out.cpu().numpy()
 
 
+@pytest.mark.parametrize("operand", [0, 1])  # automatic (e2m1), e4m3
 @pytest.mark.parametrize("norm", [0, 1])
-def test_forced_splits_equal_unsplit_and_oracle(norm):
-    n_v, n_f = 300, 5000  # 40 K stages
+def test_forced_splits_equal_unsplit_and_oracle(norm, operand):
+    # 300 SNPs: not a multiple of the unpack's 32-SNP blocks; 5,000 individuals:
+    # a ragged last K block (20 e2m1 / 40 e4m3 K stages).
+    n_v, n_f = 300, 5000
     geno = synth.panel_hwe(n_v, n_f, seed=71, p_missing=0.02)
-    t1, c1 = _run(geno, n_f, 1, norm)
+    t1, c1 = _run(geno, n_f, 1, norm, operand=operand)
     et, ec = oracle.ccc2_all(geno, n_f, norm=norm)
     assert_tally_equal(t1, et, "unsplit")
     assert_ccc_close(c1, ec, what="unsplit")
-    for split in (2, 3, 7, 40, 4096):  # 4096 is clamped to the 40 K stages
-        t, c = _run(geno, n_f, split, norm)
+    for split in (2, 3, 7, 40, 4096):  # 4096 is clamped to the K stages
+        t, c = _run(geno, n_f, split, norm, operand=operand)
         np.testing.assert_array_equal(t, t1)
         np.testing.assert_array_equal(c, c1)
 
