@@ -83,6 +83,22 @@ def test_automatic_split_on_a_long_panel():
     np.testing.assert_array_equal(c, c1)
 
 
+@pytest.mark.parametrize("operand", [0, 1])  # automatic (e2m1), e4m3
+def test_forced_split_many_snps(operand):
+    """1,300 SNPs (1,536 padded): the K-block-major unpack runs 48 blocks of 32
+    SNPs over several K ranges each, the per-SNP counts summed by atomics
+    across the ranges; 3,000 individuals end in a ragged K block."""
+    n_v, n_f = 1300, 3000
+    geno = synth.panel_hwe(n_v, n_f, seed=76, p_missing=0.03)
+    t1, c1 = _run(geno, n_f, 1, operand=operand)
+    t3, c3 = _run(geno, n_f, 3, operand=operand)
+    np.testing.assert_array_equal(t3, t1)
+    np.testing.assert_array_equal(c3, c1)
+    et, ec = oracle.ccc2_all(geno, n_f)
+    assert_tally_equal(t3, et, "split 3")
+    assert_ccc_close(c3, ec, what="split 3")
+
+
 def test_tally_only_and_host_outputs():
     n_v, n_f = 200, 9000
     geno = synth.panel_hwe(n_v, n_f, seed=73, p_missing=0.02)
