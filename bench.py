@@ -646,6 +646,33 @@ def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
     direct_launches = ccc.ccc_launch_count() - launches0
     ms_direct = d0.elapsed_time(d1) / args.steps
     clocks = sampler.stop()
+    # The same step with every panel's tiles in the one persistent tally launch
+    # (no panel launched on its own: ccc_opts.solo < 0), graph-captured as above.
+    o1 = ccc.ccc_opts_default(workspace=ws)
+    for name, _ in type(opts)._fields_:
+        setattr(o1, name, getattr(opts, name))
+    o1.solo = -1
+    with torch.cuda.stream(stream):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, o1, stream)
+    torch.cuda.synchronize(dev)
+    graph1 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph1, stream=stream):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, o1, stream)
+    graph1.replay()
+    torch.cuda.synchronize(dev)
+    launches1 = ccc.ccc_launch_count()
+    with torch.cuda.stream(stream):
+        ccc.ccc2_batched(genos, n_fs, tallies, cccs, o1, stream)
+    launches1 = ccc.ccc_launch_count() - launches1
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        graph1.replay()
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_one = g0.elapsed_time(g1) / args.steps
+    del graph1
     # 64 sequential single-panel calls, one shared workspace.
     o0 = ccc.ccc_opts_default()
     wss = torch.empty(max(ccc.ccc_workspace_size(g, f, o0, ccc.CCC_OP_2WAY)
@@ -728,6 +755,11 @@ def run_batched(args, w, ccc, torch, dev, stream, rank, world, pg):
                                   f"{bf16_peak:.0f} (nominal dense ratio)"},
         "clocks": clocks,
         "direct_calls": {"ms_per_step": ms_direct, "value": cmp_per_step / (ms_direct * 1e-3)},
+        "one_persistent_launch": {"ms_per_step": ms_one, "value": cmp_per_step / (ms_one * 1e-3),
+                                  "gpu_launches": int(launches1),
+                                  "note": "ccc_opts.solo = -1: all 64 panels' tiles (and their K "
+                                          "split units) in one persistent tally launch, the "
+                                          "operand unpacks on a side stream; graph replay"},
         "sequential_64_calls": {"ms_per_step": ms_seq, "value": cmp_per_step / (ms_seq * 1e-3),
                                 "batched_speedup": ms_seq / ms_graph},
     }
