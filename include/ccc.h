@@ -91,7 +91,7 @@ extern "C" {
                                  buffer on the device and skipped the access (ccc_status) */
 
 /* Tally paths. */
-#define CCC_PATH_TC 0   /* tcgen05 tensor cores, e4m3 count operands, FP32 accumulate */
+#define CCC_PATH_TC 0   /* tcgen05 tensor cores, e4m3 or e2m1 count operands, FP32 accumulate */
 #define CCC_PATH_POPC 1 /* bit planes, AND + population count on the CUDA cores */
 
 /* Normalisation of f_i with missing data (see above). */
