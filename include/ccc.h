@@ -135,10 +135,12 @@ typedef struct ccc_opts {
                              K (individuals) split into this many parts whose partial tallies
                              are summed (the n_pf axis of Sec. 4 on one GPU), for panels with few
                              SNP tiles and long vectors.  0 = automatic (tensor cores: when the
-                             triangle has at most half as many tiles as SM pairs and n_f >= 4,096;
-                             popcount: fewer 64-SNP tiles than four per SM, at least 4,096
-                             individuals per part), 1 = off, n >= 2 = n parts (at most n_f / 128
-                             on the tensor cores, n_f / 512 on the popcount path).  Same results;
+                             triangle has at most half as many tiles as SM pairs and at least 32
+                             128-byte K stages, n_f >= 4,096 with e4m3 and 8,192 with e2m1
+                             operands; popcount: fewer 64-SNP tiles than four per SM, at least
+                             4,096 individuals per part), 1 = off, n >= 2 = n parts (at most one
+                             per K stage: n_f / 128 with e4m3, n_f / 256 with e2m1 operands,
+                             n_f / 512 on the popcount path).  Same results;
                              the CCC values then come from the summed tallies. */
   int32_t operand;        /* encoding of the tensor-core count operands (CCC_OPERAND_*):
                              E4M3 = one byte per count, kind::f8f6f4 MMAs; E2M1 = FP4, two counts
