@@ -9,9 +9,10 @@ Workloads (``--workload``):
   2way    default; 2-way CCC at scale: n_v = 20,000 SNP vectors x n_f = 16,384
           individuals, Hardy-Weinberg genotypes, Beta(1/2,1/2) minor-allele
           frequencies floored at 0.01, 1% missing, seed 1.  Step =
-          ccc2_tally_metric: allele counts, e4m3 count-operand unpack, the
-          tcgen05 tally kernel with the fused CCC epilogue writing every
-          tally and CCC value of the upper triangle (6.4 GB).
+          ccc2_tally_metric: the count-operand unpack (e2m1 rows and the
+          per-SNP factors from one read of the codes), the tcgen05 tally
+          kernel with the fused CCC epilogue writing every tally and CCC value
+          of the upper triangle (6.4 GB).
   3way    3-way CCC: n_v = 1,536 x n_f = 8,192, same genotype model, seed 4;
           step = ccc3_tally_metric over all slabs (602,800,640 triples, 38.6 GB).
   filter  2-way with thresholded output: n_v = 200,000 x n_f = 4,096, same
@@ -23,6 +24,9 @@ Workloads (``--workload``):
           step = ccc2_batched with the schedule chosen by ccc2_batched_tune,
           captured once in a CUDA graph and replayed; compared with 64
           sequential ccc2_tally_metric calls.
+
+Panels whose inputs fit the 129 MB L2 (3way, small) get a 256 MB write before
+every timed step, outside that step's CUDA events; the others are larger than L2.
 
 Prints ONE JSON line (rank 0).  Under torchrun with N ranks every rank runs an
 independent panel of the same shape (seed + rank); there is no data-path
