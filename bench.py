@@ -22,8 +22,12 @@ Workloads (``--workload``):
   batched 64 independent 2-way panels, n_v ~ U{500..8000}, n_f ~ U{2000..50000}
           (shape draws seed 2), Hardy-Weinberg model (seed 2, panel index k);
           step = ccc2_batched with the schedule chosen by ccc2_batched_tune,
-          captured once in a CUDA graph and replayed; compared with 64
-          sequential ccc2_tally_metric calls.
+          captured once in a CUDA graph and replayed; compared with all panels
+          in one persistent launch and with 64 sequential ccc2_tally_metric calls.
+  multi   2-way CCC of markers with s = 4 allele states, 10,000 x 16,384, seed
+          6; step = ccc2_multi_tally_metric (16 tallies + 16 CCC per pair).
+  long    2-way, 512 SNPs x 1,000,000 individuals, seed 7: few tiles with long
+          vectors, computed in K parts (ccc_opts.split automatic).
 
 Panels whose inputs fit the 129 MB L2 (3way, small) get a 256 MB write before
 every timed step, outside that step's CUDA events; the others are larger than L2.
