@@ -3,8 +3,9 @@
 * The reference arm (the oracle on the host cores) prints exactly one JSON line with the
   keys of the bench line, its cpu_baseline describing the run and an e2e object with no
   host-device bytes.
-* Every stored DRAM-traffic record names a kernel whose sources bench.py hashes, and
-  carries the ncu command that produced it.
+* Every stored DRAM-traffic record names a kernel whose sources bench.py hashes, was
+  captured from the current sources (its hash matches, so the bench lines report it),
+  and carries the ncu command that produced it.
 """
 
 import json
@@ -49,7 +50,7 @@ def test_traffic_records_name_hashed_kernels():
         kernel, workload = key.split("@")
         rec = records[key]
         assert kernel in hashes, key
-        assert len(rec["source_hash"]) == 16
+        assert rec["source_hash"] == hashes[kernel], f"{key}: sources changed since the capture"
         assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
         assert f"--workload {workload}" in rec["command"]
         assert rec["read_bytes"] > 0 and rec["write_bytes"] > 0
