@@ -267,15 +267,25 @@ def source_hash(kernel="k_tally2_tc_pair"):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from profiles/ncu_traffic.json, or None
-    when that capture was taken on different CUDA sources."""
+def ncu_record(kernel, workload):
+    """The profiles/ncu_traffic.json record of `kernel` on `workload`, or None when there is
+    none or it was captured on different CUDA sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             rec = json.load(f).get(f"{kernel}@{workload}")
     except (OSError, ValueError):
         return None
     if not rec or rec.get("source_hash") != source_hash(kernel):
+        return None
+    return rec
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch (per step for the 3-way class route) of `kernel` on `workload`
+    from profiles/ncu_traffic.json, or None when that capture was taken on different CUDA
+    sources."""
+    rec = ncu_record(kernel, workload)
+    if rec is None:
         return None
     return float(rec.get("dram_bytes_per_step", rec.get("dram_bytes_per_launch")))
 
@@ -1046,6 +1056,26 @@ def run_workload(args, w, ccc, torch, dev, rank, world, local, pg):
         out_bytes = 64.0 * cmp_rank / w["n_f"]
     else:
         out_bytes = 8.0 * (w.get("states") or 2) ** 2 * cmp_rank / w["n_f"]
+    # The tally kernel against the HBM roofline as well (context; the bound above is the
+    # tensor pipe): algorithmic bytes = operand rows read once + outputs written once (the
+    # capture's own figure where one matches these sources), and the captured DRAM traffic.
+    if path == ccc.CCC_PATH_TC and not strong:
+        full = args.n_v is None and args.n_f is None
+        rec = ncu_record(kname, args.workload) if full else None
+        alg = None
+        if rec is not None:
+            alg = rec.get("algorithmic_bytes_per_step", rec.get("algorithmic_bytes_per_launch"))
+        if alg is None:
+            rows = (w.get("states") or 2) * w["n_v"] if w["kind"] == 2 else 0
+            alg = out_bytes + rows * w["n_f"] * (0.5 if fp4 else 1.0)
+        ks = kernel_step_ms * 1e-3
+        traffic = roof.get("traffic")
+        roof["hbm_context"] = {
+            "unit": "GB/s", "peak": hbm_peak, "peak_note": f"{peak_src} copy bandwidth",
+            "algorithmic_bytes": float(alg), "achieved": alg / ks / 1e9,
+            "frac": alg / ks / 1e9 / hbm_peak,
+            "dram_achieved": traffic / ks / 1e9 if traffic else None,
+            "dram_frac": traffic / ks / 1e9 / hbm_peak if traffic else None}
     result = {
         "metric": w["metric"], "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
