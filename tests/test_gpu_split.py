@@ -99,6 +99,21 @@ def test_forced_split_many_snps(operand):
     assert_ccc_close(c3, ec, what="split 3")
 
 
+@pytest.mark.parametrize("operand", [0, 1])  # automatic (e2m1), e4m3
+@pytest.mark.parametrize("n_v, n_f", [(2, 511), (3, 512), (40, 513), (33, 8191), (65, 8192)])
+def test_forced_split_at_k_block_edges(n_v, n_f, operand):
+    """n_f at and around a 128-byte K block (256 e2m1 / 128 e4m3 entries), few SNPs: the
+    K-block-major unpack's last block and its per-SNP counts, split 2 against unsplit."""
+    geno = synth.panel_hwe(n_v, n_f, seed=78 + n_v, p_missing=0.05)
+    t1, c1 = _run(geno, n_f, 1, operand=operand)
+    t2, c2 = _run(geno, n_f, 2, operand=operand)
+    np.testing.assert_array_equal(t2, t1)
+    np.testing.assert_array_equal(c2, c1)
+    et, ec = oracle.ccc2_all(geno, n_f)
+    assert_tally_equal(t2, et, "split 2")
+    assert_ccc_close(c2, ec, what="split 2")
+
+
 def test_tally_only_and_host_outputs():
     n_v, n_f = 200, 9000
     geno = synth.panel_hwe(n_v, n_f, seed=73, p_missing=0.02)
